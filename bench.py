@@ -1,0 +1,341 @@
+#!/usr/bin/env python3
+"""Benchmark of the MPLP++ Handshake solver on one GB300.
+
+Workload (default): the pose-shaped dense model -- complete graph K_60, 300
+labels per node, truncated-quadratic distance costs, 500 iterations of the
+round-robin schedule (59 matchings of 30 edges).  One step = reset the
+reparametrization, run all 500 iterations, compute the exact dual bound and
+the primal rounding with its energy: every row of the hot path.
+
+Reported: edge updates/s (whole job), the persistent Handshake kernel's
+algorithmic HBM GB/s against the measured copy bandwidth, the same workload
+through the looped (one launch per matching) driver at equal final bound,
+the end-to-end rate through the public API with host buffers, and the FP64
+oracle on the host cores.  Multi-GPU runs (torchrun) are replicas: every rank
+solves its own seeded copy (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+CONFIGS = {
+    1: ("K20_L8_uniform_T200", 200),
+    2: ("pose_K60_L300_T500", 500),
+    3: ("knn_n2000_k50_L64_T300", 300),
+    4: ("batch256_K10-80_L16-128_T100", 100),
+    5: ("batch16_K50_L64_T50", 50),
+}
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def models_for(cfg: int, seed: int):
+    from paper_2004_08227_gb300 import workloads as W
+    models, T = W.config(cfg, seed=seed)
+    if not isinstance(models, list):
+        models = [models]
+    return models, T
+
+
+def load_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.index)], stdout=self.file,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r.split(",") for r in self.file.read().strip().splitlines() if r.count(",") >= 8]
+        os.unlink(self.file.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip() == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_oracle_rate(models, T_full, budget_s: float):
+    """The FP64 oracle as it stands, single thread, on a bounded sample: the
+    first model of the workload for as many iterations as fit the budget."""
+    import oracle
+    from oracle import schedule as osched
+    m = models[0]
+    order = osched.build(m.schedule, m.n, m.edge_u, m.edge_v)[1]
+    t0 = time.perf_counter()
+    st = oracle.run(m, order, 1)
+    t1 = time.perf_counter() - t0
+    iters = int(max(1, min(T_full - 1, budget_s / max(t1, 1e-9) - 1)))
+    t0 = time.perf_counter()
+    oracle.run(m, order, iters, state=st)
+    dt = time.perf_counter() - t0
+    total_iters = iters + 1
+    rate = total_iters * m.E / (t1 + dt)
+    return rate, {"value": rate, "unit": "edge_updates/s", "cores": 1, "kind": "oracle",
+                  "sample": f"{m.name}: {total_iters} of {T_full} iterations, single-thread FP64 C oracle, "
+                            f"{t1 + dt:.1f} s"}
+
+
+def run_reference(args):
+    """--impl reference: the FP64 oracle on the host cores (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cfg = args.config
+    models, T = models_for(cfg, seed=0)
+    import oracle
+    from oracle import schedule as osched
+    m = models[0]
+    order = osched.build(m.schedule, m.n, m.edge_u, m.edge_v)[1]
+    st = None
+    per = max(1, args.ref_iters)
+    for _ in range(args.warmup):
+        st = oracle.run(m, order, per, state=st)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        st = oracle.run(m, order, per, state=st)
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * sum(times) / len(times)
+    value = per * m.E / (ms / 1e3)
+    name = CONFIGS[cfg][0]
+    line = {"impl": "reference", "metric": "edge_updates_per_s", "value": value, "unit": "edge_updates/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": name, "sample": f"{per} iteration(s) of {m.name} per step"},
+            "cpu_baseline": {"value": value, "unit": "edge_updates/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{per} of {T} iterations of {m.name} per step, single-thread FP64 C oracle"},
+            "e2e": {"value": value, "unit": "edge_updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2004_08227_gb300.solver import Solver
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev_index = local
+    cfg = args.config
+    name, T = CONFIGS[cfg]
+    if args.iters:
+        T = args.iters
+    # cpu baseline first (before any GPU work), rank 0 only
+    cpu = None
+    models, _ = models_for(cfg, seed=rank)
+    if rank == 0 and world == 1 and not args.no_cpu:
+        log("timing the oracle on the host ...")
+        _, cpu = cpu_oracle_rate(models, T, args.cpu_budget)
+    stream = torch.cuda.current_stream()
+    s = Solver(models, mode=args.mode)
+    info = s.info()
+    E_total = info["edges"]
+    log("solver:", info)
+
+    def step(sol):
+        sol.reset()
+        sol.run(T)
+        D = sol.bound(exact=True)
+        sol.labeling()
+        return D
+
+    kern_ms = []
+
+    def timed_step(sol):
+        sol.reset()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sol.run(T)
+        b.record(stream)
+        D = sol.bound(exact=True)
+        sol.labeling()
+        kern_ms.append(a.elapsed_time(b))
+        return D
+
+    for _ in range(args.warmup):
+        step(s)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(dev_index)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    D_persist = None
+    for _ in range(args.steps):
+        D_persist = timed_step(s)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    updates = T * E_total * world
+    value = updates / (ms / 1e3)
+    bytes_iter = info["bytes_per_iteration"]
+    kms = statistics.mean(kern_ms)
+    achieved = T * bytes_iter / (kms / 1e3) / 1e9
+    peak, peak_kind = load_peak()
+    kernel = "hs_persistent_kernel" if info["mode"] == "persistent" else "hs_looped_kernel"
+
+    # the looped driver (one launch per matching) on the same workload, equal bound
+    looped = None
+    if not args.no_looped:
+        sl = Solver(models, mode="looped")
+        for _ in range(2):
+            step(sl)
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        nl = max(1, min(args.steps, 3))
+        f0.record(stream)
+        for _ in range(nl):
+            D_loop = step(sl)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        lms = f0.elapsed_time(f1) / nl
+        looped = {"ms_per_step": lms, "launches_per_step": T * info["phases"],
+                  "final_bound": float(D_loop[0]), "bound_equal": bool(np.array_equal(D_loop, D_persist)),
+                  "persistent_speedup": lms / ms}
+        sl.close()
+
+    # end to end through the public API with host buffers (pinned)
+    e2e = None
+    if not args.no_e2e:
+        class _M:
+            pass
+        pinned = []
+        h2d = 0
+        for m in models:
+            pm = _M()
+            pm.labels, pm.edge_u, pm.edge_v, pm.schedule = m.labels, m.edge_u, m.edge_v, m.schedule
+            pm.unary = torch.from_numpy(m.unary).pin_memory()
+            pm.pairwise = torch.from_numpy(m.pairwise).pin_memory()
+            h2d += pm.unary.numel() * 4 + pm.pairwise.numel() * 4 + (m.labels.size + 2 * m.E) * 4
+            pinned.append(pm)
+        d2h = 8 * len(models) + 4 * sum(m.n for m in models) + 8 * len(models)
+        times = []
+        for i in range(1 + max(1, min(args.steps, 3))):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            with Solver(pinned, mode=args.mode) as se:
+                se.run(T)
+                se.bound(exact=True)
+                se.labeling()
+            torch.cuda.synchronize()
+            if i > 0:
+                times.append(time.perf_counter() - t0)
+        et = statistics.mean(times)
+        e2e = {"value": T * E_total * world / et, "unit": "edge_updates/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": et * 1e3, "timer": "host wall clock"}
+
+    launches_per_step = (1 if info["mode"] == "persistent" else T * info["phases"]) + 3 + 2
+    line = {
+        "metric": "edge_updates_per_s", "value": value, "unit": "edge_updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": name, "models": len(models), "edges": E_total, "iterations": T,
+                   "matchings": info["phases"], "mode": info["mode"], "cluster": info["cluster"],
+                   "threads": info["threads"], "grid": info["grid"], "parallelism": f"replicas{world}",
+                   "l2": "inputs larger than L2 (tables %.0f MB per model)" % (bytes_iter / 1e6)},
+        "hbm_gbs": achieved,
+        "roofline": {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_source": peak_kind, "traffic": None,
+                     "algorithmic_bytes_per_launch": T * bytes_iter, "launch_ms": kms},
+        "looped": looped,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+        "clocks": ck,
+        "gpu_launches": launches_per_step * args.steps,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    s.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", type=int, default=2, choices=sorted(CONFIGS))
+    ap.add_argument("--iters", type=int, default=0, help="override the iteration count")
+    ap.add_argument("--mode", default="auto", choices=["auto", "looped", "persistent"])
+    ap.add_argument("--no-looped", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--ref-iters", type=int, default=1)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,205 @@
+/*
+ * mplpp.h -- C ABI of the GB300 (sm_103a) MPLP++ solver.
+ *
+ * MPLP++ (Tourani, Shekhovtsov, Rother, Savchynskyy) maximizes the dual lower
+ * bound D(phi) of MAP inference in a discrete pairwise graphical model
+ * (Sec. 3, eqs. energy-min, reparametrization, LP-lower-bound) by block
+ * coordinate ascent over the messages phi_{u<->v} of one edge at a time, with
+ * the Handshake update (Sec. 4, eq. (H), three-minimization form).  Edges of
+ * one matching of an edge schedule (Sec. 6, Alg. 1) are independent and are
+ * updated in parallel; matchings are processed in order.
+ *
+ * Conventions for every entry point:
+ *  - Nodes are 0..n-1; node u has L_u >= 1 labels (0-based).  An edge (u, v)
+ *    has u < v (Sec. 3, Notation); its pairwise table is row-major, L_u rows
+ *    (labels of u) by L_v columns (labels of v).
+ *  - `unary` concatenates the node vectors in node order; `pairwise`
+ *    concatenates the tables in edge order.  Offsets are implied by the label
+ *    counts.  Costs must be finite.
+ *  - Host arrays passed to a call are read during the call only (copied); the
+ *    caller keeps ownership.  Device arrays (options.inputs_on_device) are
+ *    read during mplpp_create only, except that mplpp_backward writes the
+ *    gradients to caller-owned memory of the same kind.
+ *  - Every call returns an mplpp_status; nothing throws across the ABI.  On
+ *    failure the solver keeps a message readable with mplpp_last_error.
+ *  - Calls enqueue work on the CUDA stream given at creation.  Calls that
+ *    return host data (bound, labeling, save_state, backward) synchronize that
+ *    stream and report device-side errors (a timed-out wait, non-finite
+ *    values) through their status.
+ *  - A solver is not thread-safe; distinct solvers are independent.
+ */
+#ifndef MPLPP_H
+#define MPLPP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mplpp_solver mplpp_solver;
+
+typedef enum {
+    MPLPP_OK = 0,
+    MPLPP_E_INVALID = -1,     /* bad argument: sizes, edge order, duplicate edge, bad schedule */
+    MPLPP_E_NOMEM = -2,       /* host or device allocation failed                              */
+    MPLPP_E_CUDA = -3,        /* a CUDA runtime call failed (message has the CUDA error)       */
+    MPLPP_E_TIMEOUT = -4,     /* a device-side wait exceeded options.spin_limit polls          */
+    MPLPP_E_NONFINITE = -5,   /* a result is NaN or infinite                                   */
+    MPLPP_E_STATE = -6,       /* call not valid in the current state (e.g. backward w/o record) */
+    MPLPP_E_UNSUPPORTED = -7  /* the shape exceeds a compiled limit (message says which)       */
+} mplpp_status;
+
+/* Edge schedule kinds (Sec. 6, Alg. 1). */
+enum {
+    MPLPP_SCHED_ROUND_ROBIN = 0,  /* complete graph K_n: circle-method 1-factorization            */
+    MPLPP_SCHED_GREEDY_COLOR = 1, /* greedy edge colouring, edges in (u,v) order, smallest colour */
+    MPLPP_SCHED_ALG1 = 2,         /* Alg. 1: repeated greedy maximal matching of remaining edges  */
+    MPLPP_SCHED_USER = 3          /* caller supplies matching_off / edge_order                    */
+};
+
+/* How mplpp_run drives the matchings. */
+enum {
+    MPLPP_MODE_AUTO = 0,       /* persistent when the device allows it, else looped            */
+    MPLPP_MODE_LOOPED = 1,     /* one kernel launch per matching (launch boundary = barrier)  */
+    MPLPP_MODE_PERSISTENT = 2  /* one launch for all iterations; per-node completion counters
+                                  order the matchings on the device                           */
+};
+
+typedef struct {
+    int32_t n_nodes;
+    int32_t n_edges;
+    const int32_t *labels;       /* [n_nodes] host, L_u >= 1                                   */
+    const int32_t *edge_u;       /* [n_edges] host, edge_u[e] < edge_v[e], no duplicate pairs  */
+    const int32_t *edge_v;       /* [n_edges] host                                             */
+    const float *unary;          /* [sum_u L_u]          host, or device if inputs_on_device   */
+    const float *pairwise;       /* [sum_e L_u * L_v]    host, or device if inputs_on_device   */
+    int32_t schedule_kind;       /* MPLPP_SCHED_*                                              */
+    int32_t n_matchings;         /* MPLPP_SCHED_USER only                                      */
+    const int32_t *matching_off; /* MPLPP_SCHED_USER only: [n_matchings + 1] host              */
+    const int32_t *edge_order;   /* MPLPP_SCHED_USER only: [n_edges] host, edge ids            */
+} mplpp_model;
+
+typedef struct {
+    int32_t mode;             /* MPLPP_MODE_*                                                  */
+    int32_t use_graph;        /* nonzero: replay the launches of an iteration from a CUDA graph */
+    int32_t inputs_on_device; /* nonzero: model.unary / model.pairwise are device pointers and
+                                 mplpp_backward writes device gradients                         */
+    int32_t record_every;     /* > 0: mplpp_run keeps a state checkpoint every k iterations so
+                                 that mplpp_backward can differentiate the run; 0: no record    */
+    int32_t cluster;          /* CTAs sharing one edge (1..8); 0 = chosen from the shapes      */
+    int32_t threads;          /* threads per CTA (128, 256, 512); 0 = chosen from the shapes   */
+    int32_t test_unreachable_wait; /* testing only (0 otherwise): in the persistent driver the
+                                 first edge of the first worker waits for one node update more
+                                 than will ever happen, so the bounded wait must run out and the
+                                 run must end with MPLPP_E_TIMEOUT instead of hanging            */
+    int32_t reserved;         /* 0 */
+    int64_t spin_limit;       /* polls before a device-side wait gives up with MPLPP_E_TIMEOUT */
+} mplpp_options;
+
+/* Fills *opt with defaults: AUTO mode, graphs on, host inputs, no record,
+ * automatic mapping, spin_limit = 2^26 (well above any legitimate wait). */
+void mplpp_options_default(mplpp_options *opt);
+
+/* Builds an edge schedule (Sec. 6, Alg. 1) for one graph.
+ *   kind: MPLPP_SCHED_ROUND_ROBIN (needs the complete graph), _GREEDY_COLOR or _ALG1.
+ *   matching_off: out, capacity n_edges + 1 (n_edges + 1 >= 1); edge_order: out, [n_edges].
+ *   *n_matchings: out.  Matching k is edge_order[matching_off[k] .. matching_off[k+1]);
+ *   no two of its edges share a node, and every edge appears once.
+ * Host only; MPLPP_E_INVALID on a malformed graph. */
+mplpp_status mplpp_schedule(int32_t kind, int32_t n_nodes, int32_t n_edges, const int32_t *edge_u,
+                            const int32_t *edge_v, int32_t *matching_off, int32_t *edge_order,
+                            int32_t *n_matchings);
+
+/* Creates a solver for n_models independent models, solved together (the
+ * batched form: matching k of every model runs in the same phase).  Copies the
+ * costs to the device into the solver's layout and sets phi = 0 (the
+ * reparametrized costs start as the given ones).  `stream` is a cudaStream_t
+ * (NULL = legacy default stream) on the current device.  opt may be NULL
+ * (defaults).  On success *out owns all device memory until mplpp_destroy. */
+mplpp_status mplpp_create(const mplpp_model *models, int32_t n_models, const mplpp_options *opt,
+                          void *stream, mplpp_solver **out);
+
+/* Runs `iterations` >= 0 BCA iterations (Sec. 5: every edge updated once, in
+ * schedule order) with the Handshake update, continuing from the current
+ * state.  Asynchronous on the solver's stream. */
+mplpp_status mplpp_run(mplpp_solver *s, int32_t iterations);
+
+/* Dual bound D (eq. LP-lower-bound) of the current reparametrization, one per
+ * model, into host out[n_models].  exact != 0: node minima plus the minimum of
+ * every reparametrized pairwise table (reads all tables); exact == 0: node
+ * minima only, which equals D when every table's minimum is 0, as it is after
+ * a full iteration (Def. 1 normalization).  Minima in FP32, sums in FP64.
+ * Synchronizes. */
+mplpp_status mplpp_bound(mplpp_solver *s, double *out, int32_t exact);
+
+/* Primal rounding (Sec. 4, Primal Rounding) of the current reparametrization:
+ * nodes in increasing order, x_u = argmin_s [theta^phi_u(s) + sum over earlier
+ * neighbours v (increasing v) of theta^phi_vu(x_v, s)], FP32 sums, lowest index
+ * on ties.  labels: host [sum of n_nodes over models], model after model;
+ * energy: host [n_models] (may be NULL), E(x | original costs) in FP64
+ * (eq. energy-min).  Synchronizes. */
+mplpp_status mplpp_labeling(mplpp_solver *s, int32_t *labels, double *energy);
+
+/* Gradient of sum_m dD[m] * D_m, where D_m is model m's exact dual bound after
+ * the iterations run since the last reset, with respect to the original unary
+ * and pairwise costs.  D is piecewise linear; the gradient is that of the
+ * linear piece selected by the forward argmins (lowest index on ties).
+ * Requires options.record_every > 0 and a run that started from phi = 0.
+ * dD: host [n_models]; grad_unary [sum L], grad_pairwise [sum L_u L_v] in the
+ * input layout, host or device as options.inputs_on_device says.
+ * Synchronizes. */
+mplpp_status mplpp_backward(mplpp_solver *s, const float *dD, float *grad_unary,
+                            float *grad_pairwise);
+
+/* Resets phi = 0 and the iteration count. */
+mplpp_status mplpp_reset(mplpp_solver *s);
+
+/* Solver state (the reparametrization) in a portable host format:
+ *   header (see mplpp_state_header), then FP32 theta^phi_u for every node
+ *   ([sum L], model after model, node order), then per edge phi_{v->u} [L_u]
+ *   followed by phi_{u->v} [L_v] (edge order).  theta^phi_uv is implied:
+ *   theta_uv(s,t) - phi_{v->u}(s) - phi_{u->v}(t) (eq. reparametrization).
+ * mplpp_state_size gives the byte count; save/load need a buffer of that size.
+ * Loading checks the header against the solver's shapes (MPLPP_E_INVALID). */
+typedef struct {
+    uint32_t magic;       /* 0x4D504C50 "MPLP" */
+    uint32_t version;     /* 1 */
+    uint64_t shape_hash;  /* FNV-1a of labels, edges and schedules of all models */
+    int64_t iterations;   /* iterations run since the last reset */
+    int64_t n_unary;      /* sum L over all models */
+    int64_t n_msg;        /* sum (L_u + L_v) over all edges */
+} mplpp_state_header;
+mplpp_status mplpp_state_size(const mplpp_solver *s, size_t *bytes);
+mplpp_status mplpp_save_state(mplpp_solver *s, void *buf, size_t size);
+mplpp_status mplpp_load_state(mplpp_solver *s, const void *buf, size_t size);
+
+/* Facts about a solver, for benchmarks and tests. */
+typedef struct {
+    int64_t iterations;         /* iterations run since the last reset                        */
+    int64_t bytes_per_iteration;/* algorithmic HBM bytes: sum_e 4 L_u L_v + 16 (L_u + L_v)    */
+    int64_t edges;              /* total edges over all models                                */
+    int32_t phases;             /* matchings per iteration (max over models)                 */
+    int32_t mode;               /* MPLPP_MODE_LOOPED or _PERSISTENT actually used             */
+    int32_t cluster;            /* CTAs per edge                                              */
+    int32_t threads;            /* threads per CTA                                            */
+    int32_t grid;               /* persistent mode: CTAs launched                             */
+    int32_t launches_per_iteration; /* kernel launches one iteration takes (looped: phases)   */
+} mplpp_info_t;
+mplpp_status mplpp_info(const mplpp_solver *s, mplpp_info_t *info);
+
+/* Waits for the solver's stream and reports device-side errors. */
+mplpp_status mplpp_sync(mplpp_solver *s);
+
+/* Message of the last failed call on this solver ("" if none).  Valid until the
+ * next call on the solver.  s may be NULL: then the last mplpp_create failure. */
+const char *mplpp_last_error(const mplpp_solver *s);
+
+/* Frees the solver and its device memory (after synchronizing its stream). */
+void mplpp_destroy(mplpp_solver *s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MPLPP_H */

@@ -1,0 +1,696 @@
+// api.cu -- the C ABI (include/mplpp.h): solver creation, device layout,
+// mapping choice, the iteration drivers, bound, rounding and state I/O.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <functional>
+#include <memory>
+#include <queue>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/mplpp.h"
+#include "backward.h"
+#include "host.h"
+#include "kernels.h"
+#include "solver.h"
+
+using namespace mplpp;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+long long round4(long long x) { return (x + 3) & ~3LL; }
+
+mplpp_status fail(mplpp_solver *s, mplpp_status st, const std::string &msg)
+{
+    if (s) s->err = msg;
+    else g_create_error = msg;
+    return st;
+}
+
+mplpp_status cuda_fail(mplpp_solver *s, cudaError_t e, const char *what)
+{
+    return fail(s, MPLPP_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(s, call)                                              \
+    do {                                                         \
+        cudaError_t e_ = (call);                                 \
+        if (e_ != cudaSuccess) return cuda_fail((s), e_, #call); \
+    } while (0)
+
+template <typename T>
+cudaError_t dalloc(T **p, size_t count)
+{
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return cudaMalloc(reinterpret_cast<void **>(p), count * sizeof(T));
+}
+
+uint64_t fnv(uint64_t h, const void *data, size_t n)
+{
+    const unsigned char *p = static_cast<const unsigned char *>(data);
+    for (size_t i = 0; i < n; ++i) {
+        h ^= p[i];
+        h *= 1099511628211ULL;
+    }
+    return h;
+}
+
+}  // namespace
+
+mplpp_solver::~mplpp_solver()
+{
+    if (stream_ok) cudaStreamSynchronize(stream);
+    for (void *p : allocations) cudaFree(p);
+    if (g_looped) cudaGraphExecDestroy(g_looped);
+    if (g_persist) cudaGraphExecDestroy(g_persist);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+}
+
+extern "C" void mplpp_options_default(mplpp_options *opt)
+{
+    if (!opt) return;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->mode = MPLPP_MODE_AUTO;
+    opt->use_graph = 1;
+    opt->inputs_on_device = 0;
+    opt->record_every = 0;
+    opt->cluster = 0;
+    opt->threads = 0;
+    opt->spin_limit = 1LL << 22;
+}
+
+extern "C" const char *mplpp_last_error(const mplpp_solver *s)
+{
+    return s ? s->err.c_str() : g_create_error.c_str();
+}
+
+// Chooses CTAs per edge (C) and threads per CTA (T) from the table shapes:
+// a CTA's row slice should stay well inside shared memory (two buffers in the
+// persistent driver), and edges with large tables spread over enough CTAs to
+// fill the SMs when a matching has few edges.
+static void choose_mapping(mplpp_solver *s, int sms)
+{
+    long long tb = 0;
+    int max_phase = 1;
+    for (auto &ed : s->h_edges) tb = std::max(tb, 4LL * ed.Lu * ed.ld);
+    for (size_t p = 0; p + 1 < s->phase_off.size(); ++p)
+        max_phase = std::max(max_phase, s->phase_off[p + 1] - s->phase_off[p]);
+    int C = s->opt.cluster;
+    if (C <= 0) {
+        C = static_cast<int>((tb + 96 * 1024 - 1) / (96 * 1024));
+        if (tb > 32 * 1024) C = std::max(C, std::min(8, sms / max_phase));
+        C = std::max(1, std::min(8, C));
+    }
+    long long tile = 0, rows = 0;
+    int ldmax = 4;
+    for (auto &ed : s->h_edges) {
+        const long long R = (ed.Lu + C - 1) / C;
+        tile = std::max(tile, R * ed.ld);
+        rows = std::max(rows, R);
+        ldmax = std::max(ldmax, ed.ld);
+    }
+    int T = s->opt.threads;
+    if (T <= 0) T = (4 * tile >= 48 * 1024) ? 512 : (4 * tile <= 4096 ? 128 : 256);
+    s->C = C;
+    s->T = T;
+    s->tile_floats = static_cast<int>(round4(std::max(4LL, tile)));
+    s->rmax = static_cast<int>(round4(std::max(4LL, rows)));
+    s->ldmax = ldmax;
+    s->max_phase = max_phase;
+}
+
+// Persistent driver: distribute each matching's edges over the clusters
+// (largest table first onto the least loaded cluster); each cluster's list
+// stays in schedule order, so every wait is on an earlier matching.
+static void build_work(mplpp_solver *s, int clusters)
+{
+    const int N = s->N;
+    std::vector<int> pos(N, 0), deg(N, 0);
+    for (int e : s->phase_edges) {
+        deg[s->h_edges[e].gu]++;
+        deg[s->h_edges[e].gv]++;
+    }
+    std::vector<std::vector<WorkItem>> lists(clusters);
+    using Load = std::pair<long long, int>;
+    std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
+    for (int c = 0; c < clusters; ++c) heap.push({0, c});
+    for (size_t p = 0; p + 1 < s->phase_off.size(); ++p) {
+        std::vector<int> es(s->phase_edges.begin() + s->phase_off[p], s->phase_edges.begin() + s->phase_off[p + 1]);
+        std::stable_sort(es.begin(), es.end(), [&](int a, int b) {
+            return 1LL * s->h_edges[a].Lu * s->h_edges[a].Lv > 1LL * s->h_edges[b].Lu * s->h_edges[b].Lv;
+        });
+        for (int e : es) {
+            Load l = heap.top();
+            heap.pop();
+            const EdgeDesc &ed = s->h_edges[e];
+            WorkItem w;
+            w.edge = e;
+            w.pos_u = pos[ed.gu]++;
+            w.pos_v = pos[ed.gv]++;
+            w.deg_u = deg[ed.gu];
+            w.deg_v = deg[ed.gv];
+            lists[l.second].push_back(w);
+            heap.push({l.first + 4LL * ed.Lu * ed.ld + 16LL * (ed.Lu + ed.Lv), l.second});
+        }
+    }
+    s->work_off.assign(1, 0);
+    s->work.clear();
+    for (auto &l : lists) {
+        s->work.insert(s->work.end(), l.begin(), l.end());
+        s->work_off.push_back(static_cast<int>(s->work.size()));
+    }
+    s->max_deg = 0;
+    for (int d : deg) s->max_deg = std::max(s->max_deg, d);
+}
+
+extern "C" mplpp_status mplpp_create(const mplpp_model *models, int32_t n_models, const mplpp_options *opt,
+                                     void *stream, mplpp_solver **out)
+{
+    g_create_error.clear();
+    if (!out) return fail(nullptr, MPLPP_E_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!models || n_models < 1) return fail(nullptr, MPLPP_E_INVALID, "need at least one model");
+    std::unique_ptr<mplpp_solver> s(new mplpp_solver());
+    if (opt) s->opt = *opt;
+    else mplpp_options_default(&s->opt);
+    if (s->opt.spin_limit <= 0) s->opt.spin_limit = 1LL << 22;
+    s->stream = static_cast<cudaStream_t>(stream);
+
+    // ---- host-side validation, schedules, layout --------------------------------
+    s->models.resize(n_models);
+    long long aoff = 0, moff = 0, toff = 0;
+    int P = 0;
+    for (int m = 0; m < n_models; ++m) {
+        const mplpp_model &md = models[m];
+        ModelHost &mh = s->models[m];
+        if (md.n_nodes < 1 || md.n_edges < 0) return fail(nullptr, MPLPP_E_INVALID, "model " + std::to_string(m) + ": bad sizes");
+        if (!md.labels || !md.unary || (md.n_edges > 0 && (!md.edge_u || !md.edge_v || !md.pairwise)))
+            return fail(nullptr, MPLPP_E_INVALID, "model " + std::to_string(m) + ": NULL array");
+        mh.n = md.n_nodes;
+        mh.E = md.n_edges;
+        mh.L.assign(md.labels, md.labels + md.n_nodes);
+        mh.eu.assign(md.edge_u, md.edge_u + md.n_edges);
+        mh.ev.assign(md.edge_v, md.edge_v + md.n_edges);
+        for (int l : mh.L)
+            if (l < 1 || l > 65535) return fail(nullptr, MPLPP_E_INVALID, "model " + std::to_string(m) + ": labels must be in 1..65535");
+        std::string err;
+        if (md.schedule_kind == MPLPP_SCHED_USER) {
+            if (md.n_matchings < 0 || !md.matching_off || (md.n_edges > 0 && !md.edge_order))
+                return fail(nullptr, MPLPP_E_INVALID, "model " + std::to_string(m) + ": user schedule missing");
+            mh.off.assign(md.matching_off, md.matching_off + md.n_matchings + 1);
+            mh.order.assign(md.edge_order, md.edge_order + md.n_edges);
+            err = check_graph(mh.n, mh.eu, mh.ev);
+            if (err.empty()) err = check_schedule(mh.n, mh.eu, mh.ev, mh.off, mh.order);
+        } else {
+            err = build_schedule(md.schedule_kind, mh.n, mh.eu, mh.ev, mh.off, mh.order);
+        }
+        if (!err.empty()) return fail(nullptr, MPLPP_E_INVALID, "model " + std::to_string(m) + ": " + err);
+        mh.node_base = s->N;
+        mh.edge_base = s->EE;
+        long long uoff = 0, poff = 0;
+        for (int u = 0; u < mh.n; ++u) {
+            NodeDesc nd;
+            nd.aoff = aoff;
+            nd.uoff = uoff;
+            nd.L = mh.L[u];
+            nd.model = m;
+            s->h_nodes.push_back(nd);
+            aoff += round4(mh.L[u]);
+            uoff += mh.L[u];
+        }
+        mh.unary_size = uoff;
+        for (int e = 0; e < mh.E; ++e) {
+            EdgeDesc ed;
+            ed.gu = mh.node_base + mh.eu[e];
+            ed.gv = mh.node_base + mh.ev[e];
+            ed.Lu = mh.L[mh.eu[e]];
+            ed.Lv = mh.L[mh.ev[e]];
+            ed.ld = static_cast<int>(round4(ed.Lv));
+            ed.toff = toff;
+            ed.mu = moff;
+            ed.mv = moff + round4(ed.Lu);
+            ed.au = s->h_nodes[ed.gu].aoff;
+            ed.av = s->h_nodes[ed.gv].aoff;
+            ed.poff = poff;
+            ed.model = m;
+            s->h_edges.push_back(ed);
+            toff += 1LL * ed.Lu * ed.ld;
+            moff += round4(ed.Lu) + round4(ed.Lv);
+            poff += 1LL * ed.Lu * ed.Lv;
+            s->bytes_per_iter += 4LL * ed.Lu * ed.Lv + 16LL * (ed.Lu + ed.Lv);
+        }
+        mh.pair_size = poff;
+        s->N += mh.n;
+        s->EE += mh.E;
+        s->sum_unary += mh.unary_size;
+        s->sum_pair += mh.pair_size;
+        P = std::max(P, static_cast<int>(mh.off.size()) - 1);
+    }
+    s->aggN = aoff;
+    s->msgN = moff;
+    s->tabN = toff;
+    s->P = P;
+    for (auto &ed : s->h_edges) s->sum_msg += ed.Lu + ed.Lv;
+    // phase p = matching p of every model
+    s->phase_off.assign(1, 0);
+    for (int p = 0; p < P; ++p) {
+        for (auto &mh : s->models)
+            if (p + 1 < static_cast<int>(mh.off.size()))
+                for (int i = mh.off[p]; i < mh.off[p + 1]; ++i) s->phase_edges.push_back(mh.edge_base + mh.order[i]);
+        s->phase_off.push_back(static_cast<int>(s->phase_edges.size()));
+    }
+    // in-edges (edges whose larger end is u), sorted by the smaller end
+    s->in_off.assign(s->N + 1, 0);
+    for (auto &ed : s->h_edges) s->in_off[ed.gv + 1]++;
+    for (int u = 0; u < s->N; ++u) s->in_off[u + 1] += s->in_off[u];
+    s->in_edge.assign(s->EE, 0);
+    {
+        std::vector<int> fill(s->in_off.begin(), s->in_off.end() - 1);
+        for (int e = 0; e < s->EE; ++e) s->in_edge[fill[s->h_edges[e].gv]++] = e;
+        for (int u = 0; u < s->N; ++u)
+            std::sort(s->in_edge.begin() + s->in_off[u], s->in_edge.begin() + s->in_off[u + 1],
+                      [&](int a, int b) { return s->h_edges[a].gu < s->h_edges[b].gu; });
+    }
+    s->mnode_off.assign(1, 0);
+    s->medge_off.assign(1, 0);
+    for (auto &mh : s->models) {
+        s->mnode_off.push_back(mh.node_base + mh.n);
+        s->medge_off.push_back(mh.edge_base + mh.E);
+    }
+    uint64_t h = 1469598103934665603ULL;
+    h = fnv(h, &n_models, sizeof(n_models));
+    for (auto &mh : s->models) {
+        h = fnv(h, mh.L.data(), mh.L.size() * sizeof(int));
+        h = fnv(h, mh.eu.data(), mh.eu.size() * sizeof(int));
+        h = fnv(h, mh.ev.data(), mh.ev.size() * sizeof(int));
+        h = fnv(h, mh.off.data(), mh.off.size() * sizeof(int));
+        h = fnv(h, mh.order.data(), mh.order.size() * sizeof(int));
+    }
+    s->shape_hash = h;
+
+    // ---- device ----------------------------------------------------------------
+    mplpp_solver *S = s.get();
+    cudaError_t ce = cudaGetDevice(&S->device);
+    if (ce != cudaSuccess) return cuda_fail(nullptr, ce, "cudaGetDevice");
+    int sms = 0, optin = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, S->device);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, S->device);
+    S->sms = sms;
+    choose_mapping(S, sms);
+    S->smem_looped = hs_smem_bytes(1, S->tile_floats, S->rmax, S->ldmax, S->T);
+    S->smem_persist = hs_smem_bytes(2, S->tile_floats, S->rmax, S->ldmax, S->T);
+    if (S->smem_looped > static_cast<size_t>(optin))
+        return fail(nullptr, MPLPP_E_UNSUPPORTED,
+                    "largest table needs " + std::to_string(S->smem_looped) + " B of shared memory per CTA with " +
+                        std::to_string(S->C) + " CTAs per edge (limit " + std::to_string(optin) + ")");
+    if ((ce = hs_prepare(std::max(S->smem_looped, std::min(S->smem_persist, static_cast<size_t>(optin))))) != cudaSuccess)
+        return cuda_fail(nullptr, ce, "kernel attributes");
+    S->mode = MPLPP_MODE_LOOPED;
+    if (S->opt.mode != MPLPP_MODE_LOOPED && S->smem_persist <= static_cast<size_t>(optin) && S->EE > 0) {
+        int clusters = hs_max_active_clusters(S->C, S->T, S->smem_persist);
+        clusters = std::min(clusters, S->max_phase);
+        if (clusters >= 1) {
+            S->mode = MPLPP_MODE_PERSISTENT;
+            S->clusters = clusters;
+            build_work(S, clusters);
+        }
+    }
+    if (S->opt.mode == MPLPP_MODE_PERSISTENT && S->mode != MPLPP_MODE_PERSISTENT)
+        return fail(nullptr, MPLPP_E_UNSUPPORTED, "persistent mode is not possible for these shapes on this device");
+
+    ce = cudaStreamCreateWithFlags(&S->cap_stream, cudaStreamNonBlocking);
+    if (ce != cudaSuccess) return cuda_fail(nullptr, ce, "cudaStreamCreate");
+    S->stream_ok = true;
+#define CKC(call)                                                  \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return cuda_fail(nullptr, e_, #call); \
+    } while (0)
+    CKC(S->alloc(&S->d_edges, S->EE));
+    CKC(S->alloc(&S->d_nodes, S->N));
+    CKC(S->alloc(&S->d_tab, S->tabN));
+    CKC(S->alloc(&S->d_agg, S->aggN));
+    CKC(S->alloc(&S->d_un0, S->aggN));
+    CKC(S->alloc(&S->d_msg, S->msgN));
+    CKC(S->alloc(&S->d_phase_edges, S->phase_edges.size()));
+    CKC(S->alloc(&S->d_err, 1));
+    CKC(S->alloc(&S->d_ver, S->N));
+    CKC(S->alloc(&S->d_in_off, S->in_off.size()));
+    CKC(S->alloc(&S->d_in_edge, S->in_edge.size()));
+    CKC(S->alloc(&S->d_mnode_off, S->mnode_off.size()));
+    CKC(S->alloc(&S->d_medge_off, S->medge_off.size()));
+    CKC(S->alloc(&S->d_emin, S->EE));
+    CKC(S->alloc(&S->d_nmin, S->N));
+    CKC(S->alloc(&S->d_out, n_models));
+    CKC(S->alloc(&S->d_labels, S->N));
+    CKC(S->alloc(&S->d_energy, n_models));
+    if (S->mode == MPLPP_MODE_PERSISTENT) {
+        CKC(S->alloc(&S->d_work_off, S->work_off.size()));
+        CKC(S->alloc(&S->d_work, S->work.size()));
+    }
+    cudaStream_t st = S->stream;
+    auto h2d = [&](void *dst, const void *src, size_t bytes) {
+        return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st) : cudaSuccess;
+    };
+    CKC(h2d(S->d_edges, S->h_edges.data(), S->h_edges.size() * sizeof(EdgeDesc)));
+    CKC(h2d(S->d_nodes, S->h_nodes.data(), S->h_nodes.size() * sizeof(NodeDesc)));
+    CKC(h2d(S->d_phase_edges, S->phase_edges.data(), S->phase_edges.size() * sizeof(int)));
+    CKC(h2d(S->d_in_off, S->in_off.data(), S->in_off.size() * sizeof(int)));
+    CKC(h2d(S->d_in_edge, S->in_edge.data(), S->in_edge.size() * sizeof(int)));
+    CKC(h2d(S->d_mnode_off, S->mnode_off.data(), S->mnode_off.size() * sizeof(int)));
+    CKC(h2d(S->d_medge_off, S->medge_off.data(), S->medge_off.size() * sizeof(int)));
+    if (S->mode == MPLPP_MODE_PERSISTENT) {
+        CKC(h2d(S->d_work_off, S->work_off.data(), S->work_off.size() * sizeof(int)));
+        CKC(h2d(S->d_work, S->work.data(), S->work.size() * sizeof(WorkItem)));
+    }
+    CKC(cudaMemsetAsync(S->d_err, 0, sizeof(int), st));
+    CKC(cudaMemsetAsync(S->d_msg, 0, S->msgN * sizeof(float), st));
+
+    // costs: stage (host inputs) or read in place (device inputs), then pack
+    float *stage_u = nullptr, *stage_p = nullptr;
+    if (!S->opt.inputs_on_device) {
+        CKC(dalloc(&stage_u, S->sum_unary));
+        CKC(dalloc(&stage_p, S->sum_pair));
+    }
+    cudaError_t pe = cudaSuccess;
+    long long ub = 0, pb = 0;
+    for (int m = 0; m < n_models && pe == cudaSuccess; ++m) {
+        const ModelHost &mh = S->models[m];
+        const float *su = models[m].unary;
+        const float *sp = models[m].pairwise;
+        if (!S->opt.inputs_on_device) {
+            pe = h2d(stage_u + ub, models[m].unary, mh.unary_size * sizeof(float));
+            if (pe == cudaSuccess && mh.pair_size)
+                pe = h2d(stage_p + pb, models[m].pairwise, mh.pair_size * sizeof(float));
+            su = stage_u + ub;
+            sp = stage_p + pb;
+        }
+        if (pe == cudaSuccess)
+            pe = launch_pack(S->d_edges + mh.edge_base, mh.E, S->d_nodes + mh.node_base, mh.n, su, sp, S->d_tab,
+                             S->d_un0, S->d_agg, S->d_err, st);
+        ub += mh.unary_size;
+        pb += mh.pair_size;
+    }
+    cudaError_t se = cudaStreamSynchronize(st);
+    if (stage_u) cudaFree(stage_u);
+    if (stage_p) cudaFree(stage_p);
+    if (pe != cudaSuccess) return cuda_fail(nullptr, pe, "packing the costs");
+    if (se != cudaSuccess) return cuda_fail(nullptr, se, "packing the costs");
+    int herr = 0;
+    CKC(cudaMemcpy(&herr, S->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (herr) return fail(nullptr, MPLPP_E_INVALID, "costs must be finite");
+#undef CKC
+    *out = s.release();
+    return MPLPP_OK;
+}
+
+// ---- iteration drivers ------------------------------------------------------------
+static HsParams make_params(mplpp_solver *s)
+{
+    HsParams p = {};
+    p.edges = s->d_edges;
+    p.tab = s->d_tab;
+    p.agg = s->d_agg;
+    p.msg = s->d_msg;
+    p.items = s->d_phase_edges;
+    p.work_off = s->d_work_off;
+    p.work = s->d_work;
+    p.ver = s->d_ver;
+    p.err = s->d_err;
+    p.spin_limit = s->opt.spin_limit;
+    p.test_wait = s->opt.test_unreachable_wait ? 1 : 0;
+    p.C = s->C;
+    p.tile_floats = s->tile_floats;
+    p.rmax = s->rmax;
+    p.ldmax = s->ldmax;
+    return p;
+}
+
+// One iteration of looped launches (one per matching) on stream st.
+cudaError_t enqueue_looped_iteration(mplpp_solver *s, cudaStream_t st, unsigned char *rec)
+{
+    HsParams p = make_params(s);
+    p.rec = rec;
+    p.rec_off = s->d_rec_off;
+    for (int ph = 0; ph + 1 < static_cast<int>(s->phase_off.size()); ++ph) {
+        p.items = s->d_phase_edges + s->phase_off[ph];
+        const int n = s->phase_off[ph + 1] - s->phase_off[ph];
+        cudaError_t e = hs_launch_looped(p, n, s->T, s->smem_looped, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// `iterations` iterations of the persistent kernel (counters reset first).
+cudaError_t enqueue_persistent(mplpp_solver *s, cudaStream_t st, int iterations, unsigned char *rec,
+                               long long rec_stride)
+{
+    HsParams p = make_params(s);
+    p.rec = rec;
+    p.rec_off = s->d_rec_off;
+    p.rec_stride = rec_stride;
+    // counters stay below 2^31: C * iterations * max_deg per launch
+    const long long cap = std::max(1LL, (1LL << 31) / (static_cast<long long>(s->C) * std::max(1, s->max_deg) + 1));
+    int done = 0;
+    while (done < iterations) {
+        const int chunk = static_cast<int>(std::min<long long>(iterations - done, cap));
+        cudaError_t e = cudaMemsetAsync(s->d_ver, 0, sizeof(unsigned) * s->N, st);
+        if (e != cudaSuccess) return e;
+        p.iterations = chunk;
+        if (rec) p.rec = rec + static_cast<long long>(done) * rec_stride;
+        e = hs_launch_persistent(p, s->clusters, s->T, s->smem_persist, st);
+        if (e != cudaSuccess) return e;
+        done += chunk;
+    }
+    return cudaSuccess;
+}
+
+mplpp_status run_plain(mplpp_solver *s, int iterations)
+{
+    if (iterations == 0 || s->EE == 0) return MPLPP_OK;
+    if (s->mode == MPLPP_MODE_LOOPED) {
+        if (s->opt.use_graph) {
+            if (!s->g_looped) {
+                cudaGraph_t g = nullptr;
+                CK(s, cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
+                cudaError_t e = enqueue_looped_iteration(s, s->cap_stream, nullptr);
+                cudaError_t e2 = cudaStreamEndCapture(s->cap_stream, &g);
+                if (e != cudaSuccess) {
+                    if (g) cudaGraphDestroy(g);
+                    return cuda_fail(s, e, "capturing the looped iteration");
+                }
+                if (e2 != cudaSuccess) return cuda_fail(s, e2, "cudaStreamEndCapture");
+                e = cudaGraphInstantiate(&s->g_looped, g, 0);
+                cudaGraphDestroy(g);
+                if (e != cudaSuccess) return cuda_fail(s, e, "cudaGraphInstantiate");
+            }
+            for (int it = 0; it < iterations; ++it) CK(s, cudaGraphLaunch(s->g_looped, s->stream));
+        } else {
+            for (int it = 0; it < iterations; ++it) CK(s, enqueue_looped_iteration(s, s->stream, nullptr));
+        }
+        s->launches += static_cast<long long>(iterations) * s->P;
+    } else {
+        if (s->opt.use_graph) {
+            if (!s->g_persist || s->g_persist_iters != iterations) {
+                if (s->g_persist) {
+                    cudaGraphExecDestroy(s->g_persist);
+                    s->g_persist = nullptr;
+                }
+                cudaGraph_t g = nullptr;
+                CK(s, cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
+                cudaError_t e = enqueue_persistent(s, s->cap_stream, iterations, nullptr, 0);
+                cudaError_t e2 = cudaStreamEndCapture(s->cap_stream, &g);
+                if (e != cudaSuccess) {
+                    if (g) cudaGraphDestroy(g);
+                    return cuda_fail(s, e, "capturing the persistent launch");
+                }
+                if (e2 != cudaSuccess) return cuda_fail(s, e2, "cudaStreamEndCapture");
+                e = cudaGraphInstantiate(&s->g_persist, g, 0);
+                cudaGraphDestroy(g);
+                if (e != cudaSuccess) return cuda_fail(s, e, "cudaGraphInstantiate");
+                s->g_persist_iters = iterations;
+            }
+            CK(s, cudaGraphLaunch(s->g_persist, s->stream));
+        } else {
+            CK(s, enqueue_persistent(s, s->stream, iterations, nullptr, 0));
+        }
+        const long long cap = std::max(1LL, (1LL << 31) / (static_cast<long long>(s->C) * std::max(1, s->max_deg) + 1));
+        s->launches += (iterations + cap - 1) / cap;
+    }
+    return MPLPP_OK;
+}
+
+extern "C" mplpp_status mplpp_run(mplpp_solver *s, int32_t iterations)
+{
+    if (!s) return MPLPP_E_INVALID;
+    if (iterations < 0) return fail(s, MPLPP_E_INVALID, "iterations must be >= 0");
+    s->err.clear();
+    mplpp_status st = s->opt.record_every > 0 ? run_recorded(s, iterations) : run_plain(s, iterations);
+    if (st == MPLPP_OK) s->iterations += iterations;
+    return st;
+}
+
+static mplpp_status check_device_error(mplpp_solver *s)
+{
+    int herr = 0;
+    CK(s, cudaMemcpy(&herr, s->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (herr) {
+        CK(s, cudaMemset(s->d_err, 0, sizeof(int)));
+        if (herr == ERR_TIMEOUT)
+            return fail(s, MPLPP_E_TIMEOUT, "a device-side wait exceeded spin_limit; the state is undefined");
+        return fail(s, MPLPP_E_NONFINITE, "non-finite value on the device");
+    }
+    return MPLPP_OK;
+}
+
+extern "C" mplpp_status mplpp_sync(mplpp_solver *s)
+{
+    if (!s) return MPLPP_E_INVALID;
+    CK(s, cudaStreamSynchronize(s->stream));
+    return check_device_error(s);
+}
+
+extern "C" mplpp_status mplpp_bound(mplpp_solver *s, double *out, int32_t exact)
+{
+    if (!s || !out) return MPLPP_E_INVALID;
+    s->err.clear();
+    CK(s, launch_bound(s->d_edges, s->EE, s->d_nodes, s->N, s->d_tab, s->d_agg, s->d_msg, s->d_emin, s->d_nmin,
+                       s->d_mnode_off, s->d_medge_off, static_cast<int>(s->models.size()), exact ? 1 : 0, s->d_out,
+                       s->stream));
+    CK(s, cudaMemcpyAsync(out, s->d_out, sizeof(double) * s->models.size(), cudaMemcpyDeviceToHost, s->stream));
+    mplpp_status st = mplpp_sync(s);
+    if (st != MPLPP_OK) return st;
+    for (size_t m = 0; m < s->models.size(); ++m)
+        if (!std::isfinite(out[m])) return fail(s, MPLPP_E_NONFINITE, "dual bound is not finite");
+    return MPLPP_OK;
+}
+
+extern "C" mplpp_status mplpp_labeling(mplpp_solver *s, int32_t *labels, double *energy)
+{
+    if (!s || !labels) return MPLPP_E_INVALID;
+    s->err.clear();
+    CK(s, launch_round(s->d_edges, s->d_nodes, s->d_in_off, s->d_in_edge, s->d_mnode_off, s->d_medge_off,
+                       static_cast<int>(s->models.size()), s->d_tab, s->d_agg, s->d_msg, s->d_un0, s->d_labels,
+                       s->d_energy, s->d_err, s->stream));
+    CK(s, cudaMemcpyAsync(labels, s->d_labels, sizeof(int) * s->N, cudaMemcpyDeviceToHost, s->stream));
+    if (energy)
+        CK(s, cudaMemcpyAsync(energy, s->d_energy, sizeof(double) * s->models.size(), cudaMemcpyDeviceToHost,
+                              s->stream));
+    return mplpp_sync(s);
+}
+
+extern "C" mplpp_status mplpp_reset(mplpp_solver *s)
+{
+    if (!s) return MPLPP_E_INVALID;
+    s->err.clear();
+    CK(s, cudaMemsetAsync(s->d_msg, 0, s->msgN * sizeof(float), s->stream));
+    CK(s, cudaMemcpyAsync(s->d_agg, s->d_un0, s->aggN * sizeof(float), cudaMemcpyDeviceToDevice, s->stream));
+    s->iterations = 0;
+    s->checkpoints_valid = true;
+    return MPLPP_OK;
+}
+
+extern "C" mplpp_status mplpp_state_size(const mplpp_solver *s, size_t *bytes)
+{
+    if (!s || !bytes) return MPLPP_E_INVALID;
+    *bytes = sizeof(mplpp_state_header) + sizeof(float) * (s->sum_unary + s->sum_msg);
+    return MPLPP_OK;
+}
+
+extern "C" mplpp_status mplpp_save_state(mplpp_solver *s, void *buf, size_t size)
+{
+    if (!s || !buf) return MPLPP_E_INVALID;
+    s->err.clear();
+    size_t need = 0;
+    mplpp_state_size(s, &need);
+    if (size < need) return fail(s, MPLPP_E_INVALID, "state buffer too small");
+    std::vector<float> agg(s->aggN), msg(s->msgN);
+    CK(s, cudaMemcpyAsync(agg.data(), s->d_agg, s->aggN * sizeof(float), cudaMemcpyDeviceToHost, s->stream));
+    CK(s, cudaMemcpyAsync(msg.data(), s->d_msg, s->msgN * sizeof(float), cudaMemcpyDeviceToHost, s->stream));
+    mplpp_status st = mplpp_sync(s);
+    if (st != MPLPP_OK) return st;
+    mplpp_state_header h;
+    h.magic = 0x4D504C50u;
+    h.version = 1;
+    h.shape_hash = s->shape_hash;
+    h.iterations = s->iterations;
+    h.n_unary = s->sum_unary;
+    h.n_msg = s->sum_msg;
+    char *p = static_cast<char *>(buf);
+    std::memcpy(p, &h, sizeof(h));
+    float *f = reinterpret_cast<float *>(p + sizeof(h));
+    for (auto &nd : s->h_nodes) {
+        std::memcpy(f, agg.data() + nd.aoff, sizeof(float) * nd.L);
+        f += nd.L;
+    }
+    for (auto &ed : s->h_edges) {
+        std::memcpy(f, msg.data() + ed.mu, sizeof(float) * ed.Lu);
+        f += ed.Lu;
+        std::memcpy(f, msg.data() + ed.mv, sizeof(float) * ed.Lv);
+        f += ed.Lv;
+    }
+    return MPLPP_OK;
+}
+
+extern "C" mplpp_status mplpp_load_state(mplpp_solver *s, const void *buf, size_t size)
+{
+    if (!s || !buf) return MPLPP_E_INVALID;
+    s->err.clear();
+    size_t need = 0;
+    mplpp_state_size(s, &need);
+    if (size < need) return fail(s, MPLPP_E_INVALID, "state buffer too small");
+    mplpp_state_header h;
+    std::memcpy(&h, buf, sizeof(h));
+    if (h.magic != 0x4D504C50u || h.version != 1 || h.shape_hash != s->shape_hash || h.n_unary != s->sum_unary ||
+        h.n_msg != s->sum_msg)
+        return fail(s, MPLPP_E_INVALID, "state does not match this solver's models");
+    std::vector<float> agg(s->aggN, 0.f), msg(s->msgN, 0.f);
+    const float *f = reinterpret_cast<const float *>(static_cast<const char *>(buf) + sizeof(h));
+    for (auto &nd : s->h_nodes) {
+        for (int i = 0; i < nd.L; ++i)
+            if (!std::isfinite(f[i])) return fail(s, MPLPP_E_INVALID, "state values must be finite");
+        std::memcpy(agg.data() + nd.aoff, f, sizeof(float) * nd.L);
+        f += nd.L;
+    }
+    for (auto &ed : s->h_edges) {
+        for (int i = 0; i < ed.Lu + ed.Lv; ++i)
+            if (!std::isfinite(f[i])) return fail(s, MPLPP_E_INVALID, "state values must be finite");
+        std::memcpy(msg.data() + ed.mu, f, sizeof(float) * ed.Lu);
+        f += ed.Lu;
+        std::memcpy(msg.data() + ed.mv, f, sizeof(float) * ed.Lv);
+        f += ed.Lv;
+    }
+    CK(s, cudaMemcpyAsync(s->d_agg, agg.data(), s->aggN * sizeof(float), cudaMemcpyHostToDevice, s->stream));
+    CK(s, cudaMemcpyAsync(s->d_msg, msg.data(), s->msgN * sizeof(float), cudaMemcpyHostToDevice, s->stream));
+    CK(s, cudaStreamSynchronize(s->stream));
+    s->iterations = h.iterations;
+    s->checkpoints_valid = false;
+    return MPLPP_OK;
+}
+
+extern "C" mplpp_status mplpp_info(const mplpp_solver *s, mplpp_info_t *info)
+{
+    if (!s || !info) return MPLPP_E_INVALID;
+    info->iterations = s->iterations;
+    info->bytes_per_iteration = s->bytes_per_iter;
+    info->edges = s->EE;
+    info->phases = s->P;
+    info->mode = s->mode;
+    info->cluster = s->C;
+    info->threads = s->T;
+    info->grid = s->mode == MPLPP_MODE_PERSISTENT ? s->clusters * s->C : 0;
+    info->launches_per_iteration = s->mode == MPLPP_MODE_PERSISTENT ? 0 : s->P;
+    return MPLPP_OK;
+}
+
+extern "C" void mplpp_destroy(mplpp_solver *s)
+{
+    delete s;
+}

@@ -1,0 +1,183 @@
+// common.cuh -- device data layout and sm_103a PTX helpers shared by the
+// solver's kernels (Handshake update, dual bound, rounding, backward).
+//
+// Device layout of a solver (all models concatenated, model after model):
+//   agg  [float]  theta^phi_u of every node (Sec. 3, eq. reparametrization),
+//                 each node's vector starts on a 16-byte boundary, pad = 0;
+//   msg  [float]  per edge phi_{v->u} (L_u) then phi_{u->v} (L_v), each padded
+//                 to a multiple of 4 floats, pad = 0;
+//   tab  [float]  the ORIGINAL pairwise tables theta_uv, never written after
+//                 creation; rows of L_v entries padded to a stride `ld`
+//                 (multiple of 4) with +inf, tables 16-byte aligned.  The
+//                 reparametrized table is implied:
+//                 theta^phi_uv(s,t) = theta_uv(s,t) - phi_{v->u}(s) - phi_{u->v}(t).
+//   un0  [float]  the original unaries in agg's layout (reset, energy).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mplpp {
+
+struct EdgeDesc {
+    long long toff;   // float offset of the table in tab (Lu rows, stride ld)
+    long long mu;     // float offset of phi_{v->u} in msg (Lu entries)
+    long long mv;     // float offset of phi_{u->v} in msg (Lv entries)
+    long long au;     // float offset of node u's vector in agg
+    long long av;     // float offset of node v's vector in agg
+    long long poff;   // float offset of the table in the caller's (unpadded) layout
+    int Lu, Lv, ld;   // label counts and row stride (ld = Lv rounded up to 4)
+    int gu, gv;       // global node ids
+    int model;        // model index
+};
+static_assert(sizeof(EdgeDesc) == 72, "EdgeDesc layout");
+
+struct NodeDesc {
+    long long aoff;   // float offset in agg / un0
+    long long uoff;   // float offset in the caller's (unpadded) unary layout
+    int L;
+    int model;
+};
+static_assert(sizeof(NodeDesc) == 24, "NodeDesc layout");
+
+// One entry of a persistent worker's list: edge id plus the number of earlier
+// updates of each endpoint within one iteration (its rank among that node's
+// edges in schedule order) and the endpoint degrees.
+struct WorkItem {
+    int edge;
+    int pos_u, pos_v;
+    int deg_u, deg_v;
+};
+
+constexpr int ERR_TIMEOUT = 1;
+constexpr int ERR_NONFINITE = 2;
+
+// ----------------------------------------------------------------------------
+// PTX wrappers (sm_90+ features used on sm_103a: mbarrier transaction counts,
+// bulk asynchronous copies, thread-block clusters and distributed shared memory)
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for an mbarrier phase; returns false after `limit` polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long limit)
+{
+    for (long long i = 0; i < limit; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// Bulk (non-tensor) asynchronous copy global -> this CTA's shared memory,
+// completing `bytes` transactions on `bar`.  dst and src 16-byte aligned,
+// bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_ctarank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ void cluster_arrive_release()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void cluster_arrive_relaxed()
+{
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void cluster_wait_acquire()
+{
+    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ uint32_t mapa_shared(uint32_t addr, uint32_t rank)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+
+__device__ __forceinline__ float4 ld_dsmem_f4(uint32_t addr)
+{
+    float4 v;
+    asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"(addr)
+                 : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ float4 min4(float4 a, float4 b)
+{
+    return make_float4(fminf(a.x, b.x), fminf(a.y, b.y), fminf(a.z, b.z), fminf(a.w, b.w));
+}
+
+__device__ __forceinline__ float4 add4s(float4 a, float s)
+{
+    return make_float4(a.x + s, a.y + s, a.z + s, a.w + s);
+}
+
+__device__ __forceinline__ float hmin_add(float4 x, float4 w)
+{
+    return fminf(fminf(x.x + w.x, x.y + w.y), fminf(x.z + w.z, x.w + w.w));
+}
+
+}  // namespace mplpp

@@ -1,0 +1,562 @@
+// handshake.cu -- the MPLP++ Handshake edge update on sm_103a.
+//
+// One update of edge uv (Sec. 4, eq. (H), three-minimization form) on the
+// message-form state of common.cuh:
+//   uh(s) = agg_u(s) - phi_{v->u}(s),  vh(t) = agg_v(t) - phi_{u->v}(t)
+//           (the unaries without this edge's messages; g = theta_uv + uh + vh)
+//   a(s)  = 1/2 (min_t [theta_uv(s,t) + vh(t)] + uh(s))        = 1/2 min_t g(s,t)
+//   alpha(s) = uh(s) - a(s)
+//   b(t)  = min_s [theta_uv(s,t) + alpha(s)] + vh(t)            = min_s [g(s,t) - a(s)]
+//   beta(t) = vh(t) - b(t)
+//   c(s)  = min_t [theta_uv(s,t) + beta(t)] + uh(s)             = min_t [g(s,t) - b(t)]
+//   agg_u := c, phi_{v->u} := c - uh;  agg_v := b, phi_{u->v} := b - vh.
+// The pairwise table is only read (4 B per entry, once from HBM); all three
+// minimizations run on the copy staged in shared memory.  Min-plus is not a
+// dense contraction, so this is FP32 ALU work bound by HBM bandwidth.
+//
+// Mapping: a cluster of C CTAs shares one edge; CTA `rank` owns the rows
+// [rank*R, rank*R + R) (R = ceil(L_u / C)), loaded with one bulk asynchronous
+// copy.  Row minima (passes 1 and 3) are local to the CTA; the column minima of
+// pass 2 are combined across the cluster through distributed shared memory.
+//
+// Two drivers:
+//   looped      one launch per matching; the launch boundary orders matchings
+//               (Sec. 6, GPU implementation: a barrier between matchings);
+//   persistent  one launch for all iterations; every cluster walks a fixed
+//               list of edges in schedule order and waits, per edge, only for
+//               the earlier updates of its two end nodes (per-node completion
+//               counters), while the next edge's table is already streaming
+//               into the second buffer.  Waits are bounded: past spin_limit
+//               polls the kernel records ERR_TIMEOUT and drains without waiting.
+#include <cfloat>
+#include <cstdint>
+
+#include "kernels.h"
+
+namespace mplpp {
+
+namespace {
+
+struct Smem {
+    float *tile[2];
+    float *uh, *alpha, *vh, *beta, *bv, *pm;
+    float4 *part;
+    int *pmi;           // REC: column argmin (row index) per column
+    int4 *parti;        // REC: partial column argmins
+    uint64_t *bar;      // [2]
+};
+
+__device__ __forceinline__ Smem carve(char *base, const HsParams &p, int nbuf)
+{
+    float *f = reinterpret_cast<float *>(base);
+    Smem s;
+    s.tile[0] = f;
+    f += p.tile_floats;
+    if (nbuf > 1) {
+        s.tile[1] = f;
+        f += p.tile_floats;
+    } else {
+        s.tile[1] = s.tile[0];
+    }
+    s.uh = f; f += p.rmax;
+    s.alpha = f; f += p.rmax;
+    s.vh = f; f += p.ldmax;
+    s.beta = f; f += p.ldmax;
+    s.bv = f; f += p.ldmax;
+    s.pm = f; f += p.ldmax;
+    s.part = reinterpret_cast<float4 *>(f); f += 4 * blockDim.x;
+    s.pmi = reinterpret_cast<int *>(f); f += p.ldmax;
+    s.parti = reinterpret_cast<int4 *>(f); f += 4 * blockDim.x;
+    s.bar = reinterpret_cast<uint64_t *>(f);
+    return s;
+}
+
+// Rows per group for the row minima: a power of two <= 32 giving each lane
+// about two float4 chunks of a row.
+__device__ __forceinline__ int row_group(int Q)
+{
+    int h = Q >> 1;
+    h = h < 1 ? 1 : (h > 32 ? 32 : h);
+    return 1 << (31 - __clz(h));
+}
+
+__device__ __forceinline__ void rows_of(const EdgeDesc &ed, int rank, int C, int &r0, int &nr)
+{
+    const int R = (ed.Lu + C - 1) / C;
+    r0 = rank * R;
+    nr = ed.Lu - r0;
+    nr = nr < 0 ? 0 : (nr > R ? R : nr);
+}
+
+// Thread 0: start the bulk copy of this CTA's row slice of edge ed's table.
+__device__ __forceinline__ void issue_tile(const EdgeDesc &ed, int rank, int C, const float *tab, float *buf,
+                                           uint64_t *bar)
+{
+    int r0, nr;
+    rows_of(ed, rank, C, r0, nr);
+    const uint32_t bytes = static_cast<uint32_t>(nr) * static_cast<uint32_t>(ed.ld) * 4u;
+    if (bytes) {
+        mbar_arrive_expect_tx(bar, bytes);
+        bulk_g2s(buf, tab + ed.toff + static_cast<long long>(r0) * ed.ld, bytes, bar);
+    } else {
+        mbar_arrive(bar);
+    }
+}
+
+__device__ __forceinline__ void set_err(int *err, int code)
+{
+    atomicCAS(err, 0, code);
+}
+
+// (value, index) minimum with the lower index winning ties.
+__device__ __forceinline__ void amin(float &m, int &i, float v, int j)
+{
+    if (v < m || (v == m && j < i)) {
+        m = v;
+        i = j;
+    }
+}
+
+// Minimum over a row slice of a float4 row against a float4 vector; REC also
+// tracks the lowest column attaining it.
+template <bool REC>
+__device__ __forceinline__ void row_scan(const float4 *row, const float4 *w, int Q, int lg, int G, float &m, int &mi)
+{
+    for (int q = lg; q < Q; q += G) {
+        const float4 x = row[q];
+        const float4 y = w[q];
+        if (REC) {
+            const float v0 = x.x + y.x, v1 = x.y + y.y, v2 = x.z + y.z, v3 = x.w + y.w;
+            if (v0 < m) { m = v0; mi = 4 * q; }
+            if (v1 < m) { m = v1; mi = 4 * q + 1; }
+            if (v2 < m) { m = v2; mi = 4 * q + 2; }
+            if (v3 < m) { m = v3; mi = 4 * q + 3; }
+        } else {
+            m = fminf(m, hmin_add(x, y));
+        }
+    }
+}
+
+template <bool REC>
+__device__ __forceinline__ void group_reduce(float &m, int &mi, int G)
+{
+    for (int o = G >> 1; o > 0; o >>= 1) {
+        const float om = __shfl_xor_sync(0xffffffffu, m, o);
+        if (REC) {
+            const int oi = __shfl_xor_sync(0xffffffffu, mi, o);
+            amin(m, mi, om, oi);
+        } else {
+            m = fminf(m, om);
+        }
+    }
+}
+
+// One Handshake update of edge ed by this CTA (its row slice); the table slice
+// is (or will be) in `tile`, signalled by `bar` completing phase `parity`.
+// Returns false if the table wait timed out.
+template <bool CLUSTER, bool REC>
+__device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile, const Smem &sm, int rank,
+                        uint64_t *bar, uint32_t parity, unsigned char *rec)
+{
+    const int T = blockDim.x, tid = threadIdx.x;
+    const int C = CLUSTER ? p.C : 1;
+    int r0, nr;
+    rows_of(ed, rank, C, r0, nr);
+    const int ld = ed.ld, Q = ld >> 2, Lv = ed.Lv;
+    float *agg = p.agg;
+    float *msg = p.msg;
+
+    // unaries without this edge's messages (written by other SMs: L2 loads)
+    for (int s = tid; s < nr; s += T)
+        sm.uh[s] = __ldcg(agg + ed.au + r0 + s) - __ldcg(msg + ed.mu + r0 + s);
+    for (int t = tid; t < ld; t += T)
+        sm.vh[t] = t < Lv ? __ldcg(agg + ed.av + t) - __ldcg(msg + ed.mv + t) : 0.f;
+
+    if (!mbar_wait(bar, parity, p.spin_limit)) set_err(p.err, ERR_TIMEOUT);
+    __syncthreads();
+
+    const float4 *t4 = reinterpret_cast<const float4 *>(tile);
+    const int G = row_group(Q);
+    const int gid = tid / G, lg = tid % G, ng = T / G;
+
+    unsigned short *rt1 = nullptr, *rs2 = nullptr, *rt3 = nullptr;
+    if (REC) {
+        rt1 = reinterpret_cast<unsigned short *>(rec);
+        rs2 = rt1 + ed.Lu;
+        rt3 = rs2 + ed.Lv;
+    }
+
+    // pass 1: a(s) = 1/2 (min_t [theta(s,t) + vh(t)] + uh(s));  alpha = uh - a
+    {
+        const float4 *w = reinterpret_cast<const float4 *>(sm.vh);
+        for (int base = 0; base < nr; base += ng) {
+            const int s = base + gid;
+            float m = INFINITY;
+            int mi = 0x7fffffff;
+            if (s < nr) row_scan<REC>(t4 + static_cast<size_t>(s) * Q, w, Q, lg, G, m, mi);
+            group_reduce<REC>(m, mi, G);
+            if (s < nr && lg == 0) {
+                const float u = sm.uh[s];
+                const float a = 0.5f * (m + u);
+                sm.alpha[s] = u - a;
+                if (REC) rt1[r0 + s] = static_cast<unsigned short>(mi);
+            }
+        }
+    }
+    __syncthreads();
+
+    // pass 2 (this CTA's rows): pm(t) = min_s [theta(s,t) + alpha(s)]
+    {
+        float4 *pm4 = reinterpret_cast<float4 *>(sm.pm);
+        int nsub = T / Q;
+        if (nsub >= 1) {
+            if (tid < nsub * Q) {
+                const int q = tid % Q, sub = tid / Q;
+                float4 m = make_float4(INFINITY, INFINITY, INFINITY, INFINITY);
+                int4 mi = make_int4(0x7fffffff, 0x7fffffff, 0x7fffffff, 0x7fffffff);
+                for (int s = sub; s < nr; s += nsub) {
+                    const float4 v = add4s(t4[static_cast<size_t>(s) * Q + q], sm.alpha[s]);
+                    if (REC) {
+                        if (v.x < m.x) { m.x = v.x; mi.x = s; }
+                        if (v.y < m.y) { m.y = v.y; mi.y = s; }
+                        if (v.z < m.z) { m.z = v.z; mi.z = s; }
+                        if (v.w < m.w) { m.w = v.w; mi.w = s; }
+                    } else {
+                        m = min4(m, v);
+                    }
+                }
+                sm.part[sub * Q + q] = m;
+                if (REC) sm.parti[sub * Q + q] = mi;
+            }
+            __syncthreads();
+            for (int q = tid; q < Q; q += T) {
+                float4 m = sm.part[q];
+                int4 mi = REC ? sm.parti[q] : make_int4(0, 0, 0, 0);
+                for (int j = 1; j < nsub; ++j) {
+                    const float4 o = sm.part[j * Q + q];
+                    if (REC) {
+                        const int4 oi = sm.parti[j * Q + q];
+                        amin(m.x, mi.x, o.x, oi.x);
+                        amin(m.y, mi.y, o.y, oi.y);
+                        amin(m.z, mi.z, o.z, oi.z);
+                        amin(m.w, mi.w, o.w, oi.w);
+                    } else {
+                        m = min4(m, o);
+                    }
+                }
+                pm4[q] = m;
+                if (REC) {
+                    sm.pmi[4 * q + 0] = mi.x + r0;
+                    sm.pmi[4 * q + 1] = mi.y + r0;
+                    sm.pmi[4 * q + 2] = mi.z + r0;
+                    sm.pmi[4 * q + 3] = mi.w + r0;
+                }
+            }
+        } else {
+            for (int q = tid; q < Q; q += T) {
+                float4 m = make_float4(INFINITY, INFINITY, INFINITY, INFINITY);
+                int4 mi = make_int4(0x7fffffff, 0x7fffffff, 0x7fffffff, 0x7fffffff);
+                for (int s = 0; s < nr; ++s) {
+                    const float4 v = add4s(t4[static_cast<size_t>(s) * Q + q], sm.alpha[s]);
+                    if (REC) {
+                        if (v.x < m.x) { m.x = v.x; mi.x = s; }
+                        if (v.y < m.y) { m.y = v.y; mi.y = s; }
+                        if (v.z < m.z) { m.z = v.z; mi.z = s; }
+                        if (v.w < m.w) { m.w = v.w; mi.w = s; }
+                    } else {
+                        m = min4(m, v);
+                    }
+                }
+                pm4[q] = m;
+                if (REC) {
+                    sm.pmi[4 * q + 0] = mi.x + r0;
+                    sm.pmi[4 * q + 1] = mi.y + r0;
+                    sm.pmi[4 * q + 2] = mi.z + r0;
+                    sm.pmi[4 * q + 3] = mi.w + r0;
+                }
+            }
+        }
+    }
+
+    // combine the column minima of all CTAs of the edge:
+    //   b(t) = min_s [...] + vh(t),  beta(t) = vh(t) - b(t)
+    if (CLUSTER) {
+        cluster_arrive_release();
+        cluster_wait_acquire();
+        const uint32_t pm_addr = smem_u32(sm.pm);
+        const uint32_t pmi_addr = smem_u32(sm.pmi);
+        for (int q = tid; q < Q; q += T) {
+            float4 m = ld_dsmem_f4(mapa_shared(pm_addr + 16u * q, 0));
+            int mi[4] = {0, 0, 0, 0};
+            if (REC) {
+                for (int j = 0; j < 4; ++j) {
+                    uint32_t a = mapa_shared(pmi_addr + 4u * (4 * q + j), 0);
+                    asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(mi[j]) : "r"(a) : "memory");
+                }
+            }
+            for (int r = 1; r < C; ++r) {
+                const float4 o = ld_dsmem_f4(mapa_shared(pm_addr + 16u * q, r));
+                if (REC) {
+                    // ranks hold increasing rows: on equal values keep the lower rank
+                    float om[4] = {o.x, o.y, o.z, o.w};
+                    float cm[4] = {m.x, m.y, m.z, m.w};
+                    for (int j = 0; j < 4; ++j) {
+                        if (om[j] < cm[j]) {
+                            cm[j] = om[j];
+                            uint32_t a = mapa_shared(pmi_addr + 4u * (4 * q + j), r);
+                            asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(mi[j]) : "r"(a) : "memory");
+                        }
+                    }
+                    m = make_float4(cm[0], cm[1], cm[2], cm[3]);
+                } else {
+                    m = min4(m, o);
+                }
+            }
+            const float mm[4] = {m.x, m.y, m.z, m.w};
+            for (int j = 0; j < 4; ++j) {
+                const int t = 4 * q + j;
+                const float vh = sm.vh[t];
+                const float b = mm[j] + vh;
+                sm.bv[t] = t < Lv ? b : 0.f;
+                sm.beta[t] = t < Lv ? vh - b : 0.f;
+                if (REC && t < Lv && rank == 0) rs2[t] = static_cast<unsigned short>(mi[j]);
+            }
+        }
+        cluster_arrive_relaxed();
+    } else {
+        __syncthreads();
+        for (int t = tid; t < ld; t += T) {
+            const float vh = sm.vh[t];
+            const float b = sm.pm[t] + vh;
+            sm.bv[t] = t < Lv ? b : 0.f;
+            sm.beta[t] = t < Lv ? vh - b : 0.f;
+            if (REC && t < Lv) rs2[t] = static_cast<unsigned short>(sm.pmi[t]);
+        }
+    }
+    __syncthreads();
+
+    // pass 3: c(s) = min_t [theta(s,t) + beta(t)] + uh(s); write node u's rows
+    {
+        const float4 *w = reinterpret_cast<const float4 *>(sm.beta);
+        for (int base = 0; base < nr; base += ng) {
+            const int s = base + gid;
+            float m = INFINITY;
+            int mi = 0x7fffffff;
+            if (s < nr) row_scan<REC>(t4 + static_cast<size_t>(s) * Q, w, Q, lg, G, m, mi);
+            group_reduce<REC>(m, mi, G);
+            if (s < nr && lg == 0) {
+                const float u = sm.uh[s];
+                const float c = m + u;
+                __stcg(agg + ed.au + r0 + s, c);
+                __stcg(msg + ed.mu + r0 + s, c - u);
+                if (REC) rt3[r0 + s] = static_cast<unsigned short>(mi);
+            }
+        }
+    }
+    // node v's vector (one CTA of the cluster)
+    if (rank == 0) {
+        for (int t = tid; t < Lv; t += T) {
+            const float b = sm.bv[t];
+            __stcg(agg + ed.av + t, b);
+            __stcg(msg + ed.mv + t, b - sm.vh[t]);
+        }
+    }
+    if (CLUSTER) cluster_wait_acquire();  // every CTA has finished reading this CTA's pm
+    __syncthreads();
+}
+
+template <bool CLUSTER, bool REC>
+__global__ void __launch_bounds__(512) hs_looped_kernel(HsParams p)
+{
+    extern __shared__ __align__(16) char smem_raw[];
+    Smem sm = carve(smem_raw, p, 1);
+    const int C = CLUSTER ? p.C : 1;
+    const int rank = CLUSTER ? static_cast<int>(cluster_ctarank()) : 0;
+    const int e = p.items[blockIdx.x / C];
+    const EdgeDesc ed = p.edges[e];
+    if (threadIdx.x == 0) {
+        mbar_init(&sm.bar[0], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) issue_tile(ed, rank, C, p.tab, sm.tile[0], &sm.bar[0]);
+    unsigned char *rec = REC ? p.rec + p.rec_off[e] : nullptr;
+    hs_item<CLUSTER, REC>(p, ed, sm.tile[0], sm, rank, &sm.bar[0], 0u, rec);
+}
+
+__device__ __forceinline__ void wait_nodes(const HsParams &p, int gu, unsigned need_u, int gv, unsigned need_v)
+{
+    long long spins = 0;
+    for (;;) {
+        const unsigned a = ld_acquire_u32(p.ver + gu);
+        const unsigned b = ld_acquire_u32(p.ver + gv);
+        if (a >= need_u && b >= need_v) return;
+        if (*reinterpret_cast<volatile int *>(p.err) != 0) return;  // draining after an error
+        if (++spins > p.spin_limit) {
+            set_err(p.err, ERR_TIMEOUT);
+            return;
+        }
+        if (spins > 4096) __nanosleep(64);
+    }
+}
+
+template <bool CLUSTER, bool REC>
+__global__ void __launch_bounds__(512) hs_persistent_kernel(HsParams p)
+{
+    extern __shared__ __align__(16) char smem_raw[];
+    Smem sm = carve(smem_raw, p, 2);
+    const int C = CLUSTER ? p.C : 1;
+    const int rank = CLUSTER ? static_cast<int>(cluster_ctarank()) : 0;
+    const int cid = blockIdx.x / C;
+    const int begin = p.work_off[cid];
+    const int n = p.work_off[cid + 1] - begin;
+    const long long total = static_cast<long long>(n) * p.iterations;
+    if (threadIdx.x == 0) {
+        mbar_init(&sm.bar[0], 1);
+        mbar_init(&sm.bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (total == 0) return;
+    if (threadIdx.x == 0) issue_tile(p.edges[p.work[begin].edge], rank, C, p.tab, sm.tile[0], &sm.bar[0]);
+    int i = 0, it = 0;
+    for (long long k = 0; k < total; ++k) {
+        const WorkItem w = p.work[begin + i];
+        const EdgeDesc ed = p.edges[w.edge];
+        if (threadIdx.x == 0) {
+            if (k + 1 < total) {
+                const int inext = (i + 1 == n) ? 0 : i + 1;
+                fence_proxy_async();
+                issue_tile(p.edges[p.work[begin + inext].edge], rank, C, p.tab, sm.tile[(k + 1) & 1],
+                           &sm.bar[(k + 1) & 1]);
+            }
+            const unsigned need_u = static_cast<unsigned>(C) *
+                                        static_cast<unsigned>(it * w.deg_u + w.pos_u) +
+                                    ((p.test_wait && k == 0 && cid == 0) ? 1u : 0u);
+            const unsigned need_v = static_cast<unsigned>(C) *
+                                    static_cast<unsigned>(it * w.deg_v + w.pos_v);
+            wait_nodes(p, ed.gu, need_u, ed.gv, need_v);
+        }
+        __syncthreads();
+        unsigned char *rec = REC ? p.rec + it * p.rec_stride + p.rec_off[w.edge] : nullptr;
+        hs_item<CLUSTER, REC>(p, ed, sm.tile[k & 1], sm, rank, &sm.bar[k & 1],
+                              static_cast<uint32_t>((k >> 1) & 1), rec);
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(p.ver + ed.gu, 1u);
+            atomicAdd(p.ver + ed.gv, 1u);
+        }
+        if (++i == n) {
+            i = 0;
+            ++it;
+        }
+    }
+}
+
+template <typename K>
+cudaError_t set_attrs(K kernel, size_t smem)
+{
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+}
+
+template <typename K>
+cudaError_t launch(K kernel, const HsParams &p, int grid, int threads, size_t smem, int C, cudaStream_t st)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(grid));
+    cfg.blockDim = dim3(static_cast<unsigned>(threads));
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    int na = 0;
+    if (C > 1) {
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = static_cast<unsigned>(C);
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        na = 1;
+    }
+    cfg.attrs = attr;
+    cfg.numAttrs = na;
+    return cudaLaunchKernelEx(&cfg, kernel, p);
+}
+
+}  // namespace
+
+size_t hs_smem_bytes(int nbuf, int tile_floats, int rmax, int ldmax, int threads)
+{
+    // tiles, uh, alpha, vh, beta, bv, pm, part(float4 x T), pmi, parti(int4 x T), 2 mbarriers
+    size_t f = static_cast<size_t>(nbuf) * tile_floats + 2 * static_cast<size_t>(rmax) +
+               5 * static_cast<size_t>(ldmax) + 8 * static_cast<size_t>(threads);
+    return f * 4 + 16;
+}
+
+cudaError_t hs_prepare(size_t smem)
+{
+    cudaError_t e;
+    if ((e = set_attrs(hs_looped_kernel<false, false>, smem)) != cudaSuccess) return e;
+    if ((e = set_attrs(hs_looped_kernel<true, false>, smem)) != cudaSuccess) return e;
+    if ((e = set_attrs(hs_looped_kernel<false, true>, smem)) != cudaSuccess) return e;
+    if ((e = set_attrs(hs_looped_kernel<true, true>, smem)) != cudaSuccess) return e;
+    if ((e = set_attrs(hs_persistent_kernel<false, false>, smem)) != cudaSuccess) return e;
+    if ((e = set_attrs(hs_persistent_kernel<true, false>, smem)) != cudaSuccess) return e;
+    if ((e = set_attrs(hs_persistent_kernel<false, true>, smem)) != cudaSuccess) return e;
+    return set_attrs(hs_persistent_kernel<true, true>, smem);
+}
+
+cudaError_t hs_launch_looped(const HsParams &p, int n_items, int threads, size_t smem, cudaStream_t st)
+{
+    if (n_items <= 0) return cudaSuccess;
+    const int grid = n_items * p.C;
+    if (p.rec) {
+        return p.C > 1 ? launch(hs_looped_kernel<true, true>, p, grid, threads, smem, p.C, st)
+                       : launch(hs_looped_kernel<false, true>, p, grid, threads, smem, 1, st);
+    }
+    return p.C > 1 ? launch(hs_looped_kernel<true, false>, p, grid, threads, smem, p.C, st)
+                   : launch(hs_looped_kernel<false, false>, p, grid, threads, smem, 1, st);
+}
+
+cudaError_t hs_launch_persistent(const HsParams &p, int clusters, int threads, size_t smem, cudaStream_t st)
+{
+    const int grid = clusters * p.C;
+    if (p.rec) {
+        return p.C > 1 ? launch(hs_persistent_kernel<true, true>, p, grid, threads, smem, p.C, st)
+                       : launch(hs_persistent_kernel<false, true>, p, grid, threads, smem, 1, st);
+    }
+    return p.C > 1 ? launch(hs_persistent_kernel<true, false>, p, grid, threads, smem, p.C, st)
+                   : launch(hs_persistent_kernel<false, false>, p, grid, threads, smem, 1, st);
+}
+
+int hs_max_active_clusters(int C, int threads, size_t smem)
+{
+    if (hs_prepare(smem) != cudaSuccess) return 0;
+    if (C <= 1) {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hs_persistent_kernel<false, false>, threads,
+                                                          smem) != cudaSuccess)
+            return 0;
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        return per_sm * sms;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(C));
+    cfg.blockDim = dim3(static_cast<unsigned>(threads));
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = static_cast<unsigned>(C);
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, hs_persistent_kernel<true, false>, &cfg) != cudaSuccess) return 0;
+    return n;
+}
+
+}  // namespace mplpp

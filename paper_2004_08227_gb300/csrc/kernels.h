@@ -1,0 +1,53 @@
+// kernels.h -- host-visible launch interfaces of the solver's kernels.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace mplpp {
+
+// Arguments of the Handshake kernels (one struct, passed by value).
+struct HsParams {
+    const EdgeDesc *edges;
+    const float *tab;
+    float *agg;
+    float *msg;
+    const int *items;        // looped: edge ids of the phase being launched
+    const int *work_off;     // persistent: [clusters + 1] offsets into work
+    const WorkItem *work;    // persistent: per-cluster item lists (one iteration)
+    unsigned *ver;           // persistent: per-node completion counters
+    int *err;                // device error word (ERR_*)
+    unsigned char *rec;      // backward recording: argmin bytes, or null
+    const long long *rec_off;// per edge: byte offset of its record within one iteration
+    long long rec_stride;    // bytes of one iteration's records
+    long long spin_limit;    // polls before a wait gives up
+    int iterations;          // persistent: iterations to run
+    int test_wait;           // testing: first item of worker 0 waits for an update that never comes
+    int C;                   // CTAs per edge (cluster size)
+    int tile_floats;         // capacity of one table buffer (floats)
+    int rmax;                // capacity of row vectors (floats, multiple of 4)
+    int ldmax;               // capacity of column vectors (floats, multiple of 4)
+};
+
+size_t hs_smem_bytes(int nbuf, int tile_floats, int rmax, int ldmax, int threads);
+cudaError_t hs_prepare(size_t smem_bytes);
+cudaError_t hs_launch_looped(const HsParams &p, int n_items, int threads, size_t smem, cudaStream_t st);
+cudaError_t hs_launch_persistent(const HsParams &p, int clusters, int threads, size_t smem, cudaStream_t st);
+int hs_max_active_clusters(int C, int threads, size_t smem);
+
+// dual.cu
+cudaError_t launch_pack(const EdgeDesc *edges, int n_edges, const NodeDesc *nodes, int n_nodes,
+                        const float *unary_src, const float *pair_src, float *tab, float *un0, float *agg,
+                        int *err, cudaStream_t st);
+cudaError_t launch_bound(const EdgeDesc *edges, int n_edges, const NodeDesc *nodes, int n_nodes,
+                         const float *tab, const float *agg, const float *msg, float *emin, float *nmin,
+                         const int *model_node_off, const int *model_edge_off, int n_models, int exact,
+                         double *out, cudaStream_t st);
+cudaError_t launch_round(const EdgeDesc *edges, const NodeDesc *nodes, const int *in_off, const int *in_edge,
+                         const int *model_node_off, const int *model_edge_off, int n_models, const float *tab,
+                         const float *agg, const float *msg, const float *un0, int *labels, double *energy,
+                         int *err, cudaStream_t st);
+
+}  // namespace mplpp

@@ -1,0 +1,99 @@
+// solver.h -- the opaque mplpp_solver (host bookkeeping + device buffers).
+#pragma once
+#include <cstdint>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/mplpp.h"
+#include "common.cuh"
+
+namespace mplpp {
+struct ModelHost {
+    int n = 0, E = 0;
+    int node_base = 0, edge_base = 0;
+    long long unary_size = 0, pair_size = 0;
+    std::vector<int> L, eu, ev, off, order;
+};
+}  // namespace mplpp
+
+struct mplpp_solver {
+    ~mplpp_solver();
+    template <typename Ty>
+    cudaError_t alloc(Ty **p, size_t count);
+
+    int device = 0;
+    int sms = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    bool stream_ok = false;
+    mplpp_options opt = {};
+    std::string err;
+    std::vector<mplpp::ModelHost> models;
+
+    int N = 0, EE = 0, P = 0;
+    long long aggN = 0, msgN = 0, tabN = 0;
+    long long sum_unary = 0, sum_pair = 0, sum_msg = 0;
+    long long bytes_per_iter = 0;
+    uint64_t shape_hash = 0;
+    std::vector<mplpp::EdgeDesc> h_edges;
+    std::vector<mplpp::NodeDesc> h_nodes;
+    std::vector<int> phase_off, phase_edges;
+    std::vector<int> in_off, in_edge, mnode_off, medge_off;
+    std::vector<int> work_off;
+    std::vector<mplpp::WorkItem> work;
+
+    // mapping
+    int mode = MPLPP_MODE_LOOPED;
+    int C = 1, T = 256, tile_floats = 4, rmax = 4, ldmax = 4, max_phase = 1, clusters = 0, max_deg = 0;
+    size_t smem_looped = 0, smem_persist = 0;
+
+    // device
+    std::vector<void *> allocations;
+    mplpp::EdgeDesc *d_edges = nullptr;
+    mplpp::NodeDesc *d_nodes = nullptr;
+    float *d_tab = nullptr, *d_agg = nullptr, *d_msg = nullptr, *d_un0 = nullptr;
+    int *d_phase_edges = nullptr, *d_err = nullptr;
+    unsigned *d_ver = nullptr;
+    int *d_work_off = nullptr;
+    mplpp::WorkItem *d_work = nullptr;
+    int *d_in_off = nullptr, *d_in_edge = nullptr, *d_mnode_off = nullptr, *d_medge_off = nullptr;
+    float *d_emin = nullptr, *d_nmin = nullptr;
+    double *d_out = nullptr, *d_energy = nullptr;
+    int *d_labels = nullptr;
+
+    // record / backward
+    long long *d_rec_off = nullptr;
+    long long rec_stride = 0;
+    std::vector<float *> ckpt;       // device copies of (agg, msg) every record_every iterations
+    bool checkpoints_valid = true;   // false after load_state
+    float *d_agg_w = nullptr, *d_msg_w = nullptr;        // recompute buffers
+    float *d_adj_agg = nullptr, *d_adj_msg = nullptr, *d_gtab = nullptr;
+    unsigned char *d_rec = nullptr;  // records of one segment
+    float *d_dD = nullptr;
+    long long *d_pbase = nullptr, *d_ubase = nullptr;  // per-model offsets of the caller's layouts
+
+    long long iterations = 0;
+    long long launches = 0;
+
+    cudaGraphExec_t g_looped = nullptr;
+    cudaGraphExec_t g_persist = nullptr;
+    int g_persist_iters = -1;
+};
+
+template <typename Ty>
+cudaError_t mplpp_solver::alloc(Ty **p, size_t count)
+{
+    *p = nullptr;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(p), (count ? count : 1) * sizeof(Ty));
+    if (e == cudaSuccess) allocations.push_back(*p);
+    return e;
+}
+
+// api.cu
+cudaError_t enqueue_looped_iteration(mplpp_solver *s, cudaStream_t st, unsigned char *rec);
+cudaError_t enqueue_persistent(mplpp_solver *s, cudaStream_t st, int iterations, unsigned char *rec,
+                               long long rec_stride);
+mplpp_status run_plain(mplpp_solver *s, int iterations);

@@ -1,0 +1,131 @@
+"""GPU backward: gradient of the dual bound after T iterations against the FP64
+oracle's reverse-mode gradient and against FP64 central finite differences.
+
+D_T is piecewise linear, so gradients are sums of +-2^-k; the GPU records its
+own argmins in FP32 while the oracle decides in FP64.  Tolerance (from north
+of the FP32 rounding of the adjoint sums): |g - g_ref| <= 1e-4 max(|g_ref|, 1e-3).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import schedule as osched
+from paper_2004_08227_gb300 import workloads as W
+from paper_2004_08227_gb300._lib import MplppError
+from paper_2004_08227_gb300.solver import MPLPPBound, Solver
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4
+
+
+def _order(m):
+    return osched.build(m.schedule, m.n, m.edge_u, m.edge_v)[1]
+
+
+def _close(g, ref):
+    return np.abs(g - ref) <= TOL * np.maximum(np.abs(ref), 1e-3)
+
+
+@pytest.mark.parametrize("T,k", [(0, 1), (1, 1), (6, 2), (9, 4)])
+@pytest.mark.parametrize("mode", ["looped", "persistent"])
+def test_grad_matches_oracle_small(T, k, mode):
+    m = W.uneven_complete(7, 2, 19, seed=T * 3 + k)
+    Do, gu_o, gp_o = oracle.grad(m, _order(m), T)
+    s = Solver([m], record_every=k, mode=mode)
+    s.run(T)
+    D = s.bound()[0]
+    gu, gp = s.backward()
+    assert abs(D - Do) <= 1e-5 * max(1.0, abs(Do))
+    assert np.all(_close(gu, gu_o)), np.abs(gu - gu_o).max()
+    assert np.all(_close(gp, gp_o)), np.abs(gp - gp_o).max()
+
+
+def test_grad_batch_and_weights():
+    """Several models in one solver; dD weights scale each model's gradient."""
+    models = [W.complete(6, 5, seed=s, pairwise="normal") for s in range(3)]
+    s = Solver(models, record_every=3)
+    s.run(7)
+    w = np.asarray([1.0, -2.0, 0.5], np.float32)
+    gu, gp = s.backward(w)
+    uo = po = 0
+    for i, m in enumerate(models):
+        _, a, b = oracle.grad(m, _order(m), 7)
+        assert np.all(_close(gu[uo:uo + a.size], w[i] * a))
+        assert np.all(_close(gp[po:po + b.size], w[i] * b))
+        uo += a.size
+        po += b.size
+
+
+def test_grad_sums_to_one_per_factor_on_gpu():
+    m = W.complete(10, 12, seed=3, pairwise="normal")
+    s = Solver([m], record_every=5)
+    s.run(12)
+    gu, gp = s.backward()
+    g = oracle.Graph.of(m)
+    for u in range(m.n):
+        assert abs(gu[g.uoff[u]:g.uoff[u + 1]].sum() - 1.0) < 1e-5
+    for e in range(m.E):
+        assert abs(gp[g.poff[e]:g.poff[e + 1]].sum() - 1.0) < 1e-5
+
+
+def test_autograd_function():
+    import torch
+    graphs = [W.complete(6, 7, seed=s, pairwise="normal") for s in range(2)]
+    un = torch.tensor(np.concatenate([g.unary for g in graphs]), device="cuda", requires_grad=True)
+    pw = torch.tensor(np.concatenate([g.pairwise for g in graphs]), device="cuda", requires_grad=True)
+    D = MPLPPBound.apply(un, pw, graphs, 8, 3)
+    (D * torch.tensor([1.0, 3.0], dtype=torch.float64, device="cuda")).sum().backward()
+    uo = po = 0
+    for i, m in enumerate(graphs):
+        Do, a, b = oracle.grad(m, _order(m), 8)
+        assert abs(D[i].item() - Do) <= 1e-5 * max(1.0, abs(Do))
+        w = [1.0, 3.0][i]
+        assert np.all(_close(un.grad[uo:uo + a.size].cpu().numpy(), w * a))
+        assert np.all(_close(pw.grad[po:po + b.size].cpu().numpy(), w * b))
+        uo += a.size
+        po += b.size
+
+
+def test_backward_requires_record():
+    m = W.complete(5, 3, seed=0)
+    s = Solver([m])
+    s.run(2)
+    with pytest.raises(MplppError) as ei:
+        s.backward()
+    assert ei.value.status == -6
+
+
+def _fd(m, order, T, which, i, h):
+    un = m.unary.astype(np.float64).copy()
+    pw = m.pairwise.astype(np.float64).copy()
+    vals = []
+    for d in (h, -h):
+        u2, p2 = un.copy(), pw.copy()
+        (u2 if which == "u" else p2)[i] += d
+        th_u, th_uv = oracle.run(m, order, T, state=(u2, p2))
+        vals.append(oracle.bound(m, th_u, th_uv))
+    return (vals[0] - vals[1]) / (2 * h)
+
+
+def test_grad_central_differences_K50_L64():
+    """Differentiation workload shape (K_50, L = 64, N(0,1) pairwise, T = 50,
+    checkpoints every 10) on one model of the batch: GPU gradient against FP64
+    central differences (h = 1e-4) of the oracle's D_T on sampled entries,
+    half of them drawn where the oracle's gradient is non-zero."""
+    m = W.complete(50, 64, seed=0, pairwise="normal")
+    T = 50
+    order = _order(m)
+    s = Solver([m], record_every=10)
+    s.run(T)
+    gu, gp = s.backward()
+    _, gu_o, gp_o = oracle.grad(m, order, T)
+    rng = np.random.default_rng(0)
+    nz = np.flatnonzero(gp_o)
+    picks = [("p", int(i)) for i in rng.choice(nz, size=min(6, nz.size), replace=False)]
+    picks += [("p", int(i)) for i in rng.choice(gp_o.size, size=2, replace=False)]
+    picks += [("u", int(i)) for i in rng.choice(gu_o.size, size=4, replace=False)]
+    for which, i in picks:
+        fd = _fd(m, order, T, which, i, 1e-4)
+        g = (gu if which == "u" else gp)[i]
+        assert abs(g - fd) <= TOL * max(abs(fd), 1e-3), (which, i, g, fd)
