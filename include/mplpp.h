@@ -86,8 +86,9 @@ typedef struct {
     int32_t use_graph;        /* nonzero: replay the launches of an iteration from a CUDA graph */
     int32_t inputs_on_device; /* nonzero: model.unary / model.pairwise are device pointers and
                                  mplpp_backward writes device gradients                         */
-    int32_t record_every;     /* > 0: mplpp_run keeps a state checkpoint every k iterations so
-                                 that mplpp_backward can differentiate the run; 0: no record    */
+    int32_t record_every;     /* > 0: enables mplpp_backward, which replays the run in FP64 with
+                                 a state checkpoint every k iterations (memory ~ T/k states);
+                                 0: backward disabled                                          */
     int32_t cluster;          /* CTAs sharing one edge (1..8); 0 = chosen from the shapes      */
     int32_t threads;          /* threads per CTA (128, 256, 512); 0 = chosen from the shapes   */
     int32_t test_unreachable_wait; /* testing only (0 otherwise): in the persistent driver the
@@ -145,8 +146,11 @@ mplpp_status mplpp_labeling(mplpp_solver *s, int32_t *labels, double *energy);
 /* Gradient of sum_m dD[m] * D_m, where D_m is model m's exact dual bound after
  * the iterations run since the last reset, with respect to the original unary
  * and pairwise costs.  D is piecewise linear; the gradient is that of the
- * linear piece selected by the forward argmins (lowest index on ties).
- * Requires options.record_every > 0 and a run that started from phi = 0.
+ * linear piece selected by the argmins (lowest index on ties) of the same
+ * iterations replayed in FP64 -- the FP32 run can sit on a different piece
+ * near ties, the FP64 replay follows the exact-arithmetic one.
+ * Requires options.record_every > 0 and a run that started from phi = 0
+ * (creation or mplpp_reset, no mplpp_load_state since).
  * dD: host [n_models]; grad_unary [sum L], grad_pairwise [sum L_u L_v] in the
  * input layout, host or device as options.inputs_on_device says.
  * Synchronizes. */

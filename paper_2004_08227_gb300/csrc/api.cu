@@ -91,23 +91,9 @@ extern "C" const char *mplpp_last_error(const mplpp_solver *s)
     return s ? s->err.c_str() : g_create_error.c_str();
 }
 
-// Chooses CTAs per edge (C) and threads per CTA (T) from the table shapes:
-// a CTA's row slice should stay well inside shared memory (two buffers in the
-// persistent driver), and edges with large tables spread over enough CTAs to
-// fill the SMs when a matching has few edges.
-static void choose_mapping(mplpp_solver *s, int sms)
+// Mapping for one candidate cluster size C: per-CTA tile and vector sizes.
+static void mapping_for(mplpp_solver *s, int C)
 {
-    long long tb = 0;
-    int max_phase = 1;
-    for (auto &ed : s->h_edges) tb = std::max(tb, 4LL * ed.Lu * ed.ld);
-    for (size_t p = 0; p + 1 < s->phase_off.size(); ++p)
-        max_phase = std::max(max_phase, s->phase_off[p + 1] - s->phase_off[p]);
-    int C = s->opt.cluster;
-    if (C <= 0) {
-        C = static_cast<int>((tb + 96 * 1024 - 1) / (96 * 1024));
-        if (tb > 32 * 1024) C = std::max(C, std::min(8, sms / max_phase));
-        C = std::max(1, std::min(8, C));
-    }
     long long tile = 0, rows = 0;
     int ldmax = 4;
     for (auto &ed : s->h_edges) {
@@ -123,7 +109,54 @@ static void choose_mapping(mplpp_solver *s, int sms)
     s->tile_floats = static_cast<int>(round4(std::max(4LL, tile)));
     s->rmax = static_cast<int>(round4(std::max(4LL, rows)));
     s->ldmax = ldmax;
+    s->smem_looped = hs_smem_bytes(1, s->tile_floats, s->rmax, s->ldmax, s->T);
+    s->smem_persist = hs_smem_bytes(2, s->tile_floats, s->rmax, s->ldmax, s->T);
+}
+
+// Chooses CTAs per edge (C).  A matching's edges should run in one round of
+// co-resident clusters (the persistent driver's critical path is one edge
+// update per matching and round), and within that the CTA slices should be
+// small (less work per update).  Cost model per matching:
+//   rounds(C) * (3 us of dependency latency + slice bytes / 40 GB/s per SM).
+// Candidates whose double-buffered slice does not fit shared memory can only
+// run looped.
+static void choose_mapping(mplpp_solver *s, int sms, int optin)
+{
+    int max_phase = 1;
+    for (size_t p = 0; p + 1 < s->phase_off.size(); ++p)
+        max_phase = std::max(max_phase, s->phase_off[p + 1] - s->phase_off[p]);
     s->max_phase = max_phase;
+    if (s->opt.cluster > 0) {
+        mapping_for(s, s->opt.cluster);
+        return;
+    }
+    double best = 1e300;
+    int bestC = 0;
+    for (int C = 1; C <= 8; ++C) {
+        mapping_for(s, C);
+        if (s->smem_persist > static_cast<size_t>(optin)) continue;
+        if (C > 1 && static_cast<long long>(C) * max_phase > 2LL * sms) break;
+        const int avail = std::min(hs_max_active_clusters(C, s->T, s->smem_persist), max_phase);
+        if (avail < 1) continue;
+        const int rounds = (max_phase + avail - 1) / avail;
+        const double cost = rounds * (3e-6 + 4.0 * s->tile_floats / 40e9);
+        if (cost < best * 0.999) {
+            best = cost;
+            bestC = C;
+        }
+    }
+    if (bestC == 0) {  // nothing fits twice: the smallest slice, looped only
+        bestC = 8;
+        for (int C = 1; C <= 8; ++C) {
+            mapping_for(s, C);
+            if (s->smem_looped <= static_cast<size_t>(optin)) {
+                bestC = C;
+                break;
+            }
+        }
+    }
+    mapping_for(s, bestC);
+    (void)sms;
 }
 
 // Persistent driver: distribute each matching's edges over the clusters
@@ -303,9 +336,7 @@ extern "C" mplpp_status mplpp_create(const mplpp_model *models, int32_t n_models
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, S->device);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, S->device);
     S->sms = sms;
-    choose_mapping(S, sms);
-    S->smem_looped = hs_smem_bytes(1, S->tile_floats, S->rmax, S->ldmax, S->T);
-    S->smem_persist = hs_smem_bytes(2, S->tile_floats, S->rmax, S->ldmax, S->T);
+    choose_mapping(S, sms, optin);
     if (S->smem_looped > static_cast<size_t>(optin))
         return fail(nullptr, MPLPP_E_UNSUPPORTED,
                     "largest table needs " + std::to_string(S->smem_looped) + " B of shared memory per CTA with " +
@@ -434,11 +465,9 @@ static HsParams make_params(mplpp_solver *s)
 }
 
 // One iteration of looped launches (one per matching) on stream st.
-cudaError_t enqueue_looped_iteration(mplpp_solver *s, cudaStream_t st, unsigned char *rec)
+cudaError_t enqueue_looped_iteration(mplpp_solver *s, cudaStream_t st)
 {
     HsParams p = make_params(s);
-    p.rec = rec;
-    p.rec_off = s->d_rec_off;
     for (int ph = 0; ph + 1 < static_cast<int>(s->phase_off.size()); ++ph) {
         p.items = s->d_phase_edges + s->phase_off[ph];
         const int n = s->phase_off[ph + 1] - s->phase_off[ph];
@@ -449,13 +478,9 @@ cudaError_t enqueue_looped_iteration(mplpp_solver *s, cudaStream_t st, unsigned 
 }
 
 // `iterations` iterations of the persistent kernel (counters reset first).
-cudaError_t enqueue_persistent(mplpp_solver *s, cudaStream_t st, int iterations, unsigned char *rec,
-                               long long rec_stride)
+cudaError_t enqueue_persistent(mplpp_solver *s, cudaStream_t st, int iterations)
 {
     HsParams p = make_params(s);
-    p.rec = rec;
-    p.rec_off = s->d_rec_off;
-    p.rec_stride = rec_stride;
     // counters stay below 2^31: C * iterations * max_deg per launch
     const long long cap = std::max(1LL, (1LL << 31) / (static_cast<long long>(s->C) * std::max(1, s->max_deg) + 1));
     int done = 0;
@@ -464,7 +489,6 @@ cudaError_t enqueue_persistent(mplpp_solver *s, cudaStream_t st, int iterations,
         cudaError_t e = cudaMemsetAsync(s->d_ver, 0, sizeof(unsigned) * s->N, st);
         if (e != cudaSuccess) return e;
         p.iterations = chunk;
-        if (rec) p.rec = rec + static_cast<long long>(done) * rec_stride;
         e = hs_launch_persistent(p, s->clusters, s->T, s->smem_persist, st);
         if (e != cudaSuccess) return e;
         done += chunk;
@@ -472,7 +496,7 @@ cudaError_t enqueue_persistent(mplpp_solver *s, cudaStream_t st, int iterations,
     return cudaSuccess;
 }
 
-mplpp_status run_plain(mplpp_solver *s, int iterations)
+static mplpp_status run_plain(mplpp_solver *s, int iterations)
 {
     if (iterations == 0 || s->EE == 0) return MPLPP_OK;
     if (s->mode == MPLPP_MODE_LOOPED) {
@@ -480,7 +504,7 @@ mplpp_status run_plain(mplpp_solver *s, int iterations)
             if (!s->g_looped) {
                 cudaGraph_t g = nullptr;
                 CK(s, cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
-                cudaError_t e = enqueue_looped_iteration(s, s->cap_stream, nullptr);
+                cudaError_t e = enqueue_looped_iteration(s, s->cap_stream);
                 cudaError_t e2 = cudaStreamEndCapture(s->cap_stream, &g);
                 if (e != cudaSuccess) {
                     if (g) cudaGraphDestroy(g);
@@ -493,7 +517,7 @@ mplpp_status run_plain(mplpp_solver *s, int iterations)
             }
             for (int it = 0; it < iterations; ++it) CK(s, cudaGraphLaunch(s->g_looped, s->stream));
         } else {
-            for (int it = 0; it < iterations; ++it) CK(s, enqueue_looped_iteration(s, s->stream, nullptr));
+            for (int it = 0; it < iterations; ++it) CK(s, enqueue_looped_iteration(s, s->stream));
         }
         s->launches += static_cast<long long>(iterations) * s->P;
     } else {
@@ -505,7 +529,7 @@ mplpp_status run_plain(mplpp_solver *s, int iterations)
                 }
                 cudaGraph_t g = nullptr;
                 CK(s, cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
-                cudaError_t e = enqueue_persistent(s, s->cap_stream, iterations, nullptr, 0);
+                cudaError_t e = enqueue_persistent(s, s->cap_stream, iterations);
                 cudaError_t e2 = cudaStreamEndCapture(s->cap_stream, &g);
                 if (e != cudaSuccess) {
                     if (g) cudaGraphDestroy(g);
@@ -519,7 +543,7 @@ mplpp_status run_plain(mplpp_solver *s, int iterations)
             }
             CK(s, cudaGraphLaunch(s->g_persist, s->stream));
         } else {
-            CK(s, enqueue_persistent(s, s->stream, iterations, nullptr, 0));
+            CK(s, enqueue_persistent(s, s->stream, iterations));
         }
         const long long cap = std::max(1LL, (1LL << 31) / (static_cast<long long>(s->C) * std::max(1, s->max_deg) + 1));
         s->launches += (iterations + cap - 1) / cap;
@@ -532,7 +556,7 @@ extern "C" mplpp_status mplpp_run(mplpp_solver *s, int32_t iterations)
     if (!s) return MPLPP_E_INVALID;
     if (iterations < 0) return fail(s, MPLPP_E_INVALID, "iterations must be >= 0");
     s->err.clear();
-    mplpp_status st = s->opt.record_every > 0 ? run_recorded(s, iterations) : run_plain(s, iterations);
+    mplpp_status st = run_plain(s, iterations);
     if (st == MPLPP_OK) s->iterations += iterations;
     return st;
 }
@@ -593,7 +617,7 @@ extern "C" mplpp_status mplpp_reset(mplpp_solver *s)
     CK(s, cudaMemsetAsync(s->d_msg, 0, s->msgN * sizeof(float), s->stream));
     CK(s, cudaMemcpyAsync(s->d_agg, s->d_un0, s->aggN * sizeof(float), cudaMemcpyDeviceToDevice, s->stream));
     s->iterations = 0;
-    s->checkpoints_valid = true;
+    s->history_valid = true;
     return MPLPP_OK;
 }
 
@@ -671,7 +695,7 @@ extern "C" mplpp_status mplpp_load_state(mplpp_solver *s, const void *buf, size_
     CK(s, cudaMemcpyAsync(s->d_msg, msg.data(), s->msgN * sizeof(float), cudaMemcpyHostToDevice, s->stream));
     CK(s, cudaStreamSynchronize(s->stream));
     s->iterations = h.iterations;
-    s->checkpoints_valid = false;
+    s->history_valid = false;
     return MPLPP_OK;
 }
 

@@ -3,13 +3,15 @@
 // differentiation of the message-form iteration (handshake.cu).
 //
 // D is piecewise linear in the costs; inside one linear piece every minimum is
-// attained at a fixed argument, so the forward is a sum of selected entries.
-// The forward is recomputed segment by segment from checkpoints while the
-// argmins of the three minimizations of every update are recorded:
+// attained at a fixed argument, so D is a sum of selected entries.  The
+// iterations are replayed in FP64 (record.cu) from phi = 0, keeping a state
+// checkpoint every k iterations; then, segment by segment from the last, the
+// segment is recomputed while the argmins of the three minimizations of every
+// update are recorded:
 //   t1(s) = argmin_t [theta(s,t) + vh(t)],  s2(t) = argmin_s [theta(s,t) + alpha(s)],
 //   t3(s) = argmin_t [theta(s,t) + beta(t)]          (lowest index on ties)
-// and the updates are then replayed in reverse schedule order.  With the
-// adjoints Au, Phu (of agg_u and phi_{v->u} after the update) and Av, Phv:
+// and the updates are replayed in reverse schedule order.  With the adjoints
+// Au, Phu (of agg_u and phi_{v->u} after the update) and Av, Phv:
 //   cbar = Au + Phu;  uhbar = Au;  bbar = Av + Phv;  vhbar = -Phv
 //   betabar(t) = sum_{s: t3(s)=t} cbar(s);  thetabar(s, t3(s)) += cbar(s)
 //   vhbar += betabar;  bbar -= betabar;  vhbar += bbar
@@ -39,57 +41,59 @@ namespace {
 constexpr int kThreads = 256;
 
 // Adjoint of D = sum_u min agg_u + sum_e min residual_e at the final state.
-__global__ void bw_init_nodes_kernel(const NodeDesc *nodes, int n_nodes, const float *agg, const float *dD,
-                                     float *adj_agg)
+__global__ void bw_init_nodes_kernel(const NodeDesc *nodes, int n_nodes, const double *agg, const float *dD,
+                                     double *adj_agg)
 {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     for (int u = warp; u < n_nodes; u += nw) {
         const NodeDesc nd = nodes[u];
-        float m = INFINITY;
+        double m = INFINITY;
         int mi = INT_MAX;
         for (int s = lane; s < nd.L; s += 32) {
-            const float v = agg[nd.aoff + s];
+            const double v = agg[nd.aoff + s];
             if (v < m) {
                 m = v;
                 mi = s;
             }
         }
         for (int o = 16; o > 0; o >>= 1) {
-            const float om = __shfl_xor_sync(0xffffffffu, m, o);
+            const double om = __shfl_xor_sync(0xffffffffu, m, o);
             const int oi = __shfl_xor_sync(0xffffffffu, mi, o);
             if (om < m || (om == m && oi < mi)) {
                 m = om;
                 mi = oi;
             }
         }
-        if (lane == 0 && mi != INT_MAX) adj_agg[nd.aoff + mi] += dD[nd.model];
+        if (lane == 0 && mi != INT_MAX) adj_agg[nd.aoff + mi] += static_cast<double>(dD[nd.model]);
     }
 }
 
 __global__ void __launch_bounds__(kThreads) bw_init_edges_kernel(const EdgeDesc *edges, int n_edges, const float *tab,
-                                                                 const float *msg, const float *dD, float *adj_msg,
-                                                                 float *gtab)
+                                                                 const double *msg, const float *dD, double *adj_msg,
+                                                                 double *gtab)
 {
-    __shared__ float rv[kThreads / 32];
+    __shared__ double rv[kThreads / 32];
     __shared__ long long ri[kThreads / 32];
     for (int e = blockIdx.x; e < n_edges; e += gridDim.x) {
         const EdgeDesc ed = edges[e];
-        float m = INFINITY;
+        double m = INFINITY;
         long long mi = LLONG_MAX;
         const long long n = static_cast<long long>(ed.Lu) * ed.Lv;
         for (long long i = threadIdx.x; i < n; i += blockDim.x) {
             const int s = static_cast<int>(i / ed.Lv);
             const int t = static_cast<int>(i - static_cast<long long>(s) * ed.Lv);
-            const float r = (tab[ed.toff + static_cast<long long>(s) * ed.ld + t] - msg[ed.mu + s]) - msg[ed.mv + t];
+            const double r =
+                (static_cast<double>(tab[ed.toff + static_cast<long long>(s) * ed.ld + t]) - msg[ed.mu + s]) -
+                msg[ed.mv + t];
             if (r < m) {
                 m = r;
                 mi = i;
             }
         }
         for (int o = 16; o > 0; o >>= 1) {
-            const float om = __shfl_xor_sync(0xffffffffu, m, o);
+            const double om = __shfl_xor_sync(0xffffffffu, m, o);
             const long long oi = __shfl_xor_sync(0xffffffffu, mi, o);
             if (om < m || (om == m && oi < mi)) {
                 m = om;
@@ -111,7 +115,7 @@ __global__ void __launch_bounds__(kThreads) bw_init_edges_kernel(const EdgeDesc 
             if (ri[0] != LLONG_MAX) {
                 const int s = static_cast<int>(ri[0] / ed.Lv);
                 const int t = static_cast<int>(ri[0] - static_cast<long long>(s) * ed.Lv);
-                const float d = dD[ed.model];
+                const double d = static_cast<double>(dD[ed.model]);
                 gtab[ed.toff + static_cast<long long>(s) * ed.ld + t] += d;
                 adj_msg[ed.mu + s] -= d;
                 adj_msg[ed.mv + t] -= d;
@@ -124,27 +128,27 @@ __global__ void __launch_bounds__(kThreads) bw_init_edges_kernel(const EdgeDesc 
 // Reverse of one Handshake update per CTA (one matching per launch).
 __global__ void __launch_bounds__(kThreads) bw_phase_kernel(BwParams p, const int *items)
 {
-    extern __shared__ __align__(16) float sh[];
+    extern __shared__ __align__(16) double sh[];
     const int e = items[blockIdx.x];
     const EdgeDesc ed = p.edges[e];
     const int Lu = ed.Lu, Lv = ed.Lv, T = blockDim.x, tid = threadIdx.x;
     const int lm = p.lmax;
-    float *cb = sh;          // cbar = m3bar            [Lu]
-    float *uhb = cb + lm;    // uhbar                   [Lu]
-    float *alb = uhb + lm;   // alphabar                [Lu]
-    float *m1b = alb + lm;   // m1bar                   [Lu]
-    float *bb = m1b + lm;    // bbar = m2bar            [Lv]
-    float *vhb = bb + lm;    // vhbar                   [Lv]
-    float *beb = vhb + lm;   // betabar                 [Lv]
+    double *cb = sh;         // cbar = m3bar            [Lu]
+    double *uhb = cb + lm;   // uhbar                   [Lu]
+    double *alb = uhb + lm;  // alphabar                [Lu]
+    double *m1b = alb + lm;  // m1bar                   [Lu]
+    double *bb = m1b + lm;   // bbar = m2bar            [Lv]
+    double *vhb = bb + lm;   // vhbar                   [Lv]
+    double *beb = vhb + lm;  // betabar                 [Lv]
     int *t1 = reinterpret_cast<int *>(beb + lm);
     int *s2 = t1 + lm;
     int *t3 = s2 + lm;
     const unsigned short *rec = reinterpret_cast<const unsigned short *>(p.rec + p.rec_off[e]);
-    float *g = p.gtab + ed.toff;
+    double *g = p.gtab + ed.toff;
 
     for (int s = tid; s < Lu; s += T) {
-        const float Au = p.adj_agg[ed.au + s];
-        const float Pu = p.adj_msg[ed.mu + s];
+        const double Au = p.adj_agg[ed.au + s];
+        const double Pu = p.adj_msg[ed.mu + s];
         cb[s] = Au + Pu;
         uhb[s] = Au;
         // recorded indices are < L for finite values; clamp so that no record
@@ -153,8 +157,8 @@ __global__ void __launch_bounds__(kThreads) bw_phase_kernel(BwParams p, const in
         t3[s] = min(static_cast<int>(rec[Lu + Lv + s]), Lv - 1);
     }
     for (int t = tid; t < Lv; t += T) {
-        const float Av = p.adj_agg[ed.av + t];
-        const float Pv = p.adj_msg[ed.mv + t];
+        const double Av = p.adj_agg[ed.av + t];
+        const double Pv = p.adj_msg[ed.mv + t];
         bb[t] = Av + Pv;
         vhb[t] = -Pv;
         s2[t] = min(static_cast<int>(rec[Lu + t]), Lu - 1);
@@ -162,7 +166,7 @@ __global__ void __launch_bounds__(kThreads) bw_phase_kernel(BwParams p, const in
     __syncthreads();
     // pass 3 reversed: c(s) = theta(s, t3(s)) + beta(t3(s)) + uh(s)
     for (int t = tid; t < Lv; t += T) {
-        float acc = 0.f;
+        double acc = 0.0;
         for (int s = 0; s < Lu; ++s)
             if (t3[s] == t) acc += cb[s];
         beb[t] = acc;
@@ -171,8 +175,8 @@ __global__ void __launch_bounds__(kThreads) bw_phase_kernel(BwParams p, const in
     __syncthreads();
     // beta = vh - b;  b = m2 + vh
     for (int t = tid; t < Lv; t += T) {
-        float v = vhb[t] + beb[t];
-        const float b = bb[t] - beb[t];
+        const double v = vhb[t] + beb[t];
+        const double b = bb[t] - beb[t];
         bb[t] = b;
         vhb[t] = v + b;
     }
@@ -180,7 +184,7 @@ __global__ void __launch_bounds__(kThreads) bw_phase_kernel(BwParams p, const in
     // pass 2 reversed: m2(t) = theta(s2(t), t) + alpha(s2(t))
     for (int t = tid; t < Lv; t += T) g[static_cast<long long>(s2[t]) * ed.ld + t] += bb[t];
     for (int s = tid; s < Lu; s += T) {
-        float acc = 0.f;
+        double acc = 0.0;
         for (int t = 0; t < Lv; ++t)
             if (s2[t] == s) acc += bb[t];
         alb[s] = acc;
@@ -188,15 +192,15 @@ __global__ void __launch_bounds__(kThreads) bw_phase_kernel(BwParams p, const in
     __syncthreads();
     // alpha = uh - a;  a = (m1 + uh) / 2
     for (int s = tid; s < Lu; s += T) {
-        const float ab = -alb[s];
-        uhb[s] = (uhb[s] + alb[s]) + 0.5f * ab;
-        m1b[s] = 0.5f * ab;
+        const double ab = -alb[s];
+        uhb[s] = (uhb[s] + alb[s]) + 0.5 * ab;
+        m1b[s] = 0.5 * ab;
     }
     __syncthreads();
     // pass 1 reversed: m1(s) = theta(s, t1(s)) + vh(t1(s))
     for (int s = tid; s < Lu; s += T) g[static_cast<long long>(s) * ed.ld + t1[s]] += m1b[s];
     for (int t = tid; t < Lv; t += T) {
-        float acc = 0.f;
+        double acc = 0.0;
         for (int s = 0; s < Lu; ++s)
             if (t1[s] == t) acc += m1b[s];
         vhb[t] += acc;
@@ -214,8 +218,8 @@ __global__ void __launch_bounds__(kThreads) bw_phase_kernel(BwParams p, const in
 }
 
 __global__ void unpack_grad_kernel(const EdgeDesc *edges, int n_edges, const NodeDesc *nodes, int n_nodes,
-                                   const long long *pair_base, const long long *unary_base, const float *gtab,
-                                   const float *adj_agg, float *grad_pair, float *grad_un)
+                                   const long long *pair_base, const long long *unary_base, const double *gtab,
+                                   const double *adj_agg, float *grad_pair, float *grad_un)
 {
     for (int e = blockIdx.x; e < n_edges; e += gridDim.x) {
         const EdgeDesc ed = edges[e];
@@ -224,21 +228,21 @@ __global__ void unpack_grad_kernel(const EdgeDesc *edges, int n_edges, const Nod
         for (long long i = threadIdx.x; i < n; i += blockDim.x) {
             const int s = static_cast<int>(i / ed.Lv);
             const int t = static_cast<int>(i - static_cast<long long>(s) * ed.Lv);
-            grad_pair[dst + i] = gtab[ed.toff + static_cast<long long>(s) * ed.ld + t];
+            grad_pair[dst + i] = static_cast<float>(gtab[ed.toff + static_cast<long long>(s) * ed.ld + t]);
         }
     }
     for (int u = blockIdx.x; u < n_nodes; u += gridDim.x) {
         const NodeDesc nd = nodes[u];
         for (int s = threadIdx.x; s < nd.L; s += blockDim.x)
-            grad_un[unary_base[nd.model] + nd.uoff + s] = adj_agg[nd.aoff + s];
+            grad_un[unary_base[nd.model] + nd.uoff + s] = static_cast<float>(adj_agg[nd.aoff + s]);
     }
 }
 
 }  // namespace
 
 cudaError_t launch_bw_init(const EdgeDesc *edges, int n_edges, const NodeDesc *nodes, int n_nodes, const float *tab,
-                           const float *agg, const float *msg, const float *dD, float *adj_agg, float *adj_msg,
-                           float *gtab, cudaStream_t st)
+                           const double *agg, const double *msg, const float *dD, double *adj_agg, double *adj_msg,
+                           double *gtab, cudaStream_t st)
 {
     if (n_nodes > 0) {
         bw_init_nodes_kernel<<<std::max(1, std::min(65535, (n_nodes + 7) / 8)), kThreads, 0, st>>>(nodes, n_nodes, agg,
@@ -257,7 +261,7 @@ cudaError_t launch_bw_init(const EdgeDesc *edges, int n_edges, const NodeDesc *n
 cudaError_t launch_bw_phase(const BwParams &p, const int *items, int n_items, cudaStream_t st)
 {
     if (n_items <= 0) return cudaSuccess;
-    const size_t smem = static_cast<size_t>(p.lmax) * 10 * 4;
+    const size_t smem = static_cast<size_t>(p.lmax) * (7 * sizeof(double) + 3 * sizeof(int));
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(bw_phase_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              static_cast<int>(smem));
@@ -268,8 +272,8 @@ cudaError_t launch_bw_phase(const BwParams &p, const int *items, int n_items, cu
 }
 
 cudaError_t launch_unpack_grad(const EdgeDesc *edges, int n_edges, const NodeDesc *nodes, int n_nodes,
-                               const long long *pair_base, const long long *unary_base, const float *gtab,
-                               const float *adj_agg, float *grad_pair, float *grad_un, cudaStream_t st)
+                               const long long *pair_base, const long long *unary_base, const double *gtab,
+                               const double *adj_agg, float *grad_pair, float *grad_un, cudaStream_t st)
 {
     const int grid = std::max(1, std::min(std::max(n_edges, n_nodes), 1 << 20));
     unpack_grad_kernel<<<grid, kThreads, 0, st>>>(edges, n_edges, nodes, n_nodes, pair_base, unary_base, gtab, adj_agg,
@@ -289,9 +293,9 @@ mplpp_status bfail(mplpp_solver *s, mplpp_status st, const std::string &m)
     return st;
 }
 
-#define BCK(call)                                                                                   \
-    do {                                                                                            \
-        cudaError_t e_ = (call);                                                                    \
+#define BCK(call)                                                                                          \
+    do {                                                                                                   \
+        cudaError_t e_ = (call);                                                                           \
         if (e_ != cudaSuccess) return bfail(s, MPLPP_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
     } while (0)
 
@@ -302,40 +306,19 @@ cudaError_t ensure(mplpp_solver *s, T **p, size_t count)
     return s->alloc(p, count);
 }
 
-}  // namespace
-
-// Runs `iterations` iterations, saving (agg, msg) every record_every
-// iterations (counted from the last reset) for the backward recompute.
-mplpp_status run_recorded(mplpp_solver *s, int iterations)
+// One FP64 iteration: every matching in schedule order.
+cudaError_t rec64_iteration(mplpp_solver *s, unsigned char *rec, int lmax)
 {
-    const int k = s->opt.record_every;
-    long long cur = s->iterations;
-    int left = iterations;
-    while (left > 0) {
-        if (cur % k == 0 && s->checkpoints_valid) {
-            const size_t j = static_cast<size_t>(cur / k);
-            while (s->ckpt.size() <= j) {
-                float *c = nullptr;
-                BCK(s->alloc(&c, static_cast<size_t>(s->aggN + s->msgN)));
-                s->ckpt.push_back(c);
-            }
-            BCK(cudaMemcpyAsync(s->ckpt[j], s->d_agg, sizeof(float) * s->aggN, cudaMemcpyDeviceToDevice, s->stream));
-            BCK(cudaMemcpyAsync(s->ckpt[j] + s->aggN, s->d_msg, sizeof(float) * s->msgN, cudaMemcpyDeviceToDevice,
-                                s->stream));
-        }
-        const int chunk = static_cast<int>(std::min<long long>(left, k - cur % k));
-        if (s->EE > 0) {
-            if (s->mode == MPLPP_MODE_PERSISTENT) {
-                BCK(enqueue_persistent(s, s->stream, chunk, nullptr, 0));
-            } else {
-                for (int i = 0; i < chunk; ++i) BCK(enqueue_looped_iteration(s, s->stream, nullptr));
-            }
-        }
-        cur += chunk;
-        left -= chunk;
+    for (int ph = 0; ph < s->P; ++ph) {
+        cudaError_t e = launch_rec64_phase(s->d_edges, s->d_phase_edges + s->phase_off[ph],
+                                           s->phase_off[ph + 1] - s->phase_off[ph], s->d_tab, s->d_agg64, s->d_msg64,
+                                           rec, s->d_rec_off, lmax, s->stream);
+        if (e != cudaSuccess) return e;
     }
-    return MPLPP_OK;
+    return cudaSuccess;
 }
+
+}  // namespace
 
 extern "C" mplpp_status mplpp_backward(mplpp_solver *s, const float *dD, float *grad_unary, float *grad_pairwise)
 {
@@ -343,10 +326,18 @@ extern "C" mplpp_status mplpp_backward(mplpp_solver *s, const float *dD, float *
     s->err.clear();
     const int k = s->opt.record_every;
     if (k <= 0) return bfail(s, MPLPP_E_STATE, "backward needs options.record_every > 0");
-    if (!s->checkpoints_valid) return bfail(s, MPLPP_E_STATE, "the state was loaded: no checkpoints to replay");
+    if (!s->history_valid)
+        return bfail(s, MPLPP_E_STATE, "the state was loaded: the iterations since phi = 0 are unknown");
     const long long Ttot = s->iterations;
     const int nm = static_cast<int>(s->models.size());
     cudaStream_t st = s->stream;
+    int lmax = 1;
+    for (auto &nd : s->h_nodes) lmax = std::max(lmax, nd.L);
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->device);
+    if (rec64_smem_bytes(lmax) > static_cast<size_t>(optin) ||
+        static_cast<size_t>(lmax) * (7 * sizeof(double) + 3 * sizeof(int)) > static_cast<size_t>(optin))
+        return bfail(s, MPLPP_E_UNSUPPORTED, "backward supports at most ~2700 labels per node");
 
     // buffers
     if (!s->d_rec_off) {
@@ -360,15 +351,8 @@ extern "C" mplpp_status mplpp_backward(mplpp_solver *s, const float *dD, float *
         s->rec_stride = std::max(4LL, acc);
         BCK(s->alloc(&s->d_rec_off, std::max(1, s->EE)));
         BCK(cudaMemcpyAsync(s->d_rec_off, off.data(), sizeof(long long) * s->EE, cudaMemcpyHostToDevice, st));
+        BCK(cudaStreamSynchronize(st));
     }
-    BCK(ensure(s, &s->d_agg_w, s->aggN));
-    BCK(ensure(s, &s->d_msg_w, s->msgN));
-    BCK(ensure(s, &s->d_adj_agg, s->aggN));
-    BCK(ensure(s, &s->d_adj_msg, s->msgN));
-    BCK(ensure(s, &s->d_gtab, s->tabN));
-    BCK(ensure(s, &s->d_rec, static_cast<size_t>(s->rec_stride) * k));
-    BCK(ensure(s, &s->d_dD, nm));
-    float *d_gu = nullptr, *d_gp = nullptr;
     if (!s->d_pbase) {
         std::vector<long long> pb(nm), ub(nm);
         long long a = 0, b = 0;
@@ -382,69 +366,83 @@ extern "C" mplpp_status mplpp_backward(mplpp_solver *s, const float *dD, float *
         BCK(s->alloc(&s->d_ubase, nm));
         BCK(cudaMemcpyAsync(s->d_pbase, pb.data(), sizeof(long long) * nm, cudaMemcpyHostToDevice, st));
         BCK(cudaMemcpyAsync(s->d_ubase, ub.data(), sizeof(long long) * nm, cudaMemcpyHostToDevice, st));
+        BCK(cudaStreamSynchronize(st));
+    }
+    BCK(ensure(s, &s->d_agg64, s->aggN));
+    BCK(ensure(s, &s->d_msg64, s->msgN));
+    BCK(ensure(s, &s->d_adj_agg, s->aggN));
+    BCK(ensure(s, &s->d_adj_msg, s->msgN));
+    BCK(ensure(s, &s->d_gtab, s->tabN));
+    BCK(ensure(s, &s->d_rec, static_cast<size_t>(s->rec_stride) * k));
+    BCK(ensure(s, &s->d_dD, nm));
+    const long long nseg = (Ttot + k - 1) / k;
+    while (static_cast<long long>(s->ckpt64.size()) < nseg) {
+        double *c = nullptr;
+        BCK(s->alloc(&c, static_cast<size_t>(s->aggN + s->msgN)));
+        s->ckpt64.push_back(c);
+    }
+
+    // FP64 replay from phi = 0, checkpoint every k iterations
+    BCK(launch_widen(s->d_un0, s->d_agg64, s->aggN, st));
+    BCK(cudaMemsetAsync(s->d_msg64, 0, sizeof(double) * s->msgN, st));
+    for (long long it = 0; it < Ttot; ++it) {
+        if (it % k == 0) {
+            double *c = s->ckpt64[it / k];
+            BCK(cudaMemcpyAsync(c, s->d_agg64, sizeof(double) * s->aggN, cudaMemcpyDeviceToDevice, st));
+            BCK(cudaMemcpyAsync(c + s->aggN, s->d_msg64, sizeof(double) * s->msgN, cudaMemcpyDeviceToDevice, st));
+        }
+        BCK(rec64_iteration(s, nullptr, lmax));
     }
     BCK(cudaMemcpyAsync(s->d_dD, dD, sizeof(float) * nm, cudaMemcpyHostToDevice, st));
-    BCK(cudaMemsetAsync(s->d_adj_agg, 0, sizeof(float) * s->aggN, st));
-    BCK(cudaMemsetAsync(s->d_adj_msg, 0, sizeof(float) * s->msgN, st));
-    BCK(cudaMemsetAsync(s->d_gtab, 0, sizeof(float) * s->tabN, st));
-    BCK(launch_bw_init(s->d_edges, s->EE, s->d_nodes, s->N, s->d_tab, s->d_agg, s->d_msg, s->d_dD, s->d_adj_agg,
+    BCK(cudaMemsetAsync(s->d_adj_agg, 0, sizeof(double) * s->aggN, st));
+    BCK(cudaMemsetAsync(s->d_adj_msg, 0, sizeof(double) * s->msgN, st));
+    BCK(cudaMemsetAsync(s->d_gtab, 0, sizeof(double) * s->tabN, st));
+    BCK(launch_bw_init(s->d_edges, s->EE, s->d_nodes, s->N, s->d_tab, s->d_agg64, s->d_msg64, s->d_dD, s->d_adj_agg,
                        s->d_adj_msg, s->d_gtab, st));
 
-    int lmax = 1;
-    for (auto &nd : s->h_nodes) lmax = std::max(lmax, nd.L);
     BwParams bp = {};
     bp.edges = s->d_edges;
-    bp.nodes = s->d_nodes;
-    bp.tab = s->d_tab;
     bp.rec_off = s->d_rec_off;
     bp.adj_agg = s->d_adj_agg;
     bp.adj_msg = s->d_adj_msg;
     bp.gtab = s->d_gtab;
     bp.lmax = lmax;
-
-    // swap the working state in for the recompute
-    float *agg_keep = s->d_agg, *msg_keep = s->d_msg;
-    const long long nseg = (Ttot + k - 1) / k;
-    mplpp_status status = MPLPP_OK;
-    for (long long j = nseg - 1; j >= 0 && status == MPLPP_OK; --j) {
+    for (long long j = nseg - 1; j >= 0; --j) {
         const int len = static_cast<int>(std::min<long long>(k, Ttot - j * k));
-        cudaError_t e = cudaMemcpyAsync(s->d_agg_w, s->ckpt[j], sizeof(float) * s->aggN, cudaMemcpyDeviceToDevice, st);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(s->d_msg_w, s->ckpt[j] + s->aggN, sizeof(float) * s->msgN, cudaMemcpyDeviceToDevice, st);
-        s->d_agg = s->d_agg_w;
-        s->d_msg = s->d_msg_w;
-        for (int i = 0; i < len && e == cudaSuccess; ++i)
-            e = enqueue_looped_iteration(s, st, s->d_rec + static_cast<long long>(i) * s->rec_stride);
-        s->d_agg = agg_keep;
-        s->d_msg = msg_keep;
-        for (int i = len - 1; i >= 0 && e == cudaSuccess; --i) {
+        BCK(cudaMemcpyAsync(s->d_agg64, s->ckpt64[j], sizeof(double) * s->aggN, cudaMemcpyDeviceToDevice, st));
+        BCK(cudaMemcpyAsync(s->d_msg64, s->ckpt64[j] + s->aggN, sizeof(double) * s->msgN, cudaMemcpyDeviceToDevice,
+                            st));
+        for (int i = 0; i < len; ++i)
+            BCK(rec64_iteration(s, s->d_rec + static_cast<long long>(i) * s->rec_stride, lmax));
+        for (int i = len - 1; i >= 0; --i) {
             bp.rec = s->d_rec + static_cast<long long>(i) * s->rec_stride;
-            for (int ph = s->P - 1; ph >= 0 && e == cudaSuccess; --ph)
-                e = launch_bw_phase(bp, s->d_phase_edges + s->phase_off[ph], s->phase_off[ph + 1] - s->phase_off[ph],
-                                    st);
+            for (int ph = s->P - 1; ph >= 0; --ph)
+                BCK(launch_bw_phase(bp, s->d_phase_edges + s->phase_off[ph], s->phase_off[ph + 1] - s->phase_off[ph],
+                                    st));
         }
-        if (e != cudaSuccess) status = bfail(s, MPLPP_E_CUDA, std::string("backward: ") + cudaGetErrorString(e));
     }
-    if (status == MPLPP_OK) {
-        float *gu = grad_unary, *gp = grad_pairwise;
-        if (!s->opt.inputs_on_device) {
-            BCK(cudaMalloc(&d_gu, sizeof(float) * std::max(1LL, s->sum_unary)));
-            BCK(cudaMalloc(&d_gp, sizeof(float) * std::max(1LL, s->sum_pair)));
-            gu = d_gu;
-            gp = d_gp;
+    float *d_gu = nullptr, *d_gp = nullptr;
+    float *gu = grad_unary, *gp = grad_pairwise;
+    if (!s->opt.inputs_on_device) {
+        BCK(cudaMalloc(&d_gu, sizeof(float) * std::max(1LL, s->sum_unary)));
+        cudaError_t e = cudaMalloc(&d_gp, sizeof(float) * std::max(1LL, s->sum_pair));
+        if (e != cudaSuccess) {
+            cudaFree(d_gu);
+            return bfail(s, MPLPP_E_CUDA, std::string("cudaMalloc: ") + cudaGetErrorString(e));
         }
-        cudaError_t e = launch_unpack_grad(s->d_edges, s->EE, s->d_nodes, s->N, s->d_pbase, s->d_ubase, s->d_gtab,
-                                           s->d_adj_agg, gp, gu, st);
-        if (e == cudaSuccess && !s->opt.inputs_on_device) {
-            e = cudaMemcpyAsync(grad_unary, d_gu, sizeof(float) * s->sum_unary, cudaMemcpyDeviceToHost, st);
-            if (e == cudaSuccess && s->sum_pair)
-                e = cudaMemcpyAsync(grad_pairwise, d_gp, sizeof(float) * s->sum_pair, cudaMemcpyDeviceToHost, st);
-        }
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) status = bfail(s, MPLPP_E_CUDA, std::string("backward: ") + cudaGetErrorString(e));
+        gu = d_gu;
+        gp = d_gp;
     }
+    cudaError_t e = launch_unpack_grad(s->d_edges, s->EE, s->d_nodes, s->N, s->d_pbase, s->d_ubase, s->d_gtab,
+                                       s->d_adj_agg, gp, gu, st);
+    if (e == cudaSuccess && !s->opt.inputs_on_device) {
+        e = cudaMemcpyAsync(grad_unary, d_gu, sizeof(float) * s->sum_unary, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && s->sum_pair)
+            e = cudaMemcpyAsync(grad_pairwise, d_gp, sizeof(float) * s->sum_pair, cudaMemcpyDeviceToHost, st);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (d_gu) cudaFree(d_gu);
     if (d_gp) cudaFree(d_gp);
-    if (status == MPLPP_OK) status = mplpp_sync(s);
-    return status;
+    if (e != cudaSuccess) return bfail(s, MPLPP_E_CUDA, std::string("backward: ") + cudaGetErrorString(e));
+    return mplpp_sync(s);
 }

@@ -1,4 +1,4 @@
-// handshake.cu -- the MPLP++ Handshake edge update on sm_103a.
+// handshake.cu -- the MPLP++ Handshake edge update on sm_103a (FP32 hot path).
 //
 // One update of edge uv (Sec. 4, eq. (H), three-minimization form) on the
 // message-form state of common.cuh:
@@ -26,8 +26,10 @@
 //               list of edges in schedule order and waits, per edge, only for
 //               the earlier updates of its two end nodes (per-node completion
 //               counters), while the next edge's table is already streaming
-//               into the second buffer.  Waits are bounded: past spin_limit
-//               polls the kernel records ERR_TIMEOUT and drains without waiting.
+//               into the second buffer.  Node v's new vector is published as
+//               soon as pass 2 has produced it, before pass 3.  Waits are
+//               bounded: past spin_limit polls the kernel records ERR_TIMEOUT
+//               and drains without waiting.
 #include <cfloat>
 #include <cstdint>
 
@@ -41,9 +43,7 @@ struct Smem {
     float *tile[2];
     float *uh, *alpha, *vh, *beta, *bv, *pm;
     float4 *part;
-    int *pmi;           // REC: column argmin (row index) per column
-    int4 *parti;        // REC: partial column argmins
-    uint64_t *bar;      // [2]
+    uint64_t *bar;  // [2]
 };
 
 __device__ __forceinline__ Smem carve(char *base, const HsParams &p, int nbuf)
@@ -65,13 +65,11 @@ __device__ __forceinline__ Smem carve(char *base, const HsParams &p, int nbuf)
     s.bv = f; f += p.ldmax;
     s.pm = f; f += p.ldmax;
     s.part = reinterpret_cast<float4 *>(f); f += 4 * blockDim.x;
-    s.pmi = reinterpret_cast<int *>(f); f += p.ldmax;
-    s.parti = reinterpret_cast<int4 *>(f); f += 4 * blockDim.x;
     s.bar = reinterpret_cast<uint64_t *>(f);
     return s;
 }
 
-// Rows per group for the row minima: a power of two <= 32 giving each lane
+// Lanes per row for the row minima: a power of two <= 32 giving each lane
 // about two float4 chunks of a row.
 __device__ __forceinline__ int row_group(int Q)
 {
@@ -108,55 +106,30 @@ __device__ __forceinline__ void set_err(int *err, int code)
     atomicCAS(err, 0, code);
 }
 
-// (value, index) minimum with the lower index winning ties.
-__device__ __forceinline__ void amin(float &m, int &i, float v, int j)
+// Thread 0, after a __syncthreads that follows the CTA's global writes:
+// make them visible at GPU scope, then count `n` arrivals on node g.
+__device__ __forceinline__ void signal_node(unsigned *ver, int g, unsigned n)
 {
-    if (v < m || (v == m && j < i)) {
-        m = v;
-        i = j;
-    }
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+    asm volatile("red.relaxed.gpu.global.add.u32 [%0], %1;" ::"l"(ver + g), "r"(n) : "memory");
 }
 
-// Minimum over a row slice of a float4 row against a float4 vector; REC also
-// tracks the lowest column attaining it.
-template <bool REC>
-__device__ __forceinline__ void row_scan(const float4 *row, const float4 *w, int Q, int lg, int G, float &m, int &mi)
+__device__ __forceinline__ void row_scan(const float4 *row, const float4 *w, int Q, int lg, int G, float &m)
 {
-    for (int q = lg; q < Q; q += G) {
-        const float4 x = row[q];
-        const float4 y = w[q];
-        if (REC) {
-            const float v0 = x.x + y.x, v1 = x.y + y.y, v2 = x.z + y.z, v3 = x.w + y.w;
-            if (v0 < m) { m = v0; mi = 4 * q; }
-            if (v1 < m) { m = v1; mi = 4 * q + 1; }
-            if (v2 < m) { m = v2; mi = 4 * q + 2; }
-            if (v3 < m) { m = v3; mi = 4 * q + 3; }
-        } else {
-            m = fminf(m, hmin_add(x, y));
-        }
-    }
+    for (int q = lg; q < Q; q += G) m = fminf(m, hmin_add(row[q], w[q]));
 }
 
-template <bool REC>
-__device__ __forceinline__ void group_reduce(float &m, int &mi, int G)
+__device__ __forceinline__ void group_min(float &m, int G)
 {
-    for (int o = G >> 1; o > 0; o >>= 1) {
-        const float om = __shfl_xor_sync(0xffffffffu, m, o);
-        if (REC) {
-            const int oi = __shfl_xor_sync(0xffffffffu, mi, o);
-            amin(m, mi, om, oi);
-        } else {
-            m = fminf(m, om);
-        }
-    }
+    for (int o = G >> 1; o > 0; o >>= 1) m = fminf(m, __shfl_xor_sync(0xffffffffu, m, o));
 }
 
 // One Handshake update of edge ed by this CTA (its row slice); the table slice
 // is (or will be) in `tile`, signalled by `bar` completing phase `parity`.
-// Returns false if the table wait timed out.
-template <bool CLUSTER, bool REC>
+// SIGNAL: publish completion on the node counters (persistent driver).
+template <bool CLUSTER, bool SIGNAL>
 __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile, const Smem &sm, int rank,
-                        uint64_t *bar, uint32_t parity, unsigned char *rec)
+                        uint64_t *bar, uint32_t parity)
 {
     const int T = blockDim.x, tid = threadIdx.x;
     const int C = CLUSTER ? p.C : 1;
@@ -179,27 +152,18 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
     const int G = row_group(Q);
     const int gid = tid / G, lg = tid % G, ng = T / G;
 
-    unsigned short *rt1 = nullptr, *rs2 = nullptr, *rt3 = nullptr;
-    if (REC) {
-        rt1 = reinterpret_cast<unsigned short *>(rec);
-        rs2 = rt1 + ed.Lu;
-        rt3 = rs2 + ed.Lv;
-    }
-
     // pass 1: a(s) = 1/2 (min_t [theta(s,t) + vh(t)] + uh(s));  alpha = uh - a
     {
         const float4 *w = reinterpret_cast<const float4 *>(sm.vh);
         for (int base = 0; base < nr; base += ng) {
             const int s = base + gid;
             float m = INFINITY;
-            int mi = 0x7fffffff;
-            if (s < nr) row_scan<REC>(t4 + static_cast<size_t>(s) * Q, w, Q, lg, G, m, mi);
-            group_reduce<REC>(m, mi, G);
+            if (s < nr) row_scan(t4 + static_cast<size_t>(s) * Q, w, Q, lg, G, m);
+            group_min(m, G);
             if (s < nr && lg == 0) {
                 const float u = sm.uh[s];
                 const float a = 0.5f * (m + u);
                 sm.alpha[s] = u - a;
-                if (REC) rt1[r0 + s] = static_cast<unsigned short>(mi);
             }
         }
     }
@@ -208,72 +172,26 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
     // pass 2 (this CTA's rows): pm(t) = min_s [theta(s,t) + alpha(s)]
     {
         float4 *pm4 = reinterpret_cast<float4 *>(sm.pm);
-        int nsub = T / Q;
+        const int nsub = T / Q;
         if (nsub >= 1) {
             if (tid < nsub * Q) {
                 const int q = tid % Q, sub = tid / Q;
                 float4 m = make_float4(INFINITY, INFINITY, INFINITY, INFINITY);
-                int4 mi = make_int4(0x7fffffff, 0x7fffffff, 0x7fffffff, 0x7fffffff);
-                for (int s = sub; s < nr; s += nsub) {
-                    const float4 v = add4s(t4[static_cast<size_t>(s) * Q + q], sm.alpha[s]);
-                    if (REC) {
-                        if (v.x < m.x) { m.x = v.x; mi.x = s; }
-                        if (v.y < m.y) { m.y = v.y; mi.y = s; }
-                        if (v.z < m.z) { m.z = v.z; mi.z = s; }
-                        if (v.w < m.w) { m.w = v.w; mi.w = s; }
-                    } else {
-                        m = min4(m, v);
-                    }
-                }
+                for (int s = sub; s < nr; s += nsub)
+                    m = min4(m, add4s(t4[static_cast<size_t>(s) * Q + q], sm.alpha[s]));
                 sm.part[sub * Q + q] = m;
-                if (REC) sm.parti[sub * Q + q] = mi;
             }
             __syncthreads();
             for (int q = tid; q < Q; q += T) {
                 float4 m = sm.part[q];
-                int4 mi = REC ? sm.parti[q] : make_int4(0, 0, 0, 0);
-                for (int j = 1; j < nsub; ++j) {
-                    const float4 o = sm.part[j * Q + q];
-                    if (REC) {
-                        const int4 oi = sm.parti[j * Q + q];
-                        amin(m.x, mi.x, o.x, oi.x);
-                        amin(m.y, mi.y, o.y, oi.y);
-                        amin(m.z, mi.z, o.z, oi.z);
-                        amin(m.w, mi.w, o.w, oi.w);
-                    } else {
-                        m = min4(m, o);
-                    }
-                }
+                for (int j = 1; j < nsub; ++j) m = min4(m, sm.part[j * Q + q]);
                 pm4[q] = m;
-                if (REC) {
-                    sm.pmi[4 * q + 0] = mi.x + r0;
-                    sm.pmi[4 * q + 1] = mi.y + r0;
-                    sm.pmi[4 * q + 2] = mi.z + r0;
-                    sm.pmi[4 * q + 3] = mi.w + r0;
-                }
             }
         } else {
             for (int q = tid; q < Q; q += T) {
                 float4 m = make_float4(INFINITY, INFINITY, INFINITY, INFINITY);
-                int4 mi = make_int4(0x7fffffff, 0x7fffffff, 0x7fffffff, 0x7fffffff);
-                for (int s = 0; s < nr; ++s) {
-                    const float4 v = add4s(t4[static_cast<size_t>(s) * Q + q], sm.alpha[s]);
-                    if (REC) {
-                        if (v.x < m.x) { m.x = v.x; mi.x = s; }
-                        if (v.y < m.y) { m.y = v.y; mi.y = s; }
-                        if (v.z < m.z) { m.z = v.z; mi.z = s; }
-                        if (v.w < m.w) { m.w = v.w; mi.w = s; }
-                    } else {
-                        m = min4(m, v);
-                    }
-                }
+                for (int s = 0; s < nr; ++s) m = min4(m, add4s(t4[static_cast<size_t>(s) * Q + q], sm.alpha[s]));
                 pm4[q] = m;
-                if (REC) {
-                    sm.pmi[4 * q + 0] = mi.x + r0;
-                    sm.pmi[4 * q + 1] = mi.y + r0;
-                    sm.pmi[4 * q + 2] = mi.z + r0;
-                    sm.pmi[4 * q + 3] = mi.w + r0;
-                }
             }
         }
     }
@@ -284,42 +202,17 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
         cluster_arrive_release();
         cluster_wait_acquire();
         const uint32_t pm_addr = smem_u32(sm.pm);
-        const uint32_t pmi_addr = smem_u32(sm.pmi);
         for (int q = tid; q < Q; q += T) {
             float4 m = ld_dsmem_f4(mapa_shared(pm_addr + 16u * q, 0));
-            int mi[4] = {0, 0, 0, 0};
-            if (REC) {
-                for (int j = 0; j < 4; ++j) {
-                    uint32_t a = mapa_shared(pmi_addr + 4u * (4 * q + j), 0);
-                    asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(mi[j]) : "r"(a) : "memory");
-                }
-            }
-            for (int r = 1; r < C; ++r) {
-                const float4 o = ld_dsmem_f4(mapa_shared(pm_addr + 16u * q, r));
-                if (REC) {
-                    // ranks hold increasing rows: on equal values keep the lower rank
-                    float om[4] = {o.x, o.y, o.z, o.w};
-                    float cm[4] = {m.x, m.y, m.z, m.w};
-                    for (int j = 0; j < 4; ++j) {
-                        if (om[j] < cm[j]) {
-                            cm[j] = om[j];
-                            uint32_t a = mapa_shared(pmi_addr + 4u * (4 * q + j), r);
-                            asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(mi[j]) : "r"(a) : "memory");
-                        }
-                    }
-                    m = make_float4(cm[0], cm[1], cm[2], cm[3]);
-                } else {
-                    m = min4(m, o);
-                }
-            }
+            for (int r = 1; r < C; ++r) m = min4(m, ld_dsmem_f4(mapa_shared(pm_addr + 16u * q, r)));
             const float mm[4] = {m.x, m.y, m.z, m.w};
+#pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const int t = 4 * q + j;
                 const float vh = sm.vh[t];
                 const float b = mm[j] + vh;
                 sm.bv[t] = t < Lv ? b : 0.f;
                 sm.beta[t] = t < Lv ? vh - b : 0.f;
-                if (REC && t < Lv && rank == 0) rs2[t] = static_cast<unsigned short>(mi[j]);
             }
         }
         cluster_arrive_relaxed();
@@ -330,10 +223,22 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
             const float b = sm.pm[t] + vh;
             sm.bv[t] = t < Lv ? b : 0.f;
             sm.beta[t] = t < Lv ? vh - b : 0.f;
-            if (REC && t < Lv) rs2[t] = static_cast<unsigned short>(sm.pmi[t]);
         }
     }
     __syncthreads();
+
+    // node v's new vector (one CTA of the cluster), published before pass 3
+    if (rank == 0) {
+        for (int t = tid; t < Lv; t += T) {
+            const float b = sm.bv[t];
+            __stcg(agg + ed.av + t, b);
+            __stcg(msg + ed.mv + t, b - sm.vh[t]);
+        }
+        if (SIGNAL) {
+            __syncthreads();
+            if (tid == 0) signal_node(p.ver, ed.gv, static_cast<unsigned>(C));
+        }
+    }
 
     // pass 3: c(s) = min_t [theta(s,t) + beta(t)] + uh(s); write node u's rows
     {
@@ -341,47 +246,36 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
         for (int base = 0; base < nr; base += ng) {
             const int s = base + gid;
             float m = INFINITY;
-            int mi = 0x7fffffff;
-            if (s < nr) row_scan<REC>(t4 + static_cast<size_t>(s) * Q, w, Q, lg, G, m, mi);
-            group_reduce<REC>(m, mi, G);
+            if (s < nr) row_scan(t4 + static_cast<size_t>(s) * Q, w, Q, lg, G, m);
+            group_min(m, G);
             if (s < nr && lg == 0) {
                 const float u = sm.uh[s];
                 const float c = m + u;
                 __stcg(agg + ed.au + r0 + s, c);
                 __stcg(msg + ed.mu + r0 + s, c - u);
-                if (REC) rt3[r0 + s] = static_cast<unsigned short>(mi);
             }
-        }
-    }
-    // node v's vector (one CTA of the cluster)
-    if (rank == 0) {
-        for (int t = tid; t < Lv; t += T) {
-            const float b = sm.bv[t];
-            __stcg(agg + ed.av + t, b);
-            __stcg(msg + ed.mv + t, b - sm.vh[t]);
         }
     }
     if (CLUSTER) cluster_wait_acquire();  // every CTA has finished reading this CTA's pm
     __syncthreads();
+    if (SIGNAL && tid == 0) signal_node(p.ver, ed.gu, 1u);
 }
 
-template <bool CLUSTER, bool REC>
+template <bool CLUSTER>
 __global__ void __launch_bounds__(512) hs_looped_kernel(HsParams p)
 {
     extern __shared__ __align__(16) char smem_raw[];
     Smem sm = carve(smem_raw, p, 1);
     const int C = CLUSTER ? p.C : 1;
     const int rank = CLUSTER ? static_cast<int>(cluster_ctarank()) : 0;
-    const int e = p.items[blockIdx.x / C];
-    const EdgeDesc ed = p.edges[e];
+    const EdgeDesc ed = p.edges[p.items[blockIdx.x / C]];
     if (threadIdx.x == 0) {
         mbar_init(&sm.bar[0], 1);
         fence_mbar_init();
     }
     __syncthreads();
     if (threadIdx.x == 0) issue_tile(ed, rank, C, p.tab, sm.tile[0], &sm.bar[0]);
-    unsigned char *rec = REC ? p.rec + p.rec_off[e] : nullptr;
-    hs_item<CLUSTER, REC>(p, ed, sm.tile[0], sm, rank, &sm.bar[0], 0u, rec);
+    hs_item<CLUSTER, false>(p, ed, sm.tile[0], sm, rank, &sm.bar[0], 0u);
 }
 
 __device__ __forceinline__ void wait_nodes(const HsParams &p, int gu, unsigned need_u, int gv, unsigned need_v)
@@ -400,7 +294,7 @@ __device__ __forceinline__ void wait_nodes(const HsParams &p, int gu, unsigned n
     }
 }
 
-template <bool CLUSTER, bool REC>
+template <bool CLUSTER>
 __global__ void __launch_bounds__(512) hs_persistent_kernel(HsParams p)
 {
     extern __shared__ __align__(16) char smem_raw[];
@@ -438,14 +332,8 @@ __global__ void __launch_bounds__(512) hs_persistent_kernel(HsParams p)
             wait_nodes(p, ed.gu, need_u, ed.gv, need_v);
         }
         __syncthreads();
-        unsigned char *rec = REC ? p.rec + it * p.rec_stride + p.rec_off[w.edge] : nullptr;
-        hs_item<CLUSTER, REC>(p, ed, sm.tile[k & 1], sm, rank, &sm.bar[k & 1],
-                              static_cast<uint32_t>((k >> 1) & 1), rec);
-        if (threadIdx.x == 0) {
-            __threadfence();
-            atomicAdd(p.ver + ed.gu, 1u);
-            atomicAdd(p.ver + ed.gv, 1u);
-        }
+        hs_item<CLUSTER, true>(p, ed, sm.tile[k & 1], sm, rank, &sm.bar[k & 1],
+                               static_cast<uint32_t>((k >> 1) & 1));
         if (++i == n) {
             i = 0;
             ++it;
@@ -488,46 +376,34 @@ cudaError_t launch(K kernel, const HsParams &p, int grid, int threads, size_t sm
 
 size_t hs_smem_bytes(int nbuf, int tile_floats, int rmax, int ldmax, int threads)
 {
-    // tiles, uh, alpha, vh, beta, bv, pm, part(float4 x T), pmi, parti(int4 x T), 2 mbarriers
+    // tiles, uh, alpha, vh, beta, bv, pm, part (float4 x T), 2 mbarriers
     size_t f = static_cast<size_t>(nbuf) * tile_floats + 2 * static_cast<size_t>(rmax) +
-               5 * static_cast<size_t>(ldmax) + 8 * static_cast<size_t>(threads);
+               4 * static_cast<size_t>(ldmax) + 4 * static_cast<size_t>(threads);
     return f * 4 + 16;
 }
 
 cudaError_t hs_prepare(size_t smem)
 {
     cudaError_t e;
-    if ((e = set_attrs(hs_looped_kernel<false, false>, smem)) != cudaSuccess) return e;
-    if ((e = set_attrs(hs_looped_kernel<true, false>, smem)) != cudaSuccess) return e;
-    if ((e = set_attrs(hs_looped_kernel<false, true>, smem)) != cudaSuccess) return e;
-    if ((e = set_attrs(hs_looped_kernel<true, true>, smem)) != cudaSuccess) return e;
-    if ((e = set_attrs(hs_persistent_kernel<false, false>, smem)) != cudaSuccess) return e;
-    if ((e = set_attrs(hs_persistent_kernel<true, false>, smem)) != cudaSuccess) return e;
-    if ((e = set_attrs(hs_persistent_kernel<false, true>, smem)) != cudaSuccess) return e;
-    return set_attrs(hs_persistent_kernel<true, true>, smem);
+    if ((e = set_attrs(hs_looped_kernel<false>, smem)) != cudaSuccess) return e;
+    if ((e = set_attrs(hs_looped_kernel<true>, smem)) != cudaSuccess) return e;
+    if ((e = set_attrs(hs_persistent_kernel<false>, smem)) != cudaSuccess) return e;
+    return set_attrs(hs_persistent_kernel<true>, smem);
 }
 
 cudaError_t hs_launch_looped(const HsParams &p, int n_items, int threads, size_t smem, cudaStream_t st)
 {
     if (n_items <= 0) return cudaSuccess;
     const int grid = n_items * p.C;
-    if (p.rec) {
-        return p.C > 1 ? launch(hs_looped_kernel<true, true>, p, grid, threads, smem, p.C, st)
-                       : launch(hs_looped_kernel<false, true>, p, grid, threads, smem, 1, st);
-    }
-    return p.C > 1 ? launch(hs_looped_kernel<true, false>, p, grid, threads, smem, p.C, st)
-                   : launch(hs_looped_kernel<false, false>, p, grid, threads, smem, 1, st);
+    return p.C > 1 ? launch(hs_looped_kernel<true>, p, grid, threads, smem, p.C, st)
+                   : launch(hs_looped_kernel<false>, p, grid, threads, smem, 1, st);
 }
 
 cudaError_t hs_launch_persistent(const HsParams &p, int clusters, int threads, size_t smem, cudaStream_t st)
 {
     const int grid = clusters * p.C;
-    if (p.rec) {
-        return p.C > 1 ? launch(hs_persistent_kernel<true, true>, p, grid, threads, smem, p.C, st)
-                       : launch(hs_persistent_kernel<false, true>, p, grid, threads, smem, 1, st);
-    }
-    return p.C > 1 ? launch(hs_persistent_kernel<true, false>, p, grid, threads, smem, p.C, st)
-                   : launch(hs_persistent_kernel<false, false>, p, grid, threads, smem, 1, st);
+    return p.C > 1 ? launch(hs_persistent_kernel<true>, p, grid, threads, smem, p.C, st)
+                   : launch(hs_persistent_kernel<false>, p, grid, threads, smem, 1, st);
 }
 
 int hs_max_active_clusters(int C, int threads, size_t smem)
@@ -535,8 +411,8 @@ int hs_max_active_clusters(int C, int threads, size_t smem)
     if (hs_prepare(smem) != cudaSuccess) return 0;
     if (C <= 1) {
         int per_sm = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hs_persistent_kernel<false, false>, threads,
-                                                          smem) != cudaSuccess)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hs_persistent_kernel<false>, threads, smem) !=
+            cudaSuccess)
             return 0;
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
@@ -555,7 +431,7 @@ int hs_max_active_clusters(int C, int threads, size_t smem)
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, hs_persistent_kernel<true, false>, &cfg) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveClusters(&n, hs_persistent_kernel<true>, &cfg) != cudaSuccess) return 0;
     return n;
 }
 

@@ -19,9 +19,6 @@ struct HsParams {
     const WorkItem *work;    // persistent: per-cluster item lists (one iteration)
     unsigned *ver;           // persistent: per-node completion counters
     int *err;                // device error word (ERR_*)
-    unsigned char *rec;      // backward recording: argmin bytes, or null
-    const long long *rec_off;// per edge: byte offset of its record within one iteration
-    long long rec_stride;    // bytes of one iteration's records
     long long spin_limit;    // polls before a wait gives up
     int iterations;          // persistent: iterations to run
     int test_wait;           // testing: first item of worker 0 waits for an update that never comes

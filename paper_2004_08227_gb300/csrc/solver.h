@@ -64,14 +64,14 @@ struct mplpp_solver {
     double *d_out = nullptr, *d_energy = nullptr;
     int *d_labels = nullptr;
 
-    // record / backward
+    // backward: FP64 replay buffers (allocated on first use)
     long long *d_rec_off = nullptr;
     long long rec_stride = 0;
-    std::vector<float *> ckpt;       // device copies of (agg, msg) every record_every iterations
-    bool checkpoints_valid = true;   // false after load_state
-    float *d_agg_w = nullptr, *d_msg_w = nullptr;        // recompute buffers
-    float *d_adj_agg = nullptr, *d_adj_msg = nullptr, *d_gtab = nullptr;
-    unsigned char *d_rec = nullptr;  // records of one segment
+    std::vector<double *> ckpt64;    // FP64 (agg, msg) every record_every iterations of the replay
+    bool history_valid = true;       // the state is T iterations from phi = 0 (false after load_state)
+    double *d_agg64 = nullptr, *d_msg64 = nullptr;
+    double *d_adj_agg = nullptr, *d_adj_msg = nullptr, *d_gtab = nullptr;
+    unsigned char *d_rec = nullptr;  // argmin records of one segment
     float *d_dD = nullptr;
     long long *d_pbase = nullptr, *d_ubase = nullptr;  // per-model offsets of the caller's layouts
 
@@ -93,7 +93,5 @@ cudaError_t mplpp_solver::alloc(Ty **p, size_t count)
 }
 
 // api.cu
-cudaError_t enqueue_looped_iteration(mplpp_solver *s, cudaStream_t st, unsigned char *rec);
-cudaError_t enqueue_persistent(mplpp_solver *s, cudaStream_t st, int iterations, unsigned char *rec,
-                               long long rec_stride);
-mplpp_status run_plain(mplpp_solver *s, int iterations);
+cudaError_t enqueue_looped_iteration(mplpp_solver *s, cudaStream_t st);
+cudaError_t enqueue_persistent(mplpp_solver *s, cudaStream_t st, int iterations);

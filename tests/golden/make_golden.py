@@ -1,0 +1,90 @@
+"""Writes the full-size expected values used by the GPU tests.
+
+Calls only the FP64 oracle (oracle/) on the seeded workloads of
+paper_2004_08227_gb300.workloads: for each workload shape, the dual bound
+after the full iteration count, the rounded labeling and its energy; for the
+differentiation shape also central finite differences (h = 1e-4) of D_T at
+sampled entries.  The oracle is plain IEEE double C built without FP
+contraction, so the values do not depend on the machine that writes them.
+
+usage: python tests/golden/make_golden.py {1,2,3,4,5} [...]
+"""
+from __future__ import annotations
+
+import hashlib
+import json
+import os
+import sys
+import time
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
+
+import numpy as np  # noqa: E402
+
+import oracle  # noqa: E402
+from oracle import schedule as osched  # noqa: E402
+from paper_2004_08227_gb300 import workloads as W  # noqa: E402
+
+
+def _order(m):
+    return osched.build(m.schedule, m.n, m.edge_u, m.edge_v)[1]
+
+
+def _digest(m):
+    h = hashlib.sha256()
+    for a in (m.labels, m.edge_u, m.edge_v, m.unary, m.pairwise):
+        h.update(np.ascontiguousarray(a).tobytes())
+    return h.hexdigest()[:16]
+
+
+def solve_entry(m, T):
+    sol = oracle.solve(m, _order(m), T)
+    return {"name": m.name, "inputs_sha256_16": _digest(m), "iterations": T, "bound": sol["bound"],
+            "labels": sol["labels"].tolist(), "margins_min": float(np.min(sol["margins"])),
+            "margins": [float(x) for x in sol["margins"]], "energy": sol["energy"]}
+
+
+def fd_entries(m, T, count, seed=0, h=1e-4):
+    order = _order(m)
+    D, gu, gp = oracle.grad(m, order, T)
+    rng = np.random.default_rng(seed)
+    nz = np.flatnonzero(gp)
+    picks = [("p", int(i)) for i in rng.choice(nz, size=count // 2, replace=False)]
+    picks += [("p", int(i)) for i in rng.choice(gp.size, size=count // 4, replace=False)]
+    picks += [("u", int(i)) for i in rng.choice(gu.size, size=count - len(picks), replace=False)]
+    un0 = m.unary.astype(np.float64)
+    pw0 = m.pairwise.astype(np.float64)
+    out = []
+    for which, i in picks:
+        vals = []
+        for d in (h, -h, 0.0):
+            un, pw = un0.copy(), pw0.copy()
+            (un if which == "u" else pw)[i] += d
+            th_u, th_uv = oracle.run(m, order, T, state=(un, pw))
+            vals.append(oracle.bound(m, th_u, th_uv))
+        fp, fm, f0 = vals
+        out.append({"which": which, "index": i, "fd": (fp - fm) / (2 * h), "right": (fp - f0) / h,
+                    "left": (f0 - fm) / h, "oracle_grad": float((gu if which == "u" else gp)[i])})
+    return {"D": D, "h": h, "entries": out}
+
+
+def main(cfgs):
+    for c in cfgs:
+        t0 = time.time()
+        models, T = W.config(c)
+        if not isinstance(models, list):
+            models = [models]
+        res = {"workload_config": c, "iterations": T,
+               "writer": "tests/golden/make_golden.py (FP64 oracle only)",
+               "models": [solve_entry(m, T) for m in models]}
+        if c == 5:
+            res["finite_differences_model0"] = fd_entries(models[0], T, 200)
+        res["seconds"] = time.time() - t0
+        with open(os.path.join(HERE, f"full_size_config{c}.json"), "w") as f:
+            json.dump(res, f)
+        print(f"config {c}: {time.time() - t0:.0f} s", flush=True)
+
+
+if __name__ == "__main__":
+    main([int(a) for a in sys.argv[1:]] or [1, 2, 3, 4, 5])
