@@ -109,8 +109,8 @@ static void mapping_for(mplpp_solver *s, int C)
     s->tile_floats = static_cast<int>(round4(std::max(4LL, tile)));
     s->rmax = static_cast<int>(round4(std::max(4LL, rows)));
     s->ldmax = ldmax;
-    s->smem_looped = hs_smem_bytes(1, s->tile_floats, s->rmax, s->ldmax, s->T);
-    s->smem_persist = hs_smem_bytes(2, s->tile_floats, s->rmax, s->ldmax, s->T);
+    s->smem_looped = hs_smem_bytes(1, s->tile_floats, s->rmax, s->ldmax, s->T, C);
+    s->smem_persist = hs_smem_bytes(2, s->tile_floats, s->rmax, s->ldmax, s->T, C);
 }
 
 // Chooses CTAs per edge (C).  A matching's edges should run in one round of

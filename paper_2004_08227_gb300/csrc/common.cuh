@@ -148,14 +148,11 @@ __device__ __forceinline__ uint32_t mapa_shared(uint32_t addr, uint32_t rank)
     return r;
 }
 
-__device__ __forceinline__ float4 ld_dsmem_f4(uint32_t addr)
+__device__ __forceinline__ void st_dsmem_f4(uint32_t addr, float4 v)
 {
-    float4 v;
-    asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
-                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-                 : "r"(addr)
+    asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(v.x), "f"(v.y), "f"(v.z),
+                 "f"(v.w)
                  : "memory");
-    return v;
 }
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p)

@@ -16,8 +16,11 @@
 //
 // Mapping: a cluster of C CTAs shares one edge; CTA `rank` owns the rows
 // [rank*R, rank*R + R) (R = ceil(L_u / C)), loaded with one bulk asynchronous
-// copy.  Row minima (passes 1 and 3) are local to the CTA; the column minima of
-// pass 2 are combined across the cluster through distributed shared memory.
+// copy.  Row minima (passes 1 and 3) are local to the CTA; the partial column
+// minima of pass 2 are all-gathered across the cluster: every CTA stores its
+// vector into slot `rank` of every CTA's shared memory (remote stores do not
+// wait for a round trip), one cluster barrier, then each CTA reduces the C
+// slots locally.
 //
 // Two drivers:
 //   looped      one launch per matching; the launch boundary orders matchings
@@ -40,7 +43,7 @@ namespace mplpp {
 namespace {
 
 struct Smem {
-    float *tile[2];
+    float *tile;      // nbuf buffers of tile_floats each
     float *uh, *alpha, *vh, *beta, *bv, *pm;
     float4 *part;
     uint64_t *bar;  // [2]
@@ -50,20 +53,14 @@ __device__ __forceinline__ Smem carve(char *base, const HsParams &p, int nbuf)
 {
     float *f = reinterpret_cast<float *>(base);
     Smem s;
-    s.tile[0] = f;
-    f += p.tile_floats;
-    if (nbuf > 1) {
-        s.tile[1] = f;
-        f += p.tile_floats;
-    } else {
-        s.tile[1] = s.tile[0];
-    }
+    s.tile = f;
+    f += static_cast<size_t>(nbuf) * p.tile_floats;
     s.uh = f; f += p.rmax;
     s.alpha = f; f += p.rmax;
     s.vh = f; f += p.ldmax;
     s.beta = f; f += p.ldmax;
     s.bv = f; f += p.ldmax;
-    s.pm = f; f += p.ldmax;
+    s.pm = f; f += static_cast<size_t>(p.ldmax) * p.C;  // one slot per CTA of the cluster
     s.part = reinterpret_cast<float4 *>(f); f += 4 * blockDim.x;
     s.bar = reinterpret_cast<uint64_t *>(f);
     return s;
@@ -142,8 +139,13 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
     // unaries without this edge's messages (written by other SMs: L2 loads)
     for (int s = tid; s < nr; s += T)
         sm.uh[s] = __ldcg(agg + ed.au + r0 + s) - __ldcg(msg + ed.mu + r0 + s);
-    for (int t = tid; t < ld; t += T)
-        sm.vh[t] = t < Lv ? __ldcg(agg + ed.av + t) - __ldcg(msg + ed.mv + t) : 0.f;
+    for (int q = tid; q < (ld >> 2); q += T) {  // node vectors start 16-byte aligned
+        const float4 a = __ldcg(reinterpret_cast<const float4 *>(agg + ed.av) + q);
+        const float4 f = __ldcg(reinterpret_cast<const float4 *>(msg + ed.mv) + q);
+        const int t = 4 * q;
+        reinterpret_cast<float4 *>(sm.vh)[q] = make_float4(t < Lv ? a.x - f.x : 0.f, t + 1 < Lv ? a.y - f.y : 0.f,
+                                                           t + 2 < Lv ? a.z - f.z : 0.f, t + 3 < Lv ? a.w - f.w : 0.f);
+    }
 
     if (!mbar_wait(bar, parity, p.spin_limit)) set_err(p.err, ERR_TIMEOUT);
     __syncthreads();
@@ -169,9 +171,10 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
     }
     __syncthreads();
 
-    // pass 2 (this CTA's rows): pm(t) = min_s [theta(s,t) + alpha(s)]
+    // pass 2 (this CTA's rows): pm(t) = min_s [theta(s,t) + alpha(s)], stored
+    // into slot `rank` of the pm buffer of every CTA of the cluster
     {
-        float4 *pm4 = reinterpret_cast<float4 *>(sm.pm);
+        const uint32_t slot = smem_u32(sm.pm) + 4u * static_cast<uint32_t>(ld) * static_cast<uint32_t>(rank);
         const int nsub = T / Q;
         if (nsub >= 1) {
             if (tid < nsub * Q) {
@@ -182,16 +185,20 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
                 sm.part[sub * Q + q] = m;
             }
             __syncthreads();
-            for (int q = tid; q < Q; q += T) {
-                float4 m = sm.part[q];
+        }
+        for (int q = tid; q < Q; q += T) {
+            float4 m;
+            if (nsub >= 1) {
+                m = sm.part[q];
                 for (int j = 1; j < nsub; ++j) m = min4(m, sm.part[j * Q + q]);
-                pm4[q] = m;
-            }
-        } else {
-            for (int q = tid; q < Q; q += T) {
-                float4 m = make_float4(INFINITY, INFINITY, INFINITY, INFINITY);
+            } else {
+                m = make_float4(INFINITY, INFINITY, INFINITY, INFINITY);
                 for (int s = 0; s < nr; ++s) m = min4(m, add4s(t4[static_cast<size_t>(s) * Q + q], sm.alpha[s]));
-                pm4[q] = m;
+            }
+            if (CLUSTER) {
+                for (int r = 0; r < C; ++r) st_dsmem_f4(mapa_shared(slot + 16u * q, r), m);
+            } else {
+                reinterpret_cast<float4 *>(sm.pm)[q] = m;
             }
         }
     }
@@ -201,30 +208,19 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
     if (CLUSTER) {
         cluster_arrive_release();
         cluster_wait_acquire();
-        const uint32_t pm_addr = smem_u32(sm.pm);
-        for (int q = tid; q < Q; q += T) {
-            float4 m = ld_dsmem_f4(mapa_shared(pm_addr + 16u * q, 0));
-            for (int r = 1; r < C; ++r) m = min4(m, ld_dsmem_f4(mapa_shared(pm_addr + 16u * q, r)));
-            const float mm[4] = {m.x, m.y, m.z, m.w};
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int t = 4 * q + j;
-                const float vh = sm.vh[t];
-                const float b = mm[j] + vh;
-                sm.bv[t] = t < Lv ? b : 0.f;
-                sm.beta[t] = t < Lv ? vh - b : 0.f;
-            }
-        }
-        cluster_arrive_relaxed();
     } else {
         __syncthreads();
-        for (int t = tid; t < ld; t += T) {
-            const float vh = sm.vh[t];
-            const float b = sm.pm[t] + vh;
-            sm.bv[t] = t < Lv ? b : 0.f;
-            sm.beta[t] = t < Lv ? vh - b : 0.f;
-        }
     }
+    for (int t = tid; t < ld; t += T) {
+        float m = sm.pm[t];
+        if (CLUSTER)
+            for (int r = 1; r < C; ++r) m = fminf(m, sm.pm[r * ld + t]);
+        const float vh = sm.vh[t];
+        const float b = m + vh;
+        sm.bv[t] = t < Lv ? b : 0.f;
+        sm.beta[t] = t < Lv ? vh - b : 0.f;
+    }
+    if (CLUSTER) cluster_arrive_relaxed();  // this CTA has read every slot
     __syncthreads();
 
     // node v's new vector (one CTA of the cluster), published before pass 3
@@ -256,7 +252,7 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
             }
         }
     }
-    if (CLUSTER) cluster_wait_acquire();  // every CTA has finished reading this CTA's pm
+    if (CLUSTER) cluster_wait_acquire();  // every CTA has read its slots: they may be overwritten
     __syncthreads();
     if (SIGNAL && tid == 0) signal_node(p.ver, ed.gu, 1u);
 }
@@ -274,8 +270,12 @@ __global__ void __launch_bounds__(512) hs_looped_kernel(HsParams p)
         fence_mbar_init();
     }
     __syncthreads();
-    if (threadIdx.x == 0) issue_tile(ed, rank, C, p.tab, sm.tile[0], &sm.bar[0]);
-    hs_item<CLUSTER, false>(p, ed, sm.tile[0], sm, rank, &sm.bar[0], 0u);
+    if (threadIdx.x == 0) issue_tile(ed, rank, C, p.tab, sm.tile, &sm.bar[0]);
+    if (CLUSTER) {  // every CTA of the cluster is running before any remote store
+        cluster_arrive_relaxed();
+        cluster_wait_acquire();
+    }
+    hs_item<CLUSTER, false>(p, ed, sm.tile, sm, rank, &sm.bar[0], 0u);
 }
 
 __device__ __forceinline__ void wait_nodes(const HsParams &p, int gu, unsigned need_u, int gv, unsigned need_v)
@@ -311,8 +311,12 @@ __global__ void __launch_bounds__(512) hs_persistent_kernel(HsParams p)
         fence_mbar_init();
     }
     __syncthreads();
+    if (CLUSTER) {  // every CTA of the cluster is running before any remote store
+        cluster_arrive_relaxed();
+        cluster_wait_acquire();
+    }
     if (total == 0) return;
-    if (threadIdx.x == 0) issue_tile(p.edges[p.work[begin].edge], rank, C, p.tab, sm.tile[0], &sm.bar[0]);
+    if (threadIdx.x == 0) issue_tile(p.edges[p.work[begin].edge], rank, C, p.tab, sm.tile, &sm.bar[0]);
     int i = 0, it = 0;
     for (long long k = 0; k < total; ++k) {
         const WorkItem w = p.work[begin + i];
@@ -321,8 +325,9 @@ __global__ void __launch_bounds__(512) hs_persistent_kernel(HsParams p)
             if (k + 1 < total) {
                 const int inext = (i + 1 == n) ? 0 : i + 1;
                 fence_proxy_async();
-                issue_tile(p.edges[p.work[begin + inext].edge], rank, C, p.tab, sm.tile[(k + 1) & 1],
-                           &sm.bar[(k + 1) & 1]);
+                const int b = static_cast<int>((k + 1) & 1);
+                issue_tile(p.edges[p.work[begin + inext].edge], rank, C, p.tab, sm.tile + b * p.tile_floats,
+                           sm.bar + b);
             }
             const unsigned need_u = static_cast<unsigned>(C) *
                                         static_cast<unsigned>(it * w.deg_u + w.pos_u) +
@@ -332,7 +337,8 @@ __global__ void __launch_bounds__(512) hs_persistent_kernel(HsParams p)
             wait_nodes(p, ed.gu, need_u, ed.gv, need_v);
         }
         __syncthreads();
-        hs_item<CLUSTER, true>(p, ed, sm.tile[k & 1], sm, rank, &sm.bar[k & 1],
+        const int b = static_cast<int>(k & 1);
+        hs_item<CLUSTER, true>(p, ed, sm.tile + b * p.tile_floats, sm, rank, sm.bar + b,
                                static_cast<uint32_t>((k >> 1) & 1));
         if (++i == n) {
             i = 0;
@@ -374,11 +380,11 @@ cudaError_t launch(K kernel, const HsParams &p, int grid, int threads, size_t sm
 
 }  // namespace
 
-size_t hs_smem_bytes(int nbuf, int tile_floats, int rmax, int ldmax, int threads)
+size_t hs_smem_bytes(int nbuf, int tile_floats, int rmax, int ldmax, int threads, int C)
 {
-    // tiles, uh, alpha, vh, beta, bv, pm, part (float4 x T), 2 mbarriers
+    // tiles, uh, alpha, vh, beta, bv, pm (C slots), part (float4 x T), 2 mbarriers
     size_t f = static_cast<size_t>(nbuf) * tile_floats + 2 * static_cast<size_t>(rmax) +
-               4 * static_cast<size_t>(ldmax) + 4 * static_cast<size_t>(threads);
+               (3 + static_cast<size_t>(C)) * static_cast<size_t>(ldmax) + 4 * static_cast<size_t>(threads);
     return f * 4 + 16;
 }
 

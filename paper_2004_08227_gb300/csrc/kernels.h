@@ -28,7 +28,7 @@ struct HsParams {
     int ldmax;               // capacity of column vectors (floats, multiple of 4)
 };
 
-size_t hs_smem_bytes(int nbuf, int tile_floats, int rmax, int ldmax, int threads);
+size_t hs_smem_bytes(int nbuf, int tile_floats, int rmax, int ldmax, int threads, int C);
 cudaError_t hs_prepare(size_t smem_bytes);
 cudaError_t hs_launch_looped(const HsParams &p, int n_items, int threads, size_t smem, cudaStream_t st);
 cudaError_t hs_launch_persistent(const HsParams &p, int clusters, int threads, size_t smem, cudaStream_t st);

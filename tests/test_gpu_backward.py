@@ -1,9 +1,11 @@
 """GPU backward: gradient of the dual bound after T iterations against the FP64
 oracle's reverse-mode gradient and against FP64 central finite differences.
 
-D_T is piecewise linear, so gradients are sums of +-2^-k; the GPU records its
-own argmins in FP32 while the oracle decides in FP64.  Tolerance (from north
-of the FP32 rounding of the adjoint sums): |g - g_ref| <= 1e-4 max(|g_ref|, 1e-3).
+D_T is piecewise linear, so gradients are sums of +-2^-k.  The GPU backward
+replays the iterations in FP64, so its argmins are those of the FP64 oracle
+up to binary64 rounding order; the gradients are returned in FP32.
+Tolerance: |g - g_ref| <= 1e-4 max(|g_ref|, 1e-3) (the stated 1e-4 relative,
+with an absolute floor for entries near 0).
 """
 import numpy as np
 import pytest
@@ -96,23 +98,27 @@ def test_backward_requires_record():
     assert ei.value.status == -6
 
 
-def _fd(m, order, T, which, i, h):
-    un = m.unary.astype(np.float64).copy()
-    pw = m.pairwise.astype(np.float64).copy()
+def _fd3(m, order, T, which, i, h):
+    """D_T at +h, -h and 0 along one coordinate (FP64 oracle)."""
+    un = m.unary.astype(np.float64)
+    pw = m.pairwise.astype(np.float64)
     vals = []
-    for d in (h, -h):
+    for d in (h, -h, 0.0):
         u2, p2 = un.copy(), pw.copy()
         (u2 if which == "u" else p2)[i] += d
         th_u, th_uv = oracle.run(m, order, T, state=(u2, p2))
         vals.append(oracle.bound(m, th_u, th_uv))
-    return (vals[0] - vals[1]) / (2 * h)
+    return vals
 
 
-def test_grad_central_differences_K50_L64():
+def test_grad_K50_L64_matches_oracle_and_central_differences():
     """Differentiation workload shape (K_50, L = 64, N(0,1) pairwise, T = 50,
-    checkpoints every 10) on one model of the batch: GPU gradient against FP64
-    central differences (h = 1e-4) of the oracle's D_T on sampled entries,
-    half of them drawn where the oracle's gradient is non-zero."""
+    checkpoints every 10) on one model: the GPU gradient equals the oracle's
+    reverse-mode gradient on every entry, and FP64 central differences
+    (h = 1e-4) of the oracle's D_T on sampled entries, half of them where the
+    gradient is non-zero.  An entry whose one-sided differences disagree has a
+    kink within h (D_T is piecewise linear) and is skipped; at most a third of
+    the samples may be skipped."""
     m = W.complete(50, 64, seed=0, pairwise="normal")
     T = 50
     order = _order(m)
@@ -120,12 +126,21 @@ def test_grad_central_differences_K50_L64():
     s.run(T)
     gu, gp = s.backward()
     _, gu_o, gp_o = oracle.grad(m, order, T)
-    rng = np.random.default_rng(0)
+    assert np.all(_close(gu, gu_o)), np.abs(gu - gu_o).max()
+    assert np.all(_close(gp, gp_o)), np.abs(gp - gp_o).max()
+    rng = np.random.default_rng(1)
     nz = np.flatnonzero(gp_o)
-    picks = [("p", int(i)) for i in rng.choice(nz, size=min(6, nz.size), replace=False)]
+    picks = [("p", int(i)) for i in rng.choice(nz, size=6, replace=False)]
     picks += [("p", int(i)) for i in rng.choice(gp_o.size, size=2, replace=False)]
     picks += [("u", int(i)) for i in rng.choice(gu_o.size, size=4, replace=False)]
+    h = 1e-4
+    checked = 0
     for which, i in picks:
-        fd = _fd(m, order, T, which, i, 1e-4)
+        fp, fm, f0 = _fd3(m, order, T, which, i, h)
+        fd = (fp - fm) / (2 * h)
+        if abs((fp - f0) / h - (f0 - fm) / h) > TOL * max(abs(fd), 1e-3):
+            continue  # kink within h
         g = (gu if which == "u" else gp)[i]
         assert abs(g - fd) <= TOL * max(abs(fd), 1e-3), (which, i, g, fd)
+        checked += 1
+    assert checked >= 2 * len(picks) // 3
