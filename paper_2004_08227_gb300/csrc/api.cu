@@ -12,7 +12,7 @@
 
 #include <cuda_runtime.h>
 
-#include "../../include/mplpp.h"
+#include "mplpp.h"
 #include "backward.h"
 #include "host.h"
 #include "kernels.h"

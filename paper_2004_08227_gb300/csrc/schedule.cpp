@@ -18,7 +18,7 @@
 #include <unordered_set>
 #include <vector>
 
-#include "../../include/mplpp.h"
+#include "mplpp.h"
 #include "host.h"
 
 namespace mplpp {

@@ -7,7 +7,7 @@
 
 #include <cuda_runtime.h>
 
-#include "../../include/mplpp.h"
+#include "mplpp.h"
 #include "common.cuh"
 
 namespace mplpp {

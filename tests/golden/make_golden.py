@@ -45,7 +45,10 @@ def solve_entry(m, T):
             "margins": [float(x) for x in sol["margins"]], "energy": sol["energy"]}
 
 
-def fd_entries(m, T, count, seed=0, h=1e-4):
+def fd_entries(m, T, count, seed=0, steps=(1e-4, 1e-5, 1e-6)):
+    """Central differences of D_T at sampled entries.  D_T is piecewise linear:
+    where the one-sided differences at step h disagree (a kink within h) the
+    next smaller step is tried; `h` records the step used (None: kink at all)."""
     order = _order(m)
     D, gu, gp = oracle.grad(m, order, T)
     rng = np.random.default_rng(seed)
@@ -55,18 +58,27 @@ def fd_entries(m, T, count, seed=0, h=1e-4):
     picks += [("u", int(i)) for i in rng.choice(gu.size, size=count - len(picks), replace=False)]
     un0 = m.unary.astype(np.float64)
     pw0 = m.pairwise.astype(np.float64)
+
+    def DT(which, i, d):
+        un, pw = un0.copy(), pw0.copy()
+        (un if which == "u" else pw)[i] += d
+        th_u, th_uv = oracle.run(m, order, T, state=(un, pw))
+        return oracle.bound(m, th_u, th_uv)
+
     out = []
     for which, i in picks:
-        vals = []
-        for d in (h, -h, 0.0):
-            un, pw = un0.copy(), pw0.copy()
-            (un if which == "u" else pw)[i] += d
-            th_u, th_uv = oracle.run(m, order, T, state=(un, pw))
-            vals.append(oracle.bound(m, th_u, th_uv))
-        fp, fm, f0 = vals
-        out.append({"which": which, "index": i, "fd": (fp - fm) / (2 * h), "right": (fp - f0) / h,
-                    "left": (f0 - fm) / h, "oracle_grad": float((gu if which == "u" else gp)[i])})
-    return {"D": D, "h": h, "entries": out}
+        f0 = DT(which, i, 0.0)
+        rec = {"which": which, "index": i, "oracle_grad": float((gu if which == "u" else gp)[i]), "h": None}
+        for h in steps:
+            fp, fm = DT(which, i, h), DT(which, i, -h)
+            fd = (fp - fm) / (2 * h)
+            right, left = (fp - f0) / h, (f0 - fm) / h
+            rec.update({"fd": fd, "right": right, "left": left})
+            if abs(right - left) <= 1e-4 * max(abs(fd), 1e-3):
+                rec["h"] = h
+                break
+        out.append(rec)
+    return {"D": D, "steps": list(steps), "entries": out}
 
 
 def main(cfgs):

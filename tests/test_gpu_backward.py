@@ -116,9 +116,9 @@ def test_grad_K50_L64_matches_oracle_and_central_differences():
     checkpoints every 10) on one model: the GPU gradient equals the oracle's
     reverse-mode gradient on every entry, and FP64 central differences
     (h = 1e-4) of the oracle's D_T on sampled entries, half of them where the
-    gradient is non-zero.  An entry whose one-sided differences disagree has a
-    kink within h (D_T is piecewise linear) and is skipped; at most a third of
-    the samples may be skipped."""
+    gradient is non-zero.  Where the one-sided differences disagree there is a
+    kink within h (D_T is piecewise linear) and the step shrinks to 1e-5, then
+    1e-6; at most a quarter of the samples may have a kink at every step."""
     m = W.complete(50, 64, seed=0, pairwise="normal")
     T = 50
     order = _order(m)
@@ -133,14 +133,15 @@ def test_grad_K50_L64_matches_oracle_and_central_differences():
     picks = [("p", int(i)) for i in rng.choice(nz, size=6, replace=False)]
     picks += [("p", int(i)) for i in rng.choice(gp_o.size, size=2, replace=False)]
     picks += [("u", int(i)) for i in rng.choice(gu_o.size, size=4, replace=False)]
-    h = 1e-4
     checked = 0
     for which, i in picks:
-        fp, fm, f0 = _fd3(m, order, T, which, i, h)
-        fd = (fp - fm) / (2 * h)
-        if abs((fp - f0) / h - (f0 - fm) / h) > TOL * max(abs(fd), 1e-3):
-            continue  # kink within h
-        g = (gu if which == "u" else gp)[i]
-        assert abs(g - fd) <= TOL * max(abs(fd), 1e-3), (which, i, g, fd)
-        checked += 1
-    assert checked >= 2 * len(picks) // 3
+        for h in (1e-4, 1e-5, 1e-6):
+            fp, fm, f0 = _fd3(m, order, T, which, i, h)
+            fd = (fp - fm) / (2 * h)
+            if abs((fp - f0) / h - (f0 - fm) / h) > TOL * max(abs(fd), 1e-3):
+                continue  # kink within h: try a smaller step
+            g = (gu if which == "u" else gp)[i]
+            assert abs(g - fd) <= TOL * max(abs(fd), 1e-3), (which, i, h, g, fd)
+            checked += 1
+            break
+    assert checked >= 3 * len(picks) // 4
