@@ -20,7 +20,8 @@
 // minima of pass 2 are all-gathered across the cluster: every CTA stores its
 // vector into slot `rank` of every CTA's shared memory (remote stores do not
 // wait for a round trip), one cluster barrier, then each CTA reduces the C
-// slots locally.
+// slots locally.  The slots alternate between two buffers from one edge to
+// the next, so one barrier per edge suffices.
 //
 // Two drivers:
 //   looped      one launch per matching; the launch boundary orders matchings
@@ -60,19 +61,24 @@ __device__ __forceinline__ Smem carve(char *base, const HsParams &p, int nbuf)
     s.vh = f; f += p.ldmax;
     s.beta = f; f += p.ldmax;
     s.bv = f; f += p.ldmax;
-    s.pm = f; f += static_cast<size_t>(p.ldmax) * p.C;  // one slot per CTA of the cluster
+    s.pm = f; f += static_cast<size_t>(nbuf) * p.ldmax * p.C;  // [item parity][CTA of the cluster][column]
     s.part = reinterpret_cast<float4 *>(f); f += 4 * blockDim.x;
     s.bar = reinterpret_cast<uint64_t *>(f);
     return s;
 }
 
-// Lanes per row for the row minima: a power of two <= 32 giving each lane
-// about two float4 chunks of a row.
-__device__ __forceinline__ int row_group(int Q)
+// Lanes per row for the row minima: all of the CTA's rows in one round
+// (lanes * rows <= threads), at least two float4 chunks per lane, a power of
+// two <= 32.  Fewer lanes per row means longer independent chains per lane
+// and fewer shuffle steps.
+__device__ __forceinline__ int row_lanes(int nr, int Q, int T)
 {
+    int g = T / (nr > 0 ? nr : 1);
     int h = Q >> 1;
-    h = h < 1 ? 1 : (h > 32 ? 32 : h);
-    return 1 << (31 - __clz(h));
+    h = h < 1 ? 1 : h;
+    g = g < h ? g : h;
+    g = g > 32 ? 32 : (g < 1 ? 1 : g);
+    return 1 << (31 - __clz(g));
 }
 
 __device__ __forceinline__ void rows_of(const EdgeDesc &ed, int rank, int C, int &r0, int &nr)
@@ -111,9 +117,17 @@ __device__ __forceinline__ void signal_node(unsigned *ver, int g, unsigned n)
     asm volatile("red.relaxed.gpu.global.add.u32 [%0], %1;" ::"l"(ver + g), "r"(n) : "memory");
 }
 
-__device__ __forceinline__ void row_scan(const float4 *row, const float4 *w, int Q, int lg, int G, float &m)
+// min_t [row(t) + w(t)] over this lane's chunks q = lg, lg + G, ... (two chains)
+__device__ __forceinline__ float row_min(const float4 *row, const float4 *w, int Q, int lg, int G)
 {
-    for (int q = lg; q < Q; q += G) m = fminf(m, hmin_add(row[q], w[q]));
+    float m0 = INFINITY, m1 = INFINITY;
+    int q = lg;
+    for (; q + G < Q; q += 2 * G) {
+        m0 = fminf(m0, hmin_add(row[q], w[q]));
+        m1 = fminf(m1, hmin_add(row[q + G], w[q + G]));
+    }
+    if (q < Q) m0 = fminf(m0, hmin_add(row[q], w[q]));
+    return fminf(m0, m1);
 }
 
 __device__ __forceinline__ void group_min(float &m, int G)
@@ -123,10 +137,11 @@ __device__ __forceinline__ void group_min(float &m, int G)
 
 // One Handshake update of edge ed by this CTA (its row slice); the table slice
 // is (or will be) in `tile`, signalled by `bar` completing phase `parity`.
+// `xpar` selects the exchange buffer (alternates between consecutive items).
 // SIGNAL: publish completion on the node counters (persistent driver).
 template <bool CLUSTER, bool SIGNAL>
 __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile, const Smem &sm, int rank,
-                        uint64_t *bar, uint32_t parity)
+                        uint64_t *bar, uint32_t parity, int xpar)
 {
     const int T = blockDim.x, tid = threadIdx.x;
     const int C = CLUSTER ? p.C : 1;
@@ -151,16 +166,16 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
     __syncthreads();
 
     const float4 *t4 = reinterpret_cast<const float4 *>(tile);
-    const int G = row_group(Q);
+    const int G = row_lanes(nr, Q, T);
     const int gid = tid / G, lg = tid % G, ng = T / G;
+    float *xbuf = sm.pm + static_cast<size_t>(xpar) * C * ld;  // this item's exchange slots
 
     // pass 1: a(s) = 1/2 (min_t [theta(s,t) + vh(t)] + uh(s));  alpha = uh - a
     {
         const float4 *w = reinterpret_cast<const float4 *>(sm.vh);
         for (int base = 0; base < nr; base += ng) {
             const int s = base + gid;
-            float m = INFINITY;
-            if (s < nr) row_scan(t4 + static_cast<size_t>(s) * Q, w, Q, lg, G, m);
+            float m = s < nr ? row_min(t4 + static_cast<size_t>(s) * Q, w, Q, lg, G) : INFINITY;
             group_min(m, G);
             if (s < nr && lg == 0) {
                 const float u = sm.uh[s];
@@ -174,15 +189,18 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
     // pass 2 (this CTA's rows): pm(t) = min_s [theta(s,t) + alpha(s)], stored
     // into slot `rank` of the pm buffer of every CTA of the cluster
     {
-        const uint32_t slot = smem_u32(sm.pm) + 4u * static_cast<uint32_t>(ld) * static_cast<uint32_t>(rank);
+        const uint32_t slot = smem_u32(xbuf) + 4u * static_cast<uint32_t>(ld) * static_cast<uint32_t>(rank);
         const int nsub = T / Q;
         if (nsub >= 1) {
             if (tid < nsub * Q) {
                 const int q = tid % Q, sub = tid / Q;
-                float4 m = make_float4(INFINITY, INFINITY, INFINITY, INFINITY);
-                for (int s = sub; s < nr; s += nsub)
+                float4 m = make_float4(INFINITY, INFINITY, INFINITY, INFINITY), m2 = m;
+                for (int s = sub; s < nr; s += 2 * nsub) {
                     m = min4(m, add4s(t4[static_cast<size_t>(s) * Q + q], sm.alpha[s]));
-                sm.part[sub * Q + q] = m;
+                    const int s2 = s + nsub;
+                    if (s2 < nr) m2 = min4(m2, add4s(t4[static_cast<size_t>(s2) * Q + q], sm.alpha[s2]));
+                }
+                sm.part[sub * Q + q] = min4(m, m2);
             }
             __syncthreads();
         }
@@ -198,7 +216,7 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
             if (CLUSTER) {
                 for (int r = 0; r < C; ++r) st_dsmem_f4(mapa_shared(slot + 16u * q, r), m);
             } else {
-                reinterpret_cast<float4 *>(sm.pm)[q] = m;
+                reinterpret_cast<float4 *>(xbuf)[q] = m;
             }
         }
     }
@@ -212,15 +230,16 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
         __syncthreads();
     }
     for (int t = tid; t < ld; t += T) {
-        float m = sm.pm[t];
+        float m = xbuf[t];
         if (CLUSTER)
-            for (int r = 1; r < C; ++r) m = fminf(m, sm.pm[r * ld + t]);
+            for (int r = 1; r < C; ++r) m = fminf(m, xbuf[r * ld + t]);
         const float vh = sm.vh[t];
         const float b = m + vh;
         sm.bv[t] = t < Lv ? b : 0.f;
         sm.beta[t] = t < Lv ? vh - b : 0.f;
     }
-    if (CLUSTER) cluster_arrive_relaxed();  // this CTA has read every slot
+    // The slots of this parity are written again two items later, after every
+    // CTA has passed the next item's exchange barrier, i.e. after this read.
     __syncthreads();
 
     // node v's new vector (one CTA of the cluster), published before pass 3
@@ -241,8 +260,7 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
         const float4 *w = reinterpret_cast<const float4 *>(sm.beta);
         for (int base = 0; base < nr; base += ng) {
             const int s = base + gid;
-            float m = INFINITY;
-            if (s < nr) row_scan(t4 + static_cast<size_t>(s) * Q, w, Q, lg, G, m);
+            float m = s < nr ? row_min(t4 + static_cast<size_t>(s) * Q, w, Q, lg, G) : INFINITY;
             group_min(m, G);
             if (s < nr && lg == 0) {
                 const float u = sm.uh[s];
@@ -252,7 +270,6 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
             }
         }
     }
-    if (CLUSTER) cluster_wait_acquire();  // every CTA has read its slots: they may be overwritten
     __syncthreads();
     if (SIGNAL && tid == 0) signal_node(p.ver, ed.gu, 1u);
 }
@@ -275,7 +292,7 @@ __global__ void __launch_bounds__(512) hs_looped_kernel(HsParams p)
         cluster_arrive_relaxed();
         cluster_wait_acquire();
     }
-    hs_item<CLUSTER, false>(p, ed, sm.tile, sm, rank, &sm.bar[0], 0u);
+    hs_item<CLUSTER, false>(p, ed, sm.tile, sm, rank, &sm.bar[0], 0u, 0);
 }
 
 __device__ __forceinline__ void wait_nodes(const HsParams &p, int gu, unsigned need_u, int gv, unsigned need_v)
@@ -339,7 +356,7 @@ __global__ void __launch_bounds__(512) hs_persistent_kernel(HsParams p)
         __syncthreads();
         const int b = static_cast<int>(k & 1);
         hs_item<CLUSTER, true>(p, ed, sm.tile + b * p.tile_floats, sm, rank, sm.bar + b,
-                               static_cast<uint32_t>((k >> 1) & 1));
+                               static_cast<uint32_t>((k >> 1) & 1), b);
         if (++i == n) {
             i = 0;
             ++it;
@@ -382,9 +399,9 @@ cudaError_t launch(K kernel, const HsParams &p, int grid, int threads, size_t sm
 
 size_t hs_smem_bytes(int nbuf, int tile_floats, int rmax, int ldmax, int threads, int C)
 {
-    // tiles, uh, alpha, vh, beta, bv, pm (C slots), part (float4 x T), 2 mbarriers
+    // tiles, uh, alpha, vh, beta, bv, pm (nbuf x C slots), part (float4 x T), 2 mbarriers
     size_t f = static_cast<size_t>(nbuf) * tile_floats + 2 * static_cast<size_t>(rmax) +
-               (3 + static_cast<size_t>(C)) * static_cast<size_t>(ldmax) + 4 * static_cast<size_t>(threads);
+               (3 + static_cast<size_t>(nbuf) * C) * static_cast<size_t>(ldmax) + 4 * static_cast<size_t>(threads);
     return f * 4 + 16;
 }
 
