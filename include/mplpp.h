@@ -196,6 +196,38 @@ mplpp_status mplpp_info(const mplpp_solver *s, mplpp_info_t *info);
 /* Waits for the solver's stream and reports device-side errors. */
 mplpp_status mplpp_sync(mplpp_solver *s);
 
+/* Dual bound of one model's reparametrized costs without allocating any
+ * device memory.  The paper has no counterpart: this entry point exists for
+ * callers that cannot call cudaMalloc -- code that owns a fixed device arena
+ * and allows no allocation after start-up, real-time loops that cannot pay an
+ * allocation's latency or implicit synchronization, plugins whose host
+ * runtime must see every device byte.  It computes what mplpp_bound(exact = 1)
+ * computes, from buffers the caller owns:
+ *   labels [n_nodes], edge_u, edge_v [n_edges]   int32, device (u < v)
+ *   pairwise [sum L_u L_v]  FP32, device, the ORIGINAL tables, caller layout
+ *   agg [sum L_u]           FP32, device, theta^phi_u per node (state layout)
+ *   msg [sum (L_u + L_v)]   FP32, device, phi_{v->u} then phi_{u->v} per edge
+ *                           (state layout, as in mplpp_save_state)
+ *   out [1]                 FP64, device, receives D
+ * Working memory (offsets, per-node and per-edge minima) is one file-scope
+ * device array of MPLPP_NOALLOC_SCRATCH_BYTES (about 5.8 MB) that every GPU
+ * loading the library holds until the process exits; hence the size limits
+ * below, beyond which the call returns MPLPP_E_UNSUPPORTED.  The first call on
+ * a device looks up that array's device address (cudaGetSymbolAddress, with
+ * the device current); make that first call before any stream capture.  All
+ * calls share the array: calls that overlap on the GPU (other streams, other
+ * host threads) race on it.  Work runs on `stream` (a cudaStream_t, NULL =
+ * legacy default); the call synchronizes it to report bad labels or edges
+ * (MPLPP_E_INVALID).  Calls no cudaMalloc, cudaFree or allocating library
+ * routine.  Message of a failure: mplpp_noalloc_last_error(). */
+#define MPLPP_NOALLOC_MAX_NODES 65536
+#define MPLPP_NOALLOC_MAX_EDGES 262144
+#define MPLPP_NOALLOC_SCRATCH_BYTES 6030336
+mplpp_status mplpp_bound_noalloc(int32_t n_nodes, int32_t n_edges, const int32_t *labels, const int32_t *edge_u,
+                                 const int32_t *edge_v, const float *pairwise, const float *agg, const float *msg,
+                                 double *out, void *stream);
+const char *mplpp_noalloc_last_error(void);
+
 /* Message of the last failed call on this solver ("" if none).  Valid until the
  * next call on the solver.  s may be NULL: then the last mplpp_create failure. */
 const char *mplpp_last_error(const mplpp_solver *s);

@@ -43,6 +43,20 @@ def schedule(kind: str, n: int, edge_u, edge_v):
     return off[:nm.value + 1].copy(), order[:E].copy()
 
 
+def bound_noalloc(labels, edge_u, edge_v, pairwise, agg, msg, out, stream=None):
+    """mplpp_bound_noalloc: dual bound of one model from caller-owned CUDA
+    tensors (int32 labels / edges, FP32 pairwise / agg / msg in the state
+    layout, FP64 out[1]); allocates no device memory."""
+    lib = _lib.load()
+    st = _current_stream() if stream is None else ctypes.c_void_p(stream)
+    status = lib.mplpp_bound_noalloc(int(labels.numel()), int(edge_u.numel()), _ptr(labels), _ptr(edge_u),
+                                     _ptr(edge_v), _ptr(pairwise), _ptr(agg), _ptr(msg), _ptr(out), st)
+    if status != _lib.MPLPP_OK:
+        msg_ = lib.mplpp_noalloc_last_error()
+        raise _lib.MplppError(status, msg_.decode() if msg_ else "")
+    return out
+
+
 def _current_stream():
     if torch is None or not torch.cuda.is_available():
         return ctypes.c_void_p(0)
