@@ -131,13 +131,14 @@ mplpp_status mplpp_run(mplpp_solver *s, int32_t iterations);
  * model, into host out[n_models].  exact != 0: node minima plus the minimum of
  * every reparametrized pairwise table (reads all tables); exact == 0: node
  * minima only, which equals D when every table's minimum is 0, as it is after
- * a full iteration (Def. 1 normalization).  Minima in FP32, sums in FP64.
+ * a full iteration (Def. 1 normalization).  FP64 throughout (the state is FP64,
+ * the tables FP32).
  * Synchronizes. */
 mplpp_status mplpp_bound(mplpp_solver *s, double *out, int32_t exact);
 
 /* Primal rounding (Sec. 4, Primal Rounding) of the current reparametrization:
  * nodes in increasing order, x_u = argmin_s [theta^phi_u(s) + sum over earlier
- * neighbours v (increasing v) of theta^phi_vu(x_v, s)], FP32 sums, lowest index
+ * neighbours v (increasing v) of theta^phi_vu(x_v, s)], FP64 sums, lowest index
  * on ties.  labels: host [sum of n_nodes over models], model after model;
  * energy: host [n_models] (may be NULL), E(x | original costs) in FP64
  * (eq. energy-min).  Synchronizes. */
@@ -161,7 +162,7 @@ mplpp_status mplpp_backward(mplpp_solver *s, const float *dD, float *grad_unary,
 mplpp_status mplpp_reset(mplpp_solver *s);
 
 /* Solver state (the reparametrization) in a portable host format:
- *   header (see mplpp_state_header), then FP32 theta^phi_u for every node
+ *   header (see mplpp_state_header), then FP64 theta^phi_u for every node
  *   ([sum L], model after model, node order), then per edge phi_{v->u} [L_u]
  *   followed by phi_{u->v} [L_v] (edge order).  theta^phi_uv is implied:
  *   theta_uv(s,t) - phi_{v->u}(s) - phi_{u->v}(t) (eq. reparametrization).
@@ -169,7 +170,7 @@ mplpp_status mplpp_reset(mplpp_solver *s);
  * Loading checks the header against the solver's shapes (MPLPP_E_INVALID). */
 typedef struct {
     uint32_t magic;       /* 0x4D504C50 "MPLP" */
-    uint32_t version;     /* 1 */
+    uint32_t version;     /* 2 (FP64 values) */
     uint64_t shape_hash;  /* FNV-1a of labels, edges and schedules of all models */
     int64_t iterations;   /* iterations run since the last reset */
     int64_t n_unary;      /* sum L over all models */
@@ -182,7 +183,7 @@ mplpp_status mplpp_load_state(mplpp_solver *s, const void *buf, size_t size);
 /* Facts about a solver, for benchmarks and tests. */
 typedef struct {
     int64_t iterations;         /* iterations run since the last reset                        */
-    int64_t bytes_per_iteration;/* algorithmic HBM bytes: sum_e 4 L_u L_v + 16 (L_u + L_v)    */
+    int64_t bytes_per_iteration;/* algorithmic HBM bytes: sum_e 4 L_u L_v + 32 (L_u + L_v)    */
     int64_t edges;              /* total edges over all models                                */
     int32_t phases;             /* matchings per iteration (max over models)                 */
     int32_t mode;               /* MPLPP_MODE_LOOPED or _PERSISTENT actually used             */

@@ -277,7 +277,7 @@ extern "C" mplpp_status mplpp_create(const mplpp_model *models, int32_t n_models
             toff += 1LL * ed.Lu * ed.ld;
             moff += round4(ed.Lu) + round4(ed.Lv);
             poff += 1LL * ed.Lu * ed.Lv;
-            s->bytes_per_iter += 4LL * ed.Lu * ed.Lv + 16LL * (ed.Lu + ed.Lv);
+            s->bytes_per_iter += 4LL * ed.Lu * ed.Lv + 32LL * (ed.Lu + ed.Lv);
         }
         mh.pair_size = poff;
         s->N += mh.n;
@@ -402,7 +402,7 @@ extern "C" mplpp_status mplpp_create(const mplpp_model *models, int32_t n_models
         CKC(h2d(S->d_work, S->work.data(), S->work.size() * sizeof(WorkItem)));
     }
     CKC(cudaMemsetAsync(S->d_err, 0, sizeof(int), st));
-    CKC(cudaMemsetAsync(S->d_msg, 0, S->msgN * sizeof(float), st));
+    CKC(cudaMemsetAsync(S->d_msg, 0, S->msgN * sizeof(double), st));
 
     // costs: stage (host inputs) or read in place (device inputs), then pack
     float *stage_u = nullptr, *stage_p = nullptr;
@@ -614,8 +614,8 @@ extern "C" mplpp_status mplpp_reset(mplpp_solver *s)
 {
     if (!s) return MPLPP_E_INVALID;
     s->err.clear();
-    CK(s, cudaMemsetAsync(s->d_msg, 0, s->msgN * sizeof(float), s->stream));
-    CK(s, cudaMemcpyAsync(s->d_agg, s->d_un0, s->aggN * sizeof(float), cudaMemcpyDeviceToDevice, s->stream));
+    CK(s, cudaMemsetAsync(s->d_msg, 0, s->msgN * sizeof(double), s->stream));
+    CK(s, launch_widen(s->d_un0, s->d_agg, s->aggN, s->stream));
     s->iterations = 0;
     s->history_valid = true;
     return MPLPP_OK;
@@ -624,7 +624,7 @@ extern "C" mplpp_status mplpp_reset(mplpp_solver *s)
 extern "C" mplpp_status mplpp_state_size(const mplpp_solver *s, size_t *bytes)
 {
     if (!s || !bytes) return MPLPP_E_INVALID;
-    *bytes = sizeof(mplpp_state_header) + sizeof(float) * (s->sum_unary + s->sum_msg);
+    *bytes = sizeof(mplpp_state_header) + sizeof(double) * (s->sum_unary + s->sum_msg);
     return MPLPP_OK;
 }
 
@@ -635,29 +635,29 @@ extern "C" mplpp_status mplpp_save_state(mplpp_solver *s, void *buf, size_t size
     size_t need = 0;
     mplpp_state_size(s, &need);
     if (size < need) return fail(s, MPLPP_E_INVALID, "state buffer too small");
-    std::vector<float> agg(s->aggN), msg(s->msgN);
-    CK(s, cudaMemcpyAsync(agg.data(), s->d_agg, s->aggN * sizeof(float), cudaMemcpyDeviceToHost, s->stream));
-    CK(s, cudaMemcpyAsync(msg.data(), s->d_msg, s->msgN * sizeof(float), cudaMemcpyDeviceToHost, s->stream));
+    std::vector<double> agg(s->aggN), msg(s->msgN);
+    CK(s, cudaMemcpyAsync(agg.data(), s->d_agg, s->aggN * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    CK(s, cudaMemcpyAsync(msg.data(), s->d_msg, s->msgN * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
     mplpp_status st = mplpp_sync(s);
     if (st != MPLPP_OK) return st;
     mplpp_state_header h;
     h.magic = 0x4D504C50u;
-    h.version = 1;
+    h.version = 2;
     h.shape_hash = s->shape_hash;
     h.iterations = s->iterations;
     h.n_unary = s->sum_unary;
     h.n_msg = s->sum_msg;
     char *p = static_cast<char *>(buf);
     std::memcpy(p, &h, sizeof(h));
-    float *f = reinterpret_cast<float *>(p + sizeof(h));
+    double *f = reinterpret_cast<double *>(p + sizeof(h));
     for (auto &nd : s->h_nodes) {
-        std::memcpy(f, agg.data() + nd.aoff, sizeof(float) * nd.L);
+        std::memcpy(f, agg.data() + nd.aoff, sizeof(double) * nd.L);
         f += nd.L;
     }
     for (auto &ed : s->h_edges) {
-        std::memcpy(f, msg.data() + ed.mu, sizeof(float) * ed.Lu);
+        std::memcpy(f, msg.data() + ed.mu, sizeof(double) * ed.Lu);
         f += ed.Lu;
-        std::memcpy(f, msg.data() + ed.mv, sizeof(float) * ed.Lv);
+        std::memcpy(f, msg.data() + ed.mv, sizeof(double) * ed.Lv);
         f += ed.Lv;
     }
     return MPLPP_OK;
@@ -672,27 +672,27 @@ extern "C" mplpp_status mplpp_load_state(mplpp_solver *s, const void *buf, size_
     if (size < need) return fail(s, MPLPP_E_INVALID, "state buffer too small");
     mplpp_state_header h;
     std::memcpy(&h, buf, sizeof(h));
-    if (h.magic != 0x4D504C50u || h.version != 1 || h.shape_hash != s->shape_hash || h.n_unary != s->sum_unary ||
+    if (h.magic != 0x4D504C50u || h.version != 2 || h.shape_hash != s->shape_hash || h.n_unary != s->sum_unary ||
         h.n_msg != s->sum_msg)
         return fail(s, MPLPP_E_INVALID, "state does not match this solver's models");
-    std::vector<float> agg(s->aggN, 0.f), msg(s->msgN, 0.f);
-    const float *f = reinterpret_cast<const float *>(static_cast<const char *>(buf) + sizeof(h));
+    std::vector<double> agg(s->aggN, 0.0), msg(s->msgN, 0.0);
+    const double *f = reinterpret_cast<const double *>(static_cast<const char *>(buf) + sizeof(h));
     for (auto &nd : s->h_nodes) {
         for (int i = 0; i < nd.L; ++i)
             if (!std::isfinite(f[i])) return fail(s, MPLPP_E_INVALID, "state values must be finite");
-        std::memcpy(agg.data() + nd.aoff, f, sizeof(float) * nd.L);
+        std::memcpy(agg.data() + nd.aoff, f, sizeof(double) * nd.L);
         f += nd.L;
     }
     for (auto &ed : s->h_edges) {
         for (int i = 0; i < ed.Lu + ed.Lv; ++i)
             if (!std::isfinite(f[i])) return fail(s, MPLPP_E_INVALID, "state values must be finite");
-        std::memcpy(msg.data() + ed.mu, f, sizeof(float) * ed.Lu);
+        std::memcpy(msg.data() + ed.mu, f, sizeof(double) * ed.Lu);
         f += ed.Lu;
-        std::memcpy(msg.data() + ed.mv, f, sizeof(float) * ed.Lv);
+        std::memcpy(msg.data() + ed.mv, f, sizeof(double) * ed.Lv);
         f += ed.Lv;
     }
-    CK(s, cudaMemcpyAsync(s->d_agg, agg.data(), s->aggN * sizeof(float), cudaMemcpyHostToDevice, s->stream));
-    CK(s, cudaMemcpyAsync(s->d_msg, msg.data(), s->msgN * sizeof(float), cudaMemcpyHostToDevice, s->stream));
+    CK(s, cudaMemcpyAsync(s->d_agg, agg.data(), s->aggN * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+    CK(s, cudaMemcpyAsync(s->d_msg, msg.data(), s->msgN * sizeof(double), cudaMemcpyHostToDevice, s->stream));
     CK(s, cudaStreamSynchronize(s->stream));
     s->iterations = h.iterations;
     s->history_valid = false;

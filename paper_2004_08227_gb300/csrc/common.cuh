@@ -2,10 +2,13 @@
 // solver's kernels (Handshake update, dual bound, rounding, backward).
 //
 // Device layout of a solver (all models concatenated, model after model):
-//   agg  [float]  theta^phi_u of every node (Sec. 3, eq. reparametrization),
-//                 each node's vector starts on a 16-byte boundary, pad = 0;
-//   msg  [float]  per edge phi_{v->u} (L_u) then phi_{u->v} (L_v), each padded
-//                 to a multiple of 4 floats, pad = 0;
+//   agg  [double] theta^phi_u of every node (Sec. 3, eq. reparametrization),
+//                 each node's vector padded to a multiple of 4 entries (32-byte
+//                 aligned), pad = 0;
+//   msg  [double] per edge phi_{v->u} (L_u) then phi_{u->v} (L_v), each padded
+//                 to a multiple of 4 entries, pad = 0;
+//                 (FP64 because these sums grow large over many updates; the
+//                 O(L^2) table work stays FP32)
 //   tab  [float]  the ORIGINAL pairwise tables theta_uv, never written after
 //                 creation; rows of L_v entries padded to a stride `ld`
 //                 (multiple of 4) with +inf, tables 16-byte aligned.  The
@@ -175,6 +178,40 @@ __device__ __forceinline__ float4 add4s(float4 a, float s)
 __device__ __forceinline__ float hmin_add(float4 x, float4 w)
 {
     return fminf(fminf(x.x + w.x, x.y + w.y), fminf(x.z + w.z, x.w + w.w));
+}
+
+// Three-input minimum (one instruction on sm_100+); same value as two fminf.
+__device__ __forceinline__ float min3f(float a, float b, float c)
+{
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
+// x + w lane by lane with two packed FP32 additions (add.rn.f32x2, sm_100+);
+// each lane is rounded exactly as a scalar FP32 addition.
+__device__ __forceinline__ float4 add4(float4 x, float4 w)
+{
+    float4 r;
+    asm("{\n\t.reg .b64 a, b, c;\n\t"
+        "mov.b64 a, {%4, %5};\n\t"
+        "mov.b64 b, {%8, %9};\n\t"
+        "add.rn.f32x2 c, a, b;\n\t"
+        "mov.b64 {%0, %1}, c;\n\t"
+        "mov.b64 a, {%6, %7};\n\t"
+        "mov.b64 b, {%10, %11};\n\t"
+        "add.rn.f32x2 c, a, b;\n\t"
+        "mov.b64 {%2, %3}, c;\n\t}"
+        : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
+        : "f"(x.x), "f"(x.y), "f"(x.z), "f"(x.w), "f"(w.x), "f"(w.y), "f"(w.z), "f"(w.w));
+    return r;
+}
+
+// min(m, min over the four lanes of x + w)
+__device__ __forceinline__ float min_add4(float m, float4 x, float4 w)
+{
+    const float4 v = add4(x, w);
+    return min3f(min3f(m, v.x, v.y), v.z, v.w);
 }
 
 }  // namespace mplpp

@@ -14,7 +14,8 @@ namespace {
 constexpr int kThreads = 256;
 
 // Copies the caller's row-major tables into the padded layout (row stride ld,
-// pad +inf) and the unaries into agg / un0 (pad 0).  Flags non-finite costs.
+// pad +inf) and the unaries into un0 (FP32) and agg (FP64), pad 0.  Flags
+// non-finite costs.
 __global__ void pack_tables_kernel(const EdgeDesc *edges, int n_edges, const float *src, float *tab, int *err)
 {
     for (int e = blockIdx.x; e < n_edges; e += gridDim.x) {
@@ -33,7 +34,7 @@ __global__ void pack_tables_kernel(const EdgeDesc *edges, int n_edges, const flo
     }
 }
 
-__global__ void pack_unary_kernel(const NodeDesc *nodes, int n_nodes, const float *src, float *un0, float *agg,
+__global__ void pack_unary_kernel(const NodeDesc *nodes, int n_nodes, const float *src, float *un0, double *agg,
                                   int *err)
 {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -49,57 +50,59 @@ __global__ void pack_unary_kernel(const NodeDesc *nodes, int n_nodes, const floa
                 if (!isfinite(v)) atomicCAS(err, 0, ERR_NONFINITE);
             }
             un0[nd.aoff + s] = v;
-            agg[nd.aoff + s] = v;
+            agg[nd.aoff + s] = static_cast<double>(v);
         }
     }
 }
 
 template <int T>
-__device__ __forceinline__ float block_min(float v, float *red)
+__device__ __forceinline__ double block_min(double v, double *red)
 {
-    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     __syncthreads();
     if (l == 0) red[w] = v;
     __syncthreads();
     if (w == 0) {
         v = l < T / 32 ? red[l] : INFINITY;
-        for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+        for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
     }
     return v;  // valid in thread 0
 }
 
-// emin[e] = min_{s,t} (theta_uv(s,t) - phi_{v->u}(s)) - phi_{u->v}(t)
+// emin[e] = min_{s,t} (theta_uv(s,t) - phi_{v->u}(s)) - phi_{u->v}(t)   (FP64)
 __global__ void __launch_bounds__(kThreads) bound_edges_kernel(const EdgeDesc *edges, int n_edges,
-                                                               const float *tab, const float *msg, float *emin)
+                                                               const float *tab, const double *msg, double *emin)
 {
-    __shared__ float red[32];
+    __shared__ double red[32];
     for (int e = blockIdx.x; e < n_edges; e += gridDim.x) {
         const EdgeDesc ed = edges[e];
-        float m = INFINITY;
+        double m = INFINITY;
         const long long n = static_cast<long long>(ed.Lu) * ed.Lv;
         for (long long i = threadIdx.x; i < n; i += blockDim.x) {
             const int s = static_cast<int>(i / ed.Lv);
             const int t = static_cast<int>(i - static_cast<long long>(s) * ed.Lv);
-            const float r = (tab[ed.toff + static_cast<long long>(s) * ed.ld + t] - msg[ed.mu + s]) - msg[ed.mv + t];
-            m = fminf(m, r);
+            const double r =
+                (static_cast<double>(tab[ed.toff + static_cast<long long>(s) * ed.ld + t]) - msg[ed.mu + s]) -
+                msg[ed.mv + t];
+            m = fmin(m, r);
         }
         m = block_min<kThreads>(m, red);
         if (threadIdx.x == 0) emin[e] = m;
     }
 }
 
-// nmin[u] = min_s theta^phi_u(s)
-__global__ void bound_nodes_kernel(const NodeDesc *nodes, int n_nodes, const float *agg, float *nmin)
+// nmin[u] = min_s theta^phi_u(s)   (FP64)
+__global__ void bound_nodes_kernel(const NodeDesc *nodes, int n_nodes, const double *agg, double *nmin)
 {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     for (int u = warp; u < n_nodes; u += nw) {
         const NodeDesc nd = nodes[u];
-        float m = INFINITY;
-        for (int s = lane; s < nd.L; s += 32) m = fminf(m, agg[nd.aoff + s]);
-        for (int o = 16; o > 0; o >>= 1) m = fminf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        double m = INFINITY;
+        for (int s = lane; s < nd.L; s += 32) m = fmin(m, agg[nd.aoff + s]);
+        for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
         if (lane == 0) nmin[u] = m;
     }
 }
@@ -121,17 +124,17 @@ __device__ double block_sum_fixed(double v, double *red)
 }
 
 __global__ void __launch_bounds__(kThreads) bound_sum_kernel(const int *model_node_off, const int *model_edge_off,
-                                                             const float *nmin, const float *emin, int exact,
+                                                             const double *nmin, const double *emin, int exact,
                                                              double *out)
 {
     __shared__ double red[kThreads];
     const int m = blockIdx.x;
     double acc = 0.0;
     for (int u = model_node_off[m] + threadIdx.x; u < model_node_off[m + 1]; u += kThreads)
-        acc += static_cast<double>(nmin[u]);
+        acc += nmin[u];
     if (exact)
         for (int e = model_edge_off[m] + threadIdx.x; e < model_edge_off[m + 1]; e += kThreads)
-            acc += static_cast<double>(emin[e]);
+            acc += emin[e];
     const double D = block_sum_fixed<kThreads>(acc, red);
     if (threadIdx.x == 0) out[m] = D;
 }
@@ -139,28 +142,29 @@ __global__ void __launch_bounds__(kThreads) bound_sum_kernel(const int *model_no
 // Sequential rounding of one model per CTA: node u's objective over its
 // labels is its reparametrized unary plus, for every earlier neighbour v in
 // increasing order, theta^phi_vu(x_v, s) = (theta_vu(x_v,s) - phi_{u->v}(x_v))
-// - phi_{v->u}(s); FP32 sums in that order, argmin with the lowest index.
+// - phi_{v->u}(s); FP64 sums in that order, argmin with the lowest index.
 __global__ void __launch_bounds__(kThreads) round_kernel(const EdgeDesc *edges, const NodeDesc *nodes,
                                                          const int *in_off, const int *in_edge,
                                                          const int *model_node_off, const float *tab,
-                                                         const float *agg, const float *msg, int *labels,
+                                                         const double *agg, const double *msg, int *labels,
                                                          int *err)
 {
-    __shared__ float rv[32];
+    __shared__ double rv[32];
     __shared__ int ri[32];
     const int m = blockIdx.x;
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     for (int u = model_node_off[m]; u < model_node_off[m + 1]; ++u) {
         const NodeDesc nd = nodes[u];
-        float best = INFINITY;
+        double best = INFINITY;
         int bi = INT_MAX;
         for (int s = threadIdx.x; s < nd.L; s += kThreads) {
-            float acc = agg[nd.aoff + s];
+            double acc = agg[nd.aoff + s];
             for (int k = in_off[u]; k < in_off[u + 1]; ++k) {
                 const EdgeDesc ed = edges[in_edge[k]];
                 const int xv = labels[ed.gu];
-                const float term = (tab[ed.toff + static_cast<long long>(xv) * ed.ld + s] - msg[ed.mu + xv]) -
-                                   msg[ed.mv + s];
+                const double term =
+                    (static_cast<double>(tab[ed.toff + static_cast<long long>(xv) * ed.ld + s]) - msg[ed.mu + xv]) -
+                    msg[ed.mv + s];
                 acc = acc + term;
             }
             if (acc < best) {
@@ -169,7 +173,7 @@ __global__ void __launch_bounds__(kThreads) round_kernel(const EdgeDesc *edges, 
             }
         }
         for (int o = 16; o > 0; o >>= 1) {
-            const float ov = __shfl_xor_sync(0xffffffffu, best, o);
+            const double ov = __shfl_xor_sync(0xffffffffu, best, o);
             const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
             if (ov < best || (ov == best && oi < bi)) {
                 best = ov;
@@ -182,7 +186,7 @@ __global__ void __launch_bounds__(kThreads) round_kernel(const EdgeDesc *edges, 
         }
         __syncthreads();
         if (threadIdx.x == 0) {
-            float b = rv[0];
+            double b = rv[0];
             int i = ri[0];
             for (int j = 1; j < kThreads / 32; ++j)
                 if (rv[j] < b || (rv[j] == b && ri[j] < i)) {
@@ -229,7 +233,7 @@ int grid_for(long long work, int per_block_items)
 }  // namespace
 
 cudaError_t launch_pack(const EdgeDesc *edges, int n_edges, const NodeDesc *nodes, int n_nodes,
-                        const float *unary_src, const float *pair_src, float *tab, float *un0, float *agg, int *err,
+                        const float *unary_src, const float *pair_src, float *tab, float *un0, double *agg, int *err,
                         cudaStream_t st)
 {
     if (n_edges > 0) {
@@ -246,7 +250,7 @@ cudaError_t launch_pack(const EdgeDesc *edges, int n_edges, const NodeDesc *node
 }
 
 cudaError_t launch_bound(const EdgeDesc *edges, int n_edges, const NodeDesc *nodes, int n_nodes, const float *tab,
-                         const float *agg, const float *msg, float *emin, float *nmin, const int *model_node_off,
+                         const double *agg, const double *msg, double *emin, double *nmin, const int *model_node_off,
                          const int *model_edge_off, int n_models, int exact, double *out, cudaStream_t st)
 {
     if (exact && n_edges > 0) {
@@ -265,7 +269,7 @@ cudaError_t launch_bound(const EdgeDesc *edges, int n_edges, const NodeDesc *nod
 
 cudaError_t launch_round(const EdgeDesc *edges, const NodeDesc *nodes, const int *in_off, const int *in_edge,
                          const int *model_node_off, const int *model_edge_off, int n_models, const float *tab,
-                         const float *agg, const float *msg, const float *un0, int *labels, double *energy, int *err,
+                         const double *agg, const double *msg, const float *un0, int *labels, double *energy, int *err,
                          cudaStream_t st)
 {
     round_kernel<<<n_models, kThreads, 0, st>>>(edges, nodes, in_off, in_edge, model_node_off, tab, agg, msg, labels,

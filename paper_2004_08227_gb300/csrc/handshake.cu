@@ -4,15 +4,21 @@
 // message-form state of common.cuh:
 //   uh(s) = agg_u(s) - phi_{v->u}(s),  vh(t) = agg_v(t) - phi_{u->v}(t)
 //           (the unaries without this edge's messages; g = theta_uv + uh + vh)
-//   a(s)  = 1/2 (min_t [theta_uv(s,t) + vh(t)] + uh(s))        = 1/2 min_t g(s,t)
+//   a(s)  = 1/2 (min_t [theta_uv(s,t) + (vh(t) - vh(0))] + vh(0) + uh(s))
+//                                                               = 1/2 min_t g(s,t)
 //   alpha(s) = uh(s) - a(s)
 //   b(t)  = min_s [theta_uv(s,t) + alpha(s)] + vh(t)            = min_s [g(s,t) - a(s)]
 //   beta(t) = vh(t) - b(t)
 //   c(s)  = min_t [theta_uv(s,t) + beta(t)] + uh(s)             = min_t [g(s,t) - b(t)]
 //   agg_u := c, phi_{v->u} := c - uh;  agg_v := b, phi_{u->v} := b - vh.
-// The pairwise table is only read (4 B per entry, once from HBM); all three
-// minimizations run on the copy staged in shared memory.  Min-plus is not a
-// dense contraction, so this is FP32 ALU work bound by HBM bandwidth.
+// Precision: the O(L) state and vector arithmetic are FP64 (reparametrized
+// unaries grow to large magnitudes, where FP32 rounding would accumulate over
+// thousands of updates); the O(L^2) minimizations run in FP32 on the table
+// and on small quantities (vh shifted by vh(0), alpha, beta), rounded to FP32
+// once per update.  The pairwise table is only read (4 B per entry, once from
+// HBM); all three minimizations run on the copy staged in shared memory.
+// Min-plus is not a dense contraction, so this is FP32 ALU work bound by HBM
+// bandwidth.
 //
 // Mapping: a cluster of C CTAs shares one edge; CTA `rank` owns the rows
 // [rank*R, rank*R + R) (R = ceil(L_u / C)), loaded with one bulk asynchronous
@@ -44,23 +50,28 @@ namespace mplpp {
 namespace {
 
 struct Smem {
-    float *tile;      // nbuf buffers of tile_floats each
-    float *uh, *alpha, *vh, *beta, *bv, *pm;
+    float *tile;        // nbuf buffers of tile_floats each
+    double *uh, *vh;    // FP64 unaries without this edge's messages
+    double *bv;         // FP64 new vector of node v
+    float *w1;          // vh(t) - vh(0) in FP32 (pass 1)
+    float *alpha, *beta, *pm;
     float4 *part;
-    uint64_t *bar;  // [2]
+    uint64_t *bar;      // [2]
 };
 
 __device__ __forceinline__ Smem carve(char *base, const HsParams &p, int nbuf)
 {
-    float *f = reinterpret_cast<float *>(base);
     Smem s;
+    double *d = reinterpret_cast<double *>(base);
+    s.uh = d; d += p.rmax;
+    s.vh = d; d += p.ldmax;
+    s.bv = d; d += p.ldmax;
+    float *f = reinterpret_cast<float *>(d);
     s.tile = f;
     f += static_cast<size_t>(nbuf) * p.tile_floats;
-    s.uh = f; f += p.rmax;
+    s.w1 = f; f += p.ldmax;
     s.alpha = f; f += p.rmax;
-    s.vh = f; f += p.ldmax;
     s.beta = f; f += p.ldmax;
-    s.bv = f; f += p.ldmax;
     s.pm = f; f += static_cast<size_t>(nbuf) * p.ldmax * p.C;  // [item parity][CTA of the cluster][column]
     s.part = reinterpret_cast<float4 *>(f); f += 4 * blockDim.x;
     s.bar = reinterpret_cast<uint64_t *>(f);
@@ -117,16 +128,31 @@ __device__ __forceinline__ void signal_node(unsigned *ver, int g, unsigned n)
     asm volatile("red.relaxed.gpu.global.add.u32 [%0], %1;" ::"l"(ver + g), "r"(n) : "memory");
 }
 
+// Bounded wait (one thread) until node g's counter reaches `need`.
+__device__ __forceinline__ void wait_node(const HsParams &p, int g, unsigned need)
+{
+    long long spins = 0;
+    for (;;) {
+        if (ld_acquire_u32(p.ver + g) >= need) return;
+        if (*reinterpret_cast<volatile int *>(p.err) != 0) return;  // draining after an error
+        if (++spins > p.spin_limit) {
+            set_err(p.err, ERR_TIMEOUT);
+            return;
+        }
+        if (spins > 4096) __nanosleep(64);
+    }
+}
+
 // min_t [row(t) + w(t)] over this lane's chunks q = lg, lg + G, ... (two chains)
 __device__ __forceinline__ float row_min(const float4 *row, const float4 *w, int Q, int lg, int G)
 {
     float m0 = INFINITY, m1 = INFINITY;
     int q = lg;
     for (; q + G < Q; q += 2 * G) {
-        m0 = fminf(m0, hmin_add(row[q], w[q]));
-        m1 = fminf(m1, hmin_add(row[q + G], w[q + G]));
+        m0 = min_add4(m0, row[q], w[q]);
+        m1 = min_add4(m1, row[q + G], w[q + G]);
     }
-    if (q < Q) m0 = fminf(m0, hmin_add(row[q], w[q]));
+    if (q < Q) m0 = min_add4(m0, row[q], w[q]);
     return fminf(m0, m1);
 }
 
@@ -141,25 +167,43 @@ __device__ __forceinline__ void group_min(float &m, int G)
 // SIGNAL: publish completion on the node counters (persistent driver).
 template <bool CLUSTER, bool SIGNAL>
 __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile, const Smem &sm, int rank,
-                        uint64_t *bar, uint32_t parity, int xpar)
+                        uint64_t *bar, uint32_t parity, int xpar, unsigned need_u = 0, unsigned need_v = 0)
 {
     const int T = blockDim.x, tid = threadIdx.x;
     const int C = CLUSTER ? p.C : 1;
     int r0, nr;
     rows_of(ed, rank, C, r0, nr);
     const int ld = ed.ld, Q = ld >> 2, Lv = ed.Lv;
-    float *agg = p.agg;
-    float *msg = p.msg;
+    double *agg = p.agg;
+    double *msg = p.msg;
 
-    // unaries without this edge's messages (written by other SMs: L2 loads)
-    for (int s = tid; s < nr; s += T)
-        sm.uh[s] = __ldcg(agg + ed.au + r0 + s) - __ldcg(msg + ed.mu + r0 + s);
-    for (int q = tid; q < (ld >> 2); q += T) {  // node vectors start 16-byte aligned
-        const float4 a = __ldcg(reinterpret_cast<const float4 *>(agg + ed.av) + q);
-        const float4 f = __ldcg(reinterpret_cast<const float4 *>(msg + ed.mv) + q);
-        const int t = 4 * q;
-        reinterpret_cast<float4 *>(sm.vh)[q] = make_float4(t < Lv ? a.x - f.x : 0.f, t + 1 < Lv ? a.y - f.y : 0.f,
-                                                           t + 2 < Lv ? a.z - f.z : 0.f, t + 3 < Lv ? a.w - f.w : 0.f);
+    // unaries without this edge's messages (written by other SMs: L2 loads).
+    // Persistent driver: warp 0 waits for node v's earlier updates and loads
+    // vh, warp 1 does the same for node u, so the two waits overlap.
+    {
+        const int warp = tid >> 5, lane = tid & 31;
+        const bool do_v = SIGNAL ? warp == 0 : true;
+        const bool do_u = SIGNAL ? warp == 1 : true;
+        const int s0 = SIGNAL ? lane : tid, st = SIGNAL ? 32 : T;
+        if (SIGNAL && (warp == 0 || warp == 1)) {
+            if (lane == 0) wait_node(p, warp == 0 ? ed.gv : ed.gu, warp == 0 ? need_v : need_u);
+            __syncwarp();
+        }
+        if (do_u)
+            for (int s = s0; s < nr; s += st)
+                sm.uh[s] = __ldcg(agg + ed.au + r0 + s) - __ldcg(msg + ed.mu + r0 + s);
+        if (do_v) {
+            const double vref = __ldcg(agg + ed.av) - __ldcg(msg + ed.mv);
+            for (int q = s0; q < (ld >> 1); q += st) {  // node vectors start 32-byte aligned
+                const double2 a = __ldcg(reinterpret_cast<const double2 *>(agg + ed.av) + q);
+                const double2 f = __ldcg(reinterpret_cast<const double2 *>(msg + ed.mv) + q);
+                const int t = 2 * q;
+                const double v0 = a.x - f.x, v1 = a.y - f.y;
+                reinterpret_cast<double2 *>(sm.vh)[q] = make_double2(t < Lv ? v0 : 0.0, t + 1 < Lv ? v1 : 0.0);
+                reinterpret_cast<float2 *>(sm.w1)[q] = make_float2(t < Lv ? static_cast<float>(v0 - vref) : 0.f,
+                                                                   t + 1 < Lv ? static_cast<float>(v1 - vref) : 0.f);
+            }
+        }
     }
 
     if (!mbar_wait(bar, parity, p.spin_limit)) set_err(p.err, ERR_TIMEOUT);
@@ -170,18 +214,20 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
     const int gid = tid / G, lg = tid % G, ng = T / G;
     float *xbuf = sm.pm + static_cast<size_t>(xpar) * C * ld;  // this item's exchange slots
 
-    // pass 1: a(s) = 1/2 (min_t [theta(s,t) + vh(t)] + uh(s));  alpha = uh - a
+    // pass 1: a(s) = 1/2 (min_t [theta(s,t) + w1(t)] + vh(0) + uh(s));  alpha = uh - a
     {
-        const float4 *w = reinterpret_cast<const float4 *>(sm.vh);
+        const float4 *w = reinterpret_cast<const float4 *>(sm.w1);
+        const double vref = sm.vh[0];
+        auto emit = [&](int s, float m) {
+            const double u = sm.uh[s];
+            const double a = 0.5 * ((static_cast<double>(m) + vref) + u);
+            sm.alpha[s] = static_cast<float>(u - a);
+        };
         for (int base = 0; base < nr; base += ng) {
             const int s = base + gid;
             float m = s < nr ? row_min(t4 + static_cast<size_t>(s) * Q, w, Q, lg, G) : INFINITY;
             group_min(m, G);
-            if (s < nr && lg == 0) {
-                const float u = sm.uh[s];
-                const float a = 0.5f * (m + u);
-                sm.alpha[s] = u - a;
-            }
+            if (s < nr && lg == 0) emit(s, m);
         }
     }
     __syncthreads();
@@ -194,13 +240,17 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
         if (nsub >= 1) {
             if (tid < nsub * Q) {
                 const int q = tid % Q, sub = tid / Q;
-                float4 m = make_float4(INFINITY, INFINITY, INFINITY, INFINITY), m2 = m;
-                for (int s = sub; s < nr; s += 2 * nsub) {
-                    m = min4(m, add4s(t4[static_cast<size_t>(s) * Q + q], sm.alpha[s]));
-                    const int s2 = s + nsub;
-                    if (s2 < nr) m2 = min4(m2, add4s(t4[static_cast<size_t>(s2) * Q + q], sm.alpha[s2]));
+                float4 m = make_float4(INFINITY, INFINITY, INFINITY, INFINITY);
+                int s = sub;
+                for (; s + nsub < nr; s += 2 * nsub) {  // two rows per step: packed adds, 3-input mins
+                    const float a1 = sm.alpha[s], a2 = sm.alpha[s + nsub];
+                    const float4 v1 = add4(t4[static_cast<size_t>(s) * Q + q], make_float4(a1, a1, a1, a1));
+                    const float4 v2 = add4(t4[static_cast<size_t>(s + nsub) * Q + q], make_float4(a2, a2, a2, a2));
+                    m = make_float4(min3f(m.x, v1.x, v2.x), min3f(m.y, v1.y, v2.y), min3f(m.z, v1.z, v2.z),
+                                    min3f(m.w, v1.w, v2.w));
                 }
-                sm.part[sub * Q + q] = min4(m, m2);
+                if (s < nr) m = min4(m, add4s(t4[static_cast<size_t>(s) * Q + q], sm.alpha[s]));
+                sm.part[sub * Q + q] = m;
             }
             __syncthreads();
         }
@@ -231,12 +281,15 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
     }
     for (int t = tid; t < ld; t += T) {
         float m = xbuf[t];
-        if (CLUSTER)
-            for (int r = 1; r < C; ++r) m = fminf(m, xbuf[r * ld + t]);
-        const float vh = sm.vh[t];
-        const float b = m + vh;
-        sm.bv[t] = t < Lv ? b : 0.f;
-        sm.beta[t] = t < Lv ? vh - b : 0.f;
+        if (CLUSTER) {
+            int r = 1;
+            for (; r + 1 < C; r += 2) m = min3f(m, xbuf[r * ld + t], xbuf[(r + 1) * ld + t]);
+            if (r < C) m = fminf(m, xbuf[r * ld + t]);
+        }
+        const double vh = sm.vh[t];
+        const double b = static_cast<double>(m) + vh;
+        sm.bv[t] = t < Lv ? b : 0.0;
+        sm.beta[t] = t < Lv ? static_cast<float>(vh - b) : 0.f;
     }
     // The slots of this parity are written again two items later, after every
     // CTA has passed the next item's exchange barrier, i.e. after this read.
@@ -245,7 +298,7 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
     // node v's new vector (one CTA of the cluster), published before pass 3
     if (rank == 0) {
         for (int t = tid; t < Lv; t += T) {
-            const float b = sm.bv[t];
+            const double b = sm.bv[t];
             __stcg(agg + ed.av + t, b);
             __stcg(msg + ed.mv + t, b - sm.vh[t]);
         }
@@ -258,16 +311,17 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
     // pass 3: c(s) = min_t [theta(s,t) + beta(t)] + uh(s); write node u's rows
     {
         const float4 *w = reinterpret_cast<const float4 *>(sm.beta);
+        auto emit = [&](int s, float m) {
+            const double u = sm.uh[s];
+            const double c = static_cast<double>(m) + u;
+            __stcg(agg + ed.au + r0 + s, c);
+            __stcg(msg + ed.mu + r0 + s, c - u);
+        };
         for (int base = 0; base < nr; base += ng) {
             const int s = base + gid;
             float m = s < nr ? row_min(t4 + static_cast<size_t>(s) * Q, w, Q, lg, G) : INFINITY;
             group_min(m, G);
-            if (s < nr && lg == 0) {
-                const float u = sm.uh[s];
-                const float c = m + u;
-                __stcg(agg + ed.au + r0 + s, c);
-                __stcg(msg + ed.mu + r0 + s, c - u);
-            }
+            if (s < nr && lg == 0) emit(s, m);
         }
     }
     __syncthreads();
@@ -293,22 +347,6 @@ __global__ void __launch_bounds__(512) hs_looped_kernel(HsParams p)
         cluster_wait_acquire();
     }
     hs_item<CLUSTER, false>(p, ed, sm.tile, sm, rank, &sm.bar[0], 0u, 0);
-}
-
-__device__ __forceinline__ void wait_nodes(const HsParams &p, int gu, unsigned need_u, int gv, unsigned need_v)
-{
-    long long spins = 0;
-    for (;;) {
-        const unsigned a = ld_acquire_u32(p.ver + gu);
-        const unsigned b = ld_acquire_u32(p.ver + gv);
-        if (a >= need_u && b >= need_v) return;
-        if (*reinterpret_cast<volatile int *>(p.err) != 0) return;  // draining after an error
-        if (++spins > p.spin_limit) {
-            set_err(p.err, ERR_TIMEOUT);
-            return;
-        }
-        if (spins > 4096) __nanosleep(64);
-    }
 }
 
 template <bool CLUSTER>
@@ -346,17 +384,13 @@ __global__ void __launch_bounds__(512) hs_persistent_kernel(HsParams p)
                 issue_tile(p.edges[p.work[begin + inext].edge], rank, C, p.tab, sm.tile + b * p.tile_floats,
                            sm.bar + b);
             }
-            const unsigned need_u = static_cast<unsigned>(C) *
-                                        static_cast<unsigned>(it * w.deg_u + w.pos_u) +
-                                    ((p.test_wait && k == 0 && cid == 0) ? 1u : 0u);
-            const unsigned need_v = static_cast<unsigned>(C) *
-                                    static_cast<unsigned>(it * w.deg_v + w.pos_v);
-            wait_nodes(p, ed.gu, need_u, ed.gv, need_v);
         }
-        __syncthreads();
+        const unsigned need_u = static_cast<unsigned>(C) * static_cast<unsigned>(it * w.deg_u + w.pos_u) +
+                                ((p.test_wait && k == 0 && cid == 0) ? 1u : 0u);
+        const unsigned need_v = static_cast<unsigned>(C) * static_cast<unsigned>(it * w.deg_v + w.pos_v);
         const int b = static_cast<int>(k & 1);
         hs_item<CLUSTER, true>(p, ed, sm.tile + b * p.tile_floats, sm, rank, sm.bar + b,
-                               static_cast<uint32_t>((k >> 1) & 1), b);
+                               static_cast<uint32_t>((k >> 1) & 1), b, need_u, need_v);
         if (++i == n) {
             i = 0;
             ++it;
@@ -399,10 +433,11 @@ cudaError_t launch(K kernel, const HsParams &p, int grid, int threads, size_t sm
 
 size_t hs_smem_bytes(int nbuf, int tile_floats, int rmax, int ldmax, int threads, int C)
 {
-    // tiles, uh, alpha, vh, beta, bv, pm (nbuf x C slots), part (float4 x T), 2 mbarriers
-    size_t f = static_cast<size_t>(nbuf) * tile_floats + 2 * static_cast<size_t>(rmax) +
-               (3 + static_cast<size_t>(nbuf) * C) * static_cast<size_t>(ldmax) + 4 * static_cast<size_t>(threads);
-    return f * 4 + 16;
+    // FP64 uh, vh, bv; FP32 tiles, w1, alpha, beta, pm (nbuf x C slots), part (float4 x T); 2 mbarriers
+    const size_t d = static_cast<size_t>(rmax) + 2 * static_cast<size_t>(ldmax);
+    const size_t f = static_cast<size_t>(nbuf) * tile_floats + static_cast<size_t>(rmax) +
+                     (2 + static_cast<size_t>(nbuf) * C) * static_cast<size_t>(ldmax) + 4 * static_cast<size_t>(threads);
+    return d * 8 + f * 4 + 16;
 }
 
 cudaError_t hs_prepare(size_t smem)

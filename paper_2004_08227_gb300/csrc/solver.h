@@ -54,13 +54,14 @@ struct mplpp_solver {
     std::vector<void *> allocations;
     mplpp::EdgeDesc *d_edges = nullptr;
     mplpp::NodeDesc *d_nodes = nullptr;
-    float *d_tab = nullptr, *d_agg = nullptr, *d_msg = nullptr, *d_un0 = nullptr;
+    float *d_tab = nullptr, *d_un0 = nullptr;
+    double *d_agg = nullptr, *d_msg = nullptr;  // FP64 state
     int *d_phase_edges = nullptr, *d_err = nullptr;
     unsigned *d_ver = nullptr;
     int *d_work_off = nullptr;
     mplpp::WorkItem *d_work = nullptr;
     int *d_in_off = nullptr, *d_in_edge = nullptr, *d_mnode_off = nullptr, *d_medge_off = nullptr;
-    float *d_emin = nullptr, *d_nmin = nullptr;
+    double *d_emin = nullptr, *d_nmin = nullptr;
     double *d_out = nullptr, *d_energy = nullptr;
     int *d_labels = nullptr;
 

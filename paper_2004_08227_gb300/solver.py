@@ -212,17 +212,17 @@ class Solver:
         self._check(self._lib.mplpp_load_state(self._h, buf, len(data)))
 
     def state_arrays(self):
-        """(iterations, agg [sum L] float32, msg [sum (L_u + L_v)] float32)."""
+        """(iterations, agg [sum L] float64, msg [sum (L_u + L_v)] float64)."""
         raw = self.save_state()
         h = _lib.MplppStateHeader.from_buffer_copy(raw[:ctypes.sizeof(_lib.MplppStateHeader)])
-        f = np.frombuffer(raw[ctypes.sizeof(_lib.MplppStateHeader):], dtype=np.float32)
+        f = np.frombuffer(raw[ctypes.sizeof(_lib.MplppStateHeader):], dtype=np.float64)
         return int(h.iterations), f[:h.n_unary].copy(), f[h.n_unary:h.n_unary + h.n_msg].copy()
 
     def set_state(self, agg, msg, iterations: int = 0):
         raw = bytearray(self.save_state())
         h = _lib.MplppStateHeader.from_buffer_copy(bytes(raw[:ctypes.sizeof(_lib.MplppStateHeader)]))
         h.iterations = int(iterations)
-        body = np.concatenate([np.asarray(agg, np.float32), np.asarray(msg, np.float32)]).tobytes()
+        body = np.concatenate([np.asarray(agg, np.float64), np.asarray(msg, np.float64)]).tobytes()
         self.load_state(bytes(h) + body)
 
     def info(self) -> dict:

@@ -50,11 +50,11 @@ class Model:
 
     def bytes_per_iteration(self) -> int:
         """Algorithmic HBM bytes of one iteration of the message-form update:
-        each table read once (4 B/entry) + agg and message vectors read and
-        written (16 B per label of each endpoint)."""
+        each FP32 table read once (4 B/entry) + the FP64 agg and message
+        vectors read and written (32 B per label of each endpoint)."""
         Lu = self.labels[self.edge_u].astype(np.int64)
         Lv = self.labels[self.edge_v].astype(np.int64)
-        return int(np.sum(4 * Lu * Lv + 16 * (Lu + Lv)))
+        return int(np.sum(4 * Lu * Lv + 32 * (Lu + Lv)))
 
 
 def _complete_edges(n: int):

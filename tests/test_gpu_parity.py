@@ -187,30 +187,31 @@ def test_checkpoint_resume_bitwise():
     assert a.bound()[0] == c.bound()[0]
 
 
-def test_rounding_fp32_decisions_match_oracle():
-    """Rounding from a given FP32 state: both sides take every argmin decision
-    in binary32 with the same summation order, so labels must be identical."""
+def test_rounding_decisions_match_oracle_bit_for_bit():
+    """Rounding from a given state: both sides take every argmin decision in
+    binary64 with the same summation order (unary, then earlier neighbours by
+    increasing index), so the labels must be identical."""
     rng = np.random.default_rng(0)
     for seed in range(4):
         m = W.uneven_complete(12, 2, 33, seed=100 + seed)
         s = Solver([m])
-        agg = rng.standard_normal(int(m.labels.sum())).astype(np.float32)
+        agg = rng.standard_normal(int(m.labels.sum()))
         g = oracle.Graph.of(m)
         Lu = m.labels[m.edge_u]
         Lv = m.labels[m.edge_v]
-        msg = rng.standard_normal(int((Lu + Lv).sum())).astype(np.float32)
+        msg = rng.standard_normal(int((Lu + Lv).sum()))
         s.set_state(agg, msg)
         xg, _ = s.labeling()
-        # theta^phi_uv = (theta_uv - phi_{v->u}) - phi_{u->v} in binary32 (eq. reparametrization)
-        th_uv = np.empty_like(m.pairwise)
+        # theta^phi_uv = (theta_uv - phi_{v->u}) - phi_{u->v} (eq. reparametrization), binary64
+        th_uv = np.empty(m.pairwise.shape, np.float64)
         k = 0
         for e in range(m.E):
             pu = msg[k:k + Lu[e]]
             pv = msg[k + Lu[e]:k + Lu[e] + Lv[e]]
             k += Lu[e] + Lv[e]
-            t = g.table(m.pairwise, e).astype(np.float32)
+            t = g.table(m.pairwise, e).astype(np.float64)
             th_uv[g.poff[e]:g.poff[e + 1]] = ((t - pu[:, None]) - pv[None, :]).ravel()
-        xo = oracle.round_labels_f32(m, agg, th_uv)
+        xo = oracle.round_labels(m, agg, th_uv)
         assert np.array_equal(xg, xo)
 
 
