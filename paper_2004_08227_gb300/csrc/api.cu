@@ -402,7 +402,7 @@ extern "C" mplpp_status mplpp_create(const mplpp_model *models, int32_t n_models
         CKC(h2d(S->d_work, S->work.data(), S->work.size() * sizeof(WorkItem)));
     }
     CKC(cudaMemsetAsync(S->d_err, 0, sizeof(int), st));
-    CKC(cudaMemsetAsync(S->d_msg, 0, S->msgN * sizeof(double), st));
+    CKC(cudaMemsetAsync(S->d_msg, 0, S->msgN * sizeof(float2), st));
 
     // costs: stage (host inputs) or read in place (device inputs), then pack
     float *stage_u = nullptr, *stage_p = nullptr;
@@ -614,8 +614,7 @@ extern "C" mplpp_status mplpp_reset(mplpp_solver *s)
 {
     if (!s) return MPLPP_E_INVALID;
     s->err.clear();
-    CK(s, cudaMemsetAsync(s->d_msg, 0, s->msgN * sizeof(double), s->stream));
-    CK(s, launch_widen(s->d_un0, s->d_agg, s->aggN, s->stream));
+    CK(s, launch_init_state(s->d_un0, s->d_agg, s->aggN, s->d_msg, s->msgN, s->stream));
     s->iterations = 0;
     s->history_valid = true;
     return MPLPP_OK;
@@ -635,9 +634,9 @@ extern "C" mplpp_status mplpp_save_state(mplpp_solver *s, void *buf, size_t size
     size_t need = 0;
     mplpp_state_size(s, &need);
     if (size < need) return fail(s, MPLPP_E_INVALID, "state buffer too small");
-    std::vector<double> agg(s->aggN), msg(s->msgN);
-    CK(s, cudaMemcpyAsync(agg.data(), s->d_agg, s->aggN * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
-    CK(s, cudaMemcpyAsync(msg.data(), s->d_msg, s->msgN * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    std::vector<float2> agg(s->aggN), msg(s->msgN);
+    CK(s, cudaMemcpyAsync(agg.data(), s->d_agg, s->aggN * sizeof(float2), cudaMemcpyDeviceToHost, s->stream));
+    CK(s, cudaMemcpyAsync(msg.data(), s->d_msg, s->msgN * sizeof(float2), cudaMemcpyDeviceToHost, s->stream));
     mplpp_status st = mplpp_sync(s);
     if (st != MPLPP_OK) return st;
     mplpp_state_header h;
@@ -649,16 +648,15 @@ extern "C" mplpp_status mplpp_save_state(mplpp_solver *s, void *buf, size_t size
     h.n_msg = s->sum_msg;
     char *p = static_cast<char *>(buf);
     std::memcpy(p, &h, sizeof(h));
+    // portable format: FP64 values hi + lo (exact)
     double *f = reinterpret_cast<double *>(p + sizeof(h));
-    for (auto &nd : s->h_nodes) {
-        std::memcpy(f, agg.data() + nd.aoff, sizeof(double) * nd.L);
-        f += nd.L;
-    }
+    auto put = [&](const float2 *src, int n) {
+        for (int i = 0; i < n; ++i) *f++ = static_cast<double>(src[i].x) + static_cast<double>(src[i].y);
+    };
+    for (auto &nd : s->h_nodes) put(agg.data() + nd.aoff, nd.L);
     for (auto &ed : s->h_edges) {
-        std::memcpy(f, msg.data() + ed.mu, sizeof(double) * ed.Lu);
-        f += ed.Lu;
-        std::memcpy(f, msg.data() + ed.mv, sizeof(double) * ed.Lv);
-        f += ed.Lv;
+        put(msg.data() + ed.mu, ed.Lu);
+        put(msg.data() + ed.mv, ed.Lv);
     }
     return MPLPP_OK;
 }
@@ -675,24 +673,28 @@ extern "C" mplpp_status mplpp_load_state(mplpp_solver *s, const void *buf, size_
     if (h.magic != 0x4D504C50u || h.version != 2 || h.shape_hash != s->shape_hash || h.n_unary != s->sum_unary ||
         h.n_msg != s->sum_msg)
         return fail(s, MPLPP_E_INVALID, "state does not match this solver's models");
-    std::vector<double> agg(s->aggN, 0.0), msg(s->msgN, 0.0);
+    std::vector<float2> agg(s->aggN, make_float2(0.f, 0.f)), msg(s->msgN, make_float2(0.f, 0.f));
     const double *f = reinterpret_cast<const double *>(static_cast<const char *>(buf) + sizeof(h));
+    // FP64 value -> hi = nearest float, lo = nearest float to the remainder
+    auto get = [&](float2 *dst, int n) {
+        for (int i = 0; i < n; ++i, ++f) {
+            const float hi = static_cast<float>(*f);
+            dst[i] = make_float2(hi, static_cast<float>(*f - static_cast<double>(hi)));
+        }
+    };
     for (auto &nd : s->h_nodes) {
         for (int i = 0; i < nd.L; ++i)
-            if (!std::isfinite(f[i])) return fail(s, MPLPP_E_INVALID, "state values must be finite");
-        std::memcpy(agg.data() + nd.aoff, f, sizeof(double) * nd.L);
-        f += nd.L;
+            if (!std::isfinite(f[i]) || std::fabs(f[i]) > 1e37) return fail(s, MPLPP_E_INVALID, "state values must be finite");
+        get(agg.data() + nd.aoff, nd.L);
     }
     for (auto &ed : s->h_edges) {
         for (int i = 0; i < ed.Lu + ed.Lv; ++i)
-            if (!std::isfinite(f[i])) return fail(s, MPLPP_E_INVALID, "state values must be finite");
-        std::memcpy(msg.data() + ed.mu, f, sizeof(double) * ed.Lu);
-        f += ed.Lu;
-        std::memcpy(msg.data() + ed.mv, f, sizeof(double) * ed.Lv);
-        f += ed.Lv;
+            if (!std::isfinite(f[i]) || std::fabs(f[i]) > 1e37) return fail(s, MPLPP_E_INVALID, "state values must be finite");
+        get(msg.data() + ed.mu, ed.Lu);
+        get(msg.data() + ed.mv, ed.Lv);
     }
-    CK(s, cudaMemcpyAsync(s->d_agg, agg.data(), s->aggN * sizeof(double), cudaMemcpyHostToDevice, s->stream));
-    CK(s, cudaMemcpyAsync(s->d_msg, msg.data(), s->msgN * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+    CK(s, cudaMemcpyAsync(s->d_agg, agg.data(), s->aggN * sizeof(float2), cudaMemcpyHostToDevice, s->stream));
+    CK(s, cudaMemcpyAsync(s->d_msg, msg.data(), s->msgN * sizeof(float2), cudaMemcpyHostToDevice, s->stream));
     CK(s, cudaStreamSynchronize(s->stream));
     s->iterations = h.iterations;
     s->history_valid = false;

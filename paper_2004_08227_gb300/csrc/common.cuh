@@ -180,6 +180,55 @@ __device__ __forceinline__ float hmin_add(float4 x, float4 w)
     return fminf(fminf(x.x + w.x, x.y + w.y), fminf(x.z + w.z, x.w + w.w));
 }
 
+// ----------------------------------------------------------------------------
+// Double-float ("df") numbers: value = hi + lo with |lo| <= ulp(hi) / 2, kept
+// as a float2 {hi, lo}.  About 44 bits of precision from FP32 operations only
+// (GB300's FP64 units are slow; its FP32 units are not).  Sums use the
+// error-free transformations of Knuth (two-sum) and Dekker (fast two-sum).
+// FP32 adds are never reassociated here (no fast-math), which these rely on.
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ float2 df_renorm(float s, float e)  // |s| >= |e| (fast two-sum)
+{
+    const float h = s + e;
+    return make_float2(h, e - (h - s));
+}
+
+__device__ __forceinline__ float2 df_add(float2 a, float2 b)
+{
+    const float s = a.x + b.x;
+    const float bb = s - a.x;
+    const float e = ((a.x - (s - bb)) + (b.x - bb)) + (a.y + b.y);
+    return df_renorm(s, e);
+}
+
+__device__ __forceinline__ float2 df_add_f(float2 a, float b)
+{
+    const float s = a.x + b;
+    const float bb = s - a.x;
+    const float e = ((a.x - (s - bb)) + (b - bb)) + a.y;
+    return df_renorm(s, e);
+}
+
+__device__ __forceinline__ float2 df_sub(float2 a, float2 b)
+{
+    return df_add(a, make_float2(-b.x, -b.y));
+}
+
+__device__ __forceinline__ float2 df_half(float2 a)  // exact
+{
+    return make_float2(0.5f * a.x, 0.5f * a.y);
+}
+
+__device__ __forceinline__ float df_to_f(float2 a)
+{
+    return a.x + a.y;
+}
+
+__device__ __forceinline__ double df_to_d(float2 a)
+{
+    return static_cast<double>(a.x) + static_cast<double>(a.y);
+}
+
 // Three-input minimum (one instruction on sm_100+); same value as two fminf.
 __device__ __forceinline__ float min3f(float a, float b, float c)
 {

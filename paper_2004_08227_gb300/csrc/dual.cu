@@ -14,8 +14,8 @@ namespace {
 constexpr int kThreads = 256;
 
 // Copies the caller's row-major tables into the padded layout (row stride ld,
-// pad +inf) and the unaries into un0 (FP32) and agg (FP64), pad 0.  Flags
-// non-finite costs.
+// pad +inf) and the unaries into un0 (FP32) and agg (double-float), pad 0.
+// Flags non-finite costs.
 __global__ void pack_tables_kernel(const EdgeDesc *edges, int n_edges, const float *src, float *tab, int *err)
 {
     for (int e = blockIdx.x; e < n_edges; e += gridDim.x) {
@@ -34,7 +34,7 @@ __global__ void pack_tables_kernel(const EdgeDesc *edges, int n_edges, const flo
     }
 }
 
-__global__ void pack_unary_kernel(const NodeDesc *nodes, int n_nodes, const float *src, float *un0, double *agg,
+__global__ void pack_unary_kernel(const NodeDesc *nodes, int n_nodes, const float *src, float *un0, float2 *agg,
                                   int *err)
 {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -50,7 +50,7 @@ __global__ void pack_unary_kernel(const NodeDesc *nodes, int n_nodes, const floa
                 if (!isfinite(v)) atomicCAS(err, 0, ERR_NONFINITE);
             }
             un0[nd.aoff + s] = v;
-            agg[nd.aoff + s] = static_cast<double>(v);
+            agg[nd.aoff + s] = make_float2(v, 0.f);
         }
     }
 }
@@ -72,7 +72,7 @@ __device__ __forceinline__ double block_min(double v, double *red)
 
 // emin[e] = min_{s,t} (theta_uv(s,t) - phi_{v->u}(s)) - phi_{u->v}(t)   (FP64)
 __global__ void __launch_bounds__(kThreads) bound_edges_kernel(const EdgeDesc *edges, int n_edges,
-                                                               const float *tab, const double *msg, double *emin)
+                                                               const float *tab, const float2 *msg, double *emin)
 {
     __shared__ double red[32];
     for (int e = blockIdx.x; e < n_edges; e += gridDim.x) {
@@ -83,8 +83,8 @@ __global__ void __launch_bounds__(kThreads) bound_edges_kernel(const EdgeDesc *e
             const int s = static_cast<int>(i / ed.Lv);
             const int t = static_cast<int>(i - static_cast<long long>(s) * ed.Lv);
             const double r =
-                (static_cast<double>(tab[ed.toff + static_cast<long long>(s) * ed.ld + t]) - msg[ed.mu + s]) -
-                msg[ed.mv + t];
+                (static_cast<double>(tab[ed.toff + static_cast<long long>(s) * ed.ld + t]) - df_to_d(msg[ed.mu + s])) -
+                df_to_d(msg[ed.mv + t]);
             m = fmin(m, r);
         }
         m = block_min<kThreads>(m, red);
@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(kThreads) bound_edges_kernel(const EdgeDesc *e
 }
 
 // nmin[u] = min_s theta^phi_u(s)   (FP64)
-__global__ void bound_nodes_kernel(const NodeDesc *nodes, int n_nodes, const double *agg, double *nmin)
+__global__ void bound_nodes_kernel(const NodeDesc *nodes, int n_nodes, const float2 *agg, double *nmin)
 {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -101,7 +101,7 @@ __global__ void bound_nodes_kernel(const NodeDesc *nodes, int n_nodes, const dou
     for (int u = warp; u < n_nodes; u += nw) {
         const NodeDesc nd = nodes[u];
         double m = INFINITY;
-        for (int s = lane; s < nd.L; s += 32) m = fmin(m, agg[nd.aoff + s]);
+        for (int s = lane; s < nd.L; s += 32) m = fmin(m, df_to_d(agg[nd.aoff + s]));
         for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
         if (lane == 0) nmin[u] = m;
     }
@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(kThreads) bound_sum_kernel(const int *model_no
 __global__ void __launch_bounds__(kThreads) round_kernel(const EdgeDesc *edges, const NodeDesc *nodes,
                                                          const int *in_off, const int *in_edge,
                                                          const int *model_node_off, const float *tab,
-                                                         const double *agg, const double *msg, int *labels,
+                                                         const float2 *agg, const float2 *msg, int *labels,
                                                          int *err)
 {
     __shared__ double rv[32];
@@ -158,13 +158,14 @@ __global__ void __launch_bounds__(kThreads) round_kernel(const EdgeDesc *edges, 
         double best = INFINITY;
         int bi = INT_MAX;
         for (int s = threadIdx.x; s < nd.L; s += kThreads) {
-            double acc = agg[nd.aoff + s];
+            double acc = df_to_d(agg[nd.aoff + s]);
             for (int k = in_off[u]; k < in_off[u + 1]; ++k) {
                 const EdgeDesc ed = edges[in_edge[k]];
                 const int xv = labels[ed.gu];
                 const double term =
-                    (static_cast<double>(tab[ed.toff + static_cast<long long>(xv) * ed.ld + s]) - msg[ed.mu + xv]) -
-                    msg[ed.mv + s];
+                    (static_cast<double>(tab[ed.toff + static_cast<long long>(xv) * ed.ld + s]) -
+                     df_to_d(msg[ed.mu + xv])) -
+                    df_to_d(msg[ed.mv + s]);
                 acc = acc + term;
             }
             if (acc < best) {
@@ -222,6 +223,16 @@ __global__ void __launch_bounds__(kThreads) energy_kernel(const EdgeDesc *edges,
     if (threadIdx.x == 0) energy[m] = En;
 }
 
+// agg := (un0, 0), msg := 0: the state phi = 0
+__global__ void init_state_kernel(const float *un0, float2 *agg, long long n_agg, float2 *msg, long long n_msg)
+{
+    const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n_agg; i += stride)
+        agg[i] = make_float2(un0[i], 0.f);
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n_msg; i += stride)
+        msg[i] = make_float2(0.f, 0.f);
+}
+
 int grid_for(long long work, int per_block_items)
 {
     long long g = (work + per_block_items - 1) / per_block_items;
@@ -233,7 +244,7 @@ int grid_for(long long work, int per_block_items)
 }  // namespace
 
 cudaError_t launch_pack(const EdgeDesc *edges, int n_edges, const NodeDesc *nodes, int n_nodes,
-                        const float *unary_src, const float *pair_src, float *tab, float *un0, double *agg, int *err,
+                        const float *unary_src, const float *pair_src, float *tab, float *un0, float2 *agg, int *err,
                         cudaStream_t st)
 {
     if (n_edges > 0) {
@@ -249,8 +260,16 @@ cudaError_t launch_pack(const EdgeDesc *edges, int n_edges, const NodeDesc *node
     return cudaSuccess;
 }
 
+cudaError_t launch_init_state(const float *un0, float2 *agg, long long n_agg, float2 *msg, long long n_msg,
+                              cudaStream_t st)
+{
+    init_state_kernel<<<grid_for(n_agg > n_msg ? n_agg : n_msg, kThreads), kThreads, 0, st>>>(un0, agg, n_agg, msg,
+                                                                                           n_msg);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_bound(const EdgeDesc *edges, int n_edges, const NodeDesc *nodes, int n_nodes, const float *tab,
-                         const double *agg, const double *msg, double *emin, double *nmin, const int *model_node_off,
+                         const float2 *agg, const float2 *msg, double *emin, double *nmin, const int *model_node_off,
                          const int *model_edge_off, int n_models, int exact, double *out, cudaStream_t st)
 {
     if (exact && n_edges > 0) {
@@ -269,7 +288,7 @@ cudaError_t launch_bound(const EdgeDesc *edges, int n_edges, const NodeDesc *nod
 
 cudaError_t launch_round(const EdgeDesc *edges, const NodeDesc *nodes, const int *in_off, const int *in_edge,
                          const int *model_node_off, const int *model_edge_off, int n_models, const float *tab,
-                         const double *agg, const double *msg, const float *un0, int *labels, double *energy, int *err,
+                         const float2 *agg, const float2 *msg, const float *un0, int *labels, double *energy, int *err,
                          cudaStream_t st)
 {
     round_kernel<<<n_models, kThreads, 0, st>>>(edges, nodes, in_off, in_edge, model_node_off, tab, agg, msg, labels,

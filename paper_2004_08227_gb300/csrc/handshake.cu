@@ -11,11 +11,12 @@
 //   beta(t) = vh(t) - b(t)
 //   c(s)  = min_t [theta_uv(s,t) + beta(t)] + uh(s)             = min_t [g(s,t) - b(t)]
 //   agg_u := c, phi_{v->u} := c - uh;  agg_v := b, phi_{u->v} := b - vh.
-// Precision: the O(L) state and vector arithmetic are FP64 (reparametrized
-// unaries grow to large magnitudes, where FP32 rounding would accumulate over
-// thousands of updates); the O(L^2) minimizations run in FP32 on the table
-// and on small quantities (vh shifted by vh(0), alpha, beta), rounded to FP32
-// once per update.  The pairwise table is only read (4 B per entry, once from
+// Precision: the O(L) state and vector arithmetic are double-float (hi + lo
+// FP32 pairs, ~44 bits; reparametrized unaries grow to large magnitudes, where
+// plain FP32 rounding would accumulate over thousands of updates, and GB300's
+// FP64 units are too slow for the critical path); the O(L^2) minimizations
+// run in FP32 on the table and on small quantities (vh shifted by vh(0),
+// alpha, beta), rounded to FP32 once per update.  The pairwise table is only read (4 B per entry, once from
 // HBM); all three minimizations run on the copy staged in shared memory.
 // Min-plus is not a dense contraction, so this is FP32 ALU work bound by HBM
 // bandwidth.
@@ -51,8 +52,8 @@ namespace {
 
 struct Smem {
     float *tile;        // nbuf buffers of tile_floats each
-    double *uh, *vh;    // FP64 unaries without this edge's messages
-    double *bv;         // FP64 new vector of node v
+    float2 *uh, *vh;    // double-float unaries without this edge's messages
+    float2 *bv;         // double-float new vector of node v
     float *w1;          // vh(t) - vh(0) in FP32 (pass 1)
     float *alpha, *beta, *pm;
     float4 *part;
@@ -62,7 +63,7 @@ struct Smem {
 __device__ __forceinline__ Smem carve(char *base, const HsParams &p, int nbuf)
 {
     Smem s;
-    double *d = reinterpret_cast<double *>(base);
+    float2 *d = reinterpret_cast<float2 *>(base);
     s.uh = d; d += p.rmax;
     s.vh = d; d += p.ldmax;
     s.bv = d; d += p.ldmax;
@@ -128,6 +129,17 @@ __device__ __forceinline__ void signal_node(unsigned *ver, int g, unsigned n)
     asm volatile("red.relaxed.gpu.global.add.u32 [%0], %1;" ::"l"(ver + g), "r"(n) : "memory");
 }
 
+// Barriers 1 and 2 over `count` threads (a multiple of 32) of the CTA.
+__device__ __forceinline__ void named_barrier_1(int count)
+{
+    asm volatile("bar.sync 1, %0;" ::"r"(count) : "memory");
+}
+
+__device__ __forceinline__ void named_barrier_2(int count)
+{
+    asm volatile("bar.sync 2, %0;" ::"r"(count) : "memory");
+}
+
 // Bounded wait (one thread) until node g's counter reaches `need`.
 __device__ __forceinline__ void wait_node(const HsParams &p, int g, unsigned need)
 {
@@ -174,34 +186,44 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
     int r0, nr;
     rows_of(ed, rank, C, r0, nr);
     const int ld = ed.ld, Q = ld >> 2, Lv = ed.Lv;
-    double *agg = p.agg;
-    double *msg = p.msg;
+    float2 *agg = p.agg;
+    float2 *msg = p.msg;
 
     // unaries without this edge's messages (written by other SMs: L2 loads).
-    // Persistent driver: warp 0 waits for node v's earlier updates and loads
-    // vh, warp 1 does the same for node u, so the two waits overlap.
+    // Persistent driver: the first half of the warps waits for node v's
+    // earlier updates (one lane polls, a named barrier releases the half) and
+    // loads vh, the second half does the same for node u, so the two waits
+    // overlap and each vector is loaded by many threads at once.
     {
-        const int warp = tid >> 5, lane = tid & 31;
-        const bool do_v = SIGNAL ? warp == 0 : true;
-        const bool do_u = SIGNAL ? warp == 1 : true;
-        const int s0 = SIGNAL ? lane : tid, st = SIGNAL ? 32 : T;
-        if (SIGNAL && (warp == 0 || warp == 1)) {
-            if (lane == 0) wait_node(p, warp == 0 ? ed.gv : ed.gu, warp == 0 ? need_v : need_u);
-            __syncwarp();
+        const int half = (T >> 6) << 5;  // threads in the first half (a multiple of 32)
+        const bool vside = SIGNAL ? tid < half : true;
+        const bool uside = SIGNAL ? tid >= half : true;
+        const int i0 = SIGNAL ? (vside ? tid : tid - half) : tid;
+        const int ni = SIGNAL ? (vside ? half : T - half) : T;
+        if (SIGNAL) {
+            if (tid == 0) wait_node(p, ed.gv, need_v);
+            if (tid == half) wait_node(p, ed.gu, need_u);
+            if (vside)
+                named_barrier_1(half);
+            else
+                named_barrier_2(T - half);
         }
-        if (do_u)
-            for (int s = s0; s < nr; s += st)
-                sm.uh[s] = __ldcg(agg + ed.au + r0 + s) - __ldcg(msg + ed.mu + r0 + s);
-        if (do_v) {
-            const double vref = __ldcg(agg + ed.av) - __ldcg(msg + ed.mv);
-            for (int q = s0; q < (ld >> 1); q += st) {  // node vectors start 32-byte aligned
-                const double2 a = __ldcg(reinterpret_cast<const double2 *>(agg + ed.av) + q);
-                const double2 f = __ldcg(reinterpret_cast<const double2 *>(msg + ed.mv) + q);
+        if (uside)
+            for (int s = i0; s < nr; s += ni)
+                sm.uh[s] = df_sub(__ldcg(agg + ed.au + r0 + s), __ldcg(msg + ed.mu + r0 + s));
+        if (vside) {
+            const float2 vref = df_sub(__ldcg(agg + ed.av), __ldcg(msg + ed.mv));
+            for (int q = i0; q < (ld >> 1); q += ni) {  // node vectors start 32-byte aligned
+                const float4 a = __ldcg(reinterpret_cast<const float4 *>(agg + ed.av) + q);
+                const float4 f = __ldcg(reinterpret_cast<const float4 *>(msg + ed.mv) + q);
                 const int t = 2 * q;
-                const double v0 = a.x - f.x, v1 = a.y - f.y;
-                reinterpret_cast<double2 *>(sm.vh)[q] = make_double2(t < Lv ? v0 : 0.0, t + 1 < Lv ? v1 : 0.0);
-                reinterpret_cast<float2 *>(sm.w1)[q] = make_float2(t < Lv ? static_cast<float>(v0 - vref) : 0.f,
-                                                                   t + 1 < Lv ? static_cast<float>(v1 - vref) : 0.f);
+                const float2 v0 = df_sub(make_float2(a.x, a.y), make_float2(f.x, f.y));
+                const float2 v1 = df_sub(make_float2(a.z, a.w), make_float2(f.z, f.w));
+                reinterpret_cast<float4 *>(sm.vh)[q] =
+                    make_float4(t < Lv ? v0.x : 0.f, t < Lv ? v0.y : 0.f, t + 1 < Lv ? v1.x : 0.f,
+                                t + 1 < Lv ? v1.y : 0.f);
+                reinterpret_cast<float2 *>(sm.w1)[q] = make_float2(t < Lv ? df_to_f(df_sub(v0, vref)) : 0.f,
+                                                                   t + 1 < Lv ? df_to_f(df_sub(v1, vref)) : 0.f);
             }
         }
     }
@@ -217,11 +239,11 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
     // pass 1: a(s) = 1/2 (min_t [theta(s,t) + w1(t)] + vh(0) + uh(s));  alpha = uh - a
     {
         const float4 *w = reinterpret_cast<const float4 *>(sm.w1);
-        const double vref = sm.vh[0];
+        const float2 vref = sm.vh[0];
         auto emit = [&](int s, float m) {
-            const double u = sm.uh[s];
-            const double a = 0.5 * ((static_cast<double>(m) + vref) + u);
-            sm.alpha[s] = static_cast<float>(u - a);
+            const float2 u = sm.uh[s];
+            const float2 a = df_half(df_add(df_add_f(vref, m), u));
+            sm.alpha[s] = df_to_f(df_sub(u, a));
         };
         for (int base = 0; base < nr; base += ng) {
             const int s = base + gid;
@@ -286,10 +308,10 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
             for (; r + 1 < C; r += 2) m = min3f(m, xbuf[r * ld + t], xbuf[(r + 1) * ld + t]);
             if (r < C) m = fminf(m, xbuf[r * ld + t]);
         }
-        const double vh = sm.vh[t];
-        const double b = static_cast<double>(m) + vh;
-        sm.bv[t] = t < Lv ? b : 0.0;
-        sm.beta[t] = t < Lv ? static_cast<float>(vh - b) : 0.f;
+        const float2 vh = sm.vh[t];
+        const float2 b = df_add_f(vh, m);
+        sm.bv[t] = t < Lv ? b : make_float2(0.f, 0.f);
+        sm.beta[t] = t < Lv ? df_to_f(df_sub(vh, b)) : 0.f;
     }
     // The slots of this parity are written again two items later, after every
     // CTA has passed the next item's exchange barrier, i.e. after this read.
@@ -298,9 +320,9 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
     // node v's new vector (one CTA of the cluster), published before pass 3
     if (rank == 0) {
         for (int t = tid; t < Lv; t += T) {
-            const double b = sm.bv[t];
+            const float2 b = sm.bv[t];
             __stcg(agg + ed.av + t, b);
-            __stcg(msg + ed.mv + t, b - sm.vh[t]);
+            __stcg(msg + ed.mv + t, df_sub(b, sm.vh[t]));
         }
         if (SIGNAL) {
             __syncthreads();
@@ -312,10 +334,10 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
     {
         const float4 *w = reinterpret_cast<const float4 *>(sm.beta);
         auto emit = [&](int s, float m) {
-            const double u = sm.uh[s];
-            const double c = static_cast<double>(m) + u;
+            const float2 u = sm.uh[s];
+            const float2 c = df_add_f(u, m);
             __stcg(agg + ed.au + r0 + s, c);
-            __stcg(msg + ed.mu + r0 + s, c - u);
+            __stcg(msg + ed.mu + r0 + s, df_sub(c, u));
         };
         for (int base = 0; base < nr; base += ng) {
             const int s = base + gid;
@@ -433,7 +455,7 @@ cudaError_t launch(K kernel, const HsParams &p, int grid, int threads, size_t sm
 
 size_t hs_smem_bytes(int nbuf, int tile_floats, int rmax, int ldmax, int threads, int C)
 {
-    // FP64 uh, vh, bv; FP32 tiles, w1, alpha, beta, pm (nbuf x C slots), part (float4 x T); 2 mbarriers
+    // double-float uh, vh, bv; FP32 tiles, w1, alpha, beta, pm (nbuf x C slots), part (float4 x T); 2 mbarriers
     const size_t d = static_cast<size_t>(rmax) + 2 * static_cast<size_t>(ldmax);
     const size_t f = static_cast<size_t>(nbuf) * tile_floats + static_cast<size_t>(rmax) +
                      (2 + static_cast<size_t>(nbuf) * C) * static_cast<size_t>(ldmax) + 4 * static_cast<size_t>(threads);

@@ -12,8 +12,8 @@ namespace mplpp {
 struct HsParams {
     const EdgeDesc *edges;
     const float *tab;
-    double *agg;             // FP64 reparametrized unaries (agg layout)
-    double *msg;             // FP64 messages (msg layout)
+    float2 *agg;             // double-float reparametrized unaries (agg layout)
+    float2 *msg;             // double-float messages (msg layout)
     const int *items;        // looped: edge ids of the phase being launched
     const int *work_off;     // persistent: [clusters + 1] offsets into work
     const WorkItem *work;    // persistent: per-cluster item lists (one iteration)
@@ -36,15 +36,17 @@ int hs_max_active_clusters(int C, int threads, size_t smem);
 
 // dual.cu
 cudaError_t launch_pack(const EdgeDesc *edges, int n_edges, const NodeDesc *nodes, int n_nodes,
-                        const float *unary_src, const float *pair_src, float *tab, float *un0, double *agg,
+                        const float *unary_src, const float *pair_src, float *tab, float *un0, float2 *agg,
                         int *err, cudaStream_t st);
 cudaError_t launch_bound(const EdgeDesc *edges, int n_edges, const NodeDesc *nodes, int n_nodes,
-                         const float *tab, const double *agg, const double *msg, double *emin, double *nmin,
+                         const float *tab, const float2 *agg, const float2 *msg, double *emin, double *nmin,
                          const int *model_node_off, const int *model_edge_off, int n_models, int exact,
                          double *out, cudaStream_t st);
 cudaError_t launch_round(const EdgeDesc *edges, const NodeDesc *nodes, const int *in_off, const int *in_edge,
                          const int *model_node_off, const int *model_edge_off, int n_models, const float *tab,
-                         const double *agg, const double *msg, const float *un0, int *labels, double *energy,
+                         const float2 *agg, const float2 *msg, const float *un0, int *labels, double *energy,
                          int *err, cudaStream_t st);
+cudaError_t launch_init_state(const float *un0, float2 *agg, long long n_agg, float2 *msg, long long n_msg,
+                              cudaStream_t st);
 
 }  // namespace mplpp

@@ -55,7 +55,7 @@ struct mplpp_solver {
     mplpp::EdgeDesc *d_edges = nullptr;
     mplpp::NodeDesc *d_nodes = nullptr;
     float *d_tab = nullptr, *d_un0 = nullptr;
-    double *d_agg = nullptr, *d_msg = nullptr;  // FP64 state
+    float2 *d_agg = nullptr, *d_msg = nullptr;  // double-float state
     int *d_phase_edges = nullptr, *d_err = nullptr;
     unsigned *d_ver = nullptr;
     int *d_work_off = nullptr;
