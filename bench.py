@@ -51,6 +51,25 @@ def models_for(cfg: int, seed: int):
     return models, T
 
 
+def kernel_traffic(iterations):
+    """DRAM bytes per launch of the Handshake kernel from the committed ncu
+    summary, scaled from its 500-iteration figure; None when the kernel
+    sources changed since the capture (recorded SHA-1 of the sources)."""
+    import hashlib
+    import re
+    prof = os.path.join(ROOT, "profiles", "hs_persistent_kernel_pose_K60_L300.md")
+    try:
+        txt = open(prof).read()
+        h = hashlib.sha1()
+        for f in ("handshake.cu", "common.cuh"):
+            h.update(open(os.path.join(ROOT, "paper_2004_08227_gb300", "csrc", f), "rb").read())
+        if re.search(r"source_sha1: ([0-9a-f]+)", txt).group(1) != h.hexdigest():
+            return None
+        return float(re.search(r"dram_bytes_per_launch: ([0-9.]+)", txt).group(1)) * iterations / 500.0
+    except Exception:
+        return None
+
+
 def load_peak():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -156,6 +175,68 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def _timed(stream, fn, n):
+    import torch
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    out = None
+    for _ in range(n):
+        out = fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / n, out
+
+
+def looped_baseline(Solver, models, T, stream, step, D_ref, ms_ref, n):
+    """The plain driver: one launch per matching.  One model: the same model
+    looped; several models: a loop of per-model solves (each its own solver)."""
+    if len(models) == 1:
+        sl = Solver(models, mode="looped")
+        step(sl)
+        lms, D = _timed(stream, lambda: step(sl), n)
+        launches = T * sl.info()["phases"]
+        sl.close()
+    else:
+        solvers = [Solver([m], mode="looped") for m in models]
+
+        def loop():
+            return np.concatenate([step(s) for s in solvers])
+        loop()
+        lms, D = _timed(stream, loop, n)
+        launches = T * sum(s.info()["phases"] for s in solvers)
+        for s in solvers:
+            s.close()
+    return {"ms_per_step": lms, "launches_per_step": launches, "models": len(models),
+            "final_bound_sum": float(np.sum(D)), "bound_equal": bool(np.array_equal(D, D_ref)),
+            "persistent_speedup": lms / ms_ref}
+
+
+def batched_vs_looped(Solver, stream, args):
+    models, T = models_for(4, seed=0)
+    s = Solver(models, mode="persistent")
+    tune = s.autotune(2) if args.autotune > 0 else None
+    info = s.info()
+
+    def step_b(sol):
+        sol.reset()
+        sol.run(T)
+        return sol.bound(exact=True)
+    step_b(s)
+    bms, D = _timed(stream, lambda: step_b(s), 2)
+    s.close()
+    lp = looped_baseline(Solver, models, T, stream, step_b, D, bms, 1)
+    upd = T * info["edges"]
+    return {"workload": CONFIGS[4][0], "models": len(models), "edges": info["edges"], "iterations": T,
+            "batched_ms": bms, "batched_edge_updates_per_s": upd / (bms / 1e3),
+            "batched_gbs": T * info["bytes_per_iteration"] / (bms / 1e3) / 1e9,
+            "per_model_looped_ms": lp["ms_per_step"], "per_model_launches": lp["launches_per_step"],
+            "bound_equal": lp["bound_equal"], "speedup": lp["ms_per_step"] / bms,
+            "mapping": {k: info[k] for k in ("mode", "cluster", "threads", "grid")},
+            "autotune": tune.get("best") if tune else None}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -181,6 +262,10 @@ def run_ours(args):
         _, cpu = cpu_oracle_rate(models, T, args.cpu_budget)
     stream = torch.cuda.current_stream()
     s = Solver(models, mode=args.mode)
+    tune = None
+    if args.autotune > 0 and args.mode == "auto":
+        tune = s.autotune(args.autotune)
+        log("autotune:", tune.get("best"))
     info = s.info()
     E_total = info["edges"]
     log("solver:", info)
@@ -242,23 +327,13 @@ def run_ours(args):
     # the looped driver (one launch per matching) on the same workload, equal bound
     looped = None
     if not args.no_looped:
-        sl = Solver(models, mode="looped")
-        for _ in range(2):
-            step(sl)
-        torch.cuda.synchronize()
-        f0 = torch.cuda.Event(enable_timing=True)
-        f1 = torch.cuda.Event(enable_timing=True)
-        nl = max(1, min(args.steps, 3))
-        f0.record(stream)
-        for _ in range(nl):
-            D_loop = step(sl)
-        f1.record(stream)
-        torch.cuda.synchronize()
-        lms = f0.elapsed_time(f1) / nl
-        looped = {"ms_per_step": lms, "launches_per_step": T * info["phases"],
-                  "final_bound": float(D_loop[0]), "bound_equal": bool(np.array_equal(D_loop, D_persist)),
-                  "persistent_speedup": lms / ms}
-        sl.close()
+        looped = looped_baseline(Solver, models, T, stream, step, D_persist, ms, max(1, min(args.steps, 3)))
+
+    # the batched workload (256 uneven models): one persistent solve of the
+    # batch against a loop of plain per-model solves, equal final bounds
+    batched = None
+    if args.batched and cfg != 4:
+        batched = batched_vs_looped(Solver, stream, args)
 
     # end to end through the public API with host buffers (pinned)
     e2e = None
@@ -279,7 +354,7 @@ def run_ours(args):
         for i in range(1 + max(1, min(args.steps, 3))):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            with Solver(pinned, mode=args.mode) as se:
+            with Solver(pinned, mode=info["mode"], cluster=info["cluster"], threads=info["threads"]) as se:
                 se.run(T)
                 se.bound(exact=True)
                 se.labeling()
@@ -298,12 +373,15 @@ def run_ours(args):
         "config": {"workload": name, "models": len(models), "edges": E_total, "iterations": T,
                    "matchings": info["phases"], "mode": info["mode"], "cluster": info["cluster"],
                    "threads": info["threads"], "grid": info["grid"], "parallelism": f"replicas{world}",
+                   "autotuned": bool(tune), 
                    "l2": "inputs larger than L2 (tables %.0f MB per model)" % (bytes_iter / 1e6)},
         "hbm_gbs": achieved,
         "roofline": {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "peak_source": peak_kind, "traffic": None,
+                     "frac": achieved / peak, "peak_source": peak_kind,
+                     "traffic": kernel_traffic(T) if (cfg == 2 and info["mode"] == "persistent") else None,
                      "algorithmic_bytes_per_launch": T * bytes_iter, "launch_ms": kms},
         "looped": looped,
+        "batched": batched,
         "e2e": e2e,
         "cpu_baseline": cpu,
         "clocks": ck,
@@ -328,6 +406,8 @@ def main():
     ap.add_argument("--no-looped", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--batched", type=int, default=1, help="also time the 256-model batch against per-model loops")
+    ap.add_argument("--autotune", type=int, default=3, help="iterations per candidate of the mapping autotuner (0: off)")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-iters", type=int, default=1)
     args = ap.parse_args()

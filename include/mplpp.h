@@ -197,6 +197,16 @@ mplpp_status mplpp_info(const mplpp_solver *s, mplpp_info_t *info);
 /* Waits for the solver's stream and reports device-side errors. */
 mplpp_status mplpp_sync(mplpp_solver *s);
 
+/* Self-measured choice of the mapping (not in the paper): runs `iterations`
+ * iterations of the solver's own models under every feasible combination of
+ * CTAs per edge (1..8), threads per CTA (128, 256, 512) and driver (persistent,
+ * looped), timed with CUDA events on the solver's stream, and keeps the
+ * fastest.  All mappings compute bit-identical results; the state before the
+ * call is restored afterwards.  report (may be NULL): host buffer receiving a
+ * JSON summary (best mapping and every candidate's time in ms).
+ * Synchronizes. */
+mplpp_status mplpp_autotune(mplpp_solver *s, int32_t iterations, char *report, size_t report_size);
+
 /* Dual bound of one model's reparametrized costs without allocating any
  * device memory.  The paper has no counterpart: this entry point exists for
  * callers that cannot call cudaMalloc -- code that owns a fixed device arena

@@ -28,7 +28,7 @@ MODE_NAME = {v: k for k, v in MODE.items()}
 EXPORTS = ["mplpp_options_default", "mplpp_schedule", "mplpp_create", "mplpp_run", "mplpp_bound",
            "mplpp_labeling", "mplpp_backward", "mplpp_reset", "mplpp_state_size", "mplpp_save_state",
            "mplpp_load_state", "mplpp_info", "mplpp_sync", "mplpp_last_error", "mplpp_destroy",
-           "mplpp_bound_noalloc", "mplpp_noalloc_last_error"]
+           "mplpp_bound_noalloc", "mplpp_noalloc_last_error", "mplpp_autotune"]
 
 
 class MplppModel(ctypes.Structure):
@@ -96,6 +96,7 @@ def load(build_if_needed: bool = True):
         lib.mplpp_destroy.argtypes = [P]
         lib.mplpp_destroy.restype = None
         lib.mplpp_bound_noalloc.argtypes = [c_i32, c_i32, P, P, P, P, P, P, P, P]
+        lib.mplpp_autotune.argtypes = [P, c_i32, P, ctypes.c_size_t]
         lib.mplpp_noalloc_last_error.argtypes = []
         lib.mplpp_noalloc_last_error.restype = ctypes.c_char_p
         for name in EXPORTS:

@@ -92,7 +92,7 @@ extern "C" const char *mplpp_last_error(const mplpp_solver *s)
 }
 
 // Mapping for one candidate cluster size C: per-CTA tile and vector sizes.
-static void mapping_for(mplpp_solver *s, int C)
+static void mapping_for(mplpp_solver *s, int C, int threads = 0)
 {
     long long tile = 0, rows = 0;
     int ldmax = 4;
@@ -102,7 +102,7 @@ static void mapping_for(mplpp_solver *s, int C)
         rows = std::max(rows, R);
         ldmax = std::max(ldmax, ed.ld);
     }
-    int T = s->opt.threads;
+    int T = threads > 0 ? threads : s->opt.threads;
     if (T <= 0) T = (4 * tile >= 48 * 1024) ? 512 : (4 * tile <= 4096 ? 128 : 256);
     s->C = C;
     s->T = T;
@@ -201,6 +201,50 @@ static void build_work(mplpp_solver *s, int clusters)
     }
     s->max_deg = 0;
     for (int d : deg) s->max_deg = std::max(s->max_deg, d);
+}
+
+// Makes (C, T, mode) the solver's mapping: sizes, kernel attributes, and for
+// the persistent driver the per-cluster work lists (uploaded to the device).
+// want: MPLPP_MODE_AUTO (persistent if possible), _LOOPED or _PERSISTENT.
+static mplpp_status apply_mapping(mplpp_solver *s, int C, int T, int want)
+{
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->device);
+    mapping_for(s, C, T);
+    if (s->smem_looped > static_cast<size_t>(optin))
+        return fail(s, MPLPP_E_UNSUPPORTED,
+                    "largest table needs " + std::to_string(s->smem_looped) + " B of shared memory per CTA with " +
+                        std::to_string(C) + " CTAs per edge (limit " + std::to_string(optin) + ")");
+    cudaError_t ce = hs_prepare(std::max(s->smem_looped, std::min(s->smem_persist, static_cast<size_t>(optin))));
+    if (ce != cudaSuccess) return cuda_fail(s, ce, "kernel attributes");
+    int mode = MPLPP_MODE_LOOPED;
+    if (want != MPLPP_MODE_LOOPED && s->smem_persist <= static_cast<size_t>(optin) && s->EE > 0) {
+        int clusters = hs_max_active_clusters(C, s->T, s->smem_persist);
+        clusters = std::min(clusters, s->max_phase);
+        if (clusters >= 1 && clusters + 1 <= s->work_off_cap) {
+            mode = MPLPP_MODE_PERSISTENT;
+            s->clusters = clusters;
+            build_work(s, clusters);
+            CK(s, cudaMemcpyAsync(s->d_work_off, s->work_off.data(), s->work_off.size() * sizeof(int),
+                                  cudaMemcpyHostToDevice, s->stream));
+            CK(s, cudaMemcpyAsync(s->d_work, s->work.data(), s->work.size() * sizeof(WorkItem), cudaMemcpyHostToDevice,
+                                  s->stream));
+            CK(s, cudaStreamSynchronize(s->stream));
+        }
+    }
+    if (want == MPLPP_MODE_PERSISTENT && mode != MPLPP_MODE_PERSISTENT)
+        return fail(s, MPLPP_E_UNSUPPORTED, "persistent mode is not possible for these shapes on this device");
+    s->mode = mode;
+    if (s->g_looped) {
+        cudaGraphExecDestroy(s->g_looped);
+        s->g_looped = nullptr;
+    }
+    if (s->g_persist) {
+        cudaGraphExecDestroy(s->g_persist);
+        s->g_persist = nullptr;
+        s->g_persist_iters = -1;
+    }
+    return MPLPP_OK;
 }
 
 extern "C" mplpp_status mplpp_create(const mplpp_model *models, int32_t n_models, const mplpp_options *opt,
@@ -337,24 +381,7 @@ extern "C" mplpp_status mplpp_create(const mplpp_model *models, int32_t n_models
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, S->device);
     S->sms = sms;
     choose_mapping(S, sms, optin);
-    if (S->smem_looped > static_cast<size_t>(optin))
-        return fail(nullptr, MPLPP_E_UNSUPPORTED,
-                    "largest table needs " + std::to_string(S->smem_looped) + " B of shared memory per CTA with " +
-                        std::to_string(S->C) + " CTAs per edge (limit " + std::to_string(optin) + ")");
-    if ((ce = hs_prepare(std::max(S->smem_looped, std::min(S->smem_persist, static_cast<size_t>(optin))))) != cudaSuccess)
-        return cuda_fail(nullptr, ce, "kernel attributes");
-    S->mode = MPLPP_MODE_LOOPED;
-    if (S->opt.mode != MPLPP_MODE_LOOPED && S->smem_persist <= static_cast<size_t>(optin) && S->EE > 0) {
-        int clusters = hs_max_active_clusters(S->C, S->T, S->smem_persist);
-        clusters = std::min(clusters, S->max_phase);
-        if (clusters >= 1) {
-            S->mode = MPLPP_MODE_PERSISTENT;
-            S->clusters = clusters;
-            build_work(S, clusters);
-        }
-    }
-    if (S->opt.mode == MPLPP_MODE_PERSISTENT && S->mode != MPLPP_MODE_PERSISTENT)
-        return fail(nullptr, MPLPP_E_UNSUPPORTED, "persistent mode is not possible for these shapes on this device");
+    const int chosenC = S->C;
 
     ce = cudaStreamCreateWithFlags(&S->cap_stream, cudaStreamNonBlocking);
     if (ce != cudaSuccess) return cuda_fail(nullptr, ce, "cudaStreamCreate");
@@ -382,10 +409,9 @@ extern "C" mplpp_status mplpp_create(const mplpp_model *models, int32_t n_models
     CKC(S->alloc(&S->d_out, n_models));
     CKC(S->alloc(&S->d_labels, S->N));
     CKC(S->alloc(&S->d_energy, n_models));
-    if (S->mode == MPLPP_MODE_PERSISTENT) {
-        CKC(S->alloc(&S->d_work_off, S->work_off.size()));
-        CKC(S->alloc(&S->d_work, S->work.size()));
-    }
+    S->work_off_cap = sms * 64 + 1;  // clusters never exceed the co-resident CTAs
+    CKC(S->alloc(&S->d_work_off, S->work_off_cap));
+    CKC(S->alloc(&S->d_work, std::max(1, S->EE)));
     cudaStream_t st = S->stream;
     auto h2d = [&](void *dst, const void *src, size_t bytes) {
         return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st) : cudaSuccess;
@@ -397,9 +423,9 @@ extern "C" mplpp_status mplpp_create(const mplpp_model *models, int32_t n_models
     CKC(h2d(S->d_in_edge, S->in_edge.data(), S->in_edge.size() * sizeof(int)));
     CKC(h2d(S->d_mnode_off, S->mnode_off.data(), S->mnode_off.size() * sizeof(int)));
     CKC(h2d(S->d_medge_off, S->medge_off.data(), S->medge_off.size() * sizeof(int)));
-    if (S->mode == MPLPP_MODE_PERSISTENT) {
-        CKC(h2d(S->d_work_off, S->work_off.data(), S->work_off.size() * sizeof(int)));
-        CKC(h2d(S->d_work, S->work.data(), S->work.size() * sizeof(WorkItem)));
+    {
+        mplpp_status ms = apply_mapping(S, chosenC, S->opt.threads, S->opt.mode);
+        if (ms != MPLPP_OK) return fail(nullptr, ms, S->err);
     }
     CKC(cudaMemsetAsync(S->d_err, 0, sizeof(int), st));
     CKC(cudaMemsetAsync(S->d_msg, 0, S->msgN * sizeof(float2), st));
@@ -443,6 +469,8 @@ extern "C" mplpp_status mplpp_create(const mplpp_model *models, int32_t n_models
 }
 
 // ---- iteration drivers ------------------------------------------------------------
+static mplpp_status check_device_error(mplpp_solver *s);
+
 static HsParams make_params(mplpp_solver *s)
 {
     HsParams p = {};
@@ -698,6 +726,81 @@ extern "C" mplpp_status mplpp_load_state(mplpp_solver *s, const void *buf, size_
     CK(s, cudaStreamSynchronize(s->stream));
     s->iterations = h.iterations;
     s->history_valid = false;
+    return MPLPP_OK;
+}
+
+// Measured choice of the mapping: every feasible (CTAs per edge, threads per
+// CTA, driver) runs `iterations` iterations of the solver's own models from
+// the same state, timed with CUDA events on the solver's stream; the fastest
+// is kept.  Every mapping computes the same values bit for bit (minima are
+// exact and every addition is per element), so only time differs.
+extern "C" mplpp_status mplpp_autotune(mplpp_solver *s, int32_t iterations, char *report, size_t report_size)
+{
+    if (!s || iterations < 1) return MPLPP_E_INVALID;
+    s->err.clear();
+    if (report && report_size) report[0] = 0;
+    if (s->EE == 0) return MPLPP_OK;
+    if (!s->d_save_agg) {
+        CK(s, s->alloc(&s->d_save_agg, s->aggN));
+        CK(s, s->alloc(&s->d_save_msg, s->msgN));
+    }
+    cudaStream_t st = s->stream;
+    CK(s, cudaMemcpyAsync(s->d_save_agg, s->d_agg, sizeof(float2) * s->aggN, cudaMemcpyDeviceToDevice, st));
+    CK(s, cudaMemcpyAsync(s->d_save_msg, s->d_msg, sizeof(float2) * s->msgN, cudaMemcpyDeviceToDevice, st));
+    auto restore = [&]() -> cudaError_t {
+        cudaError_t e = cudaMemcpyAsync(s->d_agg, s->d_save_agg, sizeof(float2) * s->aggN, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(s->d_msg, s->d_save_msg, sizeof(float2) * s->msgN, cudaMemcpyDeviceToDevice, st);
+        return e;
+    };
+    const int oldC = s->C, oldT = s->T, oldMode = s->mode;
+    struct Cand {
+        int C, T, mode;
+        float ms;
+    };
+    std::vector<Cand> done;
+    cudaEvent_t e0, e1;
+    CK(s, cudaEventCreate(&e0));
+    CK(s, cudaEventCreate(&e1));
+    for (int mode : {MPLPP_MODE_PERSISTENT, MPLPP_MODE_LOOPED})
+        for (int C : {1, 2, 3, 4, 5, 6, 8})
+            for (int T : {128, 256, 512}) {
+                if (apply_mapping(s, C, T, mode) != MPLPP_OK) {
+                    s->err.clear();
+                    continue;
+                }
+                bool ok = restore() == cudaSuccess && run_plain(s, 1) == MPLPP_OK && restore() == cudaSuccess;
+                ok = ok && cudaEventRecord(e0, st) == cudaSuccess && run_plain(s, iterations) == MPLPP_OK &&
+                     cudaEventRecord(e1, st) == cudaSuccess && cudaStreamSynchronize(st) == cudaSuccess;
+                float ms = 0.f;
+                if (ok && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && check_device_error(s) == MPLPP_OK)
+                    done.push_back({C, T, mode, ms});
+                s->err.clear();
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    Cand best = {oldC, oldT, oldMode, 0.f};
+    if (!done.empty()) {
+        best = done[0];
+        for (auto &c : done)
+            if (c.ms < best.ms) best = c;
+    }
+    mplpp_status stt = apply_mapping(s, best.C, best.T, best.mode);
+    if (stt != MPLPP_OK) return stt;
+    CK(s, restore());
+    CK(s, cudaStreamSynchronize(st));
+    if (report && report_size) {
+        std::string r = "{\"iterations\": " + std::to_string(iterations) + ", \"best\": {\"cluster\": " +
+                        std::to_string(best.C) + ", \"threads\": " + std::to_string(best.T) + ", \"mode\": \"" +
+                        (best.mode == MPLPP_MODE_PERSISTENT ? "persistent" : "looped") + "\", \"ms\": " +
+                        std::to_string(best.ms) + "}, \"candidates\": [";
+        for (size_t i = 0; i < done.size(); ++i)
+            r += std::string(i ? ", " : "") + "[" + std::to_string(done[i].C) + ", " + std::to_string(done[i].T) +
+                 ", \"" + (done[i].mode == MPLPP_MODE_PERSISTENT ? "persistent" : "looped") + "\", " +
+                 std::to_string(done[i].ms) + "]";
+        r += "]}";
+        std::snprintf(report, report_size, "%s", r.c_str());
+    }
     return MPLPP_OK;
 }
 

@@ -48,6 +48,7 @@ struct mplpp_solver {
     // mapping
     int mode = MPLPP_MODE_LOOPED;
     int C = 1, T = 256, tile_floats = 4, rmax = 4, ldmax = 4, max_phase = 1, clusters = 0, max_deg = 0;
+    int work_off_cap = 0;  // capacity of d_work_off
     size_t smem_looped = 0, smem_persist = 0;
 
     // device
@@ -75,6 +76,7 @@ struct mplpp_solver {
     unsigned char *d_rec = nullptr;  // argmin records of one segment
     float *d_dD = nullptr;
     long long *d_pbase = nullptr, *d_ubase = nullptr;  // per-model offsets of the caller's layouts
+    float2 *d_save_agg = nullptr, *d_save_msg = nullptr;  // autotuner: state kept across candidates
 
     long long iterations = 0;
     long long launches = 0;

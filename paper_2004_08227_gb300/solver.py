@@ -225,6 +225,13 @@ class Solver:
         body = np.concatenate([np.asarray(agg, np.float64), np.asarray(msg, np.float64)]).tobytes()
         self.load_state(bytes(h) + body)
 
+    def autotune(self, iterations: int = 3) -> dict:
+        """Measured mapping choice (mplpp_autotune); returns its JSON report."""
+        import json
+        buf = ctypes.create_string_buffer(1 << 16)
+        self._check(self._lib.mplpp_autotune(self._h, int(iterations), buf, len(buf)))
+        return json.loads(buf.value.decode()) if buf.value else {}
+
     def info(self) -> dict:
         inf = _lib.MplppInfo()
         self._check(self._lib.mplpp_info(self._h, ctypes.byref(inf)))

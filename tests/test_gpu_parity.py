@@ -364,3 +364,24 @@ def test_full_size_pose_K60_L300_properties(pose_full):
     b.run(3)
     sa, sb = a.state_arrays(), b.state_arrays()
     assert np.array_equal(sa[1], sb[1]) and np.array_equal(sa[2], sb[2])
+
+
+def test_autotune_keeps_state_and_results():
+    """The autotuner leaves the state as it was, keeps a feasible mapping, and
+    every mapping gives bit-identical results (minima are exact, additions
+    per element), so the run after tuning matches an untuned run."""
+    m = W.uneven_complete(10, 20, 90, seed=21)
+    a = Solver([m])
+    a.run(3)
+    before = a.state_arrays()
+    rep = a.autotune(2)
+    after = a.state_arrays()
+    assert np.array_equal(before[1], after[1]) and np.array_equal(before[2], after[2])
+    assert rep["best"]["cluster"] >= 1 and len(rep["candidates"]) >= 2
+    inf = a.info()
+    assert inf["cluster"] == rep["best"]["cluster"] and inf["mode"] == rep["best"]["mode"]
+    a.run(5)
+    b = Solver([m])
+    b.run(8)
+    sa, sb = a.state_arrays(), b.state_arrays()
+    assert np.array_equal(sa[1], sb[1]) and np.array_equal(sa[2], sb[2])
