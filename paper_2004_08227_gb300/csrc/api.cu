@@ -109,6 +109,7 @@ static void mapping_for(mplpp_solver *s, int C, int threads = 0)
     s->tile_floats = static_cast<int>(round4(std::max(4LL, tile)));
     s->rmax = static_cast<int>(round4(std::max(4LL, rows)));
     s->ldmax = ldmax;
+    s->rr = hs_rr_fits(static_cast<int>(rows), ldmax >> 2, T, s->tile_floats);
     s->smem_looped = hs_smem_bytes(1, s->tile_floats, s->rmax, s->ldmax, s->T, C);
     s->smem_persist = hs_smem_bytes(2, s->tile_floats, s->rmax, s->ldmax, s->T, C);
 }
@@ -136,7 +137,7 @@ static void choose_mapping(mplpp_solver *s, int sms, int optin)
         mapping_for(s, C);
         if (s->smem_persist > static_cast<size_t>(optin)) continue;
         if (C > 1 && static_cast<long long>(C) * max_phase > 2LL * sms) break;
-        const int avail = std::min(hs_max_active_clusters(C, s->T, s->smem_persist), max_phase);
+        const int avail = std::min(hs_max_active_clusters(C, s->T, s->smem_persist, s->rr), max_phase);
         if (avail < 1) continue;
         const int rounds = (max_phase + avail - 1) / avail;
         const double cost = rounds * (3e-6 + 4.0 * s->tile_floats / 40e9);
@@ -219,7 +220,7 @@ static mplpp_status apply_mapping(mplpp_solver *s, int C, int T, int want)
     if (ce != cudaSuccess) return cuda_fail(s, ce, "kernel attributes");
     int mode = MPLPP_MODE_LOOPED;
     if (want != MPLPP_MODE_LOOPED && s->smem_persist <= static_cast<size_t>(optin) && s->EE > 0) {
-        int clusters = hs_max_active_clusters(C, s->T, s->smem_persist);
+        int clusters = hs_max_active_clusters(C, s->T, s->smem_persist, s->rr);
         clusters = std::min(clusters, s->max_phase);
         if (clusters >= 1 && clusters + 1 <= s->work_off_cap) {
             mode = MPLPP_MODE_PERSISTENT;
@@ -485,6 +486,7 @@ static HsParams make_params(mplpp_solver *s)
     p.err = s->d_err;
     p.spin_limit = s->opt.spin_limit;
     p.test_wait = s->opt.test_unreachable_wait ? 1 : 0;
+    p.rr = s->rr ? 1 : 0;
     p.C = s->C;
     p.tile_floats = s->tile_floats;
     p.rmax = s->rmax;

@@ -121,12 +121,12 @@ __device__ __forceinline__ void set_err(int *err, int code)
     atomicCAS(err, 0, code);
 }
 
-// Thread 0, after a __syncthreads that follows the CTA's global writes:
-// make them visible at GPU scope, then count `n` arrivals on node g.
-__device__ __forceinline__ void signal_node(unsigned *ver, int g, unsigned n)
+// Relaxed atomic add on a node counter; published by a preceding
+// fence.acq_rel.gpu, itself after a __syncthreads that follows the CTA's
+// global writes.
+__device__ __forceinline__ void red_add(unsigned *c, unsigned n)
 {
-    asm volatile("fence.acq_rel.gpu;" ::: "memory");
-    asm volatile("red.relaxed.gpu.global.add.u32 [%0], %1;" ::"l"(ver + g), "r"(n) : "memory");
+    asm volatile("red.relaxed.gpu.global.add.u32 [%0], %1;" ::"l"(c), "r"(n) : "memory");
 }
 
 // Barriers 1 and 2 over `count` threads (a multiple of 32) of the CTA.
@@ -173,11 +173,36 @@ __device__ __forceinline__ void group_min(float &m, int G)
     for (int o = G >> 1; o > 0; o >>= 1) m = fminf(m, __shfl_xor_sync(0xffffffffu, m, o));
 }
 
+// Register-resident passes: warp w holds rows w + W k (k < kRR) of the CTA's
+// slice, lane j the float4 chunks j + 32 i (i < kCR), loaded from shared
+// memory once; passes 1 and 3 then reduce in registers (a butterfly over the
+// warp per row), and pass 2 reduces the warp's rows in registers and the warps
+// through the (by then free) tile buffer.  Shared memory is read once per
+// update instead of three times.  For other shapes the passes stream the
+// shared-memory copy.
+constexpr int kRR = 5;
+constexpr int kCR = 3;
+
+__device__ __forceinline__ bool rr_fits(int nr, int Q, int T, int tile_floats)
+{
+    return Q > 32 && Q <= 32 * kCR && nr <= kRR * (T >> 5) && (T >> 5) * Q * 4 <= tile_floats;
+}
+
+// Butterfly minimum over the warp of kRR independent values.
+__device__ __forceinline__ void warp_min_rows(float (&acc)[kRR])
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < kRR; ++k) acc[k] = fminf(acc[k], __shfl_xor_sync(0xffffffffu, acc[k], o));
+}
+
 // One Handshake update of edge ed by this CTA (its row slice); the table slice
 // is (or will be) in `tile`, signalled by `bar` completing phase `parity`.
 // `xpar` selects the exchange buffer (alternates between consecutive items).
 // SIGNAL: publish completion on the node counters (persistent driver).
-template <bool CLUSTER, bool SIGNAL>
+// RR: register-resident passes (rr_fits must hold).
+template <bool CLUSTER, bool SIGNAL, bool RR>
 __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile, const Smem &sm, int rank,
                         uint64_t *bar, uint32_t parity, int xpar, unsigned need_u = 0, unsigned need_v = 0)
 {
@@ -192,21 +217,23 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
     // unaries without this edge's messages (written by other SMs: L2 loads).
     // Persistent driver: the first half of the warps waits for node v's
     // earlier updates (one lane polls, a named barrier releases the half) and
-    // loads vh, the second half does the same for node u, so the two waits
-    // overlap and each vector is loaded by many threads at once.
+    // loads vh; the second half, except the last warp, does the same for node
+    // u, so the two waits overlap and each vector is loaded by many threads at
+    // once.  The last warp is still publishing the previous update (its
+    // release fence) meanwhile.
     {
         const int half = (T >> 6) << 5;  // threads in the first half (a multiple of 32)
         const bool vside = SIGNAL ? tid < half : true;
-        const bool uside = SIGNAL ? tid >= half : true;
+        const bool uside = SIGNAL ? tid >= half && tid < T - 32 : true;
         const int i0 = SIGNAL ? (vside ? tid : tid - half) : tid;
-        const int ni = SIGNAL ? (vside ? half : T - half) : T;
+        const int ni = SIGNAL ? (vside ? half : T - half - 32) : T;
         if (SIGNAL) {
             if (tid == 0) wait_node(p, ed.gv, need_v);
             if (tid == half) wait_node(p, ed.gu, need_u);
             if (vside)
                 named_barrier_1(half);
-            else
-                named_barrier_2(T - half);
+            else if (uside)
+                named_barrier_2(T - half - 32);
         }
         if (uside)
             for (int s = i0; s < nr; s += ni)
@@ -235,6 +262,18 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
     const int G = row_lanes(nr, Q, T);
     const int gid = tid / G, lg = tid % G, ng = T / G;
     float *xbuf = sm.pm + static_cast<size_t>(xpar) * C * ld;  // this item's exchange slots
+    const int lane = tid & 31, warp = tid >> 5, W = T >> 5;
+    const float4 inf4 = make_float4(INFINITY, INFINITY, INFINITY, INFINITY);
+    float4 tr[RR ? kRR : 1][RR ? kCR : 1];
+    if (RR) {
+#pragma unroll
+        for (int k = 0; k < kRR; ++k)
+#pragma unroll
+            for (int i = 0; i < kCR; ++i) {
+                const int s = warp + W * k, q = lane + 32 * i;
+                tr[k][i] = (s < nr && q < Q) ? t4[static_cast<size_t>(s) * Q + q] : inf4;
+            }
+    }
 
     // pass 1: a(s) = 1/2 (min_t [theta(s,t) + w1(t)] + vh(0) + uh(s));  alpha = uh - a
     {
@@ -245,11 +284,30 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
             const float2 a = df_half(df_add(df_add_f(vref, m), u));
             sm.alpha[s] = df_to_f(df_sub(u, a));
         };
-        for (int base = 0; base < nr; base += ng) {
-            const int s = base + gid;
-            float m = s < nr ? row_min(t4 + static_cast<size_t>(s) * Q, w, Q, lg, G) : INFINITY;
-            group_min(m, G);
-            if (s < nr && lg == 0) emit(s, m);
+        if (RR) {
+            float acc[kRR];
+            float4 wv[kCR];
+#pragma unroll
+            for (int i = 0; i < kCR; ++i) wv[i] = lane + 32 * i < Q ? w[lane + 32 * i] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int k = 0; k < kRR; ++k) {
+                acc[k] = INFINITY;
+#pragma unroll
+                for (int i = 0; i < kCR; ++i) acc[k] = min_add4(acc[k], tr[k][i], wv[i]);
+            }
+            warp_min_rows(acc);
+            // every lane holds every row's minimum: lane k emits row k, all at once
+            float mk = acc[0];
+#pragma unroll
+            for (int k = 1; k < kRR; ++k) mk = lane == k ? acc[k] : mk;
+            if (lane < kRR && warp + W * lane < nr) emit(warp + W * lane, mk);
+        } else {
+            for (int base = 0; base < nr; base += ng) {
+                const int s = base + gid;
+                float m = s < nr ? row_min(t4 + static_cast<size_t>(s) * Q, w, Q, lg, G) : INFINITY;
+                group_min(m, G);
+                if (s < nr && lg == 0) emit(s, m);
+            }
         }
     }
     __syncthreads();
@@ -258,8 +316,41 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
     // into slot `rank` of the pm buffer of every CTA of the cluster
     {
         const uint32_t slot = smem_u32(xbuf) + 4u * static_cast<uint32_t>(ld) * static_cast<uint32_t>(rank);
-        const int nsub = T / Q;
-        if (nsub >= 1) {
+        auto push = [&](int q, float4 m) {
+            if (CLUSTER) {
+                for (int r = 0; r < C; ++r) st_dsmem_f4(mapa_shared(slot + 16u * q, r), m);
+            } else {
+                reinterpret_cast<float4 *>(xbuf)[q] = m;
+            }
+        };
+        const int nsub = RR ? 0 : T / Q;
+        if (RR) {
+            // the warp's rows in registers, then the warps through the tile buffer
+            float4 *part2 = reinterpret_cast<float4 *>(const_cast<float *>(tile));
+            float al[kRR];
+#pragma unroll
+            for (int k = 0; k < kRR; ++k) al[k] = warp + W * k < nr ? sm.alpha[warp + W * k] : 0.f;
+#pragma unroll
+            for (int i = 0; i < kCR; ++i) {
+                float4 m = inf4;
+#pragma unroll
+                for (int k = 0; k < kRR; ++k) m = min4(m, add4(tr[k][i], make_float4(al[k], al[k], al[k], al[k])));
+                if (lane + 32 * i < Q) part2[warp * Q + lane + 32 * i] = m;
+            }
+            __syncthreads();
+            // 4 consecutive lanes per chunk, each over every 4th warp, then 2 shuffles
+            for (int base = warp * 32; base < 4 * Q; base += T) {
+                const int idx = base + lane, q = idx >> 2, part = idx & 3;
+                float4 m = inf4;
+                if (idx < 4 * Q)
+                    for (int w = part; w < W; w += 4) m = min4(m, part2[w * Q + q]);
+#pragma unroll
+                for (int o = 1; o <= 2; o <<= 1)
+                    m = min4(m, make_float4(__shfl_xor_sync(0xffffffffu, m.x, o), __shfl_xor_sync(0xffffffffu, m.y, o),
+                                            __shfl_xor_sync(0xffffffffu, m.z, o), __shfl_xor_sync(0xffffffffu, m.w, o)));
+                if (idx < 4 * Q && part == 0) push(q, m);
+            }
+        } else if (nsub >= 1) {
             if (tid < nsub * Q) {
                 const int q = tid % Q, sub = tid / Q;
                 float4 m = make_float4(INFINITY, INFINITY, INFINITY, INFINITY);
@@ -276,7 +367,7 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
             }
             __syncthreads();
         }
-        for (int q = tid; q < Q; q += T) {
+        for (int q = tid; q < (RR ? 0 : Q); q += T) {
             float4 m;
             if (nsub >= 1) {
                 m = sm.part[q];
@@ -285,11 +376,7 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
                 m = make_float4(INFINITY, INFINITY, INFINITY, INFINITY);
                 for (int s = 0; s < nr; ++s) m = min4(m, add4s(t4[static_cast<size_t>(s) * Q + q], sm.alpha[s]));
             }
-            if (CLUSTER) {
-                for (int r = 0; r < C; ++r) st_dsmem_f4(mapa_shared(slot + 16u * q, r), m);
-            } else {
-                reinterpret_cast<float4 *>(xbuf)[q] = m;
-            }
+            push(q, m);
         }
     }
 
@@ -317,16 +404,13 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
     // CTA has passed the next item's exchange barrier, i.e. after this read.
     __syncthreads();
 
-    // node v's new vector (one CTA of the cluster), published before pass 3
+    // node v's new vector (one CTA of the cluster), stored before pass 3 and
+    // published with node u's rows at the end of the update
     if (rank == 0) {
         for (int t = tid; t < Lv; t += T) {
             const float2 b = sm.bv[t];
             __stcg(agg + ed.av + t, b);
             __stcg(msg + ed.mv + t, df_sub(b, sm.vh[t]));
-        }
-        if (SIGNAL) {
-            __syncthreads();
-            if (tid == 0) signal_node(p.ver, ed.gv, static_cast<unsigned>(C));
         }
     }
 
@@ -339,18 +423,43 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
             __stcg(agg + ed.au + r0 + s, c);
             __stcg(msg + ed.mu + r0 + s, df_sub(c, u));
         };
-        for (int base = 0; base < nr; base += ng) {
-            const int s = base + gid;
-            float m = s < nr ? row_min(t4 + static_cast<size_t>(s) * Q, w, Q, lg, G) : INFINITY;
-            group_min(m, G);
-            if (s < nr && lg == 0) emit(s, m);
+        if (RR) {
+            float acc[kRR];
+            float4 bw[kCR];
+#pragma unroll
+            for (int i = 0; i < kCR; ++i) bw[i] = lane + 32 * i < Q ? w[lane + 32 * i] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int k = 0; k < kRR; ++k) {
+                acc[k] = INFINITY;
+#pragma unroll
+                for (int i = 0; i < kCR; ++i) acc[k] = min_add4(acc[k], tr[k][i], bw[i]);
+            }
+            warp_min_rows(acc);
+            // every lane holds every row's minimum: lane k emits row k, all at once
+            float mk = acc[0];
+#pragma unroll
+            for (int k = 1; k < kRR; ++k) mk = lane == k ? acc[k] : mk;
+            if (lane < kRR && warp + W * lane < nr) emit(warp + W * lane, mk);
+        } else {
+            for (int base = 0; base < nr; base += ng) {
+                const int s = base + gid;
+                float m = s < nr ? row_min(t4 + static_cast<size_t>(s) * Q, w, Q, lg, G) : INFINITY;
+                group_min(m, G);
+                if (s < nr && lg == 0) emit(s, m);
+            }
         }
     }
     __syncthreads();
-    if (SIGNAL && tid == 0) signal_node(p.ver, ed.gu, 1u);
+    // one release for the whole update, by the last warp (which sits out the
+    // next update's load phase): C arrivals on each end node per update
+    if (SIGNAL && tid == T - 1) {
+        asm volatile("fence.acq_rel.gpu;" ::: "memory");
+        red_add(p.ver + ed.gu, 1u);
+        if (rank == 0) red_add(p.ver + ed.gv, static_cast<unsigned>(C));
+    }
 }
 
-template <bool CLUSTER>
+template <bool CLUSTER, bool RRK>
 __global__ void __launch_bounds__(512) hs_looped_kernel(HsParams p)
 {
     extern __shared__ __align__(16) char smem_raw[];
@@ -368,10 +477,15 @@ __global__ void __launch_bounds__(512) hs_looped_kernel(HsParams p)
         cluster_arrive_relaxed();
         cluster_wait_acquire();
     }
-    hs_item<CLUSTER, false>(p, ed, sm.tile, sm, rank, &sm.bar[0], 0u, 0);
+    int r0, nr;
+    rows_of(ed, rank, C, r0, nr);
+    if (RRK && rr_fits(nr, ed.ld >> 2, blockDim.x, p.tile_floats))
+        hs_item<CLUSTER, false, RRK>(p, ed, sm.tile, sm, rank, &sm.bar[0], 0u, 0);
+    else
+        hs_item<CLUSTER, false, false>(p, ed, sm.tile, sm, rank, &sm.bar[0], 0u, 0);
 }
 
-template <bool CLUSTER>
+template <bool CLUSTER, bool RRK>
 __global__ void __launch_bounds__(512) hs_persistent_kernel(HsParams p)
 {
     extern __shared__ __align__(16) char smem_raw[];
@@ -411,8 +525,14 @@ __global__ void __launch_bounds__(512) hs_persistent_kernel(HsParams p)
                                 ((p.test_wait && k == 0 && cid == 0) ? 1u : 0u);
         const unsigned need_v = static_cast<unsigned>(C) * static_cast<unsigned>(it * w.deg_v + w.pos_v);
         const int b = static_cast<int>(k & 1);
-        hs_item<CLUSTER, true>(p, ed, sm.tile + b * p.tile_floats, sm, rank, sm.bar + b,
-                               static_cast<uint32_t>((k >> 1) & 1), b, need_u, need_v);
+        int r0, nr;
+        rows_of(ed, rank, C, r0, nr);
+        if (RRK && rr_fits(nr, ed.ld >> 2, blockDim.x, p.tile_floats))
+            hs_item<CLUSTER, true, RRK>(p, ed, sm.tile + b * p.tile_floats, sm, rank, sm.bar + b,
+                                         static_cast<uint32_t>((k >> 1) & 1), b, need_u, need_v);
+        else
+            hs_item<CLUSTER, true, false>(p, ed, sm.tile + b * p.tile_floats, sm, rank, sm.bar + b,
+                                          static_cast<uint32_t>((k >> 1) & 1), b, need_u, need_v);
         if (++i == n) {
             i = 0;
             ++it;
@@ -465,35 +585,52 @@ size_t hs_smem_bytes(int nbuf, int tile_floats, int rmax, int ldmax, int threads
 cudaError_t hs_prepare(size_t smem)
 {
     cudaError_t e;
-    if ((e = set_attrs(hs_looped_kernel<false>, smem)) != cudaSuccess) return e;
-    if ((e = set_attrs(hs_looped_kernel<true>, smem)) != cudaSuccess) return e;
-    if ((e = set_attrs(hs_persistent_kernel<false>, smem)) != cudaSuccess) return e;
-    return set_attrs(hs_persistent_kernel<true>, smem);
+    if ((e = set_attrs(hs_looped_kernel<false, false>, smem)) != cudaSuccess) return e;
+    if ((e = set_attrs(hs_looped_kernel<true, false>, smem)) != cudaSuccess) return e;
+    if ((e = set_attrs(hs_looped_kernel<false, true>, smem)) != cudaSuccess) return e;
+    if ((e = set_attrs(hs_looped_kernel<true, true>, smem)) != cudaSuccess) return e;
+    if ((e = set_attrs(hs_persistent_kernel<false, false>, smem)) != cudaSuccess) return e;
+    if ((e = set_attrs(hs_persistent_kernel<true, false>, smem)) != cudaSuccess) return e;
+    if ((e = set_attrs(hs_persistent_kernel<false, true>, smem)) != cudaSuccess) return e;
+    return set_attrs(hs_persistent_kernel<true, true>, smem);
 }
 
 cudaError_t hs_launch_looped(const HsParams &p, int n_items, int threads, size_t smem, cudaStream_t st)
 {
     if (n_items <= 0) return cudaSuccess;
     const int grid = n_items * p.C;
-    return p.C > 1 ? launch(hs_looped_kernel<true>, p, grid, threads, smem, p.C, st)
-                   : launch(hs_looped_kernel<false>, p, grid, threads, smem, 1, st);
+    if (p.rr)
+        return p.C > 1 ? launch(hs_looped_kernel<true, true>, p, grid, threads, smem, p.C, st)
+                       : launch(hs_looped_kernel<false, true>, p, grid, threads, smem, 1, st);
+    return p.C > 1 ? launch(hs_looped_kernel<true, false>, p, grid, threads, smem, p.C, st)
+                   : launch(hs_looped_kernel<false, false>, p, grid, threads, smem, 1, st);
 }
 
 cudaError_t hs_launch_persistent(const HsParams &p, int clusters, int threads, size_t smem, cudaStream_t st)
 {
     const int grid = clusters * p.C;
-    return p.C > 1 ? launch(hs_persistent_kernel<true>, p, grid, threads, smem, p.C, st)
-                   : launch(hs_persistent_kernel<false>, p, grid, threads, smem, 1, st);
+    if (p.rr)
+        return p.C > 1 ? launch(hs_persistent_kernel<true, true>, p, grid, threads, smem, p.C, st)
+                       : launch(hs_persistent_kernel<false, true>, p, grid, threads, smem, 1, st);
+    return p.C > 1 ? launch(hs_persistent_kernel<true, false>, p, grid, threads, smem, p.C, st)
+                   : launch(hs_persistent_kernel<false, false>, p, grid, threads, smem, 1, st);
 }
 
-int hs_max_active_clusters(int C, int threads, size_t smem)
+bool hs_rr_fits(int nr_max, int Q_max, int threads, int tile_floats)
+{
+    return Q_max > 32 && Q_max <= 32 * kCR && nr_max <= kRR * (threads >> 5) && (threads >> 5) * Q_max * 4 <= tile_floats;
+}
+
+int hs_max_active_clusters(int C, int threads, size_t smem, bool rr)
 {
     if (hs_prepare(smem) != cudaSuccess) return 0;
     if (C <= 1) {
         int per_sm = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hs_persistent_kernel<false>, threads, smem) !=
-            cudaSuccess)
-            return 0;
+        const cudaError_t e = rr ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hs_persistent_kernel<false, true>,
+                                                                                  threads, smem)
+                                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hs_persistent_kernel<false, false>,
+                                                                                  threads, smem);
+        if (e != cudaSuccess) return 0;
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -511,8 +648,9 @@ int hs_max_active_clusters(int C, int threads, size_t smem)
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, hs_persistent_kernel<true>, &cfg) != cudaSuccess) return 0;
-    return n;
+    const cudaError_t e = rr ? cudaOccupancyMaxActiveClusters(&n, hs_persistent_kernel<true, true>, &cfg)
+                             : cudaOccupancyMaxActiveClusters(&n, hs_persistent_kernel<true, false>, &cfg);
+    return e == cudaSuccess ? n : 0;
 }
 
 }  // namespace mplpp

@@ -22,6 +22,7 @@ struct HsParams {
     long long spin_limit;    // polls before a wait gives up
     int iterations;          // persistent: iterations to run
     int test_wait;           // testing: first item of worker 0 waits for an update that never comes
+    int rr;                  // launch the variant with register-resident passes
     int C;                   // CTAs per edge (cluster size)
     int tile_floats;         // capacity of one table buffer (floats)
     int rmax;                // capacity of row vectors (floats, multiple of 4)
@@ -32,7 +33,8 @@ size_t hs_smem_bytes(int nbuf, int tile_floats, int rmax, int ldmax, int threads
 cudaError_t hs_prepare(size_t smem_bytes);
 cudaError_t hs_launch_looped(const HsParams &p, int n_items, int threads, size_t smem, cudaStream_t st);
 cudaError_t hs_launch_persistent(const HsParams &p, int clusters, int threads, size_t smem, cudaStream_t st);
-int hs_max_active_clusters(int C, int threads, size_t smem);
+int hs_max_active_clusters(int C, int threads, size_t smem, bool rr);
+bool hs_rr_fits(int nr_max, int Q_max, int threads, int tile_floats);
 
 // dual.cu
 cudaError_t launch_pack(const EdgeDesc *edges, int n_edges, const NodeDesc *nodes, int n_nodes,

@@ -49,6 +49,7 @@ struct mplpp_solver {
     int mode = MPLPP_MODE_LOOPED;
     int C = 1, T = 256, tile_floats = 4, rmax = 4, ldmax = 4, max_phase = 1, clusters = 0, max_deg = 0;
     int work_off_cap = 0;  // capacity of d_work_off
+    bool rr = false;       // register-resident pass variant
     size_t smem_looped = 0, smem_persist = 0;
 
     // device

@@ -385,3 +385,22 @@ def test_autotune_keeps_state_and_results():
     b.run(8)
     sa, sb = a.state_arrays(), b.state_arrays()
     assert np.array_equal(sa[1], sb[1]) and np.array_equal(sa[2], sb[2])
+
+
+@pytest.mark.parametrize("cluster,threads", [(3, 512), (4, 512), (4, 256)])
+@pytest.mark.parametrize("mode", ["looped", "persistent"])
+def test_register_resident_passes_ragged(cluster, threads, mode):
+    """Rows of 130..260 labels: tables whose CTA slice has at most 5 rows per
+    warp take the register-resident passes (33..96 float4 chunks per row),
+    the others the shared-memory passes, in the same solve; both must match
+    the oracle and each other bit for bit."""
+    m = W.uneven_complete(6, 130, 260, seed=cluster + threads)
+    T = 6
+    sol = oracle.solve(m, _order(m), T)
+    s, D, xs, en = _solve_gpu([m], T, mode=mode, cluster=cluster, threads=threads)
+    _check_D(D[0], sol["bound"])
+    _check_labels(m, xs[0], sol, en[0])
+    ref = Solver([m], mode="looped", cluster=8, threads=128)  # never register-resident (5 rows x 4 warps < rows)
+    ref.run(T)
+    a, b = s.state_arrays(), ref.state_arrays()
+    assert np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
