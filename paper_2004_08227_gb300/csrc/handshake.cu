@@ -214,6 +214,28 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
     float2 *agg = p.agg;
     float2 *msg = p.msg;
 
+    // The table slice: wait for its bulk copy and, for the register-resident
+    // passes, load this thread's fragment.  Independent of the node vectors:
+    // the persistent driver does it before waiting for the end nodes (the
+    // slice was prefetched), the looped one after issuing its vector loads.
+    const float4 *t4 = reinterpret_cast<const float4 *>(tile);
+    const int lane = tid & 31, warp = tid >> 5, W = T >> 5;
+    const float4 inf4 = make_float4(INFINITY, INFINITY, INFINITY, INFINITY);
+    float4 tr[RR ? kRR : 1][RR ? kCR : 1];
+    auto load_tile = [&]() {
+        if (!mbar_wait(bar, parity, p.spin_limit)) set_err(p.err, ERR_TIMEOUT);
+        if (RR) {
+#pragma unroll
+            for (int k = 0; k < kRR; ++k)
+#pragma unroll
+                for (int i = 0; i < kCR; ++i) {
+                    const int s = warp + W * k, q = lane + 32 * i;
+                    tr[k][i] = (s < nr && q < Q) ? t4[static_cast<size_t>(s) * Q + q] : inf4;
+                }
+        }
+    };
+    if (SIGNAL) load_tile();
+
     // unaries without this edge's messages (written by other SMs: L2 loads).
     // Persistent driver: the first half of the warps waits for node v's
     // earlier updates (one lane polls, a named barrier releases the half) and
@@ -255,25 +277,12 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
         }
     }
 
-    if (!mbar_wait(bar, parity, p.spin_limit)) set_err(p.err, ERR_TIMEOUT);
+    if (!SIGNAL) load_tile();
     __syncthreads();
 
-    const float4 *t4 = reinterpret_cast<const float4 *>(tile);
     const int G = row_lanes(nr, Q, T);
     const int gid = tid / G, lg = tid % G, ng = T / G;
     float *xbuf = sm.pm + static_cast<size_t>(xpar) * C * ld;  // this item's exchange slots
-    const int lane = tid & 31, warp = tid >> 5, W = T >> 5;
-    const float4 inf4 = make_float4(INFINITY, INFINITY, INFINITY, INFINITY);
-    float4 tr[RR ? kRR : 1][RR ? kCR : 1];
-    if (RR) {
-#pragma unroll
-        for (int k = 0; k < kRR; ++k)
-#pragma unroll
-            for (int i = 0; i < kCR; ++i) {
-                const int s = warp + W * k, q = lane + 32 * i;
-                tr[k][i] = (s < nr && q < Q) ? t4[static_cast<size_t>(s) * Q + q] : inf4;
-            }
-    }
 
     // pass 1: a(s) = 1/2 (min_t [theta(s,t) + w1(t)] + vh(0) + uh(s));  alpha = uh - a
     {
