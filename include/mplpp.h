@@ -63,8 +63,9 @@ enum {
 enum {
     MPLPP_MODE_AUTO = 0,       /* persistent when the device allows it, else looped            */
     MPLPP_MODE_LOOPED = 1,     /* one kernel launch per matching (launch boundary = barrier)  */
-    MPLPP_MODE_PERSISTENT = 2  /* one launch for all iterations; per-node completion counters
-                                  order the matchings on the device                           */
+    MPLPP_MODE_PERSISTENT = 2  /* one launch for all iterations; every state entry carries the
+                                  update count that wrote it, which orders the matchings on
+                                  the device (a reader polls until the count it needs)        */
 };
 
 typedef struct {

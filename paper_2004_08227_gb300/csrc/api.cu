@@ -400,7 +400,6 @@ extern "C" mplpp_status mplpp_create(const mplpp_model *models, int32_t n_models
     CKC(S->alloc(&S->d_msg, S->msgN));
     CKC(S->alloc(&S->d_phase_edges, S->phase_edges.size()));
     CKC(S->alloc(&S->d_err, 1));
-    CKC(S->alloc(&S->d_ver, S->N));
     CKC(S->alloc(&S->d_in_off, S->in_off.size()));
     CKC(S->alloc(&S->d_in_edge, S->in_edge.size()));
     CKC(S->alloc(&S->d_mnode_off, S->mnode_off.size()));
@@ -429,7 +428,7 @@ extern "C" mplpp_status mplpp_create(const mplpp_model *models, int32_t n_models
         if (ms != MPLPP_OK) return fail(nullptr, ms, S->err);
     }
     CKC(cudaMemsetAsync(S->d_err, 0, sizeof(int), st));
-    CKC(cudaMemsetAsync(S->d_msg, 0, S->msgN * sizeof(float2), st));
+    CKC(cudaMemsetAsync(S->d_msg, 0, S->msgN * sizeof(ulonglong2), st));  // 0, version 0
 
     // costs: stage (host inputs) or read in place (device inputs), then pack
     float *stage_u = nullptr, *stage_p = nullptr;
@@ -482,7 +481,6 @@ static HsParams make_params(mplpp_solver *s)
     p.items = s->d_phase_edges;
     p.work_off = s->d_work_off;
     p.work = s->d_work;
-    p.ver = s->d_ver;
     p.err = s->d_err;
     p.spin_limit = s->opt.spin_limit;
     p.test_wait = s->opt.test_unreachable_wait ? 1 : 0;
@@ -507,23 +505,16 @@ cudaError_t enqueue_looped_iteration(mplpp_solver *s, cudaStream_t st)
     return cudaSuccess;
 }
 
-// `iterations` iterations of the persistent kernel (counters reset first).
+// `iterations` iterations of the persistent kernel.  The versions of the
+// state entries count updates from 0 within one launch, so they are reset
+// first (whatever ran before: looped launches, an aborted run, load_state).
 cudaError_t enqueue_persistent(mplpp_solver *s, cudaStream_t st, int iterations)
 {
     HsParams p = make_params(s);
-    // counters stay below 2^31: C * iterations * max_deg per launch
-    const long long cap = std::max(1LL, (1LL << 31) / (static_cast<long long>(s->C) * std::max(1, s->max_deg) + 1));
-    int done = 0;
-    while (done < iterations) {
-        const int chunk = static_cast<int>(std::min<long long>(iterations - done, cap));
-        cudaError_t e = cudaMemsetAsync(s->d_ver, 0, sizeof(unsigned) * s->N, st);
-        if (e != cudaSuccess) return e;
-        p.iterations = chunk;
-        e = hs_launch_persistent(p, s->clusters, s->T, s->smem_persist, st);
-        if (e != cudaSuccess) return e;
-        done += chunk;
-    }
-    return cudaSuccess;
+    cudaError_t e = launch_restamp(s->d_agg, s->aggN, s->d_msg, s->msgN, st);
+    if (e != cudaSuccess) return e;
+    p.iterations = iterations;
+    return hs_launch_persistent(p, s->clusters, s->T, s->smem_persist, st);
 }
 
 static mplpp_status run_plain(mplpp_solver *s, int iterations)
@@ -575,8 +566,7 @@ static mplpp_status run_plain(mplpp_solver *s, int iterations)
         } else {
             CK(s, enqueue_persistent(s, s->stream, iterations));
         }
-        const long long cap = std::max(1LL, (1LL << 31) / (static_cast<long long>(s->C) * std::max(1, s->max_deg) + 1));
-        s->launches += (iterations + cap - 1) / cap;
+        s->launches += 2;  // restamp + persistent kernel
     }
     return MPLPP_OK;
 }
@@ -664,9 +654,9 @@ extern "C" mplpp_status mplpp_save_state(mplpp_solver *s, void *buf, size_t size
     size_t need = 0;
     mplpp_state_size(s, &need);
     if (size < need) return fail(s, MPLPP_E_INVALID, "state buffer too small");
-    std::vector<float2> agg(s->aggN), msg(s->msgN);
-    CK(s, cudaMemcpyAsync(agg.data(), s->d_agg, s->aggN * sizeof(float2), cudaMemcpyDeviceToHost, s->stream));
-    CK(s, cudaMemcpyAsync(msg.data(), s->d_msg, s->msgN * sizeof(float2), cudaMemcpyDeviceToHost, s->stream));
+    std::vector<ulonglong2> agg(s->aggN), msg(s->msgN);
+    CK(s, cudaMemcpyAsync(agg.data(), s->d_agg, s->aggN * sizeof(ulonglong2), cudaMemcpyDeviceToHost, s->stream));
+    CK(s, cudaMemcpyAsync(msg.data(), s->d_msg, s->msgN * sizeof(ulonglong2), cudaMemcpyDeviceToHost, s->stream));
     mplpp_status st = mplpp_sync(s);
     if (st != MPLPP_OK) return st;
     mplpp_state_header h;
@@ -680,8 +670,11 @@ extern "C" mplpp_status mplpp_save_state(mplpp_solver *s, void *buf, size_t size
     std::memcpy(p, &h, sizeof(h));
     // portable format: FP64 values hi + lo (exact)
     double *f = reinterpret_cast<double *>(p + sizeof(h));
-    auto put = [&](const float2 *src, int n) {
-        for (int i = 0; i < n; ++i) *f++ = static_cast<double>(src[i].x) + static_cast<double>(src[i].y);
+    auto put = [&](const ulonglong2 *src, int n) {
+        for (int i = 0; i < n; ++i) {
+            const float2 v = se_df(src[i]);
+            *f++ = static_cast<double>(v.x) + static_cast<double>(v.y);
+        }
     };
     for (auto &nd : s->h_nodes) put(agg.data() + nd.aoff, nd.L);
     for (auto &ed : s->h_edges) {
@@ -703,13 +696,14 @@ extern "C" mplpp_status mplpp_load_state(mplpp_solver *s, const void *buf, size_
     if (h.magic != 0x4D504C50u || h.version != 2 || h.shape_hash != s->shape_hash || h.n_unary != s->sum_unary ||
         h.n_msg != s->sum_msg)
         return fail(s, MPLPP_E_INVALID, "state does not match this solver's models");
-    std::vector<float2> agg(s->aggN, make_float2(0.f, 0.f)), msg(s->msgN, make_float2(0.f, 0.f));
+    const ulonglong2 zero = se_make(make_float2(0.f, 0.f), 0u);
+    std::vector<ulonglong2> agg(s->aggN, zero), msg(s->msgN, zero);
     const double *f = reinterpret_cast<const double *>(static_cast<const char *>(buf) + sizeof(h));
     // FP64 value -> hi = nearest float, lo = nearest float to the remainder
-    auto get = [&](float2 *dst, int n) {
+    auto get = [&](ulonglong2 *dst, int n) {
         for (int i = 0; i < n; ++i, ++f) {
             const float hi = static_cast<float>(*f);
-            dst[i] = make_float2(hi, static_cast<float>(*f - static_cast<double>(hi)));
+            dst[i] = se_make(make_float2(hi, static_cast<float>(*f - static_cast<double>(hi))), 0u);
         }
     };
     for (auto &nd : s->h_nodes) {
@@ -723,8 +717,8 @@ extern "C" mplpp_status mplpp_load_state(mplpp_solver *s, const void *buf, size_
         get(msg.data() + ed.mu, ed.Lu);
         get(msg.data() + ed.mv, ed.Lv);
     }
-    CK(s, cudaMemcpyAsync(s->d_agg, agg.data(), s->aggN * sizeof(float2), cudaMemcpyHostToDevice, s->stream));
-    CK(s, cudaMemcpyAsync(s->d_msg, msg.data(), s->msgN * sizeof(float2), cudaMemcpyHostToDevice, s->stream));
+    CK(s, cudaMemcpyAsync(s->d_agg, agg.data(), s->aggN * sizeof(ulonglong2), cudaMemcpyHostToDevice, s->stream));
+    CK(s, cudaMemcpyAsync(s->d_msg, msg.data(), s->msgN * sizeof(ulonglong2), cudaMemcpyHostToDevice, s->stream));
     CK(s, cudaStreamSynchronize(s->stream));
     s->iterations = h.iterations;
     s->history_valid = false;
@@ -747,12 +741,12 @@ extern "C" mplpp_status mplpp_autotune(mplpp_solver *s, int32_t iterations, char
         CK(s, s->alloc(&s->d_save_msg, s->msgN));
     }
     cudaStream_t st = s->stream;
-    CK(s, cudaMemcpyAsync(s->d_save_agg, s->d_agg, sizeof(float2) * s->aggN, cudaMemcpyDeviceToDevice, st));
-    CK(s, cudaMemcpyAsync(s->d_save_msg, s->d_msg, sizeof(float2) * s->msgN, cudaMemcpyDeviceToDevice, st));
+    CK(s, cudaMemcpyAsync(s->d_save_agg, s->d_agg, sizeof(ulonglong2) * s->aggN, cudaMemcpyDeviceToDevice, st));
+    CK(s, cudaMemcpyAsync(s->d_save_msg, s->d_msg, sizeof(ulonglong2) * s->msgN, cudaMemcpyDeviceToDevice, st));
     auto restore = [&]() -> cudaError_t {
-        cudaError_t e = cudaMemcpyAsync(s->d_agg, s->d_save_agg, sizeof(float2) * s->aggN, cudaMemcpyDeviceToDevice, st);
+        cudaError_t e = cudaMemcpyAsync(s->d_agg, s->d_save_agg, sizeof(ulonglong2) * s->aggN, cudaMemcpyDeviceToDevice, st);
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(s->d_msg, s->d_save_msg, sizeof(float2) * s->msgN, cudaMemcpyDeviceToDevice, st);
+            e = cudaMemcpyAsync(s->d_msg, s->d_save_msg, sizeof(ulonglong2) * s->msgN, cudaMemcpyDeviceToDevice, st);
         return e;
     };
     const int oldC = s->C, oldT = s->T, oldMode = s->mode;

@@ -2,13 +2,17 @@
 // solver's kernels (Handshake update, dual bound, rounding, backward).
 //
 // Device layout of a solver (all models concatenated, model after model):
-//   agg  [double] theta^phi_u of every node (Sec. 3, eq. reparametrization),
-//                 each node's vector padded to a multiple of 4 entries (32-byte
-//                 aligned), pad = 0;
-//   msg  [double] per edge phi_{v->u} (L_u) then phi_{u->v} (L_v), each padded
-//                 to a multiple of 4 entries, pad = 0;
-//                 (FP64 because these sums grow large over many updates; the
-//                 O(L^2) table work stays FP32)
+//   agg  [u64 x 2] theta^phi_u of every node (Sec. 3, eq. reparametrization),
+//                 each node's vector padded to a multiple of 4 entries, pad 0;
+//   msg  [u64 x 2] per edge phi_{v->u} (L_u) then phi_{u->v} (L_v), each
+//                 padded to a multiple of 4 entries, pad 0.
+//                 Every entry is a double-float (hi + lo, see below) stored as
+//                 two self-validating 8-byte words {payload float, version}:
+//                 the version counts the updates of the node (agg) or edge
+//                 (msg) that wrote it, so a reader on another SM accepts a
+//                 value only when its word carries the version it expects
+//                 (8-byte aligned accesses are single-copy atomic); no fence
+//                 or counter orders the producer and the consumer.
 //   tab  [float]  the ORIGINAL pairwise tables theta_uv, never written after
 //                 creation; rows of L_v entries padded to a stride `ld`
 //                 (multiple of 4) with +inf, tables 16-byte aligned.  The
@@ -17,16 +21,17 @@
 //   un0  [float]  the original unaries in agg's layout (reset, energy).
 #pragma once
 #include <cstdint>
+#include <cstring>
 #include <cuda_runtime.h>
 
 namespace mplpp {
 
 struct EdgeDesc {
     long long toff;   // float offset of the table in tab (Lu rows, stride ld)
-    long long mu;     // float offset of phi_{v->u} in msg (Lu entries)
-    long long mv;     // float offset of phi_{u->v} in msg (Lv entries)
-    long long au;     // float offset of node u's vector in agg
-    long long av;     // float offset of node v's vector in agg
+    long long mu;     // entry offset of phi_{v->u} in msg (Lu entries)
+    long long mv;     // entry offset of phi_{u->v} in msg (Lv entries)
+    long long au;     // entry offset of node u's vector in agg
+    long long av;     // entry offset of node v's vector in agg
     long long poff;   // float offset of the table in the caller's (unpadded) layout
     int Lu, Lv, ld;   // label counts and row stride (ld = Lv rounded up to 4)
     int gu, gv;       // global node ids
@@ -158,13 +163,6 @@ __device__ __forceinline__ void st_dsmem_f4(uint32_t addr, float4 v)
                  : "memory");
 }
 
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p)
-{
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
 __device__ __forceinline__ float4 min4(float4 a, float4 b)
 {
     return make_float4(fminf(a.x, b.x), fminf(a.y, b.y), fminf(a.z, b.z), fminf(a.w, b.w));
@@ -227,6 +225,59 @@ __device__ __forceinline__ float df_to_f(float2 a)
 __device__ __forceinline__ double df_to_d(float2 a)
 {
     return static_cast<double>(a.x) + static_cast<double>(a.y);
+}
+
+// ----------------------------------------------------------------------------
+// State entries: one double-float value as two self-validating 8-byte words,
+// x = {hi (low 32 bits), version (high 32 bits)}, y = {lo, version}.
+// ----------------------------------------------------------------------------
+__host__ __device__ __forceinline__ unsigned long long se_word(float v, unsigned version)
+{
+    unsigned bits;
+    memcpy(&bits, &v, 4);
+    return static_cast<unsigned long long>(bits) | (static_cast<unsigned long long>(version) << 32);
+}
+
+__host__ __device__ __forceinline__ float se_val(unsigned long long w)
+{
+    const unsigned bits = static_cast<unsigned>(w & 0xffffffffull);
+    float v;
+    memcpy(&v, &bits, 4);
+    return v;
+}
+
+__host__ __device__ __forceinline__ ulonglong2 se_make(float2 v, unsigned version)
+{
+    return make_ulonglong2(se_word(v.x, version), se_word(v.y, version));
+}
+
+__host__ __device__ __forceinline__ float2 se_df(ulonglong2 e)
+{
+    return make_float2(se_val(e.x), se_val(e.y));
+}
+
+// both words of the entry carry `version` (each word is read atomically)
+__device__ __forceinline__ bool se_ok(ulonglong2 e, unsigned version)
+{
+    return static_cast<unsigned>(e.x >> 32) == version && static_cast<unsigned>(e.y >> 32) == version;
+}
+
+__device__ __forceinline__ double se_d(ulonglong2 e)
+{
+    return static_cast<double>(se_val(e.x)) + static_cast<double>(se_val(e.y));
+}
+
+// Loads / stores of one entry at gpu scope (L2), one 8-byte-atomic access per word.
+__device__ __forceinline__ ulonglong2 ld_se(const ulonglong2 *p)
+{
+    ulonglong2 v;
+    asm volatile("ld.relaxed.gpu.global.v2.b64 {%0, %1}, [%2];" : "=l"(v.x), "=l"(v.y) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_se(ulonglong2 *p, ulonglong2 v)
+{
+    asm volatile("st.relaxed.gpu.global.v2.b64 [%0], {%1, %2};" ::"l"(p), "l"(v.x), "l"(v.y) : "memory");
 }
 
 // Three-input minimum (one instruction on sm_100+); same value as two fminf.

@@ -14,7 +14,8 @@ namespace {
 constexpr int kThreads = 256;
 
 // Copies the caller's row-major tables into the padded layout (row stride ld,
-// pad +inf) and the unaries into un0 (FP32) and agg (double-float), pad 0.
+// pad +inf) and the unaries into un0 (FP32) and agg (double-float entries,
+// version 0), pad 0.
 // Flags non-finite costs.
 __global__ void pack_tables_kernel(const EdgeDesc *edges, int n_edges, const float *src, float *tab, int *err)
 {
@@ -34,7 +35,7 @@ __global__ void pack_tables_kernel(const EdgeDesc *edges, int n_edges, const flo
     }
 }
 
-__global__ void pack_unary_kernel(const NodeDesc *nodes, int n_nodes, const float *src, float *un0, float2 *agg,
+__global__ void pack_unary_kernel(const NodeDesc *nodes, int n_nodes, const float *src, float *un0, ulonglong2 *agg,
                                   int *err)
 {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -50,7 +51,7 @@ __global__ void pack_unary_kernel(const NodeDesc *nodes, int n_nodes, const floa
                 if (!isfinite(v)) atomicCAS(err, 0, ERR_NONFINITE);
             }
             un0[nd.aoff + s] = v;
-            agg[nd.aoff + s] = make_float2(v, 0.f);
+            agg[nd.aoff + s] = se_make(make_float2(v, 0.f), 0u);
         }
     }
 }
@@ -72,7 +73,7 @@ __device__ __forceinline__ double block_min(double v, double *red)
 
 // emin[e] = min_{s,t} (theta_uv(s,t) - phi_{v->u}(s)) - phi_{u->v}(t)   (FP64)
 __global__ void __launch_bounds__(kThreads) bound_edges_kernel(const EdgeDesc *edges, int n_edges,
-                                                               const float *tab, const float2 *msg, double *emin)
+                                                               const float *tab, const ulonglong2 *msg, double *emin)
 {
     __shared__ double red[32];
     for (int e = blockIdx.x; e < n_edges; e += gridDim.x) {
@@ -83,8 +84,8 @@ __global__ void __launch_bounds__(kThreads) bound_edges_kernel(const EdgeDesc *e
             const int s = static_cast<int>(i / ed.Lv);
             const int t = static_cast<int>(i - static_cast<long long>(s) * ed.Lv);
             const double r =
-                (static_cast<double>(tab[ed.toff + static_cast<long long>(s) * ed.ld + t]) - df_to_d(msg[ed.mu + s])) -
-                df_to_d(msg[ed.mv + t]);
+                (static_cast<double>(tab[ed.toff + static_cast<long long>(s) * ed.ld + t]) - se_d(msg[ed.mu + s])) -
+                se_d(msg[ed.mv + t]);
             m = fmin(m, r);
         }
         m = block_min<kThreads>(m, red);
@@ -93,7 +94,7 @@ __global__ void __launch_bounds__(kThreads) bound_edges_kernel(const EdgeDesc *e
 }
 
 // nmin[u] = min_s theta^phi_u(s)   (FP64)
-__global__ void bound_nodes_kernel(const NodeDesc *nodes, int n_nodes, const float2 *agg, double *nmin)
+__global__ void bound_nodes_kernel(const NodeDesc *nodes, int n_nodes, const ulonglong2 *agg, double *nmin)
 {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -101,7 +102,7 @@ __global__ void bound_nodes_kernel(const NodeDesc *nodes, int n_nodes, const flo
     for (int u = warp; u < n_nodes; u += nw) {
         const NodeDesc nd = nodes[u];
         double m = INFINITY;
-        for (int s = lane; s < nd.L; s += 32) m = fmin(m, df_to_d(agg[nd.aoff + s]));
+        for (int s = lane; s < nd.L; s += 32) m = fmin(m, se_d(agg[nd.aoff + s]));
         for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
         if (lane == 0) nmin[u] = m;
     }
@@ -146,7 +147,7 @@ __global__ void __launch_bounds__(kThreads) bound_sum_kernel(const int *model_no
 __global__ void __launch_bounds__(kThreads) round_kernel(const EdgeDesc *edges, const NodeDesc *nodes,
                                                          const int *in_off, const int *in_edge,
                                                          const int *model_node_off, const float *tab,
-                                                         const float2 *agg, const float2 *msg, int *labels,
+                                                         const ulonglong2 *agg, const ulonglong2 *msg, int *labels,
                                                          int *err)
 {
     __shared__ double rv[32];
@@ -158,14 +159,14 @@ __global__ void __launch_bounds__(kThreads) round_kernel(const EdgeDesc *edges, 
         double best = INFINITY;
         int bi = INT_MAX;
         for (int s = threadIdx.x; s < nd.L; s += kThreads) {
-            double acc = df_to_d(agg[nd.aoff + s]);
+            double acc = se_d(agg[nd.aoff + s]);
             for (int k = in_off[u]; k < in_off[u + 1]; ++k) {
                 const EdgeDesc ed = edges[in_edge[k]];
                 const int xv = labels[ed.gu];
                 const double term =
                     (static_cast<double>(tab[ed.toff + static_cast<long long>(xv) * ed.ld + s]) -
-                     df_to_d(msg[ed.mu + xv])) -
-                    df_to_d(msg[ed.mv + s]);
+                     se_d(msg[ed.mu + xv])) -
+                    se_d(msg[ed.mv + s]);
                 acc = acc + term;
             }
             if (acc < best) {
@@ -223,14 +224,30 @@ __global__ void __launch_bounds__(kThreads) energy_kernel(const EdgeDesc *edges,
     if (threadIdx.x == 0) energy[m] = En;
 }
 
-// agg := (un0, 0), msg := 0: the state phi = 0
-__global__ void init_state_kernel(const float *un0, float2 *agg, long long n_agg, float2 *msg, long long n_msg)
+// agg := (un0, 0), msg := 0: the state phi = 0 (version 0)
+__global__ void init_state_kernel(const float *un0, ulonglong2 *agg, long long n_agg, ulonglong2 *msg,
+                                  long long n_msg)
 {
     const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
     for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n_agg; i += stride)
-        agg[i] = make_float2(un0[i], 0.f);
+        agg[i] = se_make(make_float2(un0[i], 0.f), 0u);
     for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n_msg; i += stride)
-        msg[i] = make_float2(0.f, 0.f);
+        msg[i] = se_make(make_float2(0.f, 0.f), 0u);
+}
+
+// version := 0 in both words of every entry
+__global__ void restamp_kernel(ulonglong2 *agg, long long n_agg, ulonglong2 *msg, long long n_msg)
+{
+    const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
+    const unsigned long long keep = 0xffffffffull;
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n_agg; i += stride) {
+        const ulonglong2 e = agg[i];
+        agg[i] = make_ulonglong2(e.x & keep, e.y & keep);
+    }
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n_msg; i += stride) {
+        const ulonglong2 e = msg[i];
+        msg[i] = make_ulonglong2(e.x & keep, e.y & keep);
+    }
 }
 
 int grid_for(long long work, int per_block_items)
@@ -244,7 +261,7 @@ int grid_for(long long work, int per_block_items)
 }  // namespace
 
 cudaError_t launch_pack(const EdgeDesc *edges, int n_edges, const NodeDesc *nodes, int n_nodes,
-                        const float *unary_src, const float *pair_src, float *tab, float *un0, float2 *agg, int *err,
+                        const float *unary_src, const float *pair_src, float *tab, float *un0, ulonglong2 *agg, int *err,
                         cudaStream_t st)
 {
     if (n_edges > 0) {
@@ -260,7 +277,7 @@ cudaError_t launch_pack(const EdgeDesc *edges, int n_edges, const NodeDesc *node
     return cudaSuccess;
 }
 
-cudaError_t launch_init_state(const float *un0, float2 *agg, long long n_agg, float2 *msg, long long n_msg,
+cudaError_t launch_init_state(const float *un0, ulonglong2 *agg, long long n_agg, ulonglong2 *msg, long long n_msg,
                               cudaStream_t st)
 {
     init_state_kernel<<<grid_for(n_agg > n_msg ? n_agg : n_msg, kThreads), kThreads, 0, st>>>(un0, agg, n_agg, msg,
@@ -268,8 +285,14 @@ cudaError_t launch_init_state(const float *un0, float2 *agg, long long n_agg, fl
     return cudaGetLastError();
 }
 
+cudaError_t launch_restamp(ulonglong2 *agg, long long n_agg, ulonglong2 *msg, long long n_msg, cudaStream_t st)
+{
+    restamp_kernel<<<grid_for(n_agg > n_msg ? n_agg : n_msg, kThreads), kThreads, 0, st>>>(agg, n_agg, msg, n_msg);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_bound(const EdgeDesc *edges, int n_edges, const NodeDesc *nodes, int n_nodes, const float *tab,
-                         const float2 *agg, const float2 *msg, double *emin, double *nmin, const int *model_node_off,
+                         const ulonglong2 *agg, const ulonglong2 *msg, double *emin, double *nmin, const int *model_node_off,
                          const int *model_edge_off, int n_models, int exact, double *out, cudaStream_t st)
 {
     if (exact && n_edges > 0) {
@@ -288,7 +311,7 @@ cudaError_t launch_bound(const EdgeDesc *edges, int n_edges, const NodeDesc *nod
 
 cudaError_t launch_round(const EdgeDesc *edges, const NodeDesc *nodes, const int *in_off, const int *in_edge,
                          const int *model_node_off, const int *model_edge_off, int n_models, const float *tab,
-                         const float2 *agg, const float2 *msg, const float *un0, int *labels, double *energy, int *err,
+                         const ulonglong2 *agg, const ulonglong2 *msg, const float *un0, int *labels, double *energy, int *err,
                          cudaStream_t st)
 {
     round_kernel<<<n_models, kThreads, 0, st>>>(edges, nodes, in_off, in_edge, model_node_off, tab, agg, msg, labels,

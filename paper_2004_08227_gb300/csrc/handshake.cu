@@ -35,12 +35,16 @@
 //               (Sec. 6, GPU implementation: a barrier between matchings);
 //   persistent  one launch for all iterations; every cluster walks a fixed
 //               list of edges in schedule order and waits, per edge, only for
-//               the earlier updates of its two end nodes (per-node completion
-//               counters), while the next edge's table is already streaming
-//               into the second buffer.  Node v's new vector is published as
-//               soon as pass 2 has produced it, before pass 3.  Waits are
-//               bounded: past spin_limit polls the kernel records ERR_TIMEOUT
-//               and drains without waiting.
+//               the earlier updates of its two end nodes, while the next
+//               edge's table is already streaming into the second buffer.
+//               There are no counters or fences: every state entry carries the
+//               number of updates of its node (or edge) that produced it (see
+//               common.cuh), and a thread polls the entries it needs until
+//               they carry the expected count, so the data and the signal
+//               arrive in one L2 round trip.  Node v's new vector is visible
+//               as soon as it is stored, before pass 3.  Waits are bounded:
+//               past spin_limit polls the kernel records ERR_TIMEOUT and
+//               drains without waiting.
 #include <cfloat>
 #include <cstdint>
 
@@ -121,37 +125,65 @@ __device__ __forceinline__ void set_err(int *err, int code)
     atomicCAS(err, 0, code);
 }
 
-// Relaxed atomic add on a node counter; published by a preceding
-// fence.acq_rel.gpu, itself after a __syncthreads that follows the CTA's
-// global writes.
-__device__ __forceinline__ void red_add(unsigned *c, unsigned n)
-{
-    asm volatile("red.relaxed.gpu.global.add.u32 [%0], %1;" ::"l"(c), "r"(n) : "memory");
-}
-
-// Barriers 1 and 2 over `count` threads (a multiple of 32) of the CTA.
+// Barrier 1 over `count` threads (a multiple of 32) of the CTA.
 __device__ __forceinline__ void named_barrier_1(int count)
 {
     asm volatile("bar.sync 1, %0;" ::"r"(count) : "memory");
 }
 
-__device__ __forceinline__ void named_barrier_2(int count)
-{
-    asm volatile("bar.sync 2, %0;" ::"r"(count) : "memory");
-}
+// Update counts an item expects of its inputs (persistent driver): node u's
+// and node v's entries carry u / v (earlier updates of the node in this
+// launch), the edge's messages carry e (earlier updates of the edge); the
+// item writes u + 1, v + 1, e + 1.  `bump` is added to what the u side waits
+// for (testing the bounded wait: an update that never comes).
+struct Versions {
+    unsigned u, v, e, bump;
+};
 
-// Bounded wait (one thread) until node g's counter reaches `need`.
-__device__ __forceinline__ void wait_node(const HsParams &p, int g, unsigned need)
+// Entries j = j0, j0 + stride, ... (K of them, those < n) of two state arrays:
+// f(j, a[j] - m[j]) once a[j] carries version va and m[j] version vm.  All K
+// pairs are requested at once; only entries that still carry an older
+// version are requested again.  CHECK false: plain loads, no versions.
+template <bool CHECK, int K, typename F>
+__device__ __forceinline__ void load_diff(const HsParams &p, const ulonglong2 *a, const ulonglong2 *m, int j0,
+                                          int stride, int n, unsigned va, unsigned vm, F f)
 {
-    long long spins = 0;
-    for (;;) {
-        if (ld_acquire_u32(p.ver + g) >= need) return;
-        if (*reinterpret_cast<volatile int *>(p.err) != 0) return;  // draining after an error
-        if (++spins > p.spin_limit) {
-            set_err(p.err, ERR_TIMEOUT);
-            return;
+    ulonglong2 x[K], y[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int j = j0 + k * stride;
+        if (j < n) {
+            x[k] = ld_se(a + j);
+            y[k] = ld_se(m + j);
         }
-        if (spins > 4096) __nanosleep(64);
+    }
+    if (CHECK) {
+        for (long long spins = 1;; ++spins) {
+            bool ok = true;
+#pragma unroll
+            for (int k = 0; k < K; ++k)
+                if (j0 + k * stride < n) ok = ok && se_ok(x[k], va) && se_ok(y[k], vm);
+            if (ok) break;
+            if ((spins & 63) == 0 && *reinterpret_cast<volatile int *>(p.err) != 0) break;  // draining
+            if (spins > p.spin_limit) {
+                set_err(p.err, ERR_TIMEOUT);
+                break;
+            }
+            if (spins > 64) __nanosleep(64);
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const int j = j0 + k * stride;
+                if (j < n) {
+                    if (!se_ok(x[k], va)) x[k] = ld_se(a + j);
+                    if (!se_ok(y[k], vm)) y[k] = ld_se(m + j);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int j = j0 + k * stride;
+        if (j < n) f(j, df_sub(se_df(x[k]), se_df(y[k])));
     }
 }
 
@@ -200,19 +232,19 @@ __device__ __forceinline__ void warp_min_rows(float (&acc)[kRR])
 // One Handshake update of edge ed by this CTA (its row slice); the table slice
 // is (or will be) in `tile`, signalled by `bar` completing phase `parity`.
 // `xpar` selects the exchange buffer (alternates between consecutive items).
-// SIGNAL: publish completion on the node counters (persistent driver).
+// SIGNAL: wait for the expected versions of the inputs (persistent driver).
 // RR: register-resident passes (rr_fits must hold).
 template <bool CLUSTER, bool SIGNAL, bool RR>
 __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile, const Smem &sm, int rank,
-                        uint64_t *bar, uint32_t parity, int xpar, unsigned need_u = 0, unsigned need_v = 0)
+                        uint64_t *bar, uint32_t parity, int xpar, Versions ver)
 {
     const int T = blockDim.x, tid = threadIdx.x;
     const int C = CLUSTER ? p.C : 1;
     int r0, nr;
     rows_of(ed, rank, C, r0, nr);
     const int ld = ed.ld, Q = ld >> 2, Lv = ed.Lv;
-    float2 *agg = p.agg;
-    float2 *msg = p.msg;
+    ulonglong2 *agg = p.agg;
+    ulonglong2 *msg = p.msg;
 
     // The table slice: wait for its bulk copy and, for the register-resident
     // passes, load this thread's fragment.  Independent of the node vectors:
@@ -237,43 +269,33 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
     if (SIGNAL) load_tile();
 
     // unaries without this edge's messages (written by other SMs: L2 loads).
-    // Persistent driver: the first half of the warps waits for node v's
-    // earlier updates (one lane polls, a named barrier releases the half) and
-    // loads vh; the second half, except the last warp, does the same for node
-    // u, so the two waits overlap and each vector is loaded by many threads at
-    // once.  The last warp is still publishing the previous update (its
-    // release fence) meanwhile.
+    // Persistent driver: the first warps poll node v's entries until they
+    // carry the expected versions, the last warps node u's rows (warps split
+    // in proportion to the entries), so the two waits overlap and every entry
+    // is requested at once.
     {
-        const int half = (T >> 6) << 5;  // threads in the first half (a multiple of 32)
-        const bool vside = SIGNAL ? tid < half : true;
-        const bool uside = SIGNAL ? tid >= half && tid < T - 32 : true;
-        const int i0 = SIGNAL ? (vside ? tid : tid - half) : tid;
-        const int ni = SIGNAL ? (vside ? half : T - half - 32) : T;
-        if (SIGNAL) {
-            if (tid == 0) wait_node(p, ed.gv, need_v);
-            if (tid == half) wait_node(p, ed.gu, need_u);
-            if (vside)
-                named_barrier_1(half);
-            else if (uside)
-                named_barrier_2(T - half - 32);
-        }
+        const int uw = SIGNAL ? min(W - 1, max(1, (W * nr + ((nr + Lv) >> 1)) / max(1, nr + Lv))) : 0;
+        const int nv = T - 32 * uw;  // threads on node v's side
+        const bool vside = SIGNAL ? tid < nv : true;
+        const bool uside = SIGNAL ? tid >= nv : true;
+        const int i0 = SIGNAL ? (vside ? tid : tid - nv) : tid;
+        const int ni = SIGNAL ? (vside ? nv : T - nv) : T;
         if (uside)
             for (int s = i0; s < nr; s += ni)
-                sm.uh[s] = df_sub(__ldcg(agg + ed.au + r0 + s), __ldcg(msg + ed.mu + r0 + s));
+                load_diff<SIGNAL, 1>(p, agg + ed.au + r0, msg + ed.mu + r0, s, ni, nr, ver.u + ver.bump, ver.e,
+                                     [&](int j, float2 x) { sm.uh[j] = x; });
         if (vside) {
-            const float2 vref = df_sub(__ldcg(agg + ed.av), __ldcg(msg + ed.mv));
-            for (int q = i0; q < (ld >> 1); q += ni) {  // node vectors start 32-byte aligned
-                const float4 a = __ldcg(reinterpret_cast<const float4 *>(agg + ed.av) + q);
-                const float4 f = __ldcg(reinterpret_cast<const float4 *>(msg + ed.mv) + q);
-                const int t = 2 * q;
-                const float2 v0 = df_sub(make_float2(a.x, a.y), make_float2(f.x, f.y));
-                const float2 v1 = df_sub(make_float2(a.z, a.w), make_float2(f.z, f.w));
-                reinterpret_cast<float4 *>(sm.vh)[q] =
-                    make_float4(t < Lv ? v0.x : 0.f, t < Lv ? v0.y : 0.f, t + 1 < Lv ? v1.x : 0.f,
-                                t + 1 < Lv ? v1.y : 0.f);
-                reinterpret_cast<float2 *>(sm.w1)[q] = make_float2(t < Lv ? df_to_f(df_sub(v0, vref)) : 0.f,
-                                                                   t + 1 < Lv ? df_to_f(df_sub(v1, vref)) : 0.f);
-            }
+            for (int t = i0; t < Lv; t += ni)
+                load_diff<SIGNAL, 1>(p, agg + ed.av, msg + ed.mv, t, ni, Lv, ver.v, ver.e,
+                                     [&](int j, float2 x) { sm.vh[j] = x; });
+            for (int t = Lv + i0; t < ld; t += ni) sm.vh[t] = make_float2(0.f, 0.f);
+            if (SIGNAL)
+                named_barrier_1(nv);
+            else
+                __syncthreads();
+            // w1(t) = vh(t) - vh(0), rounded once to FP32
+            const float2 vref = sm.vh[0];
+            for (int t = i0; t < ld; t += ni) sm.w1[t] = t < Lv ? df_to_f(df_sub(sm.vh[t], vref)) : 0.f;
         }
     }
 
@@ -413,13 +435,13 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
     // CTA has passed the next item's exchange barrier, i.e. after this read.
     __syncthreads();
 
-    // node v's new vector (one CTA of the cluster), stored before pass 3 and
-    // published with node u's rows at the end of the update
+    // node v's new vector (one CTA of the cluster), visible to node v's next
+    // update as soon as it is stored
     if (rank == 0) {
         for (int t = tid; t < Lv; t += T) {
             const float2 b = sm.bv[t];
-            __stcg(agg + ed.av + t, b);
-            __stcg(msg + ed.mv + t, df_sub(b, sm.vh[t]));
+            st_se(agg + ed.av + t, se_make(b, ver.v + 1u));
+            st_se(msg + ed.mv + t, se_make(df_sub(b, sm.vh[t]), ver.e + 1u));
         }
     }
 
@@ -429,8 +451,8 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
         auto emit = [&](int s, float m) {
             const float2 u = sm.uh[s];
             const float2 c = df_add_f(u, m);
-            __stcg(agg + ed.au + r0 + s, c);
-            __stcg(msg + ed.mu + r0 + s, df_sub(c, u));
+            st_se(agg + ed.au + r0 + s, se_make(c, ver.u + 1u));
+            st_se(msg + ed.mu + r0 + s, se_make(df_sub(c, u), ver.e + 1u));
         };
         if (RR) {
             float acc[kRR];
@@ -458,14 +480,8 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
             }
         }
     }
+    // the next item overwrites uh, vh, alpha and beta
     __syncthreads();
-    // one release for the whole update, by the last warp (which sits out the
-    // next update's load phase): C arrivals on each end node per update
-    if (SIGNAL && tid == T - 1) {
-        asm volatile("fence.acq_rel.gpu;" ::: "memory");
-        red_add(p.ver + ed.gu, 1u);
-        if (rank == 0) red_add(p.ver + ed.gv, static_cast<unsigned>(C));
-    }
 }
 
 template <bool CLUSTER, bool RRK>
@@ -489,9 +505,9 @@ __global__ void __launch_bounds__(512) hs_looped_kernel(HsParams p)
     int r0, nr;
     rows_of(ed, rank, C, r0, nr);
     if (RRK && rr_fits(nr, ed.ld >> 2, blockDim.x, p.tile_floats))
-        hs_item<CLUSTER, false, RRK>(p, ed, sm.tile, sm, rank, &sm.bar[0], 0u, 0);
+        hs_item<CLUSTER, false, RRK>(p, ed, sm.tile, sm, rank, &sm.bar[0], 0u, 0, Versions{0u, 0u, 0u, 0u});
     else
-        hs_item<CLUSTER, false, false>(p, ed, sm.tile, sm, rank, &sm.bar[0], 0u, 0);
+        hs_item<CLUSTER, false, false>(p, ed, sm.tile, sm, rank, &sm.bar[0], 0u, 0, Versions{0u, 0u, 0u, 0u});
 }
 
 template <bool CLUSTER, bool RRK>
@@ -530,18 +546,19 @@ __global__ void __launch_bounds__(512) hs_persistent_kernel(HsParams p)
                            sm.bar + b);
             }
         }
-        const unsigned need_u = static_cast<unsigned>(C) * static_cast<unsigned>(it * w.deg_u + w.pos_u) +
-                                ((p.test_wait && k == 0 && cid == 0) ? 1u : 0u);
-        const unsigned need_v = static_cast<unsigned>(C) * static_cast<unsigned>(it * w.deg_v + w.pos_v);
+        // update counts modulo 2^32 (only equality is tested)
+        const Versions ver = {static_cast<unsigned>(it) * static_cast<unsigned>(w.deg_u) + static_cast<unsigned>(w.pos_u),
+                              static_cast<unsigned>(it) * static_cast<unsigned>(w.deg_v) + static_cast<unsigned>(w.pos_v),
+                              static_cast<unsigned>(it), (p.test_wait && k == 0 && cid == 0) ? 1u : 0u};
         const int b = static_cast<int>(k & 1);
         int r0, nr;
         rows_of(ed, rank, C, r0, nr);
         if (RRK && rr_fits(nr, ed.ld >> 2, blockDim.x, p.tile_floats))
             hs_item<CLUSTER, true, RRK>(p, ed, sm.tile + b * p.tile_floats, sm, rank, sm.bar + b,
-                                         static_cast<uint32_t>((k >> 1) & 1), b, need_u, need_v);
+                                         static_cast<uint32_t>((k >> 1) & 1), b, ver);
         else
             hs_item<CLUSTER, true, false>(p, ed, sm.tile + b * p.tile_floats, sm, rank, sm.bar + b,
-                                          static_cast<uint32_t>((k >> 1) & 1), b, need_u, need_v);
+                                          static_cast<uint32_t>((k >> 1) & 1), b, ver);
         if (++i == n) {
             i = 0;
             ++it;

@@ -12,12 +12,11 @@ namespace mplpp {
 struct HsParams {
     const EdgeDesc *edges;
     const float *tab;
-    float2 *agg;             // double-float reparametrized unaries (agg layout)
-    float2 *msg;             // double-float messages (msg layout)
+    ulonglong2 *agg;         // reparametrized unaries (agg layout, versioned double-float entries)
+    ulonglong2 *msg;         // messages (msg layout, versioned double-float entries)
     const int *items;        // looped: edge ids of the phase being launched
     const int *work_off;     // persistent: [clusters + 1] offsets into work
     const WorkItem *work;    // persistent: per-cluster item lists (one iteration)
-    unsigned *ver;           // persistent: per-node completion counters
     int *err;                // device error word (ERR_*)
     long long spin_limit;    // polls before a wait gives up
     int iterations;          // persistent: iterations to run
@@ -38,17 +37,19 @@ bool hs_rr_fits(int nr_max, int Q_max, int threads, int tile_floats);
 
 // dual.cu
 cudaError_t launch_pack(const EdgeDesc *edges, int n_edges, const NodeDesc *nodes, int n_nodes,
-                        const float *unary_src, const float *pair_src, float *tab, float *un0, float2 *agg,
+                        const float *unary_src, const float *pair_src, float *tab, float *un0, ulonglong2 *agg,
                         int *err, cudaStream_t st);
 cudaError_t launch_bound(const EdgeDesc *edges, int n_edges, const NodeDesc *nodes, int n_nodes,
-                         const float *tab, const float2 *agg, const float2 *msg, double *emin, double *nmin,
+                         const float *tab, const ulonglong2 *agg, const ulonglong2 *msg, double *emin, double *nmin,
                          const int *model_node_off, const int *model_edge_off, int n_models, int exact,
                          double *out, cudaStream_t st);
 cudaError_t launch_round(const EdgeDesc *edges, const NodeDesc *nodes, const int *in_off, const int *in_edge,
                          const int *model_node_off, const int *model_edge_off, int n_models, const float *tab,
-                         const float2 *agg, const float2 *msg, const float *un0, int *labels, double *energy,
+                         const ulonglong2 *agg, const ulonglong2 *msg, const float *un0, int *labels, double *energy,
                          int *err, cudaStream_t st);
-cudaError_t launch_init_state(const float *un0, float2 *agg, long long n_agg, float2 *msg, long long n_msg,
+cudaError_t launch_init_state(const float *un0, ulonglong2 *agg, long long n_agg, ulonglong2 *msg, long long n_msg,
                               cudaStream_t st);
+// Sets the version of every state entry to 0, keeping the values.
+cudaError_t launch_restamp(ulonglong2 *agg, long long n_agg, ulonglong2 *msg, long long n_msg, cudaStream_t st);
 
 }  // namespace mplpp

@@ -57,9 +57,8 @@ struct mplpp_solver {
     mplpp::EdgeDesc *d_edges = nullptr;
     mplpp::NodeDesc *d_nodes = nullptr;
     float *d_tab = nullptr, *d_un0 = nullptr;
-    float2 *d_agg = nullptr, *d_msg = nullptr;  // double-float state
+    ulonglong2 *d_agg = nullptr, *d_msg = nullptr;  // double-float state, versioned entries
     int *d_phase_edges = nullptr, *d_err = nullptr;
-    unsigned *d_ver = nullptr;
     int *d_work_off = nullptr;
     mplpp::WorkItem *d_work = nullptr;
     int *d_in_off = nullptr, *d_in_edge = nullptr, *d_mnode_off = nullptr, *d_medge_off = nullptr;
@@ -77,7 +76,7 @@ struct mplpp_solver {
     unsigned char *d_rec = nullptr;  // argmin records of one segment
     float *d_dD = nullptr;
     long long *d_pbase = nullptr, *d_ubase = nullptr;  // per-model offsets of the caller's layouts
-    float2 *d_save_agg = nullptr, *d_save_msg = nullptr;  // autotuner: state kept across candidates
+    ulonglong2 *d_save_agg = nullptr, *d_save_msg = nullptr;  // autotuner: state kept across candidates
 
     long long iterations = 0;
     long long launches = 0;
