@@ -184,7 +184,8 @@ static void build_work(mplpp_solver *s, int clusters)
             Load l = heap.top();
             heap.pop();
             const EdgeDesc &ed = s->h_edges[e];
-            WorkItem w;
+            WorkItem w = {};
+            w.ed = ed;
             w.edge = e;
             w.pos_u = pos[ed.gu]++;
             w.pos_v = pos[ed.gv]++;

@@ -47,14 +47,18 @@ struct NodeDesc {
 };
 static_assert(sizeof(NodeDesc) == 24, "NodeDesc layout");
 
-// One entry of a persistent worker's list: edge id plus the number of earlier
+// One entry of a persistent worker's list: the edge's descriptor (one record,
+// so that a worker needs a single load per item) plus the number of earlier
 // updates of each endpoint within one iteration (its rank among that node's
 // edges in schedule order) and the endpoint degrees.
 struct WorkItem {
-    int edge;
+    EdgeDesc ed;
     int pos_u, pos_v;
     int deg_u, deg_v;
+    int edge;
+    int pad;
 };
+static_assert(sizeof(WorkItem) == 96 && sizeof(WorkItem) % 16 == 0, "WorkItem layout");
 
 constexpr int ERR_TIMEOUT = 1;
 constexpr int ERR_NONFINITE = 2;

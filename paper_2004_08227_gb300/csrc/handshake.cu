@@ -55,6 +55,7 @@ namespace mplpp {
 namespace {
 
 struct Smem {
+    WorkItem *wi;       // [2] the current and the next work item (persistent driver)
     float *tile;        // nbuf buffers of tile_floats each
     float2 *uh, *vh;    // double-float unaries without this edge's messages
     float2 *bv;         // double-float new vector of node v
@@ -67,7 +68,8 @@ struct Smem {
 __device__ __forceinline__ Smem carve(char *base, const HsParams &p, int nbuf)
 {
     Smem s;
-    float2 *d = reinterpret_cast<float2 *>(base);
+    s.wi = reinterpret_cast<WorkItem *>(base);
+    float2 *d = reinterpret_cast<float2 *>(base + 2 * sizeof(WorkItem));
     s.uh = d; d += p.rmax;
     s.vh = d; d += p.ldmax;
     s.bv = d; d += p.ldmax;
@@ -140,51 +142,43 @@ struct Versions {
     unsigned u, v, e, bump;
 };
 
-// Entries j = j0, j0 + stride, ... (K of them, those < n) of two state arrays:
-// f(j, a[j] - m[j]) once a[j] carries version va and m[j] version vm.  All K
-// pairs are requested at once; only entries that still carry an older
-// version are requested again.  CHECK false: plain loads, no versions.
-template <bool CHECK, int K, typename F>
-__device__ __forceinline__ void load_diff(const HsParams &p, const ulonglong2 *a, const ulonglong2 *m, int j0,
-                                          int stride, int n, unsigned va, unsigned vm, F f)
+// Persistent driver, next item: its work record (16 bytes per thread of the
+// last warp, requested at the start of this item and stored into shared
+// memory once the thread's polls are done) and its table slice (started by
+// thread 0 once the node vectors have arrived, so that the burst of table
+// reads from every SM does not delay the polls of the state entries).
+struct Next {
+    int4 rec;           // this thread's 16 bytes of the next work record
+    int4 *rec_dst;      // where they go (nullptr: none)
+    WorkItem *wi;       // the next work record in shared memory
+    float *dst;         // the next table buffer
+    uint64_t *bar;      // its mbarrier
+    bool on;            // there is a next item
+};
+
+// f(j, a[j] - m[j]) from the entries x = a[j], y = m[j] already requested;
+// CHECK: first poll until a[j] carries version va and m[j] version vm (only
+// a word that still carries an older version is requested again).  Returns
+// the number of requests of a[j] made.
+template <bool CHECK, typename F>
+__device__ __forceinline__ long long poll_diff(const HsParams &p, const ulonglong2 *a, const ulonglong2 *m, int j,
+                                               unsigned va, unsigned vm, ulonglong2 x, ulonglong2 y, F f)
 {
-    ulonglong2 x[K], y[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        const int j = j0 + k * stride;
-        if (j < n) {
-            x[k] = ld_se(a + j);
-            y[k] = ld_se(m + j);
-        }
-    }
+    long long spins = 1;
     if (CHECK) {
-        for (long long spins = 1;; ++spins) {
-            bool ok = true;
-#pragma unroll
-            for (int k = 0; k < K; ++k)
-                if (j0 + k * stride < n) ok = ok && se_ok(x[k], va) && se_ok(y[k], vm);
-            if (ok) break;
+        for (; !(se_ok(x, va) && se_ok(y, vm)); ++spins) {
             if ((spins & 63) == 0 && *reinterpret_cast<volatile int *>(p.err) != 0) break;  // draining
             if (spins > p.spin_limit) {
                 set_err(p.err, ERR_TIMEOUT);
                 break;
             }
             if (spins > 64) __nanosleep(64);
-#pragma unroll
-            for (int k = 0; k < K; ++k) {
-                const int j = j0 + k * stride;
-                if (j < n) {
-                    if (!se_ok(x[k], va)) x[k] = ld_se(a + j);
-                    if (!se_ok(y[k], vm)) y[k] = ld_se(m + j);
-                }
-            }
+            if (!se_ok(x, va)) x = ld_se(a + j);
+            if (!se_ok(y, vm)) y = ld_se(m + j);
         }
     }
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        const int j = j0 + k * stride;
-        if (j < n) f(j, df_sub(se_df(x[k]), se_df(y[k])));
-    }
+    f(j, df_sub(se_df(x), se_df(y)));
+    return spins;
 }
 
 // min_t [row(t) + w(t)] over this lane's chunks q = lg, lg + G, ... (two chains)
@@ -236,7 +230,7 @@ __device__ __forceinline__ void warp_min_rows(float (&acc)[kRR])
 // RR: register-resident passes (rr_fits must hold).
 template <bool CLUSTER, bool SIGNAL, bool RR>
 __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile, const Smem &sm, int rank,
-                        uint64_t *bar, uint32_t parity, int xpar, Versions ver)
+                        uint64_t *bar, uint32_t parity, int xpar, Versions ver, Next nx)
 {
     const int T = blockDim.x, tid = threadIdx.x;
     const int C = CLUSTER ? p.C : 1;
@@ -248,8 +242,7 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
 
     // The table slice: wait for its bulk copy and, for the register-resident
     // passes, load this thread's fragment.  Independent of the node vectors:
-    // the persistent driver does it before waiting for the end nodes (the
-    // slice was prefetched), the looped one after issuing its vector loads.
+    // both drivers do it while the requests for the vectors are in flight.
     const float4 *t4 = reinterpret_cast<const float4 *>(tile);
     const int lane = tid & 31, warp = tid >> 5, W = T >> 5;
     const float4 inf4 = make_float4(INFINITY, INFINITY, INFINITY, INFINITY);
@@ -266,41 +259,65 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
                 }
         }
     };
-    if (SIGNAL) load_tile();
-
     // unaries without this edge's messages (written by other SMs: L2 loads).
     // Persistent driver: the first warps poll node v's entries until they
     // carry the expected versions, the last warps node u's rows (warps split
     // in proportion to the entries), so the two waits overlap and every entry
-    // is requested at once.
-    {
-        const int uw = SIGNAL ? min(W - 1, max(1, (W * nr + ((nr + Lv) >> 1)) / max(1, nr + Lv))) : 0;
+    // is requested at once; the first requests are in flight while the table
+    // fragment is loaded.
+    if (SIGNAL) {
+        const int uw = min(W - 1, max(1, (W * nr + ((nr + Lv) >> 1)) / max(1, nr + Lv)));
         const int nv = T - 32 * uw;  // threads on node v's side
-        const bool vside = SIGNAL ? tid < nv : true;
-        const bool uside = SIGNAL ? tid >= nv : true;
-        const int i0 = SIGNAL ? (vside ? tid : tid - nv) : tid;
-        const int ni = SIGNAL ? (vside ? nv : T - nv) : T;
-        if (uside)
-            for (int s = i0; s < nr; s += ni)
-                load_diff<SIGNAL, 1>(p, agg + ed.au + r0, msg + ed.mu + r0, s, ni, nr, ver.u + ver.bump, ver.e,
-                                     [&](int j, float2 x) { sm.uh[j] = x; });
+        const bool vside = tid < nv;
+        const int i0 = vside ? tid : tid - nv, ni = vside ? nv : T - nv;
+        const ulonglong2 *A = vside ? agg + ed.av : agg + ed.au + r0;
+        const ulonglong2 *M = vside ? msg + ed.mv : msg + ed.mu + r0;
+        const int n = vside ? Lv : nr;
+        const unsigned va = vside ? ver.v : ver.u + ver.bump;
+        float2 *dst = vside ? sm.vh : sm.uh;
+        ulonglong2 x = make_ulonglong2(0ull, 0ull), y = x;
+        if (i0 < n) {
+            x = ld_se(A + i0);
+            y = ld_se(M + i0);
+        }
+        load_tile();
+        for (int j = i0; j < n; j += ni) {
+            if (j != i0) {
+                x = ld_se(A + j);
+                y = ld_se(M + j);
+            }
+            poll_diff<true>(p, A, M, j, va, ver.e, x, y, [&](int jj, float2 d) { dst[jj] = d; });
+        }
         if (vside) {
-            for (int t = i0; t < Lv; t += ni)
-                load_diff<SIGNAL, 1>(p, agg + ed.av, msg + ed.mv, t, ni, Lv, ver.v, ver.e,
-                                     [&](int j, float2 x) { sm.vh[j] = x; });
             for (int t = Lv + i0; t < ld; t += ni) sm.vh[t] = make_float2(0.f, 0.f);
-            if (SIGNAL)
-                named_barrier_1(nv);
-            else
-                __syncthreads();
+            named_barrier_1(nv);
             // w1(t) = vh(t) - vh(0), rounded once to FP32
             const float2 vref = sm.vh[0];
             for (int t = i0; t < ld; t += ni) sm.w1[t] = t < Lv ? df_to_f(df_sub(sm.vh[t], vref)) : 0.f;
         }
+    } else {
+        for (int s = tid; s < nr; s += T)
+            poll_diff<false>(p, agg + ed.au + r0, msg + ed.mu + r0, s, 0u, 0u, ld_se(agg + ed.au + r0 + s),
+                             ld_se(msg + ed.mu + r0 + s), [&](int j, float2 d) { sm.uh[j] = d; });
+        for (int t = tid; t < ld; t += T) {
+            if (t < Lv)
+                poll_diff<false>(p, agg + ed.av, msg + ed.mv, t, 0u, 0u, ld_se(agg + ed.av + t), ld_se(msg + ed.mv + t),
+                                 [&](int j, float2 d) { sm.vh[j] = d; });
+            else
+                sm.vh[t] = make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        const float2 vref = sm.vh[0];
+        for (int t = tid; t < ld; t += T) sm.w1[t] = t < Lv ? df_to_f(df_sub(sm.vh[t], vref)) : 0.f;
     }
 
+    if (SIGNAL && nx.rec_dst) *nx.rec_dst = nx.rec;
     if (!SIGNAL) load_tile();
     __syncthreads();
+    if (SIGNAL && tid == 0 && nx.on) {  // the buffer's previous item has finished
+        fence_proxy_async();
+        issue_tile(nx.wi->ed, rank, C, p.tab, nx.dst, nx.bar);
+    }
 
     const int G = row_lanes(nr, Q, T);
     const int gid = tid / G, lg = tid % G, ng = T / G;
@@ -505,9 +522,9 @@ __global__ void __launch_bounds__(512) hs_looped_kernel(HsParams p)
     int r0, nr;
     rows_of(ed, rank, C, r0, nr);
     if (RRK && rr_fits(nr, ed.ld >> 2, blockDim.x, p.tile_floats))
-        hs_item<CLUSTER, false, RRK>(p, ed, sm.tile, sm, rank, &sm.bar[0], 0u, 0, Versions{0u, 0u, 0u, 0u});
+        hs_item<CLUSTER, false, RRK>(p, ed, sm.tile, sm, rank, &sm.bar[0], 0u, 0, Versions{0u, 0u, 0u, 0u}, Next{});
     else
-        hs_item<CLUSTER, false, false>(p, ed, sm.tile, sm, rank, &sm.bar[0], 0u, 0, Versions{0u, 0u, 0u, 0u});
+        hs_item<CLUSTER, false, false>(p, ed, sm.tile, sm, rank, &sm.bar[0], 0u, 0, Versions{0u, 0u, 0u, 0u}, Next{});
 }
 
 template <bool CLUSTER, bool RRK>
@@ -532,18 +549,29 @@ __global__ void __launch_bounds__(512) hs_persistent_kernel(HsParams p)
         cluster_wait_acquire();
     }
     if (total == 0) return;
-    if (threadIdx.x == 0) issue_tile(p.edges[p.work[begin].edge], rank, C, p.tab, sm.tile, &sm.bar[0]);
+    constexpr int kRec = static_cast<int>(sizeof(WorkItem) / sizeof(int4));
+    const int tid = threadIdx.x, T = blockDim.x;
+    const bool rec_lane = tid >= T - kRec;  // lanes of the last warp that move work records
+    if (rec_lane)
+        reinterpret_cast<int4 *>(&sm.wi[0])[tid - (T - kRec)] =
+            reinterpret_cast<const int4 *>(p.work + begin)[tid - (T - kRec)];
+    __syncthreads();
+    if (tid == 0) issue_tile(sm.wi[0].ed, rank, C, p.tab, sm.tile, &sm.bar[0]);
     int i = 0, it = 0;
     for (long long k = 0; k < total; ++k) {
-        const WorkItem w = p.work[begin + i];
-        const EdgeDesc ed = p.edges[w.edge];
-        if (threadIdx.x == 0) {
-            if (k + 1 < total) {
-                const int inext = (i + 1 == n) ? 0 : i + 1;
-                fence_proxy_async();
-                const int b = static_cast<int>((k + 1) & 1);
-                issue_tile(p.edges[p.work[begin + inext].edge], rank, C, p.tab, sm.tile + b * p.tile_floats,
-                           sm.bar + b);
+        const WorkItem &w = sm.wi[k & 1];
+        const EdgeDesc ed = w.ed;
+        Next nx = {};
+        if (k + 1 < total) {
+            const int inext = (i + 1 == n) ? 0 : i + 1;
+            const int b1 = static_cast<int>((k + 1) & 1);
+            nx.wi = &sm.wi[b1];
+            nx.dst = sm.tile + b1 * p.tile_floats;
+            nx.bar = sm.bar + b1;
+            nx.on = true;
+            if (rec_lane) {
+                nx.rec = __ldg(reinterpret_cast<const int4 *>(p.work + begin + inext) + (tid - (T - kRec)));
+                nx.rec_dst = reinterpret_cast<int4 *>(nx.wi) + (tid - (T - kRec));
             }
         }
         // update counts modulo 2^32 (only equality is tested)
@@ -555,10 +583,10 @@ __global__ void __launch_bounds__(512) hs_persistent_kernel(HsParams p)
         rows_of(ed, rank, C, r0, nr);
         if (RRK && rr_fits(nr, ed.ld >> 2, blockDim.x, p.tile_floats))
             hs_item<CLUSTER, true, RRK>(p, ed, sm.tile + b * p.tile_floats, sm, rank, sm.bar + b,
-                                         static_cast<uint32_t>((k >> 1) & 1), b, ver);
+                                         static_cast<uint32_t>((k >> 1) & 1), b, ver, nx);
         else
             hs_item<CLUSTER, true, false>(p, ed, sm.tile + b * p.tile_floats, sm, rank, sm.bar + b,
-                                          static_cast<uint32_t>((k >> 1) & 1), b, ver);
+                                          static_cast<uint32_t>((k >> 1) & 1), b, ver, nx);
         if (++i == n) {
             i = 0;
             ++it;
@@ -601,11 +629,12 @@ cudaError_t launch(K kernel, const HsParams &p, int grid, int threads, size_t sm
 
 size_t hs_smem_bytes(int nbuf, int tile_floats, int rmax, int ldmax, int threads, int C)
 {
-    // double-float uh, vh, bv; FP32 tiles, w1, alpha, beta, pm (nbuf x C slots), part (float4 x T); 2 mbarriers
+    // 2 work records; double-float uh, vh, bv; FP32 tiles, w1, alpha, beta, pm (nbuf x C slots), part (float4 x T);
+    // 2 mbarriers
     const size_t d = static_cast<size_t>(rmax) + 2 * static_cast<size_t>(ldmax);
     const size_t f = static_cast<size_t>(nbuf) * tile_floats + static_cast<size_t>(rmax) +
                      (2 + static_cast<size_t>(nbuf) * C) * static_cast<size_t>(ldmax) + 4 * static_cast<size_t>(threads);
-    return d * 8 + f * 4 + 16;
+    return 2 * sizeof(WorkItem) + d * 8 + f * 4 + 16;
 }
 
 cudaError_t hs_prepare(size_t smem)
