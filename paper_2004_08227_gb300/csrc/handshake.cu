@@ -25,10 +25,12 @@
 // [rank*R, rank*R + R) (R = ceil(L_u / C)), loaded with one bulk asynchronous
 // copy.  Row minima (passes 1 and 3) are local to the CTA; the partial column
 // minima of pass 2 are all-gathered across the cluster: every CTA stores its
-// vector into slot `rank` of every CTA's shared memory (remote stores do not
-// wait for a round trip), one cluster barrier, then each CTA reduces the C
-// slots locally.  The slots alternate between two buffers from one edge to
-// the next, so one barrier per edge suffices.
+// vector into slot `rank` of every CTA's shared memory with st.async, each
+// store completing its bytes on the receiving CTA's mbarrier, so a CTA waits
+// only for the data it needs (no cluster-wide barrier per edge), then reduces
+// the C slots locally.  The slots and their mbarriers alternate between two
+// sets from one edge to the next: a CTA writes a set again only after it has
+// received the other set from every CTA, i.e. after every CTA has read it.
 //
 // Two drivers:
 //   looped      one launch per matching; the launch boundary orders matchings
@@ -62,7 +64,7 @@ struct Smem {
     float *w1;          // vh(t) - vh(0) in FP32 (pass 1)
     float *alpha, *beta, *pm;
     float4 *part;
-    uint64_t *bar;      // [2]
+    uint64_t *bar;      // [4]: table buffers 0 and 1, exchange slots 0 and 1
 };
 
 __device__ __forceinline__ Smem carve(char *base, const HsParams &p, int nbuf)
@@ -81,7 +83,7 @@ __device__ __forceinline__ Smem carve(char *base, const HsParams &p, int nbuf)
     s.beta = f; f += p.ldmax;
     s.pm = f; f += static_cast<size_t>(nbuf) * p.ldmax * p.C;  // [item parity][CTA of the cluster][column]
     s.part = reinterpret_cast<float4 *>(f); f += 4 * blockDim.x;
-    s.bar = reinterpret_cast<uint64_t *>(f);
+    s.bar = reinterpret_cast<uint64_t *>(f);  // 16-byte aligned: every array above is a multiple of 16 bytes
     return s;
 }
 
@@ -247,6 +249,9 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
     const int lane = tid & 31, warp = tid >> 5, W = T >> 5;
     const float4 inf4 = make_float4(INFINITY, INFINITY, INFINITY, INFINITY);
     float4 tr[RR ? kRR : 1][RR ? kCR : 1];
+    // this item's exchange: C CTAs x Q float4 column minima arrive
+    if (CLUSTER && tid == 0)
+        mbar_arrive_expect_tx(sm.bar + 2 + xpar, static_cast<uint32_t>(C) * static_cast<uint32_t>(Q) * 16u);
     auto load_tile = [&]() {
         if (!mbar_wait(bar, parity, p.spin_limit)) set_err(p.err, ERR_TIMEOUT);
         if (RR) {
@@ -322,6 +327,7 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
     const int G = row_lanes(nr, Q, T);
     const int gid = tid / G, lg = tid % G, ng = T / G;
     float *xbuf = sm.pm + static_cast<size_t>(xpar) * C * ld;  // this item's exchange slots
+    uint64_t *xbar = sm.bar + 2 + xpar;                          // ... and their mbarrier
 
     // pass 1: a(s) = 1/2 (min_t [theta(s,t) + w1(t)] + vh(0) + uh(s));  alpha = uh - a
     {
@@ -364,9 +370,10 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
     // into slot `rank` of the pm buffer of every CTA of the cluster
     {
         const uint32_t slot = smem_u32(xbuf) + 4u * static_cast<uint32_t>(ld) * static_cast<uint32_t>(rank);
+        const uint32_t xb = smem_u32(xbar);
         auto push = [&](int q, float4 m) {
             if (CLUSTER) {
-                for (int r = 0; r < C; ++r) st_dsmem_f4(mapa_shared(slot + 16u * q, r), m);
+                for (int r = 0; r < C; ++r) st_async_f4(mapa_shared(slot + 16u * q, r), m, mapa_shared(xb, r));
             } else {
                 reinterpret_cast<float4 *>(xbuf)[q] = m;
             }
@@ -431,8 +438,7 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
     // combine the column minima of all CTAs of the edge:
     //   b(t) = min_s [...] + vh(t),  beta(t) = vh(t) - b(t)
     if (CLUSTER) {
-        cluster_arrive_release();
-        cluster_wait_acquire();
+        if (!mbar_wait_cluster(xbar, parity, p.spin_limit)) set_err(p.err, ERR_TIMEOUT);
     } else {
         __syncthreads();
     }
@@ -448,8 +454,8 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
         sm.bv[t] = t < Lv ? b : make_float2(0.f, 0.f);
         sm.beta[t] = t < Lv ? df_to_f(df_sub(vh, b)) : 0.f;
     }
-    // The slots of this parity are written again two items later, after every
-    // CTA has passed the next item's exchange barrier, i.e. after this read.
+    // The slots of this parity are written again two items later, by CTAs that
+    // have received this CTA's next-item column minima, i.e. after this read.
     __syncthreads();
 
     // node v's new vector (one CTA of the cluster), visible to node v's next
@@ -511,6 +517,7 @@ __global__ void __launch_bounds__(512) hs_looped_kernel(HsParams p)
     const EdgeDesc ed = p.edges[p.items[blockIdx.x / C]];
     if (threadIdx.x == 0) {
         mbar_init(&sm.bar[0], 1);
+        mbar_init(&sm.bar[2], 1);
         fence_mbar_init();
     }
     __syncthreads();
@@ -525,6 +532,10 @@ __global__ void __launch_bounds__(512) hs_looped_kernel(HsParams p)
         hs_item<CLUSTER, false, RRK>(p, ed, sm.tile, sm, rank, &sm.bar[0], 0u, 0, Versions{0u, 0u, 0u, 0u}, Next{});
     else
         hs_item<CLUSTER, false, false>(p, ed, sm.tile, sm, rank, &sm.bar[0], 0u, 0, Versions{0u, 0u, 0u, 0u}, Next{});
+    if (CLUSTER) {  // no CTA leaves while another may still access its shared memory
+        cluster_arrive_release();
+        cluster_wait_acquire();
+    }
 }
 
 template <bool CLUSTER, bool RRK>
@@ -539,8 +550,7 @@ __global__ void __launch_bounds__(512) hs_persistent_kernel(HsParams p)
     const int n = p.work_off[cid + 1] - begin;
     const long long total = static_cast<long long>(n) * p.iterations;
     if (threadIdx.x == 0) {
-        mbar_init(&sm.bar[0], 1);
-        mbar_init(&sm.bar[1], 1);
+        for (int j = 0; j < 4; ++j) mbar_init(&sm.bar[j], 1);
         fence_mbar_init();
     }
     __syncthreads();
@@ -592,6 +602,10 @@ __global__ void __launch_bounds__(512) hs_persistent_kernel(HsParams p)
             ++it;
         }
     }
+    if (CLUSTER) {  // no CTA leaves while another may still access its shared memory
+        cluster_arrive_release();
+        cluster_wait_acquire();
+    }
 }
 
 template <typename K>
@@ -630,11 +644,11 @@ cudaError_t launch(K kernel, const HsParams &p, int grid, int threads, size_t sm
 size_t hs_smem_bytes(int nbuf, int tile_floats, int rmax, int ldmax, int threads, int C)
 {
     // 2 work records; double-float uh, vh, bv; FP32 tiles, w1, alpha, beta, pm (nbuf x C slots), part (float4 x T);
-    // 2 mbarriers
+    // 4 mbarriers
     const size_t d = static_cast<size_t>(rmax) + 2 * static_cast<size_t>(ldmax);
     const size_t f = static_cast<size_t>(nbuf) * tile_floats + static_cast<size_t>(rmax) +
                      (2 + static_cast<size_t>(nbuf) * C) * static_cast<size_t>(ldmax) + 4 * static_cast<size_t>(threads);
-    return 2 * sizeof(WorkItem) + d * 8 + f * 4 + 16;
+    return 2 * sizeof(WorkItem) + d * 8 + f * 4 + 32;
 }
 
 cudaError_t hs_prepare(size_t smem)
