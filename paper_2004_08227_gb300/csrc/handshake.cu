@@ -211,18 +211,66 @@ __device__ __forceinline__ void group_min(float &m, int G)
 constexpr int kRR = 5;
 constexpr int kCR = 3;
 
-__device__ __forceinline__ bool rr_fits(int nr, int Q, int T, int tile_floats)
+// Row stride (float4) of the per-warp column partials of pass 2: = 2 mod 8,
+// so that the reduction's reads (4 lanes per column chunk, one per warp
+// group) fall into distinct 16-byte bank groups.
+__device__ __host__ __forceinline__ int part_stride(int Q)
 {
-    return Q > 32 && Q <= 32 * kCR && nr <= kRR * (T >> 5) && (T >> 5) * Q * 4 <= tile_floats;
+    return Q + ((2 - Q) & 7);
 }
 
-// Butterfly minimum over the warp of kRR independent values.
-__device__ __forceinline__ void warp_min_rows(float (&acc)[kRR])
+__device__ __forceinline__ bool rr_fits(int nr, int Q, int T, int tile_floats)
 {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-        for (int k = 0; k < kRR; ++k) acc[k] = fminf(acc[k], __shfl_xor_sync(0xffffffffu, acc[k], o));
+    return Q > 32 && Q <= 32 * kCR && nr <= kRR * (T >> 5) && (T >> 5) * part_stride(Q) * 4 <= tile_floats;
+}
+
+// Minimum over the warp of each of the kRR = 5 row values, reduce-scatter
+// style (each exchange step halves the rows a lane keeps): 8 shuffles instead
+// of 25.  The result is the minimum of row rs_row(lane); lanes 0, 8, 4, 16
+// and 24 own rows 0..4 (rs_owner).
+static_assert(kRR == 5, "the reduce-scatter below splits exactly five rows");
+
+__device__ __forceinline__ float warp_min_rows5(const float (&a)[kRR], int lane)
+{
+    constexpr unsigned kAll = 0xffffffffu;
+    const bool up = lane & 16, b3 = lane & 8, b2 = lane & 4;
+    // xor 16: lanes < 16 keep rows 0, 1, 2; lanes >= 16 keep rows 3, 4
+    const float r0 = __shfl_xor_sync(kAll, up ? a[0] : a[3], 16);
+    const float r1 = __shfl_xor_sync(kAll, up ? a[1] : a[4], 16);
+    const float r2 = __shfl_xor_sync(kAll, a[2], 16);
+    const float b0 = fminf(up ? a[3] : a[0], r0);
+    const float b1 = fminf(up ? a[4] : a[1], r1);
+    const float c2 = fminf(a[2], r2);
+    // xor 8: lower lanes with bit 3 clear keep rows 0 and 2, with bit 3 set
+    // row 1; upper lanes keep row 3 (bit 3 clear) or row 4
+    const float t0 = __shfl_xor_sync(kAll, b3 ? b0 : b1, 8);
+    const float t1 = __shfl_xor_sync(kAll, c2, 8);
+    const float c0 = fminf(b3 ? b1 : b0, t0);
+    const float c1 = fminf(c2, t1);
+    // xor 4: the lanes holding rows 0 and 2 split them (bit 2); then 2, 1
+    const bool two = !up && !b3;
+    const float own = (two && b2) ? c1 : c0;
+    const float snd = two ? (b2 ? c0 : c1) : c0;
+    float d = fminf(own, __shfl_xor_sync(kAll, snd, 4));
+    d = fminf(d, __shfl_xor_sync(kAll, d, 2));
+    return fminf(d, __shfl_xor_sync(kAll, d, 1));
+}
+
+__device__ __forceinline__ int rs_row(int lane)
+{
+    return (lane & 16) ? ((lane & 8) ? 4 : 3) : ((lane & 8) ? 1 : ((lane & 4) ? 2 : 0));
+}
+
+__device__ __forceinline__ bool rs_owner(int lane)
+{
+    return lane == 0 || lane == 4 || lane == 8 || lane == 16 || lane == 24;
+}
+
+// Lane-wise minimum of five float4
+__device__ __forceinline__ float4 min5_4(float4 a, float4 b, float4 c, float4 d, float4 e)
+{
+    return make_float4(min3f(min3f(a.x, b.x, c.x), d.x, e.x), min3f(min3f(a.y, b.y, c.y), d.y, e.y),
+                       min3f(min3f(a.z, b.z, c.z), d.z, e.z), min3f(min3f(a.w, b.w, c.w), d.w, e.w));
 }
 
 // One Handshake update of edge ed by this CTA (its row slice); the table slice
@@ -349,12 +397,9 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
 #pragma unroll
                 for (int i = 0; i < kCR; ++i) acc[k] = min_add4(acc[k], tr[k][i], wv[i]);
             }
-            warp_min_rows(acc);
-            // every lane holds every row's minimum: lane k emits row k, all at once
-            float mk = acc[0];
-#pragma unroll
-            for (int k = 1; k < kRR; ++k) mk = lane == k ? acc[k] : mk;
-            if (lane < kRR && warp + W * lane < nr) emit(warp + W * lane, mk);
+            const float mk = warp_min_rows5(acc, lane);
+            const int s = warp + W * rs_row(lane);  // the five owners emit at once
+            if (rs_owner(lane) && s < nr) emit(s, mk);
         } else {
             for (int base = 0; base < nr; base += ng) {
                 const int s = base + gid;
@@ -382,15 +427,18 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
         if (RR) {
             // the warp's rows in registers, then the warps through the tile buffer
             float4 *part2 = reinterpret_cast<float4 *>(const_cast<float *>(tile));
-            float al[kRR];
+            float4 al[kRR];
 #pragma unroll
-            for (int k = 0; k < kRR; ++k) al[k] = warp + W * k < nr ? sm.alpha[warp + W * k] : 0.f;
+            for (int k = 0; k < kRR; ++k) {
+                const float a = warp + W * k < nr ? sm.alpha[warp + W * k] : 0.f;
+                al[k] = make_float4(a, a, a, a);
+            }
+            const int Qp = part_stride(Q);
 #pragma unroll
             for (int i = 0; i < kCR; ++i) {
-                float4 m = inf4;
-#pragma unroll
-                for (int k = 0; k < kRR; ++k) m = min4(m, add4(tr[k][i], make_float4(al[k], al[k], al[k], al[k])));
-                if (lane + 32 * i < Q) part2[warp * Q + lane + 32 * i] = m;
+                const float4 m = min5_4(add4(tr[0][i], al[0]), add4(tr[1][i], al[1]), add4(tr[2][i], al[2]),
+                                        add4(tr[3][i], al[3]), add4(tr[4][i], al[4]));
+                if (lane + 32 * i < Q) part2[warp * Qp + lane + 32 * i] = m;
             }
             __syncthreads();
             // 4 consecutive lanes per chunk, each over every 4th warp, then 2 shuffles
@@ -398,7 +446,7 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
                 const int idx = base + lane, q = idx >> 2, part = idx & 3;
                 float4 m = inf4;
                 if (idx < 4 * Q)
-                    for (int w = part; w < W; w += 4) m = min4(m, part2[w * Q + q]);
+                    for (int w = part; w < W; w += 4) m = min4(m, part2[w * Qp + q]);
 #pragma unroll
                 for (int o = 1; o <= 2; o <<= 1)
                     m = min4(m, make_float4(__shfl_xor_sync(0xffffffffu, m.x, o), __shfl_xor_sync(0xffffffffu, m.y, o),
@@ -488,12 +536,9 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
 #pragma unroll
                 for (int i = 0; i < kCR; ++i) acc[k] = min_add4(acc[k], tr[k][i], bw[i]);
             }
-            warp_min_rows(acc);
-            // every lane holds every row's minimum: lane k emits row k, all at once
-            float mk = acc[0];
-#pragma unroll
-            for (int k = 1; k < kRR; ++k) mk = lane == k ? acc[k] : mk;
-            if (lane < kRR && warp + W * lane < nr) emit(warp + W * lane, mk);
+            const float mk = warp_min_rows5(acc, lane);
+            const int s = warp + W * rs_row(lane);  // the five owners emit at once
+            if (rs_owner(lane) && s < nr) emit(s, mk);
         } else {
             for (int base = 0; base < nr; base += ng) {
                 const int s = base + gid;
@@ -687,7 +732,9 @@ cudaError_t hs_launch_persistent(const HsParams &p, int clusters, int threads, s
 
 bool hs_rr_fits(int nr_max, int Q_max, int threads, int tile_floats)
 {
-    return Q_max > 32 && Q_max <= 32 * kCR && nr_max <= kRR * (threads >> 5) && (threads >> 5) * Q_max * 4 <= tile_floats;
+    // every row count up to nr_max and chunk count up to Q_max must fit
+    return Q_max > 32 && Q_max <= 32 * kCR && nr_max <= kRR * (threads >> 5) &&
+           (threads >> 5) * (Q_max + 7) * 4 <= tile_floats;
 }
 
 int hs_max_active_clusters(int C, int threads, size_t smem, bool rr)
