@@ -95,13 +95,15 @@ extern "C" const char *mplpp_last_error(const mplpp_solver *s)
 static void mapping_for(mplpp_solver *s, int C, int threads = 0)
 {
     long long tile = 0, rows = 0;
-    int ldmax = 4;
+    int ldmax = 4, lmax = 1;
     for (auto &ed : s->h_edges) {
         const long long R = (ed.Lu + C - 1) / C;
         tile = std::max(tile, R * ed.ld);
         rows = std::max(rows, R);
         ldmax = std::max(ldmax, ed.ld);
+        lmax = std::max(lmax, std::max(ed.Lu, ed.ld));
     }
+    s->lmax = lmax;
     int T = threads > 0 ? threads : s->opt.threads;
     if (T <= 0) T = (4 * tile >= 48 * 1024) ? 512 : (4 * tile <= 4096 ? 128 : 256);
     s->C = C;
@@ -356,6 +358,11 @@ extern "C" mplpp_status mplpp_create(const mplpp_model *models, int32_t n_models
         for (int u = 0; u < s->N; ++u)
             std::sort(s->in_edge.begin() + s->in_off[u], s->in_edge.begin() + s->in_off[u + 1],
                       [&](int a, int b) { return s->h_edges[a].gu < s->h_edges[b].gu; });
+        s->in_rec.resize(s->EE);
+        for (int k = 0; k < s->EE; ++k) {
+            const EdgeDesc &ed = s->h_edges[s->in_edge[k]];
+            s->in_rec[k] = InRec{ed.toff, ed.mu, ed.mv, ed.ld, ed.gu};
+        }
     }
     s->mnode_off.assign(1, 0);
     s->medge_off.assign(1, 0);
@@ -402,7 +409,7 @@ extern "C" mplpp_status mplpp_create(const mplpp_model *models, int32_t n_models
     CKC(S->alloc(&S->d_phase_edges, S->phase_edges.size()));
     CKC(S->alloc(&S->d_err, 1));
     CKC(S->alloc(&S->d_in_off, S->in_off.size()));
-    CKC(S->alloc(&S->d_in_edge, S->in_edge.size()));
+    CKC(S->alloc(&S->d_in_rec, std::max<size_t>(1, S->in_rec.size())));
     CKC(S->alloc(&S->d_mnode_off, S->mnode_off.size()));
     CKC(S->alloc(&S->d_medge_off, S->medge_off.size()));
     CKC(S->alloc(&S->d_emin, S->EE));
@@ -421,7 +428,7 @@ extern "C" mplpp_status mplpp_create(const mplpp_model *models, int32_t n_models
     CKC(h2d(S->d_nodes, S->h_nodes.data(), S->h_nodes.size() * sizeof(NodeDesc)));
     CKC(h2d(S->d_phase_edges, S->phase_edges.data(), S->phase_edges.size() * sizeof(int)));
     CKC(h2d(S->d_in_off, S->in_off.data(), S->in_off.size() * sizeof(int)));
-    CKC(h2d(S->d_in_edge, S->in_edge.data(), S->in_edge.size() * sizeof(int)));
+    CKC(h2d(S->d_in_rec, S->in_rec.data(), S->in_rec.size() * sizeof(InRec)));
     CKC(h2d(S->d_mnode_off, S->mnode_off.data(), S->mnode_off.size() * sizeof(int)));
     CKC(h2d(S->d_medge_off, S->medge_off.data(), S->medge_off.size() * sizeof(int)));
     {
@@ -607,8 +614,8 @@ extern "C" mplpp_status mplpp_bound(mplpp_solver *s, double *out, int32_t exact)
     if (!s || !out) return MPLPP_E_INVALID;
     s->err.clear();
     CK(s, launch_bound(s->d_edges, s->EE, s->d_nodes, s->N, s->d_tab, s->d_agg, s->d_msg, s->d_emin, s->d_nmin,
-                       s->d_mnode_off, s->d_medge_off, static_cast<int>(s->models.size()), exact ? 1 : 0, s->d_out,
-                       s->stream));
+                       s->d_mnode_off, s->d_medge_off, static_cast<int>(s->models.size()), exact ? 1 : 0, s->lmax,
+                       s->d_out, s->stream));
     CK(s, cudaMemcpyAsync(out, s->d_out, sizeof(double) * s->models.size(), cudaMemcpyDeviceToHost, s->stream));
     mplpp_status st = mplpp_sync(s);
     if (st != MPLPP_OK) return st;
@@ -621,7 +628,7 @@ extern "C" mplpp_status mplpp_labeling(mplpp_solver *s, int32_t *labels, double 
 {
     if (!s || !labels) return MPLPP_E_INVALID;
     s->err.clear();
-    CK(s, launch_round(s->d_edges, s->d_nodes, s->d_in_off, s->d_in_edge, s->d_mnode_off, s->d_medge_off,
+    CK(s, launch_round(s->d_edges, s->d_nodes, s->d_in_off, s->d_in_rec, s->d_mnode_off, s->d_medge_off,
                        static_cast<int>(s->models.size()), s->d_tab, s->d_agg, s->d_msg, s->d_un0, s->d_labels,
                        s->d_energy, s->d_err, s->stream));
     CK(s, cudaMemcpyAsync(labels, s->d_labels, sizeof(int) * s->N, cudaMemcpyDeviceToHost, s->stream));

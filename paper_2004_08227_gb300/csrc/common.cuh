@@ -60,6 +60,18 @@ struct WorkItem {
 };
 static_assert(sizeof(WorkItem) == 96 && sizeof(WorkItem) % 16 == 0, "WorkItem layout");
 
+// One earlier neighbour of a node in the rounding order, i.e. an edge (v, u)
+// whose first node v precedes u: the edge's table offset and row stride, the
+// offsets of its two messages and the neighbour's global id.
+struct InRec {
+    long long toff;   // table (rows x_v, stride ld)
+    long long mu;     // phi of the edge's first node v (indexed by x_v)
+    long long mv;     // phi of the edge's second node u (indexed by u's labels)
+    int ld;
+    int gu;           // v
+};
+static_assert(sizeof(InRec) == 32, "InRec layout");
+
 constexpr int ERR_TIMEOUT = 1;
 constexpr int ERR_NONFINITE = 2;
 

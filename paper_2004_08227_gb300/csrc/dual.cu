@@ -71,25 +71,97 @@ __device__ __forceinline__ double block_min(double v, double *red)
     return v;  // valid in thread 0
 }
 
-// emin[e] = min_{s,t} (theta_uv(s,t) - phi_{v->u}(s)) - phi_{u->v}(t)   (FP64)
+// emin[e] = min_{s,t} (theta_uv(s,t) - phi_{v->u}(s)) - phi_{u->v}(t), the
+// FP64 value of that expression minimized over all (s,t), computed with FP64
+// arithmetic only where it can decide the minimum (GB300's FP64 rate is far
+// below its FP32 rate).  Per row s, an FP32 screen first:
+//   e(t) = fl32(theta(s,t) - d(t)),  d(t) = fl32(phi_{u->v}(t) - phi_{u->v}(0)).
+// With D = max_t |d(t)| and Th = max_t |theta(s,t)|, every e(t) is within
+//   eps1 = 2^-22 (D + Th)
+// of the exact theta(s,t) - phi_{u->v}(t) + phi_{u->v}(0)  (d(t): two
+// roundings, <= 2^-23 |d|(1 + 2^-23); the FP32 difference: <= 2^-24 (Th + D)),
+// and the FP64 evaluation of an entry is within
+//   eps2 = 2^-50 (Th + |phi_{v->u}(s)| + |phi_{u->v}(0)| + 2 D)
+// of its exact value.  An entry with e(t) > min_t e + 4 eps1 + 2 eps2 is then
+// strictly above the row's minimizer in exact arithmetic by more than 2 eps2,
+// so its FP64 value cannot be the row's FP64 minimum; the remaining
+// candidates (usually one or two) are evaluated in FP64.  The threshold is
+// formed in FP32 with upward rounding (a superset of the candidates), the
+// messages are decoded to FP64 once per edge, FP64 instructions issue only
+// where a lane of the warp holds a candidate, and a row's minimum needs no
+// FP64 reduction when one lane holds all its candidates.  The result equals
+// the FP64 minimum over every entry, bit for bit.
 __global__ void __launch_bounds__(kThreads) bound_edges_kernel(const EdgeDesc *edges, int n_edges,
-                                                               const float *tab, const ulonglong2 *msg, double *emin)
+                                                               const float *tab, const ulonglong2 *msg, int lmax,
+                                                               double *emin)
 {
+    extern __shared__ double dyn[];
+    double *p1 = dyn;                                       // [lmax] phi_{v->u}(s)
+    double *p2 = dyn + lmax;                                // [lmax] phi_{u->v}(t)
+    float *a1 = reinterpret_cast<float *>(dyn + 2 * lmax);  // [lmax] |phi_{v->u}(s)| rounded up
+    float *dsh = a1 + lmax;                                 // [lmax] d(t)
     __shared__ double red[32];
+    __shared__ float redf[32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = kThreads / 32;
     for (int e = blockIdx.x; e < n_edges; e += gridDim.x) {
         const EdgeDesc ed = edges[e];
+        const double ref = se_d(msg[ed.mv]);
+        const float aref = __double2float_ru(fabs(ref));
+        float dmax = 0.f;
+        for (int t = threadIdx.x; t < ed.Lv; t += kThreads) {
+            const double v = se_d(msg[ed.mv + t]);
+            const float d = static_cast<float>(v - ref);
+            p2[t] = v;
+            dsh[t] = d;
+            dmax = fmaxf(dmax, fabsf(d));
+        }
+        for (int s = threadIdx.x; s < ed.Lu; s += kThreads) {
+            const double v = se_d(msg[ed.mu + s]);
+            p1[s] = v;
+            a1[s] = __double2float_ru(fabs(v));
+        }
+        for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+        if (lane == 0) redf[warp] = dmax;
+        __syncthreads();
+        float D = 0.f;
+        for (int w = 0; w < nw; ++w) D = fmaxf(D, redf[w]);
         double m = INFINITY;
-        const long long n = static_cast<long long>(ed.Lu) * ed.Lv;
-        for (long long i = threadIdx.x; i < n; i += blockDim.x) {
-            const int s = static_cast<int>(i / ed.Lv);
-            const int t = static_cast<int>(i - static_cast<long long>(s) * ed.Lv);
-            const double r =
-                (static_cast<double>(tab[ed.toff + static_cast<long long>(s) * ed.ld + t]) - se_d(msg[ed.mu + s])) -
-                se_d(msg[ed.mv + t]);
-            m = fmin(m, r);
+        for (int s = warp; s < ed.Lu; s += nw) {
+            const float *row = tab + ed.toff + static_cast<long long>(s) * ed.ld;
+            float me = INFINITY, th = 0.f;
+            for (int t = lane; t < ed.Lv; t += 32) {
+                const float x = row[t];
+                me = fminf(me, x - dsh[t]);
+                th = fmaxf(th, fabsf(x));
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                me = fminf(me, __shfl_xor_sync(0xffffffffu, me, o));
+                th = fmaxf(th, __shfl_xor_sync(0xffffffffu, th, o));
+            }
+            // me + 4 eps1 + 2 eps2, every operation rounded upwards
+            const float eps1 = __fmul_ru(0x1p-22f, __fadd_ru(D, th));
+            const float eps2 = __fmul_ru(0x1p-50f, __fadd_ru(__fadd_ru(th, a1[s]), __fadd_ru(aref, __fmul_ru(2.f, D))));
+            const float thr = __fadd_ru(__fadd_ru(me, __fmul_ru(4.f, eps1)), __fadd_ru(__fmul_ru(2.f, eps2), 0x1p-126f));
+            const double ph1 = p1[s];
+            double rm = INFINITY;
+            for (int t0 = 0; t0 < ed.Lv; t0 += 32) {  // warp-uniform trip count
+                const int t = t0 + lane;
+                const float x = t < ed.Lv ? row[t] : INFINITY;
+                const bool c = t < ed.Lv && x - dsh[t] <= thr;
+                if (__ballot_sync(0xffffffffu, c) != 0u && c)  // FP64 only where a lane has a candidate
+                    rm = fmin(rm, (static_cast<double>(x) - ph1) - p2[t]);
+            }
+            const unsigned who = __ballot_sync(0xffffffffu, rm < INFINITY);
+            if (__popc(who) == 1) {
+                rm = __shfl_sync(0xffffffffu, rm, __ffs(who) - 1);
+            } else {
+                for (int o = 16; o > 0; o >>= 1) rm = fmin(rm, __shfl_xor_sync(0xffffffffu, rm, o));
+            }
+            m = fmin(m, rm);
         }
         m = block_min<kThreads>(m, red);
         if (threadIdx.x == 0) emin[e] = m;
+        __syncthreads();  // p1, p2, a1, dsh and redf are rewritten for the next edge
     }
 }
 
@@ -144,42 +216,188 @@ __global__ void __launch_bounds__(kThreads) bound_sum_kernel(const int *model_no
 // labels is its reparametrized unary plus, for every earlier neighbour v in
 // increasing order, theta^phi_vu(x_v, s) = (theta_vu(x_v,s) - phi_{u->v}(x_v))
 // - phi_{v->u}(s); FP64 sums in that order, argmin with the lowest index.
-__global__ void __launch_bounds__(kThreads) round_kernel(const EdgeDesc *edges, const NodeDesc *nodes,
-                                                         const int *in_off, const int *in_edge,
-                                                         const int *model_node_off, const float *tab,
-                                                         const ulonglong2 *agg, const ulonglong2 *msg, int *labels,
-                                                         int *err)
+// GB300's FP64 rate is far below its FP32 rate, so every label's objective
+// is first evaluated in double-float (FP32 operations), O(s), with
+//   |O(s) - exact| and |FP64 value - exact| <= B(s) = (K + 3) 2^-43 S(s),
+// S(s) = |agg_u(s)| + sum_k (|theta| + |phi_{u->v}| + |phi_{v->u}(s)|), K
+// earlier neighbours (each double-float addition errs by at most
+// 3 * 2^-48 (|a| + |b|); B carries a factor 8 of margin).  With O(s) bracketed
+// in FP32 (upward / downward rounding) as [lo(s), hi(s)], a label with
+// lo(s) > H = min_s hi(s) cannot attain the FP64 minimum, nor tie with it;
+// the remaining candidates (usually one) are summed in FP64 in neighbour
+// order, so the decision equals the all-FP64 one.
+constexpr int kRoundThreads = 512;
+
+__global__ void __launch_bounds__(kRoundThreads) round_kernel(const NodeDesc *nodes, const int *in_off,
+                                                              const InRec *in_rec, const int *model_node_off,
+                                                              const float *tab, const ulonglong2 *agg,
+                                                              const ulonglong2 *msg, int *labels, int *err)
 {
-    __shared__ double rv[32];
-    __shared__ int ri[32];
+    constexpr int T = kRoundThreads;
+    __shared__ double rv[T / 32];
+    __shared__ int ri[T / 32];
+    __shared__ float rh[T / 32];
+    // per earlier neighbour (one chunk of T of them at a time): the offset of
+    // row x_v of its table, phi_{u->v}(x_v) of the edge's first node (FP64 and
+    // double-float) and the offset of the edge's phi_{v->u}, fetched in parallel
+    __shared__ long long k_row[T], k_mv[T];
+    __shared__ double k_phi[T];
+    __shared__ float2 k_phf[T];
     const int m = blockIdx.x;
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    const int tid = threadIdx.x;
+    const int w = tid >> 5, l = tid & 31;
+    constexpr int kLab = 2;     // labels s = tid + j * T, j < kLab, screened
+    constexpr int kBatch = 16;  // table rows of different edges miss in L2: loads in flight
     for (int u = model_node_off[m]; u < model_node_off[m + 1]; ++u) {
         const NodeDesc nd = nodes[u];
+        const int k0 = in_off[u], k1 = in_off[u + 1], K = k1 - k0;
+        auto stage = [&](int c0, int nc) {
+            __syncthreads();  // the previous chunk's entries are no longer read
+            if (tid < nc) {
+                const InRec r = in_rec[c0 + tid];
+                const int xv = labels[r.gu];
+                k_row[tid] = r.toff + static_cast<long long>(xv) * r.ld;
+                k_mv[tid] = r.mv;
+                const double ph = se_d(msg[r.mu + xv]);
+                const float hi = static_cast<float>(ph);
+                k_phi[tid] = ph;
+                k_phf[tid] = make_float2(hi, static_cast<float>(ph - static_cast<double>(hi)));
+            }
+            __syncthreads();
+        };
+        // double-float screen
+        float2 o[kLab];
+        float sa[kLab];
+#pragma unroll
+        for (int j = 0; j < kLab; ++j) {
+            const int s = tid + j * T;
+            o[j] = s < nd.L ? se_df(agg[nd.aoff + s]) : make_float2(0.f, 0.f);
+            sa[j] = fabsf(o[j].x);
+        }
+        for (int c0 = k0; c0 < k1; c0 += T) {
+            const int nc = min(T, k1 - c0);
+            stage(c0, nc);
+            // warps without labels of this node: bring the next node's table
+            // rows of its already decided neighbours into L2 meanwhile
+            const int idle0 = ((nd.L + 31) >> 5) << 5;
+            if (c0 == k0 && tid >= idle0 && u + 1 < model_node_off[m + 1]) {
+                const int Ln = nodes[u + 1].L;
+                for (int k = in_off[u + 1] + tid - idle0; k < in_off[u + 2]; k += T - idle0) {
+                    const InRec r = in_rec[k];
+                    if (r.gu < u) {
+                        const float *p = tab + r.toff + static_cast<long long>(labels[r.gu]) * r.ld;
+                        for (int q = 0; q < Ln; q += 32) asm volatile("prefetch.global.L2 [%0];" ::"l"(p + q));
+                    }
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < kLab; ++j) {
+                const int s = tid + j * T;
+                if (s < nd.L)
+                    for (int kb = 0; kb < nc; kb += kBatch) {
+                        float tv[kBatch];
+                        ulonglong2 mv[kBatch];
+#pragma unroll
+                        for (int q = 0; q < kBatch; ++q)
+                            if (kb + q < nc) {
+                                tv[q] = tab[k_row[kb + q] + s];
+                                mv[q] = msg[k_mv[kb + q] + s];
+                            }
+#pragma unroll
+                        for (int q = 0; q < kBatch; ++q)
+                            if (kb + q < nc) {
+                                const float2 f1 = k_phf[kb + q], f2 = se_df(mv[q]);
+                                o[j] = df_add(o[j], df_sub(df_sub(make_float2(tv[q], 0.f), f1), f2));
+                                sa[j] += fabsf(tv[q]) + fabsf(f1.x) + fabsf(f2.x);
+                            }
+                    }
+            }
+        }
+        // FP32 brackets [lo, hi] of every objective; H = min hi
+        float lo[kLab];
+        float h = INFINITY;
+        const float cK = static_cast<float>(K + 3);
+#pragma unroll
+        for (int j = 0; j < kLab; ++j) {
+            const float b = __fadd_ru(__fmul_ru(cK, __fadd_ru(__fmul_ru(0x1.1p-43f, sa[j]), 0x1p-120f)), fabsf(o[j].y));
+            lo[j] = __fsub_rd(o[j].x, b);
+            if (tid + j * T < nd.L) h = fminf(h, __fadd_ru(o[j].x, b));
+        }
+        for (int q = 16; q > 0; q >>= 1) h = fminf(h, __shfl_xor_sync(0xffffffffu, h, q));
+        if (l == 0) rh[w] = h;
+        __syncthreads();
+        float H = rh[0];
+        for (int q = 1; q < T / 32; ++q) H = fminf(H, rh[q]);
+        // exact FP64 objective of the candidates, in neighbour order
+        bool cand[kLab];
+        double ex[kLab];
+#pragma unroll
+        for (int j = 0; j < kLab; ++j) {
+            const int s = tid + j * T;
+            cand[j] = s < nd.L && lo[j] <= H;
+            ex[j] = cand[j] ? se_d(agg[nd.aoff + s]) : 0.0;
+        }
+        for (int c0 = k0; c0 < k1; c0 += T) {
+            const int nc = min(T, k1 - c0);
+            if (K > T) stage(c0, nc);  // else the single chunk is still staged
+#pragma unroll
+            for (int j = 0; j < kLab; ++j) {
+                const int s = tid + j * T;
+                if (cand[j])
+                    for (int kb = 0; kb < nc; kb += kBatch) {
+                        float tv[kBatch];
+                        ulonglong2 mv[kBatch];
+#pragma unroll
+                        for (int q = 0; q < kBatch; ++q)
+                            if (kb + q < nc) {
+                                tv[q] = tab[k_row[kb + q] + s];
+                                mv[q] = msg[k_mv[kb + q] + s];
+                            }
+#pragma unroll
+                        for (int q = 0; q < kBatch; ++q)
+                            if (kb + q < nc)
+                                ex[j] = ex[j] + ((static_cast<double>(tv[q]) - k_phi[kb + q]) - se_d(mv[q]));
+                    }
+            }
+        }
         double best = INFINITY;
         int bi = INT_MAX;
-        for (int s = threadIdx.x; s < nd.L; s += kThreads) {
-            double acc = se_d(agg[nd.aoff + s]);
-            for (int k = in_off[u]; k < in_off[u + 1]; ++k) {
-                const EdgeDesc ed = edges[in_edge[k]];
-                const int xv = labels[ed.gu];
-                const double term =
-                    (static_cast<double>(tab[ed.toff + static_cast<long long>(xv) * ed.ld + s]) -
-                     se_d(msg[ed.mu + xv])) -
-                    se_d(msg[ed.mv + s]);
-                acc = acc + term;
+#pragma unroll
+        for (int j = 0; j < kLab; ++j)
+            if (cand[j] && ex[j] < best) {
+                best = ex[j];
+                bi = tid + j * T;
             }
-            if (acc < best) {
-                best = acc;
+        // labels beyond kLab * T: the FP64 sums directly, one label at a time
+        for (int s = tid + kLab * T; s < nd.L; s += T) {
+            double a = se_d(agg[nd.aoff + s]);
+            for (int k = k0; k < k1; ++k) {
+                const InRec r = in_rec[k];
+                const int xv = labels[r.gu];
+                a = a + ((static_cast<double>(tab[r.toff + static_cast<long long>(xv) * r.ld + s]) -
+                          se_d(msg[r.mu + xv])) -
+                         se_d(msg[r.mv + s]));
+            }
+            if (a < best) {
+                best = a;
                 bi = s;
             }
         }
-        for (int o = 16; o > 0; o >>= 1) {
-            const double ov = __shfl_xor_sync(0xffffffffu, best, o);
-            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-            if (ov < best || (ov == best && oi < bi)) {
-                best = ov;
-                bi = oi;
+        // argmin, lowest index on ties; a warp with at most one candidate
+        // needs no FP64 comparison
+        const unsigned who = __ballot_sync(0xffffffffu, bi != INT_MAX);
+        if (__popc(who) == 1) {
+            const int src = __ffs(who) - 1;
+            best = __shfl_sync(0xffffffffu, best, src);
+            bi = __shfl_sync(0xffffffffu, bi, src);
+        } else if (who != 0) {
+            for (int o2 = 16; o2 > 0; o2 >>= 1) {
+                const double ov = __shfl_xor_sync(0xffffffffu, best, o2);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, o2);
+                if (ov < best || (ov == best && oi < bi)) {
+                    best = ov;
+                    bi = oi;
+                }
             }
         }
         if (l == 0) {
@@ -187,15 +405,15 @@ __global__ void __launch_bounds__(kThreads) round_kernel(const EdgeDesc *edges, 
             ri[w] = bi;
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
-            double b = rv[0];
-            int i = ri[0];
-            for (int j = 1; j < kThreads / 32; ++j)
-                if (rv[j] < b || (rv[j] == b && ri[j] < i)) {
-                    b = rv[j];
-                    i = ri[j];
+        if (tid == 0) {
+            double b = INFINITY;
+            int i = INT_MAX;
+            for (int q = 0; q < T / 32; ++q)
+                if (ri[q] != INT_MAX && (rv[q] < b || (rv[q] == b && ri[q] < i))) {
+                    b = rv[q];
+                    i = ri[q];
                 }
-            if (i == INT_MAX) {  // every objective value was NaN
+            if (i == INT_MAX) {  // no candidate: every objective value was NaN
                 i = 0;
                 atomicCAS(err, 0, ERR_NONFINITE);
             }
@@ -293,10 +511,17 @@ cudaError_t launch_restamp(ulonglong2 *agg, long long n_agg, ulonglong2 *msg, lo
 
 cudaError_t launch_bound(const EdgeDesc *edges, int n_edges, const NodeDesc *nodes, int n_nodes, const float *tab,
                          const ulonglong2 *agg, const ulonglong2 *msg, double *emin, double *nmin, const int *model_node_off,
-                         const int *model_edge_off, int n_models, int exact, double *out, cudaStream_t st)
+                         const int *model_edge_off, int n_models, int exact, int lmax, double *out, cudaStream_t st)
 {
     if (exact && n_edges > 0) {
-        bound_edges_kernel<<<grid_for(n_edges, 1), kThreads, 0, st>>>(edges, n_edges, tab, msg, emin);
+        const int lm = lmax > 0 ? lmax : 1;
+        const size_t smem = (2 * sizeof(double) + 2 * sizeof(float)) * static_cast<size_t>(lm);
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(bound_edges_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 static_cast<int>(smem));
+            if (e != cudaSuccess) return e;
+        }
+        bound_edges_kernel<<<grid_for(n_edges, 1), kThreads, smem, st>>>(edges, n_edges, tab, msg, lm, emin);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -309,13 +534,12 @@ cudaError_t launch_bound(const EdgeDesc *edges, int n_edges, const NodeDesc *nod
     return cudaGetLastError();
 }
 
-cudaError_t launch_round(const EdgeDesc *edges, const NodeDesc *nodes, const int *in_off, const int *in_edge,
+cudaError_t launch_round(const EdgeDesc *edges, const NodeDesc *nodes, const int *in_off, const InRec *in_rec,
                          const int *model_node_off, const int *model_edge_off, int n_models, const float *tab,
                          const ulonglong2 *agg, const ulonglong2 *msg, const float *un0, int *labels, double *energy, int *err,
                          cudaStream_t st)
 {
-    round_kernel<<<n_models, kThreads, 0, st>>>(edges, nodes, in_off, in_edge, model_node_off, tab, agg, msg, labels,
-                                               err);
+    round_kernel<<<n_models, kRoundThreads, 0, st>>>(nodes, in_off, in_rec, model_node_off, tab, agg, msg, labels, err);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     energy_kernel<<<n_models, kThreads, 0, st>>>(edges, nodes, model_node_off, model_edge_off, tab, un0, labels,

@@ -42,8 +42,8 @@ cudaError_t launch_pack(const EdgeDesc *edges, int n_edges, const NodeDesc *node
 cudaError_t launch_bound(const EdgeDesc *edges, int n_edges, const NodeDesc *nodes, int n_nodes,
                          const float *tab, const ulonglong2 *agg, const ulonglong2 *msg, double *emin, double *nmin,
                          const int *model_node_off, const int *model_edge_off, int n_models, int exact,
-                         double *out, cudaStream_t st);
-cudaError_t launch_round(const EdgeDesc *edges, const NodeDesc *nodes, const int *in_off, const int *in_edge,
+                         int lmax, double *out, cudaStream_t st);  // lmax >= every label count and row stride
+cudaError_t launch_round(const EdgeDesc *edges, const NodeDesc *nodes, const int *in_off, const InRec *in_rec,
                          const int *model_node_off, const int *model_edge_off, int n_models, const float *tab,
                          const ulonglong2 *agg, const ulonglong2 *msg, const float *un0, int *labels, double *energy,
                          int *err, cudaStream_t st);

@@ -42,12 +42,14 @@ struct mplpp_solver {
     std::vector<mplpp::NodeDesc> h_nodes;
     std::vector<int> phase_off, phase_edges;
     std::vector<int> in_off, in_edge, mnode_off, medge_off;
+    std::vector<mplpp::InRec> in_rec;  // in_edge's records (rounding)
     std::vector<int> work_off;
     std::vector<mplpp::WorkItem> work;
 
     // mapping
     int mode = MPLPP_MODE_LOOPED;
     int C = 1, T = 256, tile_floats = 4, rmax = 4, ldmax = 4, max_phase = 1, clusters = 0, max_deg = 0;
+    int lmax = 1;          // >= every label count and row stride (exact bound's buffers)
     int work_off_cap = 0;  // capacity of d_work_off
     bool rr = false;       // register-resident pass variant
     size_t smem_looped = 0, smem_persist = 0;
@@ -61,7 +63,8 @@ struct mplpp_solver {
     int *d_phase_edges = nullptr, *d_err = nullptr;
     int *d_work_off = nullptr;
     mplpp::WorkItem *d_work = nullptr;
-    int *d_in_off = nullptr, *d_in_edge = nullptr, *d_mnode_off = nullptr, *d_medge_off = nullptr;
+    int *d_in_off = nullptr, *d_mnode_off = nullptr, *d_medge_off = nullptr;
+    mplpp::InRec *d_in_rec = nullptr;
     double *d_emin = nullptr, *d_nmin = nullptr;
     double *d_out = nullptr, *d_energy = nullptr;
     int *d_labels = nullptr;

@@ -215,6 +215,53 @@ def test_rounding_decisions_match_oracle_bit_for_bit():
         assert np.array_equal(xg, xo)
 
 
+@pytest.mark.parametrize("case", ["ties", "large", "near_ties"])
+def test_rounding_screen_matches_fp64_decisions(case):
+    """The rounding kernel screens labels in double-float with an error bound
+    and sums only the surviving candidates in FP64; its decisions must equal
+    the all-FP64 ones (oracle, same summation order) on the solver's own
+    state: exact ties (values on a 1/8 grid, lowest index wins), large
+    message magnitudes, and pairs of labels whose objectives differ by 2^-40."""
+    rng = np.random.default_rng(21)
+    m = _tied_model() if case == "ties" else W.uneven_complete(10, 4, 40, seed=8)
+    g = oracle.Graph.of(m)
+    Lu, Lv = m.labels[m.edge_u], m.labels[m.edge_v]
+    nagg, nmsg = int(m.labels.sum()), int((Lu + Lv).sum())
+    uoff = np.concatenate([[0], np.cumsum(m.labels.astype(np.int64))])
+    moff = np.concatenate([[0], np.cumsum((Lu + Lv).astype(np.int64))])
+    if case == "ties":
+        agg = np.floor(rng.uniform(-4, 4, nagg) * 8) / 8
+        msg = np.floor(rng.uniform(-4, 4, nmsg) * 8) / 8
+    elif case == "large":
+        agg, msg = rng.normal(0.0, 1e4, nagg), rng.normal(0.0, 1e4, nmsg)
+    else:
+        # labels 0 and 1 of every node enter its objective identically except
+        # for the unary, which differs by 2^-40 (sign alternating by node)
+        pw = m.pairwise.copy()
+        for e in range(m.E):
+            t = pw[g.poff[e]:g.poff[e + 1]].reshape(int(Lu[e]), int(Lv[e]))
+            t[:, 1] = t[:, 0]
+        m.pairwise = pw
+        agg, msg = rng.normal(0.0, 1.0, nagg), rng.normal(0.0, 1.0, nmsg)
+        for e in range(m.E):
+            b0 = moff[e] + Lu[e]
+            msg[b0 + 1] = msg[b0]
+        for u in range(m.n):
+            agg[uoff[u] + 1] = agg[uoff[u]] + (1 if u % 2 else -1) * 2.0 ** -40
+    s = Solver([m])
+    s.set_state(agg, msg)
+    _, agg, msg = s.state_arrays()  # the double-float values the device holds
+    xg, _ = s.labeling()
+    th_uv = np.empty(m.pairwise.shape, np.float64)
+    for e in range(m.E):
+        pu = msg[moff[e]:moff[e] + Lu[e]]
+        pv = msg[moff[e] + Lu[e]:moff[e + 1]]
+        t = g.table(m.pairwise, e).astype(np.float64)
+        th_uv[g.poff[e]:g.poff[e + 1]] = ((t - pu[:, None]) - pv[None, :]).ravel()
+    xo = oracle.round_labels(m, agg, th_uv)
+    assert np.array_equal(xg, xo)
+
+
 def test_bound_fast_equals_exact_after_full_iteration():
     """After a full iteration every reparametrized table has minimum 0 (Def. 1),
     so the node-only bound equals the exact one up to FP32 rounding."""
@@ -223,6 +270,57 @@ def test_bound_fast_equals_exact_after_full_iteration():
     s.run(5)
     De, Df = s.bound(exact=True)[0], s.bound(exact=False)[0]
     assert abs(De - Df) <= 1e-5 * max(1.0, abs(De))
+
+
+def _bound_from_state(m, agg, msg):
+    """D(phi) (eq. LP-lower-bound) evaluated entry by entry in FP64 from a
+    saved state: every node's and every table's minimum, each table entry as
+    (theta - phi_{v->u}(s)) - phi_{u->v}(t).  Returns (D, sum of |terms|)."""
+    g = oracle.Graph.of(m)
+    uoff = np.concatenate([[0], np.cumsum(m.labels.astype(np.int64))])
+    terms = [float(agg[uoff[u]:uoff[u + 1]].min()) for u in range(m.n)]
+    k = 0
+    for e in range(m.E):
+        Lu, Lv = int(m.labels[m.edge_u[e]]), int(m.labels[m.edge_v[e]])
+        pu, pv = msg[k:k + Lu], msg[k + Lu:k + Lu + Lv]
+        k += Lu + Lv
+        th = g.table(m.pairwise.astype(np.float64), e)
+        terms.append(float(((th - pu[:, None]) - pv[None, :]).min()))
+    return float(np.sum(terms)), float(np.sum(np.abs(terms)))
+
+
+def _tied_model():
+    """Costs on a coarse grid (many equal entries and equal minima)."""
+    m = W.complete(10, 12, seed=3, pairwise="uniform")
+    m.pairwise = (np.floor(m.pairwise * 4.0) / 4.0).astype(np.float32)
+    m.unary = (np.floor(m.unary * 2.0) / 2.0).astype(np.float32)
+    return m
+
+
+@pytest.mark.parametrize("case", ["normal_T0", "normal_T4", "uneven_T2", "tied_T3", "large_state"])
+def test_exact_bound_equals_entrywise_fp64_definition(case):
+    """The exact bound's per-table minima are decided by an FP32 screen with
+    an error bound and evaluated in FP64 only for the surviving candidates;
+    the result must equal the entrywise FP64 definition on the solver's own
+    state (up to the order of the final sum)."""
+    rng = np.random.default_rng(11)
+    if case.startswith("normal"):
+        m, T = W.complete(12, 16, seed=5, pairwise="normal"), int(case[-1])
+    elif case == "uneven_T2":
+        m, T = W.uneven_complete(8, 5, 60, seed=12), 2
+    elif case == "tied_T3":
+        m, T = _tied_model(), 3
+    else:
+        m, T = W.uneven_complete(9, 3, 70, seed=4), 0
+    s = Solver([m])
+    s.run(T)
+    if case == "large_state":  # messages and unaries far from the costs' scale
+        _, agg, msg = s.state_arrays()
+        s.set_state(rng.normal(0.0, 1e3, agg.size), rng.normal(0.0, 1e3, msg.size))
+    _, agg, msg = s.state_arrays()
+    Dg = s.bound(exact=True)[0]
+    Dd, scale = _bound_from_state(m, agg, msg)
+    assert abs(Dg - Dd) <= 1e-13 * (scale + 1.0), (Dg, Dd)
 
 
 def test_residual_rows_and_columns_zero_after_update():
