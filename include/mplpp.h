@@ -63,9 +63,12 @@ enum {
 enum {
     MPLPP_MODE_AUTO = 0,       /* persistent when the device allows it, else looped            */
     MPLPP_MODE_LOOPED = 1,     /* one kernel launch per matching (launch boundary = barrier)  */
-    MPLPP_MODE_PERSISTENT = 2  /* one launch for all iterations; every state entry carries the
+    MPLPP_MODE_PERSISTENT = 2, /* one launch for all iterations; every state entry carries the
                                   update count that wrote it, which orders the matchings on
                                   the device (a reader polls until the count it needs)        */
+    MPLPP_MODE_WARP = 3        /* as PERSISTENT with one warp per edge instead of a cluster of
+                                  CTAs per edge (for many small tables: every label count
+                                  <= 256); options.cluster is ignored                          */
 };
 
 typedef struct {

@@ -21,7 +21,7 @@ MPLPP_OK = 0
 STATUS = {0: "MPLPP_OK", -1: "MPLPP_E_INVALID", -2: "MPLPP_E_NOMEM", -3: "MPLPP_E_CUDA",
           -4: "MPLPP_E_TIMEOUT", -5: "MPLPP_E_NONFINITE", -6: "MPLPP_E_STATE", -7: "MPLPP_E_UNSUPPORTED"}
 SCHED = {"round_robin": 0, "greedy_color": 1, "alg1": 2, "user": 3}
-MODE = {"auto": 0, "looped": 1, "persistent": 2}
+MODE = {"auto": 0, "looped": 1, "persistent": 2, "warp": 3}
 MODE_NAME = {v: k for k, v in MODE.items()}
 
 # Every symbol include/mplpp.h declares.

@@ -207,6 +207,71 @@ static void build_work(mplpp_solver *s, int clusters)
     for (int d : deg) s->max_deg = std::max(s->max_deg, d);
 }
 
+static void drop_graphs(mplpp_solver *s)
+{
+    if (s->g_looped) {
+        cudaGraphExecDestroy(s->g_looped);
+        s->g_looped = nullptr;
+    }
+    if (s->g_persist) {
+        cudaGraphExecDestroy(s->g_persist);
+        s->g_persist = nullptr;
+        s->g_persist_iters = -1;
+    }
+}
+
+// The warp driver (one warp per edge) with T threads per block: per-warp
+// vectors sized for the largest label count, as many warp workers as are
+// co-resident (at most one per edge of the largest matching), work lists as
+// for the cluster driver.
+static mplpp_status apply_warp_mapping(mplpp_solver *s, int T, int optin)
+{
+    if (T % 32 || T < 0 || T > 512) return fail(s, MPLPP_E_INVALID, "threads must be a multiple of 32 in 32..512");
+    mapping_for(s, 1, T > 0 ? T : 256);  // sizes of the other drivers stay consistent
+    if (T == 0) {  // the widest block (<= 256 threads) whose warps' buffers fit
+        T = 32;
+        for (int t : {256, 128, 64})
+            if (static_cast<size_t>(t / 32) *
+                    hs_warp_bytes_per_warp(static_cast<int>(round4(s->lmax)), 32 * s->ldmax) <=
+                static_cast<size_t>(optin)) {
+                T = t;
+                break;
+            }
+    }
+    s->T = T;
+    if (s->EE == 0) return fail(s, MPLPP_E_UNSUPPORTED, "the warp driver needs edges");
+    if (s->lmax > kWarpMaxL)
+        return fail(s, MPLPP_E_UNSUPPORTED,
+                    "the warp driver takes label counts up to " + std::to_string(kWarpMaxL) + " (largest here " +
+                        std::to_string(s->lmax) + ")");
+    const int lw = static_cast<int>(round4(s->lmax));
+    const int wpb = T / 32;
+    // table buffers of 32 rows of the widest table (the fewest bytes per warp:
+    // the most warps per SM); smaller tables are resident, larger ones stream
+    const int cap = 32 * s->ldmax;
+    const size_t smem = static_cast<size_t>(wpb) * hs_warp_bytes_per_warp(lw, cap);
+    if (smem > static_cast<size_t>(optin)) return fail(s, MPLPP_E_UNSUPPORTED, "warp driver: shared memory");
+    const int blocks_max = hs_warp_max_blocks(T, smem);
+    if (blocks_max < 1) return fail(s, MPLPP_E_UNSUPPORTED, "warp driver: no block fits");
+    int workers = std::min(blocks_max * wpb, s->max_phase);
+    workers = std::min(workers, s->work_off_cap - 1);
+    if (workers < 1) return fail(s, MPLPP_E_UNSUPPORTED, "warp driver: no worker fits");
+    build_work(s, workers);
+    CK(s, cudaMemcpyAsync(s->d_work_off, s->work_off.data(), s->work_off.size() * sizeof(int), cudaMemcpyHostToDevice,
+                          s->stream));
+    CK(s, cudaMemcpyAsync(s->d_work, s->work.data(), s->work.size() * sizeof(WorkItem), cudaMemcpyHostToDevice,
+                          s->stream));
+    CK(s, cudaStreamSynchronize(s->stream));
+    s->mode = MPLPP_MODE_WARP;
+    s->clusters = workers;
+    s->warp_blocks = (workers + wpb - 1) / wpb;
+    s->lw = lw;
+    s->cap = cap;
+    s->smem_warp = smem;
+    drop_graphs(s);
+    return MPLPP_OK;
+}
+
 // Makes (C, T, mode) the solver's mapping: sizes, kernel attributes, and for
 // the persistent driver the per-cluster work lists (uploaded to the device).
 // want: MPLPP_MODE_AUTO (persistent if possible), _LOOPED or _PERSISTENT.
@@ -214,6 +279,7 @@ static mplpp_status apply_mapping(mplpp_solver *s, int C, int T, int want)
 {
     int optin = 0;
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->device);
+    if (want == MPLPP_MODE_WARP) return apply_warp_mapping(s, T, optin);
     mapping_for(s, C, T);
     if (s->smem_looped > static_cast<size_t>(optin))
         return fail(s, MPLPP_E_UNSUPPORTED,
@@ -239,15 +305,7 @@ static mplpp_status apply_mapping(mplpp_solver *s, int C, int T, int want)
     if (want == MPLPP_MODE_PERSISTENT && mode != MPLPP_MODE_PERSISTENT)
         return fail(s, MPLPP_E_UNSUPPORTED, "persistent mode is not possible for these shapes on this device");
     s->mode = mode;
-    if (s->g_looped) {
-        cudaGraphExecDestroy(s->g_looped);
-        s->g_looped = nullptr;
-    }
-    if (s->g_persist) {
-        cudaGraphExecDestroy(s->g_persist);
-        s->g_persist = nullptr;
-        s->g_persist_iters = -1;
-    }
+    drop_graphs(s);
     return MPLPP_OK;
 }
 
@@ -495,6 +553,9 @@ static HsParams make_params(mplpp_solver *s)
     p.rr = s->rr ? 1 : 0;
     p.C = s->C;
     p.tile_floats = s->tile_floats;
+    p.workers = s->mode == MPLPP_MODE_WARP ? s->clusters : 0;
+    p.lw = s->lw;
+    p.cap = s->cap;
     p.rmax = s->rmax;
     p.ldmax = s->ldmax;
     return p;
@@ -522,6 +583,7 @@ cudaError_t enqueue_persistent(mplpp_solver *s, cudaStream_t st, int iterations)
     cudaError_t e = launch_restamp(s->d_agg, s->aggN, s->d_msg, s->msgN, st);
     if (e != cudaSuccess) return e;
     p.iterations = iterations;
+    if (s->mode == MPLPP_MODE_WARP) return hs_launch_warp(p, s->warp_blocks, s->T, s->smem_warp, st);
     return hs_launch_persistent(p, s->clusters, s->T, s->smem_persist, st);
 }
 
@@ -733,6 +795,11 @@ extern "C" mplpp_status mplpp_load_state(mplpp_solver *s, const void *buf, size_
     return MPLPP_OK;
 }
 
+static const char *mode_name(int mode)
+{
+    return mode == MPLPP_MODE_PERSISTENT ? "persistent" : mode == MPLPP_MODE_WARP ? "warp" : "looped";
+}
+
 // Measured choice of the mapping: every feasible (CTAs per edge, threads per
 // CTA, driver) runs `iterations` iterations of the solver's own models from
 // the same state, timed with CUDA events on the solver's stream; the fastest
@@ -766,9 +833,11 @@ extern "C" mplpp_status mplpp_autotune(mplpp_solver *s, int32_t iterations, char
     cudaEvent_t e0, e1;
     CK(s, cudaEventCreate(&e0));
     CK(s, cudaEventCreate(&e1));
-    for (int mode : {MPLPP_MODE_PERSISTENT, MPLPP_MODE_LOOPED})
+    for (int mode : {MPLPP_MODE_PERSISTENT, MPLPP_MODE_LOOPED, MPLPP_MODE_WARP})
         for (int C : {1, 2, 3, 4, 5, 6, 8})
             for (int T : {128, 256, 512}) {
+                if (mode == MPLPP_MODE_WARP && C != 1) continue;  // one warp per edge
+                if (mode == MPLPP_MODE_WARP && T == 512) T = 32;  // small blocks: shared memory per warp
                 if (apply_mapping(s, C, T, mode) != MPLPP_OK) {
                     s->err.clear();
                     continue;
@@ -796,11 +865,11 @@ extern "C" mplpp_status mplpp_autotune(mplpp_solver *s, int32_t iterations, char
     if (report && report_size) {
         std::string r = "{\"iterations\": " + std::to_string(iterations) + ", \"best\": {\"cluster\": " +
                         std::to_string(best.C) + ", \"threads\": " + std::to_string(best.T) + ", \"mode\": \"" +
-                        (best.mode == MPLPP_MODE_PERSISTENT ? "persistent" : "looped") + "\", \"ms\": " +
+                        mode_name(best.mode) + "\", \"ms\": " +
                         std::to_string(best.ms) + "}, \"candidates\": [";
         for (size_t i = 0; i < done.size(); ++i)
             r += std::string(i ? ", " : "") + "[" + std::to_string(done[i].C) + ", " + std::to_string(done[i].T) +
-                 ", \"" + (done[i].mode == MPLPP_MODE_PERSISTENT ? "persistent" : "looped") + "\", " +
+                 ", \"" + mode_name(done[i].mode) + "\", " +
                  std::to_string(done[i].ms) + "]";
         r += "]}";
         std::snprintf(report, report_size, "%s", r.c_str());
@@ -818,8 +887,10 @@ extern "C" mplpp_status mplpp_info(const mplpp_solver *s, mplpp_info_t *info)
     info->mode = s->mode;
     info->cluster = s->C;
     info->threads = s->T;
-    info->grid = s->mode == MPLPP_MODE_PERSISTENT ? s->clusters * s->C : 0;
-    info->launches_per_iteration = s->mode == MPLPP_MODE_PERSISTENT ? 0 : s->P;
+    info->grid = s->mode == MPLPP_MODE_PERSISTENT ? s->clusters * s->C
+                 : s->mode == MPLPP_MODE_WARP     ? s->warp_blocks
+                                                  : 0;
+    info->launches_per_iteration = s->mode == MPLPP_MODE_LOOPED ? s->P : 0;
     return MPLPP_OK;
 }
 

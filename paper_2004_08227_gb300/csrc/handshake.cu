@@ -135,14 +135,6 @@ __device__ __forceinline__ void named_barrier_1(int count)
     asm volatile("bar.sync 1, %0;" ::"r"(count) : "memory");
 }
 
-// Update counts an item expects of its inputs (persistent driver): node u's
-// and node v's entries carry u / v (earlier updates of the node in this
-// launch), the edge's messages carry e (earlier updates of the edge); the
-// item writes u + 1, v + 1, e + 1.  `bump` is added to what the u side waits
-// for (testing the bounded wait: an update that never comes).
-struct Versions {
-    unsigned u, v, e, bump;
-};
 
 // Persistent driver, next item: its work record (16 bytes per thread of the
 // last warp, requested at the start of this item and stored into shared

@@ -24,11 +24,35 @@ struct HsParams {
     int rr;                  // launch the variant with register-resident passes
     int C;                   // CTAs per edge (cluster size)
     int tile_floats;         // capacity of one table buffer (floats)
+    int workers;             // warp driver: number of warp workers (lists in work_off / work)
+    int lw;                  // warp driver: per-warp vector capacity (entries, multiple of 4)
+    int cap;                 // warp driver: floats per table buffer (>= 32 rows of any table)
     int rmax;                // capacity of row vectors (floats, multiple of 4)
     int ldmax;               // capacity of column vectors (floats, multiple of 4)
 };
 
+// Update counts an item expects of its inputs (persistent drivers): node u's
+// and node v's entries carry u / v (earlier updates of the node in this
+// launch), the edge's messages carry e (earlier updates of the edge); the
+// item writes u + 1, v + 1, e + 1.  `bump` is added to what the u side waits
+// for (testing the bounded wait: an update that never comes).
+struct Versions {
+    unsigned u, v, e, bump;
+};
+
 size_t hs_smem_bytes(int nbuf, int tile_floats, int rmax, int ldmax, int threads, int C);
+
+// warp.cu: one warp per edge (persistent).  Shared memory per warp for vector
+// capacity lw and table buffers of cap floats: the work record, two
+// mbarriers, two buffers, double-float uh and vh, FP32 w1, alpha, beta.
+__host__ __device__ inline size_t hs_warp_bytes_per_warp(int lw, int cap)
+{
+    return sizeof(WorkItem) + 16 + 8 * static_cast<size_t>(cap) + 28 * static_cast<size_t>(lw);
+}
+constexpr int kWarpMaxL = 128;  // largest label count (and row stride) the warp driver takes
+cudaError_t hs_warp_prepare(size_t smem_bytes);
+int hs_warp_max_blocks(int threads, size_t smem_bytes);  // co-resident blocks on the device
+cudaError_t hs_launch_warp(const HsParams &p, int blocks, int threads, size_t smem, cudaStream_t st);
 cudaError_t hs_prepare(size_t smem_bytes);
 cudaError_t hs_launch_looped(const HsParams &p, int n_items, int threads, size_t smem, cudaStream_t st);
 cudaError_t hs_launch_persistent(const HsParams &p, int clusters, int threads, size_t smem, cudaStream_t st);

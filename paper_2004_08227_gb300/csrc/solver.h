@@ -53,6 +53,8 @@ struct mplpp_solver {
     int work_off_cap = 0;  // capacity of d_work_off
     bool rr = false;       // register-resident pass variant
     size_t smem_looped = 0, smem_persist = 0;
+    int warp_blocks = 0, lw = 0, cap = 0;  // warp driver: blocks, per-warp vector and buffer capacity
+    size_t smem_warp = 0;
 
     // device
     std::vector<void *> allocations;
