@@ -227,6 +227,21 @@ def batched_vs_looped(Solver, stream, args):
     bms, D = _timed(stream, lambda: step_b(s), 2)
     s.close()
     lp = looped_baseline(Solver, models, T, stream, step_b, D, bms, 1)
+    # the same batch through each persistent driver: one kernel launch per solve
+    persistent = {}
+    for name, kw in (("cluster", {"mode": "persistent"}), ("warp", {"mode": "warp"})):
+        try:
+            sp = Solver(models, **kw)
+        except Exception as e:  # a driver the shapes do not admit
+            persistent[name] = {"unavailable": str(e)}
+            continue
+        step_b(sp)
+        pms, Dp = _timed(stream, lambda: step_b(sp), 1)
+        pin = sp.info()
+        persistent[name] = {"ms": pms, "run_launches": 2, "bound_equal": bool(np.array_equal(Dp, D)),
+                            "speedup_vs_per_model_loop": lp["ms_per_step"] / pms,
+                            "mapping": {k: pin[k] for k in ("cluster", "threads", "grid")}}
+        sp.close()
     upd = T * info["edges"]
     return {"workload": CONFIGS[4][0], "models": len(models), "edges": info["edges"], "iterations": T,
             "batched_ms": bms, "batched_edge_updates_per_s": upd / (bms / 1e3),
@@ -234,7 +249,7 @@ def batched_vs_looped(Solver, stream, args):
             "per_model_looped_ms": lp["ms_per_step"], "per_model_launches": lp["launches_per_step"],
             "bound_equal": lp["bound_equal"], "speedup": lp["ms_per_step"] / bms,
             "mapping": {k: info[k] for k in ("mode", "cluster", "threads", "grid")},
-            "autotune": tune.get("best") if tune else None}
+            "autotune": tune.get("best") if tune else None, "persistent_drivers": persistent}
 
 
 def run_ours(args):

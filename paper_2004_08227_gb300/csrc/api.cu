@@ -228,15 +228,19 @@ static mplpp_status apply_warp_mapping(mplpp_solver *s, int T, int optin)
 {
     if (T % 32 || T < 0 || T > 512) return fail(s, MPLPP_E_INVALID, "threads must be a multiple of 32 in 32..512");
     mapping_for(s, 1, T > 0 ? T : 256);  // sizes of the other drivers stay consistent
-    if (T == 0) {  // the widest block (<= 256 threads) whose warps' buffers fit
+    if (T == 0) {  // the block size (<= 256 threads) with the most co-resident warps
         T = 32;
-        for (int t : {256, 128, 64})
-            if (static_cast<size_t>(t / 32) *
-                    hs_warp_bytes_per_warp(static_cast<int>(round4(s->lmax)), 32 * s->ldmax) <=
-                static_cast<size_t>(optin)) {
+        int best = 0;
+        for (int t : {256, 128, 64, 32}) {
+            const size_t b =
+                static_cast<size_t>(t / 32) * hs_warp_bytes_per_warp(static_cast<int>(round4(s->lmax)), 32 * s->ldmax);
+            if (b > static_cast<size_t>(optin)) continue;
+            const int w = hs_warp_max_blocks(t, b) * (t / 32);
+            if (w > best) {
+                best = w;
                 T = t;
-                break;
             }
+        }
     }
     s->T = T;
     if (s->EE == 0) return fail(s, MPLPP_E_UNSUPPORTED, "the warp driver needs edges");

@@ -218,14 +218,20 @@ __global__ void __launch_bounds__(kThreads) bound_sum_kernel(const int *model_no
 // - phi_{v->u}(s); FP64 sums in that order, argmin with the lowest index.
 // GB300's FP64 rate is far below its FP32 rate, so every label's objective
 // is first evaluated in double-float (FP32 operations), O(s), with
-//   |O(s) - exact| and |FP64 value - exact| <= B(s) = (K + 3) 2^-43 S(s),
+//   |O(s) - exact| and |FP64 value - exact| <= B(s) = (K + 8) 2^-43 S(s),
 // S(s) = |agg_u(s)| + sum_k (|theta| + |phi_{u->v}| + |phi_{v->u}(s)|), K
 // earlier neighbours (each double-float addition errs by at most
-// 3 * 2^-48 (|a| + |b|); B carries a factor 8 of margin).  With O(s) bracketed
-// in FP32 (upward / downward rounding) as [lo(s), hi(s)], a label with
-// lo(s) > H = min_s hi(s) cannot attain the FP64 minimum, nor tie with it;
-// the remaining candidates (usually one) are summed in FP64 in neighbour
-// order, so the decision equals the all-FP64 one.
+// 3 * 2^-48 (|a| + |b|), and a label's terms are summed by up to 16 threads
+// whose partial sums are then added in a tree: at most K + 4 additions per
+// label plus two per term; B carries a factor of more than 10 of margin).  With O(s)
+// bracketed in FP32 (upward / downward rounding) as [lo(s), hi(s)], a label
+// with lo(s) > H = min_s hi(s) can neither attain the FP64 minimum nor tie
+// with it.  A single remaining candidate is therefore the FP64 argmin without
+// any FP64 work; several (ties, near-ties) are summed in FP64 in neighbour
+// order and compared, so the decision always equals the all-FP64 one.
+// Latency: the in-edges of node u + 1 whose neighbour is already decided are
+// staged (table row offset, messages) and their table rows prefetched into
+// L2 by the threads without labels while node u is decided.
 constexpr int kRoundThreads = 512;
 
 __global__ void __launch_bounds__(kRoundThreads) round_kernel(const NodeDesc *nodes, const int *in_off,
@@ -237,160 +243,168 @@ __global__ void __launch_bounds__(kRoundThreads) round_kernel(const NodeDesc *no
     __shared__ double rv[T / 32];
     __shared__ int ri[T / 32];
     __shared__ float rh[T / 32];
-    // per earlier neighbour (one chunk of T of them at a time): the offset of
-    // row x_v of its table, phi_{u->v}(x_v) of the edge's first node (FP64 and
-    // double-float) and the offset of the edge's phi_{v->u}, fetched in parallel
-    __shared__ long long k_row[T], k_mv[T];
-    __shared__ double k_phi[T];
-    __shared__ float2 k_phf[T];
+    // staged earlier neighbours (up to T per chunk), two sets: node u's and,
+    // prepared meanwhile, node u + 1's
+    __shared__ long long k_row[2][T], k_mv[2][T];
+    __shared__ double k_phi[2][T];
+    __shared__ float2 k_phf[2][T];
     const int m = blockIdx.x;
     const int tid = threadIdx.x;
     const int w = tid >> 5, l = tid & 31;
-    constexpr int kLab = 2;     // labels s = tid + j * T, j < kLab, screened
-    constexpr int kBatch = 16;  // table rows of different edges miss in L2: loads in flight
-    for (int u = model_node_off[m]; u < model_node_off[m + 1]; ++u) {
+    constexpr int kBatch = 16;  // rows of different tables miss in L2: loads in flight
+    const int u0 = model_node_off[m], u1 = model_node_off[m + 1];
+    auto stage_one = [&](int set, int slot, const InRec &r, int xv) {
+        k_row[set][slot] = r.toff + static_cast<long long>(xv) * r.ld;
+        k_mv[set][slot] = r.mv;
+        const double ph = se_d(msg[r.mu + xv]);
+        const float hi = static_cast<float>(ph);
+        k_phi[set][slot] = ph;
+        k_phf[set][slot] = make_float2(hi, static_cast<float>(ph - static_cast<double>(hi)));
+    };
+    bool pre = false;  // node u's set was staged (except a neighbour u - 1) during node u - 1
+    for (int u = u0; u < u1; ++u) {
+        const int set = (u - u0) & 1;
         const NodeDesc nd = nodes[u];
+        const int L = nd.L;
         const int k0 = in_off[u], k1 = in_off[u + 1], K = k1 - k0;
-        auto stage = [&](int c0, int nc) {
-            __syncthreads();  // the previous chunk's entries are no longer read
-            if (tid < nc) {
-                const InRec r = in_rec[c0 + tid];
-                const int xv = labels[r.gu];
-                k_row[tid] = r.toff + static_cast<long long>(xv) * r.ld;
-                k_mv[tid] = r.mv;
-                const double ph = se_d(msg[r.mu + xv]);
-                const float hi = static_cast<float>(ph);
-                k_phi[tid] = ph;
-                k_phf[tid] = make_float2(hi, static_cast<float>(ph - static_cast<double>(hi)));
+        const bool chunked = K > T;
+        // threads per label: the largest power of two (<= 16) leaving half the
+        // block free to prepare the next node; labels beyond T / P loop (P = 1)
+        int P = 1;
+        while (P < 16 && 2 * P * L <= T / 2) P *= 2;
+        const int s_of = tid / P, part = tid % P;
+        const int nlab = T / P;  // labels per sweep
+        // node u's staged neighbours: complete the set (the neighbour u - 1 was
+        // still undecided) or stage it now
+        if (!chunked) {
+            if (pre) {
+                if (K > 0 && tid == K - 1) {
+                    const InRec r = in_rec[k0 + tid];
+                    if (r.gu == u - 1) stage_one(set, tid, r, labels[r.gu]);
+                }
+            } else if (tid < K) {
+                const InRec r = in_rec[k0 + tid];
+                stage_one(set, tid, r, labels[r.gu]);
             }
             __syncthreads();
-        };
-        // double-float screen
-        float2 o[kLab];
-        float sa[kLab];
-#pragma unroll
-        for (int j = 0; j < kLab; ++j) {
-            const int s = tid + j * T;
-            o[j] = s < nd.L ? se_df(agg[nd.aoff + s]) : make_float2(0.f, 0.f);
-            sa[j] = fabsf(o[j].x);
+        }
+        // the next node's neighbours decided by now, by threads without labels
+        const int busy = ((L < nlab ? L : nlab) * P + 31) & ~31;
+        const bool prep = u + 1 < u1 && in_off[u + 2] - in_off[u + 1] <= T && T - busy >= 32;
+        if (prep && tid >= busy) {
+            const int Ln = nodes[u + 1].L;
+            for (int k = in_off[u + 1] + tid - busy; k < in_off[u + 2]; k += T - busy) {
+                const InRec r = in_rec[k];
+                if (r.gu < u) {
+                    const int xv = labels[r.gu];
+                    stage_one(set ^ 1, k - in_off[u + 1], r, xv);
+                    const float *pr = tab + r.toff + static_cast<long long>(xv) * r.ld;
+                    for (int q = 0; q < Ln; q += 32) asm volatile("prefetch.global.L2 [%0];" ::"l"(pr + q));
+                }
+            }
+        }
+        // double-float screen; thread (s, part) sums neighbours k = part, part + P, ...
+        float hsel = INFINITY;
+        float lo_own = INFINITY;
+        float2 o = make_float2(0.f, 0.f);
+        float sa = 0.f;
+        const int s = s_of;
+        const bool mine = s < L && s < nlab;
+        if (mine && part == 0) {
+            o = se_df(agg[nd.aoff + s]);
+            sa = fabsf(o.x);
         }
         for (int c0 = k0; c0 < k1; c0 += T) {
             const int nc = min(T, k1 - c0);
-            stage(c0, nc);
-            // warps without labels of this node: bring the next node's table
-            // rows of its already decided neighbours into L2 meanwhile
-            const int idle0 = ((nd.L + 31) >> 5) << 5;
-            if (c0 == k0 && tid >= idle0 && u + 1 < model_node_off[m + 1]) {
-                const int Ln = nodes[u + 1].L;
-                for (int k = in_off[u + 1] + tid - idle0; k < in_off[u + 2]; k += T - idle0) {
-                    const InRec r = in_rec[k];
-                    if (r.gu < u) {
-                        const float *p = tab + r.toff + static_cast<long long>(labels[r.gu]) * r.ld;
-                        for (int q = 0; q < Ln; q += 32) asm volatile("prefetch.global.L2 [%0];" ::"l"(p + q));
+            if (chunked) {  // long neighbour lists: staged chunk by chunk
+                __syncthreads();
+                if (tid < nc) {
+                    const InRec r = in_rec[c0 + tid];
+                    stage_one(set, tid, r, labels[r.gu]);
+                }
+                __syncthreads();
+            }
+            if (mine)
+                for (int kb = part; kb < nc; kb += kBatch * P) {
+                    float tv[kBatch];
+                    ulonglong2 mv[kBatch];
+#pragma unroll
+                    for (int q = 0; q < kBatch; ++q) {
+                        const int k = kb + q * P;
+                        if (k < nc) {
+                            tv[q] = tab[k_row[set][k] + s];
+                            mv[q] = msg[k_mv[set][k] + s];
+                        }
+                    }
+#pragma unroll
+                    for (int q = 0; q < kBatch; ++q) {
+                        const int k = kb + q * P;
+                        if (k < nc) {
+                            const float2 f1 = k_phf[set][k], f2 = se_df(mv[q]);
+                            o = df_add(o, df_sub(df_sub(make_float2(tv[q], 0.f), f1), f2));
+                            sa += fabsf(tv[q]) + fabsf(f1.x) + fabsf(f2.x);
+                        }
                     }
                 }
-            }
-#pragma unroll
-            for (int j = 0; j < kLab; ++j) {
-                const int s = tid + j * T;
-                if (s < nd.L)
-                    for (int kb = 0; kb < nc; kb += kBatch) {
-                        float tv[kBatch];
-                        ulonglong2 mv[kBatch];
-#pragma unroll
-                        for (int q = 0; q < kBatch; ++q)
-                            if (kb + q < nc) {
-                                tv[q] = tab[k_row[kb + q] + s];
-                                mv[q] = msg[k_mv[kb + q] + s];
-                            }
-#pragma unroll
-                        for (int q = 0; q < kBatch; ++q)
-                            if (kb + q < nc) {
-                                const float2 f1 = k_phf[kb + q], f2 = se_df(mv[q]);
-                                o[j] = df_add(o[j], df_sub(df_sub(make_float2(tv[q], 0.f), f1), f2));
-                                sa[j] += fabsf(tv[q]) + fabsf(f1.x) + fabsf(f2.x);
-                            }
-                    }
-            }
         }
-        // FP32 brackets [lo, hi] of every objective; H = min hi
-        float lo[kLab];
-        float h = INFINITY;
-        const float cK = static_cast<float>(K + 3);
-#pragma unroll
-        for (int j = 0; j < kLab; ++j) {
-            const float b = __fadd_ru(__fmul_ru(cK, __fadd_ru(__fmul_ru(0x1.1p-43f, sa[j]), 0x1p-120f)), fabsf(o[j].y));
-            lo[j] = __fsub_rd(o[j].x, b);
-            if (tid + j * T < nd.L) h = fminf(h, __fadd_ru(o[j].x, b));
+        // the P partial sums of a label (consecutive lanes), added in a tree
+        for (int q = 1; q < P; q <<= 1) {
+            const float ox = __shfl_xor_sync(0xffffffffu, o.x, q), oy = __shfl_xor_sync(0xffffffffu, o.y, q);
+            o = df_add(o, make_float2(ox, oy));
+            sa += __shfl_xor_sync(0xffffffffu, sa, q);
         }
-        for (int q = 16; q > 0; q >>= 1) h = fminf(h, __shfl_xor_sync(0xffffffffu, h, q));
-        if (l == 0) rh[w] = h;
+        if (mine) {
+            const float cK = static_cast<float>(K + 8);
+            const float b = __fadd_ru(__fmul_ru(cK, __fadd_ru(__fmul_ru(0x1.1p-43f, sa), 0x1p-120f)), fabsf(o.y));
+            lo_own = __fsub_rd(o.x, b);
+            hsel = __fadd_ru(o.x, b);
+        }
+        for (int q = 16; q > 0; q >>= 1) hsel = fminf(hsel, __shfl_xor_sync(0xffffffffu, hsel, q));
+        if (l == 0) rh[w] = hsel;
         __syncthreads();
         float H = rh[0];
         for (int q = 1; q < T / 32; ++q) H = fminf(H, rh[q]);
-        // exact FP64 objective of the candidates, in neighbour order
-        bool cand[kLab];
-        double ex[kLab];
-#pragma unroll
-        for (int j = 0; j < kLab; ++j) {
-            const int s = tid + j * T;
-            cand[j] = s < nd.L && lo[j] <= H;
-            ex[j] = cand[j] ? se_d(agg[nd.aoff + s]) : 0.0;
-        }
-        for (int c0 = k0; c0 < k1; c0 += T) {
-            const int nc = min(T, k1 - c0);
-            if (K > T) stage(c0, nc);  // else the single chunk is still staged
-#pragma unroll
-            for (int j = 0; j < kLab; ++j) {
-                const int s = tid + j * T;
-                if (cand[j])
-                    for (int kb = 0; kb < nc; kb += kBatch) {
-                        float tv[kBatch];
-                        ulonglong2 mv[kBatch];
-#pragma unroll
-                        for (int q = 0; q < kBatch; ++q)
-                            if (kb + q < nc) {
-                                tv[q] = tab[k_row[kb + q] + s];
-                                mv[q] = msg[k_mv[kb + q] + s];
-                            }
-#pragma unroll
-                        for (int q = 0; q < kBatch; ++q)
-                            if (kb + q < nc)
-                                ex[j] = ex[j] + ((static_cast<double>(tv[q]) - k_phi[kb + q]) - se_d(mv[q]));
-                    }
-            }
-        }
-        double best = INFINITY;
-        int bi = INT_MAX;
-#pragma unroll
-        for (int j = 0; j < kLab; ++j)
-            if (cand[j] && ex[j] < best) {
-                best = ex[j];
-                bi = tid + j * T;
-            }
-        // labels beyond kLab * T: the FP64 sums directly, one label at a time
-        for (int s = tid + kLab * T; s < nd.L; s += T) {
-            double a = se_d(agg[nd.aoff + s]);
-            for (int k = k0; k < k1; ++k) {
-                const InRec r = in_rec[k];
-                const int xv = labels[r.gu];
-                a = a + ((static_cast<double>(tab[r.toff + static_cast<long long>(xv) * r.ld + s]) -
-                          se_d(msg[r.mu + xv])) -
-                         se_d(msg[r.mv + s]));
-            }
-            if (a < best) {
+        bool cand = mine && part == 0 && lo_own <= H;
+        // labels beyond one sweep (L > T, P = 1) are never screened: decided the
+        // exact way below
+        const bool extra = L > nlab;
+        const int ncand = __syncthreads_count(cand);
+        if (ncand == 1 && !extra) {
+            // the only label that can attain the FP64 minimum
+            if (cand) labels[u] = s;
+            __syncthreads();
+        } else {
+            // several candidates (ties or near-ties), none (NaN objectives), or
+            // labels beyond one sweep: FP64 sums in neighbour order
+            double best = INFINITY;
+            int bi = INT_MAX;
+            if (cand) {
+                double a = se_d(agg[nd.aoff + s]);
+                for (int k = k0; k < k1; ++k) {
+                    const InRec r = in_rec[k];
+                    const int xv = labels[r.gu];
+                    a = a + ((static_cast<double>(tab[r.toff + static_cast<long long>(xv) * r.ld + s]) -
+                              se_d(msg[r.mu + xv])) -
+                             se_d(msg[r.mv + s]));
+                }
                 best = a;
                 bi = s;
             }
-        }
-        // argmin, lowest index on ties; a warp with at most one candidate
-        // needs no FP64 comparison
-        const unsigned who = __ballot_sync(0xffffffffu, bi != INT_MAX);
-        if (__popc(who) == 1) {
-            const int src = __ffs(who) - 1;
-            best = __shfl_sync(0xffffffffu, best, src);
-            bi = __shfl_sync(0xffffffffu, bi, src);
-        } else if (who != 0) {
+            if (extra && part == 0)
+                for (int s2 = nlab + s_of; s2 < L; s2 += nlab) {
+                    double a = se_d(agg[nd.aoff + s2]);
+                    for (int k = k0; k < k1; ++k) {
+                        const InRec r = in_rec[k];
+                        const int xv = labels[r.gu];
+                        a = a + ((static_cast<double>(tab[r.toff + static_cast<long long>(xv) * r.ld + s2]) -
+                                  se_d(msg[r.mu + xv])) -
+                                 se_d(msg[r.mv + s2]));
+                    }
+                    if (a < best || (a == best && s2 < bi)) {
+                        best = a;
+                        bi = s2;
+                    }
+                }
             for (int o2 = 16; o2 > 0; o2 >>= 1) {
                 const double ov = __shfl_xor_sync(0xffffffffu, best, o2);
                 const int oi = __shfl_xor_sync(0xffffffffu, bi, o2);
@@ -399,27 +413,28 @@ __global__ void __launch_bounds__(kRoundThreads) round_kernel(const NodeDesc *no
                     bi = oi;
                 }
             }
-        }
-        if (l == 0) {
-            rv[w] = best;
-            ri[w] = bi;
-        }
-        __syncthreads();
-        if (tid == 0) {
-            double b = INFINITY;
-            int i = INT_MAX;
-            for (int q = 0; q < T / 32; ++q)
-                if (ri[q] != INT_MAX && (rv[q] < b || (rv[q] == b && ri[q] < i))) {
-                    b = rv[q];
-                    i = ri[q];
-                }
-            if (i == INT_MAX) {  // no candidate: every objective value was NaN
-                i = 0;
-                atomicCAS(err, 0, ERR_NONFINITE);
+            if (l == 0) {
+                rv[w] = best;
+                ri[w] = bi;
             }
-            labels[u] = i;
+            __syncthreads();
+            if (tid == 0) {
+                double bb = INFINITY;
+                int i = INT_MAX;
+                for (int q = 0; q < T / 32; ++q)
+                    if (ri[q] != INT_MAX && (rv[q] < bb || (rv[q] == bb && ri[q] < i))) {
+                        bb = rv[q];
+                        i = ri[q];
+                    }
+                if (i == INT_MAX) {  // no candidate: every objective value was NaN
+                    i = 0;
+                    atomicCAS(err, 0, ERR_NONFINITE);
+                }
+                labels[u] = i;
+            }
+            __syncthreads();
         }
-        __syncthreads();
+        pre = prep;
     }
 }
 
