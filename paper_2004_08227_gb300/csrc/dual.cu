@@ -84,13 +84,15 @@ __device__ __forceinline__ double block_min(double v, double *red)
 //   eps2 = 2^-50 (Th + |phi_{v->u}(s)| + |phi_{u->v}(0)| + 2 D)
 // of its exact value.  An entry with e(t) > min_t e + 4 eps1 + 2 eps2 is then
 // strictly above the row's minimizer in exact arithmetic by more than 2 eps2,
-// so its FP64 value cannot be the row's FP64 minimum; the remaining
-// candidates (usually one or two) are evaluated in FP64.  The threshold is
-// formed in FP32 with upward rounding (a superset of the candidates), the
-// messages are decoded to FP64 once per edge, FP64 instructions issue only
-// where a lane of the warp holds a candidate, and a row's minimum needs no
-// FP64 reduction when one lane holds all its candidates.  The result equals
-// the FP64 minimum over every entry, bit for bit.
+// so its FP64 value cannot be the row's (hence the table's) FP64 minimum.  The
+// threshold is formed in FP32 with upward rounding (a superset of the
+// candidates); each warp appends its rows' candidates (usually one or two per
+// row) to a list in shared memory and evaluates them in FP64 32 at a time, one
+// per lane, so FP64 instructions run with full warps; the table's minimum is
+// the minimum over all candidates.  Messages are decoded to FP64 once per
+// edge.  The result equals the FP64 minimum over every entry, bit for bit.
+constexpr int kCandCap = 64;  // candidate list entries per warp
+
 __global__ void __launch_bounds__(kThreads) bound_edges_kernel(const EdgeDesc *edges, int n_edges,
                                                                const float *tab, const ulonglong2 *msg, int lmax,
                                                                double *emin)
@@ -102,7 +104,9 @@ __global__ void __launch_bounds__(kThreads) bound_edges_kernel(const EdgeDesc *e
     float *dsh = a1 + lmax;                                 // [lmax] d(t)
     __shared__ double red[32];
     __shared__ float redf[32];
+    __shared__ int2 cands[kThreads / 32][kCandCap];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = kThreads / 32;
+    int2 *cl = cands[warp];
     for (int e = blockIdx.x; e < n_edges; e += gridDim.x) {
         const EdgeDesc ed = edges[e];
         const double ref = se_d(msg[ed.mv]);
@@ -125,9 +129,20 @@ __global__ void __launch_bounds__(kThreads) bound_edges_kernel(const EdgeDesc *e
         __syncthreads();
         float D = 0.f;
         for (int w = 0; w < nw; ++w) D = fmaxf(D, redf[w]);
-        double m = INFINITY;
+        const float *trow = tab + ed.toff;
+        double m = INFINITY;  // this lane's minimum over the candidates it evaluated
+        int ncl = 0;          // list length (the same in every lane)
+        auto flush = [&]() {
+            __syncwarp();
+            for (int i = lane; i < ncl; i += 32) {
+                const int2 c = cl[i];
+                m = fmin(m, (static_cast<double>(trow[static_cast<long long>(c.x) * ed.ld + c.y]) - p1[c.x]) - p2[c.y]);
+            }
+            __syncwarp();
+            ncl = 0;
+        };
         for (int s = warp; s < ed.Lu; s += nw) {
-            const float *row = tab + ed.toff + static_cast<long long>(s) * ed.ld;
+            const float *row = trow + static_cast<long long>(s) * ed.ld;
             float me = INFINITY, th = 0.f;
             for (int t = lane; t < ed.Lv; t += 32) {
                 const float x = row[t];
@@ -142,26 +157,21 @@ __global__ void __launch_bounds__(kThreads) bound_edges_kernel(const EdgeDesc *e
             const float eps1 = __fmul_ru(0x1p-22f, __fadd_ru(D, th));
             const float eps2 = __fmul_ru(0x1p-50f, __fadd_ru(__fadd_ru(th, a1[s]), __fadd_ru(aref, __fmul_ru(2.f, D))));
             const float thr = __fadd_ru(__fadd_ru(me, __fmul_ru(4.f, eps1)), __fadd_ru(__fmul_ru(2.f, eps2), 0x1p-126f));
-            const double ph1 = p1[s];
-            double rm = INFINITY;
             for (int t0 = 0; t0 < ed.Lv; t0 += 32) {  // warp-uniform trip count
                 const int t = t0 + lane;
-                const float x = t < ed.Lv ? row[t] : INFINITY;
-                const bool c = t < ed.Lv && x - dsh[t] <= thr;
-                if (__ballot_sync(0xffffffffu, c) != 0u && c)  // FP64 only where a lane has a candidate
-                    rm = fmin(rm, (static_cast<double>(x) - ph1) - p2[t]);
+                const bool c = t < ed.Lv && row[t] - dsh[t] <= thr;
+                const unsigned mask = __ballot_sync(0xffffffffu, c);
+                if (mask) {
+                    if (ncl + __popc(mask) > kCandCap) flush();
+                    if (c) cl[ncl + __popc(mask & ((1u << lane) - 1u))] = make_int2(s, t);
+                    ncl += __popc(mask);
+                }
             }
-            const unsigned who = __ballot_sync(0xffffffffu, rm < INFINITY);
-            if (__popc(who) == 1) {
-                rm = __shfl_sync(0xffffffffu, rm, __ffs(who) - 1);
-            } else {
-                for (int o = 16; o > 0; o >>= 1) rm = fmin(rm, __shfl_xor_sync(0xffffffffu, rm, o));
-            }
-            m = fmin(m, rm);
         }
+        flush();
         m = block_min<kThreads>(m, red);
         if (threadIdx.x == 0) emin[e] = m;
-        __syncthreads();  // p1, p2, a1, dsh and redf are rewritten for the next edge
+        __syncthreads();  // p1, p2, a1, dsh, redf and the lists are rewritten for the next edge
     }
 }
 
