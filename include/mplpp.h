@@ -165,6 +165,18 @@ mplpp_status mplpp_backward(mplpp_solver *s, const float *dD, float *grad_unary,
 /* Resets phi = 0 and the iteration count. */
 mplpp_status mplpp_reset(mplpp_solver *s);
 
+/* Replaces the costs of every model by new ones of the same shapes (same
+ * labels, edges and schedules; eq. energy-min's theta) and resets phi = 0 and
+ * the iteration count, as a new solver with these costs would start: the
+ * device layout, mapping, work lists and captured graphs are kept, so a loop
+ * over many cost sets (learning, serving) pays only the copy and the packing.
+ *   unary[m], pairwise[m]: model m's costs in the layout of mplpp_model, host
+ *   pointers (copied through a device staging buffer allocated on the first
+ *   call and kept) or device pointers if options.inputs_on_device.
+ * Non-finite costs: MPLPP_E_INVALID (the state is then reset but the costs
+ * are undefined until a successful call).  Synchronizes. */
+mplpp_status mplpp_update_costs(mplpp_solver *s, const float *const *unary, const float *const *pairwise);
+
 /* Solver state (the reparametrization) in a portable host format:
  *   header (see mplpp_state_header), then FP64 theta^phi_u for every node
  *   ([sum L], model after model, node order), then per edge phi_{v->u} [L_u]

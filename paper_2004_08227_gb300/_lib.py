@@ -28,7 +28,7 @@ MODE_NAME = {v: k for k, v in MODE.items()}
 EXPORTS = ["mplpp_options_default", "mplpp_schedule", "mplpp_create", "mplpp_run", "mplpp_bound",
            "mplpp_labeling", "mplpp_backward", "mplpp_reset", "mplpp_state_size", "mplpp_save_state",
            "mplpp_load_state", "mplpp_info", "mplpp_sync", "mplpp_last_error", "mplpp_destroy",
-           "mplpp_bound_noalloc", "mplpp_noalloc_last_error", "mplpp_autotune"]
+           "mplpp_bound_noalloc", "mplpp_noalloc_last_error", "mplpp_autotune", "mplpp_update_costs"]
 
 
 class MplppModel(ctypes.Structure):
@@ -86,6 +86,7 @@ def load(build_if_needed: bool = True):
         lib.mplpp_labeling.argtypes = [P, P, P]
         lib.mplpp_backward.argtypes = [P, P, P, P]
         lib.mplpp_reset.argtypes = [P]
+        lib.mplpp_update_costs.argtypes = [P, P, P]
         lib.mplpp_state_size.argtypes = [P, P]
         lib.mplpp_save_state.argtypes = [P, P, ctypes.c_size_t]
         lib.mplpp_load_state.argtypes = [P, P, ctypes.c_size_t]

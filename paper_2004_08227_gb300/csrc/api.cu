@@ -714,6 +714,51 @@ extern "C" mplpp_status mplpp_reset(mplpp_solver *s)
     return MPLPP_OK;
 }
 
+extern "C" mplpp_status mplpp_update_costs(mplpp_solver *s, const float *const *unary, const float *const *pairwise)
+{
+    if (!s || !unary || !pairwise) return MPLPP_E_INVALID;
+    s->err.clear();
+    const int n_models = static_cast<int>(s->models.size());
+    for (int m = 0; m < n_models; ++m)
+        if (!unary[m] || (!pairwise[m] && s->models[m].pair_size))
+            return fail(s, MPLPP_E_INVALID, "model " + std::to_string(m) + ": NULL cost array");
+    cudaStream_t st = s->stream;
+    if (!s->opt.inputs_on_device && !s->d_stage_u) {
+        CK(s, s->alloc(&s->d_stage_u, std::max<long long>(1, s->sum_unary)));
+        CK(s, s->alloc(&s->d_stage_p, std::max<long long>(1, s->sum_pair)));
+    }
+    CK(s, cudaMemsetAsync(s->d_err, 0, sizeof(int), st));
+    long long ub = 0, pb = 0;
+    for (int m = 0; m < n_models; ++m) {
+        const ModelHost &mh = s->models[m];
+        const float *su = unary[m];
+        const float *sp = pairwise[m];
+        if (!s->opt.inputs_on_device) {
+            CK(s, cudaMemcpyAsync(s->d_stage_u + ub, unary[m], mh.unary_size * sizeof(float), cudaMemcpyHostToDevice, st));
+            if (mh.pair_size)
+                CK(s, cudaMemcpyAsync(s->d_stage_p + pb, pairwise[m], mh.pair_size * sizeof(float),
+                                      cudaMemcpyHostToDevice, st));
+            su = s->d_stage_u + ub;
+            sp = s->d_stage_p + pb;
+        }
+        CK(s, launch_pack(s->d_edges + mh.edge_base, mh.E, s->d_nodes + mh.node_base, mh.n, su, sp, s->d_tab, s->d_un0,
+                          s->d_agg, s->d_err, st));
+        ub += mh.unary_size;
+        pb += mh.pair_size;
+    }
+    CK(s, launch_init_state(s->d_un0, s->d_agg, s->aggN, s->d_msg, s->msgN, st));
+    s->iterations = 0;
+    s->history_valid = true;
+    CK(s, cudaStreamSynchronize(st));
+    int herr = 0;
+    CK(s, cudaMemcpy(&herr, s->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (herr) {
+        CK(s, cudaMemset(s->d_err, 0, sizeof(int)));
+        return fail(s, MPLPP_E_INVALID, "costs must be finite");
+    }
+    return MPLPP_OK;
+}
+
 extern "C" mplpp_status mplpp_state_size(const mplpp_solver *s, size_t *bytes)
 {
     if (!s || !bytes) return MPLPP_E_INVALID;

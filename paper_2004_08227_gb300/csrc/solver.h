@@ -81,7 +81,8 @@ struct mplpp_solver {
     unsigned char *d_rec = nullptr;  // argmin records of one segment
     float *d_dD = nullptr;
     long long *d_pbase = nullptr, *d_ubase = nullptr;  // per-model offsets of the caller's layouts
-    ulonglong2 *d_save_agg = nullptr, *d_save_msg = nullptr;  // autotuner: state kept across candidates
+    ulonglong2 *d_save_agg = nullptr, *d_save_msg = nullptr;
+    float *d_stage_u = nullptr, *d_stage_p = nullptr;  // update_costs: host inputs staged here  // autotuner: state kept across candidates
 
     long long iterations = 0;
     long long launches = 0;

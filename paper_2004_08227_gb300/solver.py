@@ -127,6 +127,26 @@ class Solver:
         self.pair_sizes = [int((np.asarray(m.labels, np.int64)[_i32(m.edge_u)] *
                                 np.asarray(m.labels, np.int64)[_i32(m.edge_v)]).sum()) for m in models]
 
+    def update_costs(self, unaries, pairwises):
+        """mplpp_update_costs: new costs of the same shapes for every model
+        (host arrays / tensors, or device tensors if device_inputs), phi reset
+        to 0; the mapping, work lists and captured graphs are kept."""
+        keep = []
+        if len(unaries) != self.n_models or len(pairwises) != self.n_models:
+            raise ValueError("one unary and one pairwise array per model")
+        for un, pw in zip(unaries, pairwises):
+            if self.device_inputs or (torch is not None and isinstance(un, torch.Tensor)):
+                assert un.dtype == torch.float32 and un.is_contiguous()
+                assert pw.dtype == torch.float32 and pw.is_contiguous()
+            else:
+                un = np.ascontiguousarray(un, dtype=np.float32)
+                pw = np.ascontiguousarray(pw, dtype=np.float32)
+            keep += [un, pw]
+        pu = (ctypes.c_void_p * self.n_models)(*[_ptr(a).value for a in keep[0::2]])
+        pp = (ctypes.c_void_p * self.n_models)(*[_ptr(a).value for a in keep[1::2]])
+        self._check(self._lib.mplpp_update_costs(self._h, pu, pp))
+        del keep
+
     # ---- lifecycle -------------------------------------------------------------------
     def close(self):
         if self._h and self._h.value:

@@ -262,6 +262,37 @@ def test_rounding_screen_matches_fp64_decisions(case):
     assert np.array_equal(xg, xo)
 
 
+def test_update_costs_equals_a_new_solver_bitwise():
+    """mplpp_update_costs keeps the layout, mapping and graphs and restarts from
+    phi = 0: the run afterwards equals a new solver's on those costs, bit for
+    bit; a second update in a row does too; non-finite costs are rejected."""
+    models = [W.uneven_complete(8, 4, 40, seed=30), W.uneven_complete(6, 10, 60, seed=31)]
+    new = [W.uneven_complete(8, 4, 40, seed=30), W.uneven_complete(6, 10, 60, seed=31)]
+    rng = np.random.default_rng(5)
+    for m in new:
+        m.unary = rng.random(m.unary.shape).astype(np.float32)
+        m.pairwise = rng.standard_normal(m.pairwise.shape).astype(np.float32)
+    for mode in ("persistent", "looped", "warp"):
+        s = Solver(models, mode=mode)
+        s.run(7)
+        for _ in range(2):
+            s.update_costs([m.unary for m in new], [m.pairwise for m in new])
+            s.run(9)
+            ref = Solver(new, mode=mode)
+            ref.run(9)
+            a, b = s.state_arrays(), ref.state_arrays()
+            assert a[0] == b[0] == 9
+            assert np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
+            assert np.array_equal(s.bound(), ref.bound())
+            assert np.array_equal(s.labeling()[0], ref.labeling()[0])
+            ref.close()
+        bad = new[0].pairwise.copy()
+        bad[3] = np.inf
+        with pytest.raises(MplppError):
+            s.update_costs([m.unary for m in new], [bad, new[1].pairwise])
+        s.close()
+
+
 def test_bound_fast_equals_exact_after_full_iteration():
     """After a full iteration every reparametrized table has minimum 0 (Def. 1),
     so the node-only bound equals the exact one up to FP32 rounding."""
