@@ -193,6 +193,7 @@ static void build_work(mplpp_solver *s, int clusters)
             w.pos_v = pos[ed.gv]++;
             w.deg_u = deg[ed.gu];
             w.deg_v = deg[ed.gv];
+            w.rows = (ed.Lu + s->C - 1) / s->C;
             lists[l.second].push_back(w);
             heap.push({l.first + 4LL * ed.Lu * ed.ld + 16LL * (ed.Lu + ed.Lv), l.second});
         }

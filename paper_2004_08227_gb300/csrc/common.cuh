@@ -56,7 +56,7 @@ struct WorkItem {
     int pos_u, pos_v;
     int deg_u, deg_v;
     int edge;
-    int pad;
+    int rows;         // rows per CTA of the edge's cluster of C CTAs: ceil(L_u / C)
 };
 static_assert(sizeof(WorkItem) == 96 && sizeof(WorkItem) % 16 == 0, "WorkItem layout");
 

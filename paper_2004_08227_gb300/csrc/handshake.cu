@@ -101,20 +101,22 @@ __device__ __forceinline__ int row_lanes(int nr, int Q, int T)
     return 1 << (31 - __clz(g));
 }
 
-__device__ __forceinline__ void rows_of(const EdgeDesc &ed, int rank, int C, int &r0, int &nr)
+// This CTA's rows [r0, r0 + nr) of edge ed, R = ceil(L_u / C) rows per CTA
+// (the persistent driver's work records carry R: no division on the way to
+// the first poll).
+__device__ __forceinline__ void rows_of_R(const EdgeDesc &ed, int rank, int R, int &r0, int &nr)
 {
-    const int R = (ed.Lu + C - 1) / C;
     r0 = rank * R;
     nr = ed.Lu - r0;
     nr = nr < 0 ? 0 : (nr > R ? R : nr);
 }
 
 // Thread 0: start the bulk copy of this CTA's row slice of edge ed's table.
-__device__ __forceinline__ void issue_tile(const EdgeDesc &ed, int rank, int C, const float *tab, float *buf,
+__device__ __forceinline__ void issue_tile(const EdgeDesc &ed, int rank, int R, const float *tab, float *buf,
                                            uint64_t *bar)
 {
     int r0, nr;
-    rows_of(ed, rank, C, r0, nr);
+    rows_of_R(ed, rank, R, r0, nr);
     const uint32_t bytes = static_cast<uint32_t>(nr) * static_cast<uint32_t>(ed.ld) * 4u;
     if (bytes) {
         mbar_arrive_expect_tx(bar, bytes);
@@ -272,12 +274,10 @@ __device__ __forceinline__ float4 min5_4(float4 a, float4 b, float4 c, float4 d,
 // RR: register-resident passes (rr_fits must hold).
 template <bool CLUSTER, bool SIGNAL, bool RR>
 __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile, const Smem &sm, int rank,
-                        uint64_t *bar, uint32_t parity, int xpar, Versions ver, Next nx)
+                        int r0, int nr, uint64_t *bar, uint32_t parity, int xpar, Versions ver, Next nx)
 {
     const int T = blockDim.x, tid = threadIdx.x;
     const int C = CLUSTER ? p.C : 1;
-    int r0, nr;
-    rows_of(ed, rank, C, r0, nr);
     const int ld = ed.ld, Q = ld >> 2, Lv = ed.Lv;
     ulonglong2 *agg = p.agg;
     ulonglong2 *msg = p.msg;
@@ -311,7 +311,9 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
     // is requested at once; the first requests are in flight while the table
     // fragment is loaded.
     if (SIGNAL) {
-        const int uw = min(W - 1, max(1, (W * nr + ((nr + Lv) >> 1)) / max(1, nr + Lv)));
+        // (any split in 1 .. W - 1 is correct: a float estimate, no division)
+        const int uw = min(W - 1, max(1, __float2int_rn(static_cast<float>(W * nr) *
+                                                         __frcp_rn(static_cast<float>(nr + Lv)))));
         const int nv = T - 32 * uw;  // threads on node v's side
         const bool vside = tid < nv;
         const int i0 = vside ? tid : tid - nv, ni = vside ? nv : T - nv;
@@ -361,7 +363,7 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
     __syncthreads();
     if (SIGNAL && tid == 0 && nx.on) {  // the buffer's previous item has finished
         fence_proxy_async();
-        issue_tile(nx.wi->ed, rank, C, p.tab, nx.dst, nx.bar);
+        issue_tile(nx.wi->ed, rank, nx.wi->rows, p.tab, nx.dst, nx.bar);
     }
 
     const int G = row_lanes(nr, Q, T);
@@ -558,17 +560,20 @@ __global__ void __launch_bounds__(512) hs_looped_kernel(HsParams p)
         fence_mbar_init();
     }
     __syncthreads();
-    if (threadIdx.x == 0) issue_tile(ed, rank, C, p.tab, sm.tile, &sm.bar[0]);
+    const int R = (ed.Lu + C - 1) / C;
+    if (threadIdx.x == 0) issue_tile(ed, rank, R, p.tab, sm.tile, &sm.bar[0]);
     if (CLUSTER) {  // every CTA of the cluster is running before any remote store
         cluster_arrive_relaxed();
         cluster_wait_acquire();
     }
     int r0, nr;
-    rows_of(ed, rank, C, r0, nr);
+    rows_of_R(ed, rank, R, r0, nr);
     if (RRK && rr_fits(nr, ed.ld >> 2, blockDim.x, p.tile_floats))
-        hs_item<CLUSTER, false, RRK>(p, ed, sm.tile, sm, rank, &sm.bar[0], 0u, 0, Versions{0u, 0u, 0u, 0u}, Next{});
+        hs_item<CLUSTER, false, RRK>(p, ed, sm.tile, sm, rank, r0, nr, &sm.bar[0], 0u, 0, Versions{0u, 0u, 0u, 0u},
+                                     Next{});
     else
-        hs_item<CLUSTER, false, false>(p, ed, sm.tile, sm, rank, &sm.bar[0], 0u, 0, Versions{0u, 0u, 0u, 0u}, Next{});
+        hs_item<CLUSTER, false, false>(p, ed, sm.tile, sm, rank, r0, nr, &sm.bar[0], 0u, 0, Versions{0u, 0u, 0u, 0u},
+                                       Next{});
     if (CLUSTER) {  // no CTA leaves while another may still access its shared memory
         cluster_arrive_release();
         cluster_wait_acquire();
@@ -603,7 +608,7 @@ __global__ void __launch_bounds__(512) hs_persistent_kernel(HsParams p)
         reinterpret_cast<int4 *>(&sm.wi[0])[tid - (T - kRec)] =
             reinterpret_cast<const int4 *>(p.work + begin)[tid - (T - kRec)];
     __syncthreads();
-    if (tid == 0) issue_tile(sm.wi[0].ed, rank, C, p.tab, sm.tile, &sm.bar[0]);
+    if (tid == 0) issue_tile(sm.wi[0].ed, rank, sm.wi[0].rows, p.tab, sm.tile, &sm.bar[0]);
     int i = 0, it = 0;
     for (long long k = 0; k < total; ++k) {
         const WorkItem &w = sm.wi[k & 1];
@@ -627,12 +632,12 @@ __global__ void __launch_bounds__(512) hs_persistent_kernel(HsParams p)
                               static_cast<unsigned>(it), (p.test_wait && k == 0 && cid == 0) ? 1u : 0u};
         const int b = static_cast<int>(k & 1);
         int r0, nr;
-        rows_of(ed, rank, C, r0, nr);
+        rows_of_R(ed, rank, w.rows, r0, nr);
         if (RRK && rr_fits(nr, ed.ld >> 2, blockDim.x, p.tile_floats))
-            hs_item<CLUSTER, true, RRK>(p, ed, sm.tile + b * p.tile_floats, sm, rank, sm.bar + b,
+            hs_item<CLUSTER, true, RRK>(p, ed, sm.tile + b * p.tile_floats, sm, rank, r0, nr, sm.bar + b,
                                          static_cast<uint32_t>((k >> 1) & 1), b, ver, nx);
         else
-            hs_item<CLUSTER, true, false>(p, ed, sm.tile + b * p.tile_floats, sm, rank, sm.bar + b,
+            hs_item<CLUSTER, true, false>(p, ed, sm.tile + b * p.tile_floats, sm, rank, r0, nr, sm.bar + b,
                                           static_cast<uint32_t>((k >> 1) & 1), b, ver, nx);
         if (++i == n) {
             i = 0;
