@@ -361,7 +361,9 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
     if (SIGNAL && nx.rec_dst) *nx.rec_dst = nx.rec;
     if (!SIGNAL) load_tile();
     __syncthreads();
-    if (SIGNAL && tid == 0 && nx.on) {  // the buffer's previous item has finished
+    // the last thread (its warp has the fewest rows in the passes): the buffer's
+    // previous item has finished
+    if (SIGNAL && tid == T - 1 && nx.on) {
         fence_proxy_async();
         issue_tile(nx.wi->ed, rank, nx.wi->rows, p.tab, nx.dst, nx.bar);
     }
