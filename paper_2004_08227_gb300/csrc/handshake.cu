@@ -60,7 +60,6 @@ struct Smem {
     WorkItem *wi;       // [2] the current and the next work item (persistent driver)
     float *tile;        // nbuf buffers of tile_floats each
     float2 *uh, *vh;    // double-float unaries without this edge's messages
-    float2 *bv;         // double-float new vector of node v
     float *w1;          // vh(t) - vh(0) in FP32 (pass 1)
     float *alpha, *beta, *pm;
     float4 *part;
@@ -74,7 +73,6 @@ __device__ __forceinline__ Smem carve(char *base, const HsParams &p, int nbuf)
     float2 *d = reinterpret_cast<float2 *>(base + 2 * sizeof(WorkItem));
     s.uh = d; d += p.rmax;
     s.vh = d; d += p.ldmax;
-    s.bv = d; d += p.ldmax;
     float *f = reinterpret_cast<float *>(d);
     s.tile = f;
     f += static_cast<size_t>(nbuf) * p.tile_floats;
@@ -495,22 +493,17 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
         }
         const float2 vh = sm.vh[t];
         const float2 b = df_add_f(vh, m);
-        sm.bv[t] = t < Lv ? b : make_float2(0.f, 0.f);
         sm.beta[t] = t < Lv ? df_to_f(df_sub(vh, b)) : 0.f;
+        // node v's new vector (one CTA of the cluster), visible to node v's
+        // next update as soon as it is stored
+        if (rank == 0 && t < Lv) {
+            st_se(agg + ed.av + t, se_make(b, ver.v + 1u));
+            st_se(msg + ed.mv + t, se_make(df_sub(b, vh), ver.e + 1u));
+        }
     }
     // The slots of this parity are written again two items later, by CTAs that
     // have received this CTA's next-item column minima, i.e. after this read.
     __syncthreads();
-
-    // node v's new vector (one CTA of the cluster), visible to node v's next
-    // update as soon as it is stored
-    if (rank == 0) {
-        for (int t = tid; t < Lv; t += T) {
-            const float2 b = sm.bv[t];
-            st_se(agg + ed.av + t, se_make(b, ver.v + 1u));
-            st_se(msg + ed.mv + t, se_make(df_sub(b, sm.vh[t]), ver.e + 1u));
-        }
-    }
 
     // pass 3: c(s) = min_t [theta(s,t) + beta(t)] + uh(s); write node u's rows
     {
@@ -687,9 +680,9 @@ cudaError_t launch(K kernel, const HsParams &p, int grid, int threads, size_t sm
 
 size_t hs_smem_bytes(int nbuf, int tile_floats, int rmax, int ldmax, int threads, int C)
 {
-    // 2 work records; double-float uh, vh, bv; FP32 tiles, w1, alpha, beta, pm (nbuf x C slots), part (float4 x T);
+    // 2 work records; double-float uh, vh; FP32 tiles, w1, alpha, beta, pm (nbuf x C slots), part (float4 x T);
     // 4 mbarriers
-    const size_t d = static_cast<size_t>(rmax) + 2 * static_cast<size_t>(ldmax);
+    const size_t d = static_cast<size_t>(rmax) + static_cast<size_t>(ldmax);
     const size_t f = static_cast<size_t>(nbuf) * tile_floats + static_cast<size_t>(rmax) +
                      (2 + static_cast<size_t>(nbuf) * C) * static_cast<size_t>(ldmax) + 4 * static_cast<size_t>(threads);
     return 2 * sizeof(WorkItem) + d * 8 + f * 4 + 32;
