@@ -94,7 +94,8 @@ typedef struct {
                                  a state checkpoint every k iterations (memory ~ T/k states);
                                  0: backward disabled                                          */
     int32_t cluster;          /* CTAs sharing one edge (1..8); 0 = chosen from the shapes      */
-    int32_t threads;          /* threads per CTA (128, 256, 512); 0 = chosen from the shapes   */
+    int32_t threads;          /* threads per CTA: 0 = chosen from the shapes, else a multiple
+                                 of 32 in 64..512 (32..512 for MPLPP_MODE_WARP)                */
     int32_t test_unreachable_wait; /* testing only (0 otherwise): in the persistent driver the
                                  first edge of the first worker waits for one node update more
                                  than will ever happen, so the bounded wait must run out and the

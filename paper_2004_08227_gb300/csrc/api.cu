@@ -326,6 +326,17 @@ extern "C" mplpp_status mplpp_create(const mplpp_model *models, int32_t n_models
     else mplpp_options_default(&s->opt);
     if (s->opt.spin_limit <= 0) s->opt.spin_limit = 1LL << 22;
     s->stream = static_cast<cudaStream_t>(stream);
+    {
+        const mplpp_options &o = s->opt;
+        if (o.mode < MPLPP_MODE_AUTO || o.mode > MPLPP_MODE_WARP) return fail(nullptr, MPLPP_E_INVALID, "unknown mode");
+        if (o.cluster < 0 || o.cluster > 8) return fail(nullptr, MPLPP_E_INVALID, "cluster must be 0 or 1..8");
+        // a CTA of the cluster drivers splits its warps between the two node
+        // vectors, so it needs two warps at least
+        const int tmin = o.mode == MPLPP_MODE_WARP ? 32 : 64;
+        if (o.threads != 0 && (o.threads % 32 || o.threads < tmin || o.threads > 512))
+            return fail(nullptr, MPLPP_E_INVALID,
+                        "threads must be 0 or a multiple of 32 in " + std::to_string(tmin) + "..512");
+    }
 
     // ---- host-side validation, schedules, layout --------------------------------
     s->models.resize(n_models);

@@ -265,12 +265,84 @@ __device__ __forceinline__ float4 min5_4(float4 a, float4 b, float4 c, float4 d,
                        min3f(min3f(a.z, b.z, c.z), d.z, e.z), min3f(min3f(a.w, b.w, c.w), d.w, e.w));
 }
 
+// Register-resident passes for narrow rows (Q <= 32 float4 chunks): lanes
+// form slots of G lanes (G the power of two >= Q), lane c of a slot holds
+// chunk c of kSR rows: rows (warp * P + slot) + W * P * k, k < kSR, P = 32 / G
+// slots per warp.  Row minima reduce over the G lanes of a slot, column minima
+// over a thread's rows, the warp's slots, then the warps.
+constexpr int kSR = 8;
+
+__device__ __forceinline__ int rs_group(int Q)
+{
+    return Q <= 1 ? 1 : 1 << (32 - __clz(Q - 1));
+}
+
+__device__ __forceinline__ bool rs_fits(int nr, int Q, int T, int tile_floats)
+{
+    if (Q < 1 || Q > 32) return false;
+    const int P = 32 / rs_group(Q), W = T >> 5;
+    return nr <= W * P * kSR && W * part_stride(Q) * 4 <= tile_floats;
+}
+
+// Minimum over the G lanes of a slot of each of the kSR = 8 row values; lane c
+// of the slot receives emit(k, minimum of row k) for the rows it owns.  For G
+// >= 8 a reduce-scatter (the lane keeps the half of the rows given by its bits
+// G/2, G/4, G/8, then plain exchanges): lanes c with c % (G/8) == 0 own row
+// c / (G/8).  For G < 8 every lane gets every row; lane c owns rows c mod G.
+static_assert(kSR == 8, "the reduce-scatter below splits exactly eight rows");
+
+template <typename F>
+__device__ __forceinline__ void slot_min8(float (&a)[kSR], int c, int G, F emit)
+{
+    constexpr unsigned kAll = 0xffffffffu;
+    if (G >= 8) {
+        int o = G >> 1;
+        {
+            const bool up = (c & o) != 0;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float send = up ? a[i] : a[i + 4];
+                const float keep = up ? a[i + 4] : a[i];
+                a[i] = fminf(keep, __shfl_xor_sync(kAll, send, o));
+            }
+        }
+        o >>= 1;
+        {
+            const bool up = (c & o) != 0;
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const float send = up ? a[i] : a[i + 2];
+                const float keep = up ? a[i + 2] : a[i];
+                a[i] = fminf(keep, __shfl_xor_sync(kAll, send, o));
+            }
+        }
+        o >>= 1;
+        {
+            const bool up = (c & o) != 0;
+            const float send = up ? a[0] : a[1];
+            const float keep = up ? a[1] : a[0];
+            a[0] = fminf(keep, __shfl_xor_sync(kAll, send, o));
+        }
+        for (o >>= 1; o > 0; o >>= 1) a[0] = fminf(a[0], __shfl_xor_sync(kAll, a[0], o));
+        const int sh = 31 - __clz(G >> 3);  // log2(G / 8)
+        if ((c & ((G >> 3) - 1)) == 0) emit(c >> sh, a[0]);
+    } else {
+        for (int o = G >> 1; o > 0; o >>= 1)
+#pragma unroll
+            for (int k = 0; k < kSR; ++k) a[k] = fminf(a[k], __shfl_xor_sync(kAll, a[k], o));
+#pragma unroll
+        for (int k = 0; k < kSR; ++k)
+            if ((k & (G - 1)) == c) emit(k, a[k]);
+    }
+}
+
 // One Handshake update of edge ed by this CTA (its row slice); the table slice
 // is (or will be) in `tile`, signalled by `bar` completing phase `parity`.
 // `xpar` selects the exchange buffer (alternates between consecutive items).
 // SIGNAL: wait for the expected versions of the inputs (persistent driver).
-// RR: register-resident passes (rr_fits must hold).
-template <bool CLUSTER, bool SIGNAL, bool RR>
+// RM: 0 passes over the shared-memory slice, 1 register-resident passes
+// (rr_fits must hold), 2 register-resident passes for narrow rows (rs_fits).
+template <bool CLUSTER, bool SIGNAL, int RM>
 __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile, const Smem &sm, int rank,
                         int r0, int nr, uint64_t *bar, uint32_t parity, int xpar, Versions ver, Next nx)
 {
@@ -286,13 +358,18 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
     const float4 *t4 = reinterpret_cast<const float4 *>(tile);
     const int lane = tid & 31, warp = tid >> 5, W = T >> 5;
     const float4 inf4 = make_float4(INFINITY, INFINITY, INFINITY, INFINITY);
-    float4 tr[RR ? kRR : 1][RR ? kCR : 1];
+    float4 tr[RM == 1 ? kRR : 1][RM == 1 ? kCR : 1];
+    float4 ts[RM == 2 ? kSR : 1];
+    // narrow-row mapping (RM == 2): slot size, this lane's chunk, its rows
+    const int sg = RM == 2 ? rs_group(Q) : 1;
+    const int sc = lane & (sg - 1);
+    const int sbase = warp * (32 / sg) + lane / sg, sstride = W * (32 / sg);
     // this item's exchange: C CTAs x Q float4 column minima arrive
     if (CLUSTER && tid == 0)
         mbar_arrive_expect_tx(sm.bar + 2 + xpar, static_cast<uint32_t>(C) * static_cast<uint32_t>(Q) * 16u);
     auto load_tile = [&]() {
         if (!mbar_wait(bar, parity, p.spin_limit)) set_err(p.err, ERR_TIMEOUT);
-        if (RR) {
+        if (RM == 1) {
 #pragma unroll
             for (int k = 0; k < kRR; ++k)
 #pragma unroll
@@ -300,6 +377,13 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
                     const int s = warp + W * k, q = lane + 32 * i;
                     tr[k][i] = (s < nr && q < Q) ? t4[static_cast<size_t>(s) * Q + q] : inf4;
                 }
+        }
+        if (RM == 2) {
+#pragma unroll
+            for (int k = 0; k < kSR; ++k) {
+                const int s = sbase + sstride * k;
+                ts[k] = (s < nr && sc < Q) ? t4[static_cast<size_t>(s) * Q + sc] : inf4;
+            }
         }
     };
     // unaries without this edge's messages (written by other SMs: L2 loads).
@@ -380,7 +464,7 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
             const float2 a = df_half(df_add(df_add_f(vref, m), u));
             sm.alpha[s] = df_to_f(df_sub(u, a));
         };
-        if (RR) {
+        if (RM == 1) {
             float acc[kRR];
             float4 wv[kCR];
 #pragma unroll
@@ -394,6 +478,15 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
             const float mk = warp_min_rows5(acc, lane);
             const int s = warp + W * rs_row(lane);  // the five owners emit at once
             if (rs_owner(lane) && s < nr) emit(s, mk);
+        } else if (RM == 2) {
+            const float4 wv = sc < Q ? w[sc] : make_float4(0.f, 0.f, 0.f, 0.f);
+            float acc[kSR];
+#pragma unroll
+            for (int k = 0; k < kSR; ++k) acc[k] = min_add4(INFINITY, ts[k], wv);
+            slot_min8(acc, sc, sg, [&](int k, float m) {
+                const int s = sbase + sstride * k;
+                if (s < nr) emit(s, m);
+            });
         } else {
             for (int base = 0; base < nr; base += ng) {
                 const int s = base + gid;
@@ -417,8 +510,8 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
                 reinterpret_cast<float4 *>(xbuf)[q] = m;
             }
         };
-        const int nsub = RR ? 0 : T / Q;
-        if (RR) {
+        const int nsub = RM ? 0 : T / Q;
+        if (RM == 1) {
             // the warp's rows in registers, then the warps through the tile buffer
             float4 *part2 = reinterpret_cast<float4 *>(const_cast<float *>(tile));
             float4 al[kRR];
@@ -447,6 +540,28 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
                                             __shfl_xor_sync(0xffffffffu, m.z, o), __shfl_xor_sync(0xffffffffu, m.w, o)));
                 if (idx < 4 * Q && part == 0) push(q, m);
             }
+        } else if (RM == 2) {
+            // the thread's rows, the warp's slots (lanes c, c + G, ...), then
+            // the warps through the (by then free) tile buffer
+            float4 *part2 = reinterpret_cast<float4 *>(const_cast<float *>(tile));
+            float4 m = inf4;
+#pragma unroll
+            for (int k = 0; k < kSR; ++k) {
+                const int s = sbase + sstride * k;
+                const float a = s < nr ? sm.alpha[s] : 0.f;
+                m = min4(m, add4(ts[k], make_float4(a, a, a, a)));
+            }
+            for (int o = sg; o < 32; o <<= 1)
+                m = min4(m, make_float4(__shfl_xor_sync(0xffffffffu, m.x, o), __shfl_xor_sync(0xffffffffu, m.y, o),
+                                        __shfl_xor_sync(0xffffffffu, m.z, o), __shfl_xor_sync(0xffffffffu, m.w, o)));
+            const int Qp = part_stride(Q);
+            if (lane < sg && sc < Q) part2[warp * Qp + sc] = m;
+            __syncthreads();
+            for (int q = tid; q < Q; q += T) {
+                float4 mm = part2[q];
+                for (int w2 = 1; w2 < W; ++w2) mm = min4(mm, part2[w2 * Qp + q]);
+                push(q, mm);
+            }
         } else if (nsub >= 1) {
             if (tid < nsub * Q) {
                 const int q = tid % Q, sub = tid / Q;
@@ -464,7 +579,7 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
             }
             __syncthreads();
         }
-        for (int q = tid; q < (RR ? 0 : Q); q += T) {
+        for (int q = tid; q < (RM ? 0 : Q); q += T) {
             float4 m;
             if (nsub >= 1) {
                 m = sm.part[q];
@@ -514,7 +629,7 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
             st_se(agg + ed.au + r0 + s, se_make(c, ver.u + 1u));
             st_se(msg + ed.mu + r0 + s, se_make(df_sub(c, u), ver.e + 1u));
         };
-        if (RR) {
+        if (RM == 1) {
             float acc[kRR];
             float4 bw[kCR];
 #pragma unroll
@@ -528,6 +643,15 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
             const float mk = warp_min_rows5(acc, lane);
             const int s = warp + W * rs_row(lane);  // the five owners emit at once
             if (rs_owner(lane) && s < nr) emit(s, mk);
+        } else if (RM == 2) {
+            const float4 bv = sc < Q ? w[sc] : make_float4(0.f, 0.f, 0.f, 0.f);
+            float acc[kSR];
+#pragma unroll
+            for (int k = 0; k < kSR; ++k) acc[k] = min_add4(INFINITY, ts[k], bv);
+            slot_min8(acc, sc, sg, [&](int k, float m) {
+                const int s = sbase + sstride * k;
+                if (s < nr) emit(s, m);
+            });
         } else {
             for (int base = 0; base < nr; base += ng) {
                 const int s = base + gid;
@@ -541,6 +665,9 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
     __syncthreads();
 }
 
+// RRK: an item whose rows fit takes the register-resident passes for wide rows
+// (models with tables wider than 128 labels); without RRK those for narrow
+// rows.  Any other item takes the shared-memory passes.
 template <bool CLUSTER, bool RRK>
 __global__ void __launch_bounds__(512) hs_looped_kernel(HsParams p)
 {
@@ -564,11 +691,11 @@ __global__ void __launch_bounds__(512) hs_looped_kernel(HsParams p)
     int r0, nr;
     rows_of_R(ed, rank, R, r0, nr);
     if (RRK && rr_fits(nr, ed.ld >> 2, blockDim.x, p.tile_floats))
-        hs_item<CLUSTER, false, RRK>(p, ed, sm.tile, sm, rank, r0, nr, &sm.bar[0], 0u, 0, Versions{0u, 0u, 0u, 0u},
-                                     Next{});
+        hs_item<CLUSTER, false, 1>(p, ed, sm.tile, sm, rank, r0, nr, &sm.bar[0], 0u, 0, Versions{0u, 0u, 0u, 0u}, Next{});
+    else if (!RRK && rs_fits(nr, ed.ld >> 2, blockDim.x, p.tile_floats))
+        hs_item<CLUSTER, false, 2>(p, ed, sm.tile, sm, rank, r0, nr, &sm.bar[0], 0u, 0, Versions{0u, 0u, 0u, 0u}, Next{});
     else
-        hs_item<CLUSTER, false, false>(p, ed, sm.tile, sm, rank, r0, nr, &sm.bar[0], 0u, 0, Versions{0u, 0u, 0u, 0u},
-                                       Next{});
+        hs_item<CLUSTER, false, 0>(p, ed, sm.tile, sm, rank, r0, nr, &sm.bar[0], 0u, 0, Versions{0u, 0u, 0u, 0u}, Next{});
     if (CLUSTER) {  // no CTA leaves while another may still access its shared memory
         cluster_arrive_release();
         cluster_wait_acquire();
@@ -628,12 +755,13 @@ __global__ void __launch_bounds__(512) hs_persistent_kernel(HsParams p)
         const int b = static_cast<int>(k & 1);
         int r0, nr;
         rows_of_R(ed, rank, w.rows, r0, nr);
+        const uint32_t par = static_cast<uint32_t>((k >> 1) & 1);
         if (RRK && rr_fits(nr, ed.ld >> 2, blockDim.x, p.tile_floats))
-            hs_item<CLUSTER, true, RRK>(p, ed, sm.tile + b * p.tile_floats, sm, rank, r0, nr, sm.bar + b,
-                                         static_cast<uint32_t>((k >> 1) & 1), b, ver, nx);
+            hs_item<CLUSTER, true, 1>(p, ed, sm.tile + b * p.tile_floats, sm, rank, r0, nr, sm.bar + b, par, b, ver, nx);
+        else if (!RRK && rs_fits(nr, ed.ld >> 2, blockDim.x, p.tile_floats))
+            hs_item<CLUSTER, true, 2>(p, ed, sm.tile + b * p.tile_floats, sm, rank, r0, nr, sm.bar + b, par, b, ver, nx);
         else
-            hs_item<CLUSTER, true, false>(p, ed, sm.tile + b * p.tile_floats, sm, rank, r0, nr, sm.bar + b,
-                                          static_cast<uint32_t>((k >> 1) & 1), b, ver, nx);
+            hs_item<CLUSTER, true, 0>(p, ed, sm.tile + b * p.tile_floats, sm, rank, r0, nr, sm.bar + b, par, b, ver, nx);
         if (++i == n) {
             i = 0;
             ++it;

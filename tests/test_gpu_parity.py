@@ -430,6 +430,19 @@ def test_invalid_inputs_rejected(what):
     assert ei.value.status == -1
 
 
+@pytest.mark.parametrize("kw", [{"mode": "persistent", "threads": 32}, {"mode": "looped", "threads": 96 + 1},
+                                {"threads": 544}, {"mode": "warp", "threads": 16}, {"cluster": 9},
+                                {"cluster": -1}])
+def test_invalid_options_rejected(kw):
+    """Block sizes the drivers cannot run (a cluster-driver CTA splits its
+    warps between the two node vectors: two warps at least) and cluster sizes
+    outside 1..8 are argument errors, not silent misbehaviour."""
+    m = W.complete(5, 3, seed=0)
+    with pytest.raises(MplppError) as ei:
+        Solver([m], **kw)
+    assert ei.value.status == -1
+
+
 def test_bounded_wait_times_out_without_hanging():
     """A wait that nothing satisfies ends with MPLPP_E_TIMEOUT (bounded spin,
     drain without waiting), and the device stays usable afterwards."""
@@ -530,6 +543,26 @@ def test_register_resident_passes_ragged(cluster, threads, mode):
     _check_D(D[0], sol["bound"])
     _check_labels(m, xs[0], sol, en[0])
     ref = Solver([m], mode="looped", cluster=8, threads=128)  # never register-resident (5 rows x 4 warps < rows)
+    ref.run(T)
+    a, b = s.state_arrays(), ref.state_arrays()
+    assert np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
+
+
+@pytest.mark.parametrize("cluster,threads", [(1, 64), (1, 128), (1, 256), (1, 512), (2, 64), (3, 256)])
+@pytest.mark.parametrize("mode", ["looped", "persistent"])
+def test_narrow_row_passes_ragged(cluster, threads, mode):
+    """Rows of 1..128 labels (1..32 float4 chunks, slots of 1, 2, 4, 8, 16 and
+    32 lanes): a CTA slice with at most 8 rows per lane slot takes the
+    register-resident passes for narrow rows, the others the shared-memory
+    passes, in the same solve; both must match the oracle, and the warp
+    driver (its own code, no such passes) bit for bit."""
+    m = W.uneven_complete(9, 1, 128, seed=7 * cluster + threads)
+    T = 8
+    sol = oracle.solve(m, _order(m), T)
+    s, D, xs, en = _solve_gpu([m], T, mode=mode, cluster=cluster, threads=threads)
+    _check_D(D[0], sol["bound"])
+    _check_labels(m, xs[0], sol, en[0])
+    ref = Solver([m], mode="warp")
     ref.run(T)
     a, b = s.state_arrays(), ref.state_arrays()
     assert np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
