@@ -496,7 +496,12 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
             }
         }
     }
-    __syncthreads();
+    // The register-resident passes read in pass 2 only the alpha of their own
+    // warp's rows, which pass 1 emitted from that warp.
+    if (RM)
+        __syncwarp();
+    else
+        __syncthreads();
 
     // pass 2 (this CTA's rows): pm(t) = min_s [theta(s,t) + alpha(s)], stored
     // into slot `rank` of the pm buffer of every CTA of the cluster
@@ -557,7 +562,8 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
             const int Qp = part_stride(Q);
             if (lane < sg && sc < Q) part2[warp * Qp + sc] = m;
             __syncthreads();
-            for (int q = tid; q < Q; q += T) {
+            // one CTA per edge: the combine below reads the warps' partials
+            for (int q = tid; q < (CLUSTER ? Q : 0); q += T) {
                 float4 mm = part2[q];
                 for (int w2 = 1; w2 < W; ++w2) mm = min4(mm, part2[w2 * Qp + q]);
                 push(q, mm);
@@ -596,11 +602,19 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
     //   b(t) = min_s [...] + vh(t),  beta(t) = vh(t) - b(t)
     if (CLUSTER) {
         if (!mbar_wait_cluster(xbar, parity, p.spin_limit)) set_err(p.err, ERR_TIMEOUT);
-    } else {
+    } else if (RM != 2) {
         __syncthreads();
     }
     for (int t = tid; t < ld; t += T) {
-        float m = xbuf[t];
+        float m;
+        if (!CLUSTER && RM == 2) {  // the minimum over the warps' partial column minima
+            const float *pf = tile;
+            const int wst = 4 * part_stride(Q);
+            m = pf[t];
+            for (int w2 = 1; w2 < W; ++w2) m = fminf(m, pf[w2 * wst + t]);
+        } else {
+            m = xbuf[t];
+        }
         if (CLUSTER) {
             int r = 1;
             for (; r + 1 < C; r += 2) m = min3f(m, xbuf[r * ld + t], xbuf[(r + 1) * ld + t]);
