@@ -59,7 +59,8 @@ namespace {
 struct Smem {
     WorkItem *wi;       // [2] the current and the next work item (persistent driver)
     float *tile;        // nbuf buffers of tile_floats each
-    float2 *uh, *vh;    // double-float unaries without this edge's messages
+    float2 *uh, *vh;    // double-float unaries without this edge's messages (uh: nbuf
+                        // buffers, by item parity)
     float *w1;          // vh(t) - vh(0) in FP32 (pass 1)
     float *alpha, *beta, *pm;
     float4 *part;
@@ -71,7 +72,7 @@ __device__ __forceinline__ Smem carve(char *base, const HsParams &p, int nbuf)
     Smem s;
     s.wi = reinterpret_cast<WorkItem *>(base);
     float2 *d = reinterpret_cast<float2 *>(base + 2 * sizeof(WorkItem));
-    s.uh = d; d += p.rmax;
+    s.uh = d; d += static_cast<size_t>(nbuf) * p.rmax;
     s.vh = d; d += p.ldmax;
     float *f = reinterpret_cast<float *>(d);
     s.tile = f;
@@ -349,6 +350,7 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
     const int T = blockDim.x, tid = threadIdx.x;
     const int C = CLUSTER ? p.C : 1;
     const int ld = ed.ld, Q = ld >> 2, Lv = ed.Lv;
+    float2 *const uh = sm.uh + static_cast<size_t>(xpar) * p.rmax;  // pass 3 of the previous item may still read the other
     ulonglong2 *agg = p.agg;
     ulonglong2 *msg = p.msg;
 
@@ -403,7 +405,7 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
         const ulonglong2 *M = vside ? msg + ed.mv : msg + ed.mu + r0;
         const int n = vside ? Lv : nr;
         const unsigned va = vside ? ver.v : ver.u + ver.bump;
-        float2 *dst = vside ? sm.vh : sm.uh;
+        float2 *dst = vside ? sm.vh : uh;
         ulonglong2 x = make_ulonglong2(0ull, 0ull), y = x;
         if (i0 < n) {
             x = ld_se(A + i0);
@@ -427,7 +429,7 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
     } else {
         for (int s = tid; s < nr; s += T)
             poll_diff<false>(p, agg + ed.au + r0, msg + ed.mu + r0, s, 0u, 0u, ld_se(agg + ed.au + r0 + s),
-                             ld_se(msg + ed.mu + r0 + s), [&](int j, float2 d) { sm.uh[j] = d; });
+                             ld_se(msg + ed.mu + r0 + s), [&](int j, float2 d) { uh[j] = d; });
         for (int t = tid; t < ld; t += T) {
             if (t < Lv)
                 poll_diff<false>(p, agg + ed.av, msg + ed.mv, t, 0u, 0u, ld_se(agg + ed.av + t), ld_se(msg + ed.mv + t),
@@ -460,7 +462,7 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
         const float4 *w = reinterpret_cast<const float4 *>(sm.w1);
         const float2 vref = sm.vh[0];
         auto emit = [&](int s, float m) {
-            const float2 u = sm.uh[s];
+            const float2 u = uh[s];
             const float2 a = df_half(df_add(df_add_f(vref, m), u));
             sm.alpha[s] = df_to_f(df_sub(u, a));
         };
@@ -638,7 +640,7 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
     {
         const float4 *w = reinterpret_cast<const float4 *>(sm.beta);
         auto emit = [&](int s, float m) {
-            const float2 u = sm.uh[s];
+            const float2 u = uh[s];
             const float2 c = df_add_f(u, m);
             st_se(agg + ed.au + r0 + s, se_make(c, ver.u + 1u));
             st_se(msg + ed.mu + r0 + s, se_make(df_sub(c, u), ver.e + 1u));
@@ -675,15 +677,16 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
             }
         }
     }
-    // the next item overwrites uh, vh, alpha and beta
-    __syncthreads();
+    // No barrier before the next item: up to its first block-wide barrier it
+    // writes only vh, w1 and the other parity's uh, record and table buffer,
+    // none of which pass 3 reads.
 }
 
 // RRK: an item whose rows fit takes the register-resident passes for wide rows
 // (models with tables wider than 128 labels); without RRK those for narrow
 // rows.  Any other item takes the shared-memory passes.
 template <bool CLUSTER, bool RRK>
-__global__ void __launch_bounds__(512) hs_looped_kernel(HsParams p)
+__global__ void __launch_bounds__(512, CLUSTER || RRK ? 1 : 2) hs_looped_kernel(HsParams p)
 {
     extern __shared__ __align__(16) char smem_raw[];
     Smem sm = carve(smem_raw, p, 1);
@@ -822,9 +825,9 @@ cudaError_t launch(K kernel, const HsParams &p, int grid, int threads, size_t sm
 
 size_t hs_smem_bytes(int nbuf, int tile_floats, int rmax, int ldmax, int threads, int C)
 {
-    // 2 work records; double-float uh, vh; FP32 tiles, w1, alpha, beta, pm (nbuf x C slots), part (float4 x T);
+    // 2 work records; double-float uh (nbuf), vh; FP32 tiles, w1, alpha, beta, pm (nbuf x C slots), part (float4 x T);
     // 4 mbarriers
-    const size_t d = static_cast<size_t>(rmax) + static_cast<size_t>(ldmax);
+    const size_t d = static_cast<size_t>(nbuf) * rmax + static_cast<size_t>(ldmax);
     const size_t f = static_cast<size_t>(nbuf) * tile_floats + static_cast<size_t>(rmax) +
                      (2 + static_cast<size_t>(nbuf) * C) * static_cast<size_t>(ldmax) + 4 * static_cast<size_t>(threads);
     return 2 * sizeof(WorkItem) + d * 8 + f * 4 + 32;
