@@ -217,36 +217,27 @@ __device__ __forceinline__ bool rr_fits(int nr, int Q, int T, int tile_floats)
     return Q > 32 && Q <= 32 * kCR && nr <= kRR * (T >> 5) && (T >> 5) * part_stride(Q) * 4 <= tile_floats;
 }
 
-// Minimum over the warp of each of the kRR = 5 row values, reduce-scatter
-// style (each exchange step halves the rows a lane keeps): 8 shuffles instead
-// of 25.  The result is the minimum of row rs_row(lane); lanes 0, 8, 4, 16
-// and 24 own rows 0..4 (rs_owner).
-static_assert(kRR == 5, "the reduce-scatter below splits exactly five rows");
+// Minimum over the warp of each of the kRR = 5 row values (five independent
+// warp reductions in hardware; min.f32 semantics, as fminf).  The result is
+// the minimum of row rs_row(lane); lanes 0, 8, 4, 16 and 24 own rows 0..4
+// (rs_owner).
+static_assert(kRR == 5, "five rows per warp");
+
+__device__ __forceinline__ float warp_min_f32(float v)
+{
+    float r;
+    asm volatile("redux.sync.min.f32 %0, %1, 0xffffffff;" : "=f"(r) : "f"(v));
+    return r;
+}
+
+__device__ __forceinline__ int rs_row(int lane);
 
 __device__ __forceinline__ float warp_min_rows5(const float (&a)[kRR], int lane)
 {
-    constexpr unsigned kAll = 0xffffffffu;
-    const bool up = lane & 16, b3 = lane & 8, b2 = lane & 4;
-    // xor 16: lanes < 16 keep rows 0, 1, 2; lanes >= 16 keep rows 3, 4
-    const float r0 = __shfl_xor_sync(kAll, up ? a[0] : a[3], 16);
-    const float r1 = __shfl_xor_sync(kAll, up ? a[1] : a[4], 16);
-    const float r2 = __shfl_xor_sync(kAll, a[2], 16);
-    const float b0 = fminf(up ? a[3] : a[0], r0);
-    const float b1 = fminf(up ? a[4] : a[1], r1);
-    const float c2 = fminf(a[2], r2);
-    // xor 8: lower lanes with bit 3 clear keep rows 0 and 2, with bit 3 set
-    // row 1; upper lanes keep row 3 (bit 3 clear) or row 4
-    const float t0 = __shfl_xor_sync(kAll, b3 ? b0 : b1, 8);
-    const float t1 = __shfl_xor_sync(kAll, c2, 8);
-    const float c0 = fminf(b3 ? b1 : b0, t0);
-    const float c1 = fminf(c2, t1);
-    // xor 4: the lanes holding rows 0 and 2 split them (bit 2); then 2, 1
-    const bool two = !up && !b3;
-    const float own = (two && b2) ? c1 : c0;
-    const float snd = two ? (b2 ? c0 : c1) : c0;
-    float d = fminf(own, __shfl_xor_sync(kAll, snd, 4));
-    d = fminf(d, __shfl_xor_sync(kAll, d, 2));
-    return fminf(d, __shfl_xor_sync(kAll, d, 1));
+    const float m0 = warp_min_f32(a[0]), m1 = warp_min_f32(a[1]), m2 = warp_min_f32(a[2]);
+    const float m3 = warp_min_f32(a[3]), m4 = warp_min_f32(a[4]);
+    const int k = rs_row(lane);
+    return k == 0 ? m0 : (k == 1 ? m1 : (k == 2 ? m2 : (k == 3 ? m3 : m4)));
 }
 
 __device__ __forceinline__ int rs_row(int lane)
