@@ -252,6 +252,44 @@ def batched_vs_looped(Solver, stream, args):
             "autotune": tune.get("best") if tune else None, "persistent_drivers": persistent}
 
 
+def rules_comparison(Solver, stream, args):
+    """The dense pose model and the semi-dense kNN model under the Handshake
+    (H), MPLP (M) and uniform (U) updates (Sec. 4, eqs. (H), (M), (U)) from
+    phi = 0 with the same schedule: the bound after one iteration (Thm. 2:
+    H >= M >= U) and after 50, and the device time of the 50-iteration run
+    (H: the autotuned mapping; M, U: one CTA per edge, one launch per
+    matching)."""
+    T = 50
+    res = {}
+    for cfg, name in ((2, "pose_K60_L300"), (3, "knn_n2000_k50_L64")):
+        models, _ = models_for(cfg, seed=0)
+        out = {"iterations": T}
+        for rule in ("H", "M", "U"):
+            s = Solver(models, rule=rule)
+            if rule == "H" and args.autotune > 0:
+                s.autotune(2)
+            s.reset()
+            s.run(1)
+            d1 = float(s.bound(exact=True).sum())
+
+            def run(sol=s):
+                sol.reset()
+                sol.run(T)
+            run()
+            ms, _ = _timed(stream, run, 2)
+            inf = s.info()
+            out[rule] = {"ms": ms, "edge_updates_per_s": T * inf["edges"] / (ms / 1e3),
+                         "bound_1": d1, "bound": float(s.bound(exact=True).sum()),
+                         "mode": inf["mode"], "threads": inf["threads"]}
+            s.close()
+        tol = 1e-6 * max(1.0, abs(out["H"]["bound_1"]))
+        out["one_iteration_H_ge_M_ge_U"] = bool(out["H"]["bound_1"] >= out["M"]["bound_1"] - tol
+                                                and out["M"]["bound_1"] >= out["U"]["bound_1"] - tol)
+        out["highest_bound"] = max("HMU", key=lambda r: out[r]["bound"])
+        res[name] = out
+    return res
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -276,9 +314,9 @@ def run_ours(args):
         log("timing the oracle on the host ...")
         _, cpu = cpu_oracle_rate(models, T, args.cpu_budget)
     stream = torch.cuda.current_stream()
-    s = Solver(models, mode=args.mode)
+    s = Solver(models, mode=args.mode, cluster=args.cluster, threads=args.threads)
     tune = None
-    if args.autotune > 0 and args.mode == "auto":
+    if args.autotune > 0 and args.mode == "auto" and not (args.cluster or args.threads):
         tune = s.autotune(args.autotune)
         log("autotune:", tune.get("best"))
     info = s.info()
@@ -350,6 +388,11 @@ def run_ours(args):
     if args.batched and cfg != 4:
         batched = batched_vs_looped(Solver, stream, args)
 
+    # the M and U updates beside H (equal iterations)
+    rules = None
+    if args.rules and rank == 0:
+        rules = rules_comparison(Solver, stream, args)
+
     # end to end through the public API with host buffers (pinned)
     e2e = None
     if not args.no_e2e:
@@ -402,6 +445,7 @@ def run_ours(args):
                      "algorithmic_bytes_per_launch": T * bytes_iter, "launch_ms": kms},
         "looped": looped,
         "batched": batched,
+        "rules": rules,
         "e2e": e2e,
         "cpu_baseline": cpu,
         "clocks": ck,
@@ -423,10 +467,13 @@ def main():
     ap.add_argument("--config", type=int, default=2, choices=sorted(CONFIGS))
     ap.add_argument("--iters", type=int, default=0, help="override the iteration count")
     ap.add_argument("--mode", default="auto", choices=["auto", "looped", "persistent"])
+    ap.add_argument("--cluster", type=int, default=0, help="CTAs per edge (0: chosen; set: no autotuning)")
+    ap.add_argument("--threads", type=int, default=0, help="threads per CTA (0: chosen; set: no autotuning)")
     ap.add_argument("--no-looped", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--batched", type=int, default=1, help="also time the 256-model batch against per-model loops")
+    ap.add_argument("--rules", type=int, default=1, help="also run the M and U updates beside H (pose and kNN)")
     ap.add_argument("--autotune", type=int, default=3, help="iterations per candidate of the mapping autotuner (0: off)")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-iters", type=int, default=1)

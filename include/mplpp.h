@@ -68,7 +68,21 @@ enum {
                                   the device (a reader polls until the count it needs)        */
     MPLPP_MODE_WARP = 3        /* as PERSISTENT with one warp per edge instead of a cluster of
                                   CTAs per edge (for many small tables: every label count
-                                  <= 256); options.cluster is ignored                          */
+                                  <= 128); options.cluster is ignored                          */
+};
+
+/* Which block-coordinate-ascent update mplpp_run applies to each edge (Sec. 4;
+ * g = theta_uv + theta_u + theta_v of the current reparametrization).  H is
+ * the solver's purpose; M and U are there for the paper's comparison (Prop. 2:
+ * after one update of the same edge D_H >= D_M >= D_U; Thm. 2: the same for
+ * one iteration from equal states).  M and U run in the looped driver only
+ * (MPLPP_MODE_AUTO or _LOOPED; persistent or warp mode: MPLPP_E_UNSUPPORTED),
+ * one CTA per edge, and have no backward (record_every must be 0). */
+enum {
+    MPLPP_RULE_H = 0, /* eq. (H), the Handshake (MPLP++) update: three minimizations     */
+    MPLPP_RULE_M = 1, /* eq. (M), the MPLP update: theta_u := 1/2 min_t g(.,t),
+                         theta_v := 1/2 min_s g(s,.)                                     */
+    MPLPP_RULE_U = 2  /* eq. (U), the uniform update: theta_u := theta_v := 1/2 min g    */
 };
 
 typedef struct {
@@ -100,7 +114,7 @@ typedef struct {
                                  first edge of the first worker waits for one node update more
                                  than will ever happen, so the bounded wait must run out and the
                                  run must end with MPLPP_E_TIMEOUT instead of hanging            */
-    int32_t reserved;         /* 0 */
+    int32_t rule;             /* MPLPP_RULE_* (0 = the Handshake update)                        */
     int64_t spin_limit;       /* polls before a device-side wait gives up with MPLPP_E_TIMEOUT */
 } mplpp_options;
 

@@ -23,6 +23,7 @@ STATUS = {0: "MPLPP_OK", -1: "MPLPP_E_INVALID", -2: "MPLPP_E_NOMEM", -3: "MPLPP_
 SCHED = {"round_robin": 0, "greedy_color": 1, "alg1": 2, "user": 3}
 MODE = {"auto": 0, "looped": 1, "persistent": 2, "warp": 3}
 MODE_NAME = {v: k for k, v in MODE.items()}
+RULE = {"H": 0, "M": 1, "U": 2}  # Sec. 4: eqs. (H), (M), (U)
 
 # Every symbol include/mplpp.h declares.
 EXPORTS = ["mplpp_options_default", "mplpp_schedule", "mplpp_create", "mplpp_run", "mplpp_bound",
@@ -40,7 +41,7 @@ class MplppModel(ctypes.Structure):
 
 class MplppOptions(ctypes.Structure):
     _fields_ = [("mode", c_i32), ("use_graph", c_i32), ("inputs_on_device", c_i32), ("record_every", c_i32),
-                ("cluster", c_i32), ("threads", c_i32), ("test_unreachable_wait", c_i32), ("reserved", c_i32),
+                ("cluster", c_i32), ("threads", c_i32), ("test_unreachable_wait", c_i32), ("rule", c_i32),
                 ("spin_limit", c_i64)]
 
 

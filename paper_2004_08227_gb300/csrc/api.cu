@@ -280,10 +280,32 @@ static mplpp_status apply_warp_mapping(mplpp_solver *s, int T, int optin)
 // Makes (C, T, mode) the solver's mapping: sizes, kernel attributes, and for
 // the persistent driver the per-cluster work lists (uploaded to the device).
 // want: MPLPP_MODE_AUTO (persistent if possible), _LOOPED or _PERSISTENT.
+static_assert(kRuleH == MPLPP_RULE_H && kRuleM == MPLPP_RULE_M && kRuleU == MPLPP_RULE_U, "rule ids");
+
+// The M and U updates: one CTA of 256 threads per edge, looped driver only;
+// the node vectors of the largest edge must fit shared memory.
+static mplpp_status apply_rule_mapping(mplpp_solver *s, int optin)
+{
+    mapping_for(s, 1, 256);  // sizes of the other drivers stay consistent
+    int lumax = 1;
+    for (auto &ed : s->h_edges) lumax = std::max(lumax, ed.Lu);
+    s->smem_rule = rule_smem_bytes(lumax, s->ldmax);
+    if (s->smem_rule > static_cast<size_t>(optin))
+        return fail(s, MPLPP_E_UNSUPPORTED,
+                    "the node vectors of the largest edge need " + std::to_string(s->smem_rule) +
+                        " B of shared memory (limit " + std::to_string(optin) + ")");
+    cudaError_t ce = rule_prepare(s->smem_rule);
+    if (ce != cudaSuccess) return cuda_fail(s, ce, "kernel attributes");
+    s->mode = MPLPP_MODE_LOOPED;
+    drop_graphs(s);
+    return MPLPP_OK;
+}
+
 static mplpp_status apply_mapping(mplpp_solver *s, int C, int T, int want)
 {
     int optin = 0;
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->device);
+    if (s->opt.rule != kRuleH) return apply_rule_mapping(s, optin);
     if (want == MPLPP_MODE_WARP) return apply_warp_mapping(s, T, optin);
     mapping_for(s, C, T);
     if (s->smem_looped > static_cast<size_t>(optin))
@@ -330,6 +352,11 @@ extern "C" mplpp_status mplpp_create(const mplpp_model *models, int32_t n_models
         const mplpp_options &o = s->opt;
         if (o.mode < MPLPP_MODE_AUTO || o.mode > MPLPP_MODE_WARP) return fail(nullptr, MPLPP_E_INVALID, "unknown mode");
         if (o.cluster < 0 || o.cluster > 8) return fail(nullptr, MPLPP_E_INVALID, "cluster must be 0 or 1..8");
+        if (o.rule < MPLPP_RULE_H || o.rule > MPLPP_RULE_U) return fail(nullptr, MPLPP_E_INVALID, "unknown rule");
+        if (o.rule != MPLPP_RULE_H && o.record_every > 0)
+            return fail(nullptr, MPLPP_E_INVALID, "backward is defined for the Handshake update only");
+        if (o.rule != MPLPP_RULE_H && (o.mode == MPLPP_MODE_PERSISTENT || o.mode == MPLPP_MODE_WARP))
+            return fail(nullptr, MPLPP_E_UNSUPPORTED, "the M and U updates run in the looped driver only");
         // a CTA of the cluster drivers splits its warps between the two node
         // vectors, so it needs two warps at least
         const int tmin = o.mode == MPLPP_MODE_WARP ? 32 : 64;
@@ -580,6 +607,15 @@ static HsParams make_params(mplpp_solver *s)
 // One iteration of looped launches (one per matching) on stream st.
 cudaError_t enqueue_looped_iteration(mplpp_solver *s, cudaStream_t st)
 {
+    if (s->opt.rule != kRuleH) {
+        RuleParams rp = {s->d_edges, nullptr, s->d_tab, s->d_agg, s->d_msg};
+        for (int ph = 0; ph + 1 < static_cast<int>(s->phase_off.size()); ++ph) {
+            rp.items = s->d_phase_edges + s->phase_off[ph];
+            cudaError_t e = launch_rule(rp, s->opt.rule, s->phase_off[ph + 1] - s->phase_off[ph], s->smem_rule, st);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
     HsParams p = make_params(s);
     for (int ph = 0; ph + 1 < static_cast<int>(s->phase_off.size()); ++ph) {
         p.items = s->d_phase_edges + s->phase_off[ph];
@@ -872,6 +908,13 @@ extern "C" mplpp_status mplpp_autotune(mplpp_solver *s, int32_t iterations, char
     s->err.clear();
     if (report && report_size) report[0] = 0;
     if (s->EE == 0) return MPLPP_OK;
+    if (s->opt.rule != kRuleH) {  // the M and U updates have one mapping
+        if (report && report_size)
+            std::snprintf(report, report_size,
+                          "{\"best\": {\"cluster\": 1, \"threads\": 256, \"mode\": \"looped\", \"ms\": 0}, "
+                          "\"candidates\": []}");
+        return MPLPP_OK;
+    }
     if (!s->d_save_agg) {
         CK(s, s->alloc(&s->d_save_agg, s->aggN));
         CK(s, s->alloc(&s->d_save_msg, s->msgN));

@@ -59,6 +59,20 @@ cudaError_t hs_launch_persistent(const HsParams &p, int clusters, int threads, s
 int hs_max_active_clusters(int C, int threads, size_t smem, bool rr);
 bool hs_rr_fits(int nr_max, int Q_max, int threads, int tile_floats);
 
+// rules.cu: the MPLP (eq. (M)) and uniform (eq. (U)) updates of Sec. 4, one
+// CTA per edge, one launch per matching.
+constexpr int kRuleH = 0, kRuleM = 1, kRuleU = 2;  // the MPLPP_RULE_* values
+struct RuleParams {
+    const EdgeDesc *edges;
+    const int *items;  // edge ids of the matching being launched
+    const float *tab;
+    ulonglong2 *agg;
+    ulonglong2 *msg;
+};
+size_t rule_smem_bytes(int lumax, int ldmax);  // lumax >= every L_u, ldmax >= every row stride
+cudaError_t rule_prepare(size_t smem_bytes);
+cudaError_t launch_rule(const RuleParams &p, int rule, int n_items, size_t smem, cudaStream_t st);
+
 // dual.cu
 cudaError_t launch_pack(const EdgeDesc *edges, int n_edges, const NodeDesc *nodes, int n_nodes,
                         const float *unary_src, const float *pair_src, float *tab, float *un0, ulonglong2 *agg,

@@ -55,6 +55,7 @@ struct mplpp_solver {
     size_t smem_looped = 0, smem_persist = 0;
     int warp_blocks = 0, lw = 0, cap = 0;  // warp driver: blocks, per-warp vector and buffer capacity
     size_t smem_warp = 0;
+    size_t smem_rule = 0;  // M and U updates (rules.cu)
 
     // device
     std::vector<void *> allocations;

@@ -71,11 +71,14 @@ class Solver:
     ``device_inputs=True`` the unary / pairwise attributes are float32 CUDA
     tensors; otherwise host arrays (numpy or pinned torch tensors).
     ``user_schedules`` optionally gives ``(matching_off, edge_order)`` per model.
+    ``rule`` is the update applied to each edge (Sec. 4): "H" (Handshake, the
+    default), or "M" / "U" (MPLP and uniform updates, for comparison; looped
+    driver only, no backward).
     """
 
     def __init__(self, models, *, mode: str = "auto", use_graph: bool = True, record_every: int = 0,
                  cluster: int = 0, threads: int = 0, spin_limit: int = 1 << 22, device_inputs: bool = False,
-                 user_schedules=None, stream=None, test_unreachable_wait: bool = False):
+                 user_schedules=None, stream=None, test_unreachable_wait: bool = False, rule: str = "H"):
         self._lib = _lib.load()
         self._h = ctypes.c_void_p(0)
         models = list(models)
@@ -118,6 +121,8 @@ class Solver:
         opt.threads = int(threads)
         opt.spin_limit = int(spin_limit)
         opt.test_unreachable_wait = int(bool(test_unreachable_wait))
+        opt.rule = _lib.RULE[rule]
+        self.rule = rule
         self.device_inputs = bool(device_inputs)
         self._stream = _current_stream() if stream is None else ctypes.c_void_p(stream)
         st = self._lib.mplpp_create(arr, self.n_models, ctypes.byref(opt), self._stream, ctypes.byref(self._h))
