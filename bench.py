@@ -290,6 +290,52 @@ def rules_comparison(Solver, stream, args):
     return res
 
 
+def _time_run(Solver, stream, models, T, args):
+    s = Solver(models)
+    if args.autotune > 0:
+        s.autotune(2)
+
+    def run():
+        s.reset()
+        s.run(T)
+    run()
+    ms, _ = _timed(stream, run, 2)
+    inf = s.info()
+    s.close()
+    return ms, inf
+
+
+def sparsity_study(Solver, stream, args, peak):
+    """The Handshake solver on the pose model with edges removed at random
+    (the paper's density study, Sec. 7; greedy edge colouring): per density,
+    edge updates/s and algorithmic GB/s of the run (autotuned mapping)."""
+    from paper_2004_08227_gb300 import workloads as W
+    T = 100
+    rows = []
+    for keep in (1.0, 0.4, 0.1, 0.05, 0.01):
+        ms, inf = _time_run(Solver, stream, [W.pose_sparse(keep, 60, 300, seed=0)], T, args)
+        gbs = T * inf["bytes_per_iteration"] / (ms / 1e3) / 1e9
+        rows.append({"keep": keep, "edges": inf["edges"], "matchings": inf["phases"], "ms": ms,
+                     "edge_updates_per_s": T * inf["edges"] / (ms / 1e3), "gbs": gbs, "frac_of_peak": gbs / peak,
+                     "mapping": {k: inf[k] for k in ("mode", "cluster", "threads", "grid")}})
+    return {"workload": "pose_K60_L300, every edge kept with probability keep", "iterations": T, "rows": rows}
+
+
+def pose_dense_study(Solver, stream, args):
+    """The shape of the paper's pose dataset: fully connected, L = 13, n in the
+    hundreds to thousands (round robin: n - 1 matchings of n / 2 edges)."""
+    from paper_2004_08227_gb300 import workloads as W
+    T = 20
+    rows = []
+    for n in (600, 1200):
+        ms, inf = _time_run(Solver, stream, [W.pose_dense(n, 13, seed=0)], T, args)
+        rows.append({"n": n, "edges": inf["edges"], "matchings": inf["phases"], "ms": ms,
+                     "edge_updates_per_s": T * inf["edges"] / (ms / 1e3),
+                     "gbs": T * inf["bytes_per_iteration"] / (ms / 1e3) / 1e9,
+                     "mapping": {k: inf[k] for k in ("mode", "cluster", "threads", "grid")}})
+    return {"workload": "pose_dense_Kn_L13", "iterations": T, "rows": rows}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -393,6 +439,12 @@ def run_ours(args):
     if args.rules and rank == 0:
         rules = rules_comparison(Solver, stream, args)
 
+    # the pose model sparsified, and the pose dataset's dense small-L shape
+    sparsity = dense13 = None
+    if args.studies and rank == 0:
+        sparsity = sparsity_study(Solver, stream, args, peak)
+        dense13 = pose_dense_study(Solver, stream, args)
+
     # end to end through the public API with host buffers (pinned)
     e2e = None
     if not args.no_e2e:
@@ -446,6 +498,8 @@ def run_ours(args):
         "looped": looped,
         "batched": batched,
         "rules": rules,
+        "sparsity": sparsity,
+        "pose_dense_L13": dense13,
         "e2e": e2e,
         "cpu_baseline": cpu,
         "clocks": ck,
@@ -473,6 +527,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--batched", type=int, default=1, help="also time the 256-model batch against per-model loops")
+    ap.add_argument("--studies", type=int, default=1, help="also run the sparsified pose and dense L=13 workloads")
     ap.add_argument("--rules", type=int, default=1, help="also run the M and U updates beside H (pose and kNN)")
     ap.add_argument("--autotune", type=int, default=3, help="iterations per candidate of the mapping autotuner (0: off)")
     ap.add_argument("--cpu-budget", type=float, default=15.0)

@@ -103,6 +103,49 @@ def pose_like(n: int = 60, L: int = 300, seed: int = 0, sigma: float = 0.05) -> 
                  name=f"pose_K{n}_L{L}_s{seed}")
 
 
+def _pose_tables(pts: np.ndarray, eu: np.ndarray, ev: np.ndarray, Duv: np.ndarray, sigma: float,
+                 block: int = 4096) -> np.ndarray:
+    """Truncated quadratic distance-consistency tables of the given edges,
+    min(((|p_us - p_vt| - D_uv) / sigma)^2, 1), row-major, in blocks of edges."""
+    L = pts.shape[1]
+    out = np.empty(eu.shape[0] * L * L, np.float32)
+    for s in range(0, eu.shape[0], block):
+        e = slice(s, min(s + block, eu.shape[0]))
+        d = np.linalg.norm(pts[eu[e]][:, :, None, :] - pts[ev[e]][:, None, :, :], axis=3)
+        c = np.minimum(((d - Duv[e, None, None]) / sigma) ** 2, 1.0)
+        out[s * L * L:e.stop * L * L] = c.ravel()
+    return out
+
+
+def pose_sparse(keep: float, n: int = 60, L: int = 300, seed: int = 0, sigma: float = 0.05) -> Model:
+    """The pose-shaped model with every edge kept with probability `keep`
+    (random sparsification, as in the paper's density study, Sec. 7), scheduled
+    by greedy edge colouring.  Points, distances and unaries are drawn as in
+    pose_like, so a kept edge has the table it has in the complete model."""
+    rng = np.random.default_rng(seed)
+    eu, ev = _complete_edges(n)
+    labels = np.full(n, L, np.int32)
+    unary = rng.random(n * L).astype(np.float32)
+    pts = rng.random((n, L, 3))
+    Duv = rng.uniform(0.1, 1.0, size=eu.shape[0])
+    kept = np.random.default_rng(seed + 7919).random(eu.shape[0]) < keep
+    if not kept.any():
+        kept[0] = True
+    eu, ev, Duv = eu[kept], ev[kept], Duv[kept]
+    return Model(labels, eu.astype(np.int32), ev.astype(np.int32), unary, _pose_tables(pts, eu, ev, Duv, sigma),
+                 schedule="greedy_color", name=f"pose_K{n}_L{L}_keep{keep:g}_s{seed}")
+
+
+def pose_dense(n: int, L: int = 13, seed: int = 0, sigma: float = 0.05) -> Model:
+    """The shape of the paper's pose dataset (Sec. 7: fully connected, a few
+    hundred to a few thousand nodes, 13 labels): huge edge counts with tiny
+    tables; round-robin schedule (n - 1 matchings of n / 2 edges)."""
+    m = pose_sparse(1.0, n, L, seed, sigma)
+    m.schedule = "round_robin"
+    m.name = f"pose_dense_K{n}_L{L}_s{seed}"
+    return m
+
+
 def knn(n: int = 2000, k: int = 50, L: int = 64, seed: int = 0) -> Model:
     """Semi-dense model: n random points in [0,1]^3, each linked to its k
     nearest neighbours (symmetrised by union); pairwise N(0,1)."""
