@@ -336,6 +336,35 @@ def pose_dense_study(Solver, stream, args):
     return {"workload": "pose_dense_Kn_L13", "iterations": T, "rows": rows}
 
 
+def structured_study(Solver, stream, args):
+    """Stereo-like grids with truncated-linear and Potts costs: the structured
+    Handshake path (O(L) minimizations, no table reads) against the dense
+    drivers on the same costs given as tables (autotuned), equal iterations."""
+    from paper_2004_08227_gb300 import workloads as W
+    T = 50
+    rows = []
+    for name, kw in (("truncated_linear_tau4", dict(weight=1.0, tau=4.0)), ("potts", dict(weight=1.0, tau=1.0))):
+        m = W.grid_trunc_linear(128, 128, 64, seed=0, **kw)
+        row = {"costs": name}
+        for key, structured in (("structured", True), ("dense", False)):
+            s = Solver([m], structured=structured)
+            if args.autotune > 0:
+                s.autotune(2)
+
+            def run(sol=s):
+                sol.reset()
+                sol.run(T)
+            run()
+            ms, _ = _timed(stream, run, 2)
+            inf = s.info()
+            row[key] = {"ms": ms, "edge_updates_per_s": T * inf["edges"] / (ms / 1e3),
+                        "bound": float(s.bound(exact=True)[0]), "mode": inf["mode"]}
+            s.close()
+        row["speedup"] = row["dense"]["ms"] / row["structured"]["ms"]
+        rows.append(row)
+    return {"workload": "grid128x128_L64", "edges": int(m.E), "iterations": T, "rows": rows}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -440,10 +469,11 @@ def run_ours(args):
         rules = rules_comparison(Solver, stream, args)
 
     # the pose model sparsified, and the pose dataset's dense small-L shape
-    sparsity = dense13 = None
+    sparsity = dense13 = structured = None
     if args.studies and rank == 0:
         sparsity = sparsity_study(Solver, stream, args, peak)
         dense13 = pose_dense_study(Solver, stream, args)
+        structured = structured_study(Solver, stream, args)
 
     # end to end through the public API with host buffers (pinned)
     e2e = None
@@ -500,6 +530,7 @@ def run_ours(args):
         "rules": rules,
         "sparsity": sparsity,
         "pose_dense_L13": dense13,
+        "structured": structured,
         "e2e": e2e,
         "cpu_baseline": cpu,
         "clocks": ck,
@@ -527,7 +558,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--batched", type=int, default=1, help="also time the 256-model batch against per-model loops")
-    ap.add_argument("--studies", type=int, default=1, help="also run the sparsified pose and dense L=13 workloads")
+    ap.add_argument("--studies", type=int, default=1, help="also run the sparsified pose, dense L=13 and structured-cost workloads")
     ap.add_argument("--rules", type=int, default=1, help="also run the M and U updates beside H (pose and kNN)")
     ap.add_argument("--autotune", type=int, default=3, help="iterations per candidate of the mapping autotuner (0: off)")
     ap.add_argument("--cpu-budget", type=float, default=15.0)

@@ -66,9 +66,23 @@ enum {
     MPLPP_MODE_PERSISTENT = 2, /* one launch for all iterations; every state entry carries the
                                   update count that wrote it, which orders the matchings on
                                   the device (a reader polls until the count it needs)        */
-    MPLPP_MODE_WARP = 3        /* as PERSISTENT with one warp per edge instead of a cluster of
+    MPLPP_MODE_WARP = 3,       /* as PERSISTENT with one warp per edge instead of a cluster of
                                   CTAs per edge (for many small tables: every label count
                                   <= 128); options.cluster is ignored                          */
+    MPLPP_MODE_STRUCTURED = 4  /* every model MPLPP_PAIR_TRUNC_LINEAR, rule H, label counts
+                                  <= 256: one launch per matching, one warp per edge, O(L)
+                                  minimizations (AUTO picks it when all models qualify)       */
+};
+
+/* How a model's pairwise costs are given.  TRUNC_LINEAR: theta_uv(s,t) =
+ * w_uv * min(|s - t|, tau_uv) (labels on a line; Potts is tau = 1), the FP32
+ * product rounded once, as if the caller had passed those tables.  The
+ * solver materializes the tables on the device (bound, rounding, the dense
+ * drivers, backward) and, in MPLPP_MODE_STRUCTURED, runs the Handshake update
+ * with O(L) minimizations that never read them. */
+enum {
+    MPLPP_PAIR_DENSE = 0,
+    MPLPP_PAIR_TRUNC_LINEAR = 1
 };
 
 /* Which block-coordinate-ascent update mplpp_run applies to each edge (Sec. 4;
@@ -97,6 +111,11 @@ typedef struct {
     int32_t n_matchings;         /* MPLPP_SCHED_USER only                                      */
     const int32_t *matching_off; /* MPLPP_SCHED_USER only: [n_matchings + 1] host              */
     const int32_t *edge_order;   /* MPLPP_SCHED_USER only: [n_edges] host, edge ids            */
+    int32_t pair_kind;           /* MPLPP_PAIR_*; 0 = dense tables in `pairwise`                */
+    int32_t reserved;            /* 0                                                          */
+    const float *pair_param;     /* MPLPP_PAIR_TRUNC_LINEAR only: [n_edges][2] = (w, tau) per
+                                    edge, w >= 0, tau >= 0, finite (host, or device if
+                                    inputs_on_device); `pairwise` must then be NULL            */
 } mplpp_model;
 
 typedef struct {
@@ -189,7 +208,8 @@ mplpp_status mplpp_reset(mplpp_solver *s);
  *   pointers (copied through a device staging buffer allocated on the first
  *   call and kept) or device pointers if options.inputs_on_device.
  * Non-finite costs: MPLPP_E_INVALID (the state is then reset but the costs
- * are undefined until a successful call).  Synchronizes. */
+ * are undefined until a successful call).  Models with MPLPP_PAIR_TRUNC_LINEAR
+ * costs: MPLPP_E_UNSUPPORTED (create a new solver).  Synchronizes. */
 mplpp_status mplpp_update_costs(mplpp_solver *s, const float *const *unary, const float *const *pairwise);
 
 /* Solver state (the reparametrization) in a portable host format:

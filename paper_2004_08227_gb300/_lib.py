@@ -21,7 +21,8 @@ MPLPP_OK = 0
 STATUS = {0: "MPLPP_OK", -1: "MPLPP_E_INVALID", -2: "MPLPP_E_NOMEM", -3: "MPLPP_E_CUDA",
           -4: "MPLPP_E_TIMEOUT", -5: "MPLPP_E_NONFINITE", -6: "MPLPP_E_STATE", -7: "MPLPP_E_UNSUPPORTED"}
 SCHED = {"round_robin": 0, "greedy_color": 1, "alg1": 2, "user": 3}
-MODE = {"auto": 0, "looped": 1, "persistent": 2, "warp": 3}
+MODE = {"auto": 0, "looped": 1, "persistent": 2, "warp": 3, "structured": 4}
+PAIR = {"dense": 0, "trunc_linear": 1}  # pairwise given as tables, or as w min(|s - t|, tau) per edge
 MODE_NAME = {v: k for k, v in MODE.items()}
 RULE = {"H": 0, "M": 1, "U": 2}  # Sec. 4: eqs. (H), (M), (U)
 
@@ -36,7 +37,8 @@ class MplppModel(ctypes.Structure):
     _fields_ = [("n_nodes", c_i32), ("n_edges", c_i32), ("labels", ctypes.c_void_p),
                 ("edge_u", ctypes.c_void_p), ("edge_v", ctypes.c_void_p), ("unary", ctypes.c_void_p),
                 ("pairwise", ctypes.c_void_p), ("schedule_kind", c_i32), ("n_matchings", c_i32),
-                ("matching_off", ctypes.c_void_p), ("edge_order", ctypes.c_void_p)]
+                ("matching_off", ctypes.c_void_p), ("edge_order", ctypes.c_void_p), ("pair_kind", c_i32),
+                ("reserved", c_i32), ("pair_param", ctypes.c_void_p)]
 
 
 class MplppOptions(ctypes.Structure):

@@ -301,11 +301,42 @@ static mplpp_status apply_rule_mapping(mplpp_solver *s, int optin)
     return MPLPP_OK;
 }
 
+// The structured Handshake kernel: every model truncated-linear, one warp per
+// edge, vectors of up to kStructMaxL labels in shared memory.
+static bool struct_fits(mplpp_solver *s)
+{
+    int lmax = 1;
+    for (auto &nd : s->h_nodes) lmax = std::max(lmax, nd.L);
+    return lmax <= kStructMaxL;
+}
+
+static mplpp_status apply_struct_mapping(mplpp_solver *s, int optin)
+{
+    if (!s->all_structured)
+        return fail(s, MPLPP_E_UNSUPPORTED, "structured mode needs every model's costs as MPLPP_PAIR_TRUNC_LINEAR");
+    if (!struct_fits(s))
+        return fail(s, MPLPP_E_UNSUPPORTED,
+                    "structured mode takes label counts up to " + std::to_string(kStructMaxL));
+    mapping_for(s, 1, 256);  // sizes of the other drivers stay consistent
+    int lmax = 1;
+    for (auto &nd : s->h_nodes) lmax = std::max(lmax, nd.L);
+    s->struct_lmax = static_cast<int>(round4(lmax));
+    if (8 * struct_bytes_per_warp(s->struct_lmax) > static_cast<size_t>(optin))
+        return fail(s, MPLPP_E_UNSUPPORTED, "structured mode: vectors exceed shared memory");
+    cudaError_t ce = struct_prepare(s->struct_lmax);
+    if (ce != cudaSuccess) return cuda_fail(s, ce, "kernel attributes");
+    s->mode = MPLPP_MODE_STRUCTURED;
+    drop_graphs(s);
+    return MPLPP_OK;
+}
+
 static mplpp_status apply_mapping(mplpp_solver *s, int C, int T, int want)
 {
     int optin = 0;
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->device);
     if (s->opt.rule != kRuleH) return apply_rule_mapping(s, optin);
+    if (want == MPLPP_MODE_STRUCTURED || (want == MPLPP_MODE_AUTO && s->all_structured && struct_fits(s)))
+        return apply_struct_mapping(s, optin);
     if (want == MPLPP_MODE_WARP) return apply_warp_mapping(s, T, optin);
     mapping_for(s, C, T);
     if (s->smem_looped > static_cast<size_t>(optin))
@@ -350,12 +381,14 @@ extern "C" mplpp_status mplpp_create(const mplpp_model *models, int32_t n_models
     s->stream = static_cast<cudaStream_t>(stream);
     {
         const mplpp_options &o = s->opt;
-        if (o.mode < MPLPP_MODE_AUTO || o.mode > MPLPP_MODE_WARP) return fail(nullptr, MPLPP_E_INVALID, "unknown mode");
+        if (o.mode < MPLPP_MODE_AUTO || o.mode > MPLPP_MODE_STRUCTURED)
+            return fail(nullptr, MPLPP_E_INVALID, "unknown mode");
         if (o.cluster < 0 || o.cluster > 8) return fail(nullptr, MPLPP_E_INVALID, "cluster must be 0 or 1..8");
         if (o.rule < MPLPP_RULE_H || o.rule > MPLPP_RULE_U) return fail(nullptr, MPLPP_E_INVALID, "unknown rule");
         if (o.rule != MPLPP_RULE_H && o.record_every > 0)
             return fail(nullptr, MPLPP_E_INVALID, "backward is defined for the Handshake update only");
-        if (o.rule != MPLPP_RULE_H && (o.mode == MPLPP_MODE_PERSISTENT || o.mode == MPLPP_MODE_WARP))
+        if (o.rule != MPLPP_RULE_H &&
+            (o.mode == MPLPP_MODE_PERSISTENT || o.mode == MPLPP_MODE_WARP || o.mode == MPLPP_MODE_STRUCTURED))
             return fail(nullptr, MPLPP_E_UNSUPPORTED, "the M and U updates run in the looped driver only");
         // a CTA of the cluster drivers splits its warps between the two node
         // vectors, so it needs two warps at least
@@ -373,8 +406,22 @@ extern "C" mplpp_status mplpp_create(const mplpp_model *models, int32_t n_models
         const mplpp_model &md = models[m];
         ModelHost &mh = s->models[m];
         if (md.n_nodes < 1 || md.n_edges < 0) return fail(nullptr, MPLPP_E_INVALID, "model " + std::to_string(m) + ": bad sizes");
-        if (!md.labels || !md.unary || (md.n_edges > 0 && (!md.edge_u || !md.edge_v || !md.pairwise)))
+        if (md.pair_kind != MPLPP_PAIR_DENSE && md.pair_kind != MPLPP_PAIR_TRUNC_LINEAR)
+            return fail(nullptr, MPLPP_E_INVALID, "model " + std::to_string(m) + ": unknown pair_kind");
+        mh.structured = md.pair_kind == MPLPP_PAIR_TRUNC_LINEAR;
+        const bool pairs_given = mh.structured ? (md.pair_param != nullptr) : (md.pairwise != nullptr);
+        if (!md.labels || !md.unary || (md.n_edges > 0 && (!md.edge_u || !md.edge_v || !pairs_given)))
             return fail(nullptr, MPLPP_E_INVALID, "model " + std::to_string(m) + ": NULL array");
+        if (mh.structured && md.pairwise)
+            return fail(nullptr, MPLPP_E_INVALID,
+                        "model " + std::to_string(m) + ": structured costs come in pair_param; pairwise must be NULL");
+        if (mh.structured && s->opt.record_every > 0)
+            return fail(nullptr, MPLPP_E_INVALID, "model " + std::to_string(m) + ": no backward for structured costs");
+        if (mh.structured && !s->opt.inputs_on_device)
+            for (long long i = 0; i < 2LL * md.n_edges; ++i)
+                if (!std::isfinite(md.pair_param[i]) || md.pair_param[i] < 0.f)
+                    return fail(nullptr, MPLPP_E_INVALID,
+                                "model " + std::to_string(m) + ": pair_param must be finite and >= 0");
         mh.n = md.n_nodes;
         mh.E = md.n_edges;
         mh.L.assign(md.labels, md.labels + md.n_nodes);
@@ -532,6 +579,23 @@ extern "C" mplpp_status mplpp_create(const mplpp_model *models, int32_t n_models
     CKC(h2d(S->d_in_rec, S->in_rec.data(), S->in_rec.size() * sizeof(InRec)));
     CKC(h2d(S->d_mnode_off, S->mnode_off.data(), S->mnode_off.size() * sizeof(int)));
     CKC(h2d(S->d_medge_off, S->medge_off.data(), S->medge_off.size() * sizeof(int)));
+    // structured costs: (w, tau) per edge
+    S->all_structured = S->EE > 0;
+    bool any_structured = false;
+    for (auto &mh : S->models) {
+        S->all_structured = S->all_structured && mh.structured;
+        any_structured = any_structured || (mh.structured && mh.E > 0);
+    }
+    if (any_structured) {
+        CKC(S->alloc(&S->d_pair_param, S->EE));
+        CKC(cudaMemsetAsync(S->d_pair_param, 0, sizeof(float2) * S->EE, st));
+        for (int m = 0; m < n_models; ++m) {
+            const ModelHost &mh = S->models[m];
+            if (!mh.structured || mh.E == 0) continue;
+            CKC(cudaMemcpyAsync(S->d_pair_param + mh.edge_base, models[m].pair_param, sizeof(float2) * mh.E,
+                                S->opt.inputs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+        }
+    }
     {
         mplpp_status ms = apply_mapping(S, chosenC, S->opt.threads, S->opt.mode);
         if (ms != MPLPP_OK) return fail(nullptr, ms, S->err);
@@ -553,14 +617,17 @@ extern "C" mplpp_status mplpp_create(const mplpp_model *models, int32_t n_models
         const float *sp = models[m].pairwise;
         if (!S->opt.inputs_on_device) {
             pe = h2d(stage_u + ub, models[m].unary, mh.unary_size * sizeof(float));
-            if (pe == cudaSuccess && mh.pair_size)
+            if (pe == cudaSuccess && mh.pair_size && !mh.structured)
                 pe = h2d(stage_p + pb, models[m].pairwise, mh.pair_size * sizeof(float));
             su = stage_u + ub;
             sp = stage_p + pb;
         }
         if (pe == cudaSuccess)
-            pe = launch_pack(S->d_edges + mh.edge_base, mh.E, S->d_nodes + mh.node_base, mh.n, su, sp, S->d_tab,
-                             S->d_un0, S->d_agg, S->d_err, st);
+            pe = launch_pack(S->d_edges + mh.edge_base, mh.structured ? 0 : mh.E, S->d_nodes + mh.node_base, mh.n, su,
+                             sp, S->d_tab, S->d_un0, S->d_agg, S->d_err, st);
+        if (pe == cudaSuccess && mh.structured)
+            pe = launch_materialize(S->d_edges + mh.edge_base, S->d_pair_param + mh.edge_base, mh.E, S->d_tab,
+                                    S->d_err, st);
         ub += mh.unary_size;
         pb += mh.pair_size;
     }
@@ -607,6 +674,16 @@ static HsParams make_params(mplpp_solver *s)
 // One iteration of looped launches (one per matching) on stream st.
 cudaError_t enqueue_looped_iteration(mplpp_solver *s, cudaStream_t st)
 {
+    if (s->mode == MPLPP_MODE_STRUCTURED) {
+        StructParams sp = {s->d_edges, nullptr, 0, s->struct_lmax, s->d_pair_param, s->d_agg, s->d_msg};
+        for (int ph = 0; ph + 1 < static_cast<int>(s->phase_off.size()); ++ph) {
+            sp.items = s->d_phase_edges + s->phase_off[ph];
+            sp.n_items = s->phase_off[ph + 1] - s->phase_off[ph];
+            cudaError_t e = launch_struct(sp, st);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
     if (s->opt.rule != kRuleH) {
         RuleParams rp = {s->d_edges, nullptr, s->d_tab, s->d_agg, s->d_msg};
         for (int ph = 0; ph + 1 < static_cast<int>(s->phase_off.size()); ++ph) {
@@ -642,7 +719,7 @@ cudaError_t enqueue_persistent(mplpp_solver *s, cudaStream_t st, int iterations)
 static mplpp_status run_plain(mplpp_solver *s, int iterations)
 {
     if (iterations == 0 || s->EE == 0) return MPLPP_OK;
-    if (s->mode == MPLPP_MODE_LOOPED) {
+    if (s->mode == MPLPP_MODE_LOOPED || s->mode == MPLPP_MODE_STRUCTURED) {
         if (s->opt.use_graph) {
             if (!s->g_looped) {
                 cudaGraph_t g = nullptr;
@@ -767,6 +844,9 @@ extern "C" mplpp_status mplpp_update_costs(mplpp_solver *s, const float *const *
     if (!s || !unary || !pairwise) return MPLPP_E_INVALID;
     s->err.clear();
     const int n_models = static_cast<int>(s->models.size());
+    for (int m = 0; m < n_models; ++m)
+        if (s->models[m].structured)
+            return fail(s, MPLPP_E_UNSUPPORTED, "model " + std::to_string(m) + ": structured costs: create a new solver");
     for (int m = 0; m < n_models; ++m)
         if (!unary[m] || (!pairwise[m] && s->models[m].pair_size))
             return fail(s, MPLPP_E_INVALID, "model " + std::to_string(m) + ": NULL cost array");
@@ -894,7 +974,10 @@ extern "C" mplpp_status mplpp_load_state(mplpp_solver *s, const void *buf, size_
 
 static const char *mode_name(int mode)
 {
-    return mode == MPLPP_MODE_PERSISTENT ? "persistent" : mode == MPLPP_MODE_WARP ? "warp" : "looped";
+    return mode == MPLPP_MODE_PERSISTENT   ? "persistent"
+           : mode == MPLPP_MODE_WARP       ? "warp"
+           : mode == MPLPP_MODE_STRUCTURED ? "structured"
+                                           : "looped";
 }
 
 // Measured choice of the mapping: every feasible (CTAs per edge, threads per
@@ -937,9 +1020,10 @@ extern "C" mplpp_status mplpp_autotune(mplpp_solver *s, int32_t iterations, char
     cudaEvent_t e0, e1;
     CK(s, cudaEventCreate(&e0));
     CK(s, cudaEventCreate(&e1));
-    for (int mode : {MPLPP_MODE_PERSISTENT, MPLPP_MODE_LOOPED, MPLPP_MODE_WARP})
+    for (int mode : {MPLPP_MODE_PERSISTENT, MPLPP_MODE_LOOPED, MPLPP_MODE_WARP, MPLPP_MODE_STRUCTURED})
         for (int C : {1, 2, 3, 4, 5, 6, 8})
             for (int T : {128, 256, 512}) {
+                if (mode == MPLPP_MODE_STRUCTURED && (C != 1 || T != 256 || !s->all_structured)) continue;
                 if (mode == MPLPP_MODE_WARP && C != 1) continue;  // one warp per edge
                 if (mode == MPLPP_MODE_WARP && T == 512) T = 32;  // small blocks: shared memory per warp
                 if (apply_mapping(s, C, T, mode) != MPLPP_OK) {
@@ -994,7 +1078,7 @@ extern "C" mplpp_status mplpp_info(const mplpp_solver *s, mplpp_info_t *info)
     info->grid = s->mode == MPLPP_MODE_PERSISTENT ? s->clusters * s->C
                  : s->mode == MPLPP_MODE_WARP     ? s->warp_blocks
                                                   : 0;
-    info->launches_per_iteration = s->mode == MPLPP_MODE_LOOPED ? s->P : 0;
+    info->launches_per_iteration = (s->mode == MPLPP_MODE_LOOPED || s->mode == MPLPP_MODE_STRUCTURED) ? s->P : 0;
     return MPLPP_OK;
 }
 

@@ -73,6 +73,28 @@ size_t rule_smem_bytes(int lumax, int ldmax);  // lumax >= every L_u, ldmax >= e
 cudaError_t rule_prepare(size_t smem_bytes);
 cudaError_t launch_rule(const RuleParams &p, int rule, int n_items, size_t smem, cudaStream_t st);
 
+// structured.cu: the Handshake update for truncated-linear costs
+// w min(|s - t|, tau) in O(L) per minimization, one warp per edge, looped.
+constexpr int kStructMaxL = 256;  // largest label count the structured kernel takes
+struct StructParams {
+    const EdgeDesc *edges;
+    const int *items;      // edge ids of the matching being launched
+    int n_items;
+    int lmax;              // >= every label count of the solver, multiple of 4
+    const float2 *param;   // [edges] (w, tau) per edge id
+    ulonglong2 *agg;
+    ulonglong2 *msg;
+};
+__host__ __device__ inline size_t struct_bytes_per_warp(int lmax)
+{
+    return 40 * static_cast<size_t>(lmax);  // uh, vh double-float; h, m FP32; prefix and suffix (value, index)
+}
+cudaError_t struct_prepare(int lmax);
+cudaError_t launch_struct(const StructParams &p, cudaStream_t st);
+// tables of n consecutive edges from their (w, tau): w min(|s - t|, tau),
+// rows padded with +inf; a negative or non-finite parameter sets ERR_NONFINITE
+cudaError_t launch_materialize(const EdgeDesc *edges, const float2 *param, int n, float *tab, int *err, cudaStream_t st);
+
 // dual.cu
 cudaError_t launch_pack(const EdgeDesc *edges, int n_edges, const NodeDesc *nodes, int n_nodes,
                         const float *unary_src, const float *pair_src, float *tab, float *un0, ulonglong2 *agg,

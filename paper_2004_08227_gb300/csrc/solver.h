@@ -15,6 +15,7 @@ struct ModelHost {
     int n = 0, E = 0;
     int node_base = 0, edge_base = 0;
     long long unary_size = 0, pair_size = 0;
+    bool structured = false;  // MPLPP_PAIR_TRUNC_LINEAR
     std::vector<int> L, eu, ev, off, order;
 };
 }  // namespace mplpp
@@ -56,6 +57,9 @@ struct mplpp_solver {
     int warp_blocks = 0, lw = 0, cap = 0;  // warp driver: blocks, per-warp vector and buffer capacity
     size_t smem_warp = 0;
     size_t smem_rule = 0;  // M and U updates (rules.cu)
+    bool all_structured = false;  // every model MPLPP_PAIR_TRUNC_LINEAR (and at least one edge)
+    int struct_lmax = 0;          // structured kernel: vector capacity (multiple of 4)
+    float2 *d_pair_param = nullptr;  // [EE] (w, tau) per edge (structured models)
 
     // device
     std::vector<void *> allocations;

@@ -1,0 +1,277 @@
+// structured.cu -- the Handshake update (Sec. 4, eq. (H), three-minimization
+// form) for truncated-linear pairwise costs theta_uv(s,t) = w_uv min(|s - t|,
+// tau_uv) (Potts: tau = 1), with O(L) minimizations instead of O(L^2) table
+// passes (the paper notes the speed-up that lower envelopes give in message
+// passing for such costs, Sec. 1 and Sec. 4).
+//
+// Each of the three minimizations has the form
+//   m(s) = min_t [w min(|s - t|, tau) + h(t)],   t < Lh, s < Ls,
+// and for w, tau >= 0 splits into three parts:
+//   min_{t <= s} (h(t) - w t) + w s,   min_{t >= s} (h(t) + w t) - w s,
+//   min_t h(t) + w tau,
+// i.e. a prefix minimum, a suffix minimum and the global minimum of h, all
+// three warp-parallel scans.  For short truncation (tau <= 8, Potts included)
+// a window of candidates around s and the global minimizer are evaluated
+// directly instead, which reproduces the dense minimum bit for bit.  The scans only choose a minimizer in each part;
+// the three are then evaluated as the dense path evaluates an entry,
+// theta(s,t) + h(t) with theta rounded to FP32 once (the entry of the
+// materialized table), and the smallest is taken, so a minimum differs from
+// the dense kernel's only where rounding decides between candidates of equal
+// exact value (common: reparametrized vectors form linear ramps along which
+// w |s - t| + h(t) is constant), by rounding.  The vectors h, the O(L) double-float arithmetic and the write-back
+// are those of the dense kernel (uh, vh; w1 = vh - vh(0), alpha, beta).
+//
+// One warp per edge of a matching, looped (one launch per matching): the
+// tables are not read at all, so an update moves O(L) bytes.
+#include "kernels.h"
+
+namespace mplpp {
+
+namespace {
+
+constexpr int kStructThreads = 256;
+constexpr int kStructWarps = kStructThreads / 32;
+constexpr unsigned kAll = 0xffffffffu;
+constexpr int kWindowMax = 7;  // truncation radius up to which the direct window beats the scans
+
+struct VI {
+    float v;
+    int i;
+};
+
+// smaller value, then smaller index
+__device__ __forceinline__ VI vi_min(VI a, VI b)
+{
+    return (b.v < a.v || (b.v == a.v && b.i < a.i)) ? b : a;
+}
+
+__device__ __forceinline__ VI vi_shfl_up(VI a, int o)
+{
+    return {__shfl_up_sync(kAll, a.v, o), __shfl_up_sync(kAll, a.i, o)};
+}
+
+__device__ __forceinline__ VI vi_shfl_down(VI a, int o)
+{
+    return {__shfl_down_sync(kAll, a.v, o), __shfl_down_sync(kAll, a.i, o)};
+}
+
+__device__ __forceinline__ VI vi_shfl_xor(VI a, int o)
+{
+    return {__shfl_xor_sync(kAll, a.v, o), __shfl_xor_sync(kAll, a.i, o)};
+}
+
+// the dense table's entry theta(s,t) in FP32: the product rounded on its own
+// (never fused with a following addition, as a table entry is not)
+__device__ __forceinline__ float theta_tl(int s, int t, float w, float tau)
+{
+    return __fmul_rn(w, fminf(fabsf(static_cast<float>(s - t)), tau));
+}
+
+// out[s] = min_t [theta(s,t) + h[t]] for s < Ls, t < Lh (1 <= Lh, Ls <= 32 k);
+// lane owns t in [lane k, lane k + k).  pre / suf: [Lh] scratch of the warp.
+__device__ void dt_trunc_linear(const float *h, int Lh, int Ls, float w, float tau, float *out, VI *pre, VI *suf,
+                                int lane, int k)
+{
+    const VI none = {INFINITY, 0x7fffffff};
+    const int t0 = lane * k;
+    // global minimum of h (lowest index on ties)
+    VI g = none;
+    for (int t = lane; t < Lh; t += 32) g = vi_min(g, VI{h[t], t});
+    for (int o = 16; o > 0; o >>= 1) g = vi_min(g, vi_shfl_xor(g, o));
+    // Short truncation (Potts included): only t with |s - t| < tau can cost
+    // less than w tau, so the window |s - t| <= R = ceil(tau) - 1 plus the
+    // global minimizer hold the minimum.  Every t outside the window costs w
+    // tau + h(t) >= w tau + h(t_g) >= theta(s, t_g) + h(t_g) after rounding
+    // (rounding is monotone), so the result is the dense kernel's minimum of
+    // the same rounded values, bit for bit.
+    const int R = static_cast<int>(ceilf(tau)) - 1;
+    if (R <= kWindowMax) {
+        for (int s = lane; s < Ls; s += 32) {
+            float best = theta_tl(s, g.i, w, tau) + g.v;
+            const int lo = s - R > 0 ? s - R : 0, hi = s + R < Lh - 1 ? s + R : Lh - 1;
+            for (int t = lo; t <= hi; ++t) best = fminf(best, theta_tl(s, t, w, tau) + h[t]);
+            out[s] = best;
+        }
+        __syncwarp();
+        return;
+    }
+    // prefix minima of h(t) - w t: this lane's run, the warp's exclusive scan
+    VI run = none;
+    for (int j = 0; j < k; ++j) {
+        const int t = t0 + j;
+        if (t < Lh) {
+            run = vi_min(run, VI{h[t] - w * static_cast<float>(t), t});
+            pre[t] = run;
+        }
+    }
+    VI inc = run;
+    for (int o = 1; o < 32; o <<= 1) {
+        const VI x = vi_shfl_up(inc, o);
+        if (lane >= o) inc = vi_min(x, inc);  // the earlier lanes' (lower t) minimum first
+    }
+    VI exc = vi_shfl_up(inc, 1);
+    if (lane == 0) exc = none;
+    for (int j = 0; j < k; ++j) {
+        const int t = t0 + j;
+        if (t < Lh) pre[t] = vi_min(exc, pre[t]);
+    }
+    // suffix minima of h(t) + w t
+    run = none;
+    for (int j = k - 1; j >= 0; --j) {
+        const int t = t0 + j;
+        if (t < Lh) {
+            run = vi_min(run, VI{h[t] + w * static_cast<float>(t), t});
+            suf[t] = run;
+        }
+    }
+    inc = run;
+    for (int o = 1; o < 32; o <<= 1) {
+        const VI x = vi_shfl_down(inc, o);
+        if (lane + o < 32) inc = vi_min(inc, x);
+    }
+    exc = vi_shfl_down(inc, 1);
+    if (lane == 31) exc = none;
+    for (int j = 0; j < k; ++j) {
+        const int t = t0 + j;
+        if (t < Lh) suf[t] = vi_min(suf[t], exc);
+    }
+    __syncwarp();
+    // the three parts' minimizers, each evaluated exactly as the dense path
+    // evaluates an entry (the scans' keys h(t) -+ w t round at the scale of
+    // w t, so they only choose within each part)
+    for (int s = lane; s < Ls; s += 32) {
+        const int tp = pre[min(s, Lh - 1)].i;
+        VI best = {theta_tl(s, tp, w, tau) + h[tp], tp};
+        if (s < Lh) {
+            const int ts = suf[s].i;
+            best = vi_min(best, VI{theta_tl(s, ts, w, tau) + h[ts], ts});
+        }
+        best = vi_min(best, VI{theta_tl(s, g.i, w, tau) + g.v, g.i});
+        out[s] = best.v;
+    }
+    __syncwarp();
+}
+
+__global__ void __launch_bounds__(kStructThreads) struct_kernel(StructParams p)
+{
+    extern __shared__ __align__(16) char smem_raw[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int item = blockIdx.x * kStructWarps + wib;
+    if (item >= p.n_items) return;
+    const int lmax = p.lmax;
+    // per warp: uh, vh (double-float), h and m (FP32), pre and suf (value, index)
+    char *base = smem_raw + static_cast<size_t>(wib) * struct_bytes_per_warp(lmax);
+    float2 *uh = reinterpret_cast<float2 *>(base);
+    float2 *vh = uh + lmax;
+    float *h = reinterpret_cast<float *>(vh + lmax);
+    float *m = h + lmax;
+    VI *pre = reinterpret_cast<VI *>(m + lmax);
+    VI *suf = pre + lmax;
+
+    const int e = p.items[item];
+    const EdgeDesc ed = p.edges[e];
+    const float2 wt = p.param[e];
+    const float w = wt.x, tau = wt.y;
+    const int Lu = ed.Lu, Lv = ed.Lv;
+    ulonglong2 *agg = p.agg;
+    ulonglong2 *msg = p.msg;
+
+    // unaries without this edge's messages: up to 4 entries of each node per
+    // lane requested before any is used (one round trip per 128 labels)
+    const int Lm = Lu > Lv ? Lu : Lv;
+    for (int base = 0; base < Lm; base += 128) {
+        ulonglong2 xu[4], mu[4], xv[4], mv[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int i = base + lane + 32 * j;
+            if (i < Lu) {
+                xu[j] = ld_se(agg + ed.au + i);
+                mu[j] = ld_se(msg + ed.mu + i);
+            }
+            if (i < Lv) {
+                xv[j] = ld_se(agg + ed.av + i);
+                mv[j] = ld_se(msg + ed.mv + i);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int i = base + lane + 32 * j;
+            if (i < Lu) uh[i] = df_sub(se_df(xu[j]), se_df(mu[j]));
+            if (i < Lv) vh[i] = df_sub(se_df(xv[j]), se_df(mv[j]));
+        }
+    }
+    __syncwarp();
+    const float2 vref = vh[0];
+    for (int t = lane; t < Lv; t += 32) h[t] = df_to_f(df_sub(vh[t], vref));
+    __syncwarp();
+    const int ku = (Lu + 31) >> 5, kv = (Lv + 31) >> 5;
+
+    // pass 1: a(s) = 1/2 (min_t [theta(s,t) + w1(t)] + vh(0) + uh(s)); alpha = uh - a
+    dt_trunc_linear(h, Lv, Lu, w, tau, m, pre, suf, lane, kv);
+    for (int s = lane; s < Lu; s += 32) {
+        const float2 a = df_half(df_add(df_add_f(vref, m[s]), uh[s]));
+        h[s] = df_to_f(df_sub(uh[s], a));
+    }
+    __syncwarp();
+    // pass 2: b(t) = min_s [theta(s,t) + alpha(s)] + vh(t); beta = vh - b; node v's new vector
+    dt_trunc_linear(h, Lu, Lv, w, tau, m, pre, suf, lane, ku);
+    for (int t = lane; t < Lv; t += 32) {
+        const float2 b = df_add_f(vh[t], m[t]);
+        h[t] = df_to_f(df_sub(vh[t], b));
+        st_se(agg + ed.av + t, se_make(b, 1u));
+        st_se(msg + ed.mv + t, se_make(df_sub(b, vh[t]), 1u));
+    }
+    __syncwarp();
+    // pass 3: c(s) = min_t [theta(s,t) + beta(t)] + uh(s); node u's new vector
+    dt_trunc_linear(h, Lv, Lu, w, tau, m, pre, suf, lane, kv);
+    for (int s = lane; s < Lu; s += 32) {
+        const float2 c = df_add_f(uh[s], m[s]);
+        st_se(agg + ed.au + s, se_make(c, 1u));
+        st_se(msg + ed.mu + s, se_make(df_sub(c, uh[s]), 1u));
+    }
+}
+
+// tables of structured edges from their parameters, as the caller would have
+// given them densely (rows padded to ld with +inf)
+__global__ void materialize_kernel(const EdgeDesc *edges, const float2 *param, int n, float *tab, int *err)
+{
+    for (int e = blockIdx.x; e < n; e += gridDim.x) {
+        const EdgeDesc ed = edges[e];
+        const float2 wt = param[e];
+        if (!(isfinite(wt.x) && isfinite(wt.y) && wt.x >= 0.f && wt.y >= 0.f)) {
+            if (threadIdx.x == 0) atomicCAS(err, 0, ERR_NONFINITE);
+            continue;
+        }
+        const long long n_ent = static_cast<long long>(ed.Lu) * ed.ld;
+        for (long long i = threadIdx.x; i < n_ent; i += blockDim.x) {
+            const int s = static_cast<int>(i / ed.ld);
+            const int t = static_cast<int>(i - static_cast<long long>(s) * ed.ld);
+            tab[ed.toff + i] = t < ed.Lv ? theta_tl(s, t, wt.x, wt.y) : INFINITY;
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t struct_prepare(int lmax)
+{
+    return cudaFuncSetAttribute(struct_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(kStructWarps * struct_bytes_per_warp(lmax)));
+}
+
+cudaError_t launch_struct(const StructParams &p, cudaStream_t st)
+{
+    if (p.n_items <= 0) return cudaSuccess;
+    const int blocks = (p.n_items + kStructWarps - 1) / kStructWarps;
+    struct_kernel<<<blocks, kStructThreads, kStructWarps * struct_bytes_per_warp(p.lmax), st>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_materialize(const EdgeDesc *edges, const float2 *param, int n, float *tab, int *err, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    materialize_kernel<<<n < 4096 ? n : 4096, 256, 0, st>>>(edges, param, n, tab, err);
+    return cudaGetLastError();
+}
+
+}  // namespace mplpp

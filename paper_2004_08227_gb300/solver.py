@@ -73,12 +73,15 @@ class Solver:
     ``user_schedules`` optionally gives ``(matching_off, edge_order)`` per model.
     ``rule`` is the update applied to each edge (Sec. 4): "H" (Handshake, the
     default), or "M" / "U" (MPLP and uniform updates, for comparison; looped
-    driver only, no backward).
+    driver only, no backward).  A model with ``pair_kind == "trunc_linear"``
+    passes its costs as ``pair_param`` ([E, 2]: w, tau per edge) unless
+    ``structured=False``, which passes its dense ``pairwise`` tables instead.
     """
 
     def __init__(self, models, *, mode: str = "auto", use_graph: bool = True, record_every: int = 0,
                  cluster: int = 0, threads: int = 0, spin_limit: int = 1 << 22, device_inputs: bool = False,
-                 user_schedules=None, stream=None, test_unreachable_wait: bool = False, rule: str = "H"):
+                 user_schedules=None, stream=None, test_unreachable_wait: bool = False, rule: str = "H",
+                 structured: bool = True):
         self._lib = _lib.load()
         self._h = ctypes.c_void_p(0)
         models = list(models)
@@ -89,20 +92,28 @@ class Solver:
         for i, m in enumerate(models):
             L, eu, ev = _i32(m.labels), _i32(m.edge_u), _i32(m.edge_v)
             keep += [L, eu, ev]
+            # structured costs (w, tau per edge) go in pair_param instead of tables
+            kind = getattr(m, "pair_kind", "dense") if structured else "dense"
+            src = m.pair_param if kind != "dense" else m.pairwise
             if device_inputs:
-                un, pw = m.unary, m.pairwise
+                un, pw = m.unary, src
                 assert un.is_cuda and un.dtype == torch.float32 and un.is_contiguous()
                 assert pw.is_cuda and pw.dtype == torch.float32 and pw.is_contiguous()
             else:
                 un = m.unary if (torch is not None and isinstance(m.unary, torch.Tensor)) else \
                     np.ascontiguousarray(m.unary, dtype=np.float32)
-                pw = m.pairwise if (torch is not None and isinstance(m.pairwise, torch.Tensor)) else \
-                    np.ascontiguousarray(m.pairwise, dtype=np.float32)
+                pw = src if (torch is not None and isinstance(src, torch.Tensor)) else \
+                    np.ascontiguousarray(src, dtype=np.float32)
             keep += [un, pw]
             md = arr[i]
             md.n_nodes, md.n_edges = int(L.shape[0]), int(eu.shape[0])
             md.labels, md.edge_u, md.edge_v = _ptr(L), _ptr(eu), _ptr(ev)
-            md.unary, md.pairwise = _ptr(un), _ptr(pw)
+            md.unary = _ptr(un)
+            md.pair_kind = _lib.PAIR[kind]
+            if kind == "dense":
+                md.pairwise = _ptr(pw)
+            else:
+                md.pair_param = _ptr(pw)
             if user_schedules is not None and user_schedules[i] is not None:
                 off, order = _i32(user_schedules[i][0]), _i32(user_schedules[i][1])
                 keep += [off, order]

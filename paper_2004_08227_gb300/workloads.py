@@ -36,6 +36,8 @@ class Model:
     schedule: str = "greedy_color"
     name: str = ""
     meta: dict = field(default_factory=dict)
+    pair_kind: str = "dense"    # "trunc_linear": pairwise(s,t) = w_e min(|s - t|, tau_e) (also given densely)
+    pair_param: np.ndarray = None  # float32 [E, 2]: (w_e, tau_e) for "trunc_linear"
 
     @property
     def n(self) -> int:
@@ -144,6 +146,38 @@ def pose_dense(n: int, L: int = 13, seed: int = 0, sigma: float = 0.05) -> Model
     m.schedule = "round_robin"
     m.name = f"pose_dense_K{n}_L{L}_s{seed}"
     return m
+
+
+def trunc_linear_tables(labels: np.ndarray, eu: np.ndarray, ev: np.ndarray, param: np.ndarray) -> np.ndarray:
+    """Dense tables of truncated-linear costs w min(|s - t|, tau), in float32
+    arithmetic (the distance exact, the product rounded once)."""
+    out = []
+    for e in range(eu.shape[0]):
+        Lu, Lv = int(labels[eu[e]]), int(labels[ev[e]])
+        d = np.abs(np.arange(Lu, dtype=np.float32)[:, None] - np.arange(Lv, dtype=np.float32)[None, :])
+        out.append((np.float32(param[e, 0]) * np.minimum(d, np.float32(param[e, 1]))).astype(np.float32).ravel())
+    return np.concatenate(out) if out else np.zeros(0, np.float32)
+
+
+def grid_trunc_linear(rows: int, cols: int, L: int, weight: float, tau: float, seed: int = 0,
+                      Lmin: int = 0) -> Model:
+    """Stereo-like model: a 4-connected rows x cols grid, labels on a line
+    (L per node, or U{Lmin..L} when Lmin > 0), unary U[0, 4), pairwise
+    w_e min(|s - t|, tau) with w_e = weight * U[0.5, 1.5) (tau = 1: Potts);
+    greedy edge colouring.  Carries both the parameters and the dense tables."""
+    rng = np.random.default_rng(seed)
+    n = rows * cols
+    labels = (rng.integers(Lmin, L + 1, size=n) if Lmin > 0 else np.full(n, L)).astype(np.int32)
+    unary = (4.0 * rng.random(int(labels.sum()))).astype(np.float32)
+    idx = np.arange(n).reshape(rows, cols)
+    eu = np.concatenate([idx[:, :-1].ravel(), idx[:-1, :].ravel()])
+    ev = np.concatenate([idx[:, 1:].ravel(), idx[1:, :].ravel()])
+    order = np.lexsort((ev, eu))
+    eu, ev = eu[order].astype(np.int32), ev[order].astype(np.int32)
+    param = np.stack([weight * rng.uniform(0.5, 1.5, size=eu.shape[0]), np.full(eu.shape[0], tau)], axis=1)
+    param = param.astype(np.float32)
+    return Model(labels, eu, ev, unary, trunc_linear_tables(labels, eu, ev, param), schedule="greedy_color",
+                 name=f"grid{rows}x{cols}_L{L}_tl{tau:g}_s{seed}", pair_kind="trunc_linear", pair_param=param)
 
 
 def knn(n: int = 2000, k: int = 50, L: int = 64, seed: int = 0) -> Model:

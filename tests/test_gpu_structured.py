@@ -1,0 +1,140 @@
+"""GPU parity of the structured Handshake path (truncated-linear costs
+w min(|s - t|, tau), Potts for tau = 1; O(L) minimizations by prefix, suffix
+and global minima) against the FP64 oracle on the same costs given as dense
+tables, and against the dense GPU drivers.  Tolerances as in
+test_gpu_parity.py."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import schedule as osched
+from paper_2004_08227_gb300 import workloads as W
+from paper_2004_08227_gb300._lib import MplppError
+from paper_2004_08227_gb300.solver import Solver
+
+pytestmark = pytest.mark.gpu
+
+RTOL_D = 1e-5
+
+
+def _order(m):
+    return osched.build(m.schedule, m.n, m.edge_u, m.edge_v)[1]
+
+
+def _check(m, T, s):
+    sol = oracle.solve(m, _order(m), T)
+    s.run(T)
+    D = s.bound(exact=True)[0]
+    assert abs(D - sol["bound"]) <= RTOL_D * max(abs(sol["bound"]), 1.0), (D, sol["bound"])
+    xs, _ = s.labels_per_model()
+    diff = np.flatnonzero(xs[0] != sol["labels"])
+    if diff.size:
+        u = int(diff[0])
+        assert sol["margins"][u] <= 1e-4 * max(1.0, float(np.abs(sol["th_u"]).max())), (u, sol["margins"][u])
+    return D
+
+
+CASES = {
+    "potts_L16": dict(rows=6, cols=7, L=16, weight=1.0, tau=1.0),
+    "tl_L40": dict(rows=5, cols=6, L=40, weight=0.7, tau=4.0),
+    "tl_L200": dict(rows=4, cols=5, L=200, weight=0.5, tau=12.0),
+    "tl_L256_untruncated": dict(rows=3, cols=4, L=256, weight=0.05, tau=1000.0),
+    "ragged_1_33": dict(rows=6, cols=6, L=33, weight=1.0, tau=3.0, Lmin=1),
+    "ragged_2_70": dict(rows=5, cols=5, L=70, weight=0.3, tau=8.0, Lmin=2),
+}
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_structured_parity_with_oracle(case):
+    m = W.grid_trunc_linear(seed=3, **CASES[case])
+    s = Solver([m])
+    assert s.info()["mode"] == "structured"
+    _check(m, 15, s)
+
+
+@pytest.mark.parametrize("case,exact", [("potts_L16", True), ("tl_L40", True), ("ragged_2_70", True),
+                                        ("tl_L200", False), ("tl_L256_untruncated", False)])
+def test_structured_equals_dense_drivers(case, exact):
+    """Short truncation (tau <= 8, Potts included): the window of candidates
+    plus the global minimizer give the dense kernel's minimum of the same
+    rounded values, so the states agree bit for bit.  Longer truncation: the
+    scans pick the minimizers, which rounding may decide differently where
+    several have the same exact value (reparametrized vectors form linear
+    ramps along which w|s - t| + h(t) is constant): bounds within 1e-6
+    relative, state entries within 1e-5."""
+    m = W.grid_trunc_linear(seed=5, **CASES[case])
+    T = 20
+    a = Solver([m])
+    assert a.info()["mode"] == "structured"
+    a.run(T)
+    b = Solver([m], structured=False)
+    assert b.info()["mode"] != "structured"
+    b.run(T)
+    sa, sb = a.state_arrays(), b.state_arrays()
+    if exact:
+        assert np.array_equal(sa[1], sb[1]) and np.array_equal(sa[2], sb[2])
+        return
+    Da, Db = a.bound(exact=True)[0], b.bound(exact=True)[0]
+    assert abs(Da - Db) <= 1e-6 * max(1.0, abs(Db)), (Da, Db)
+    for x, y in ((sa[1], sb[1]), (sa[2], sb[2])):
+        assert np.all(np.abs(x - y) <= 1e-5 * np.maximum(1.0, np.abs(y))), np.abs(x - y).max()
+
+
+@pytest.mark.parametrize("mode", ["persistent", "looped", "warp"])
+def test_materialized_tables_in_the_dense_drivers(mode):
+    """Structured input, dense drivers: the tables built on the device from
+    (w, tau) give the oracle's result."""
+    m = W.grid_trunc_linear(seed=7, **CASES["ragged_1_33"])
+    _check(m, 12, Solver([m], mode=mode))
+
+
+def test_structured_device_inputs_bitwise_equal_host_inputs():
+    import torch
+    m = W.grid_trunc_linear(seed=9, **CASES["tl_L40"])
+    a = Solver([m])
+    a.run(10)
+    md = W.Model(m.labels, m.edge_u, m.edge_v, torch.from_numpy(m.unary).cuda(), None, schedule=m.schedule,
+                 pair_kind="trunc_linear", pair_param=torch.from_numpy(np.ascontiguousarray(m.pair_param)).cuda())
+    b = Solver([md], device_inputs=True)
+    b.run(10)
+    sa, sb = a.state_arrays(), b.state_arrays()
+    assert np.array_equal(sa[1], sb[1]) and np.array_equal(sa[2], sb[2])
+
+
+def test_large_labels_fall_back_to_the_dense_drivers():
+    m = W.grid_trunc_linear(rows=2, cols=3, L=300, weight=0.5, tau=10.0, seed=1)
+    s = Solver([m])
+    assert s.info()["mode"] != "structured"
+    _check(m, 6, s)
+    with pytest.raises(MplppError) as ei:
+        Solver([m], mode="structured")
+    assert ei.value.status == -7
+
+
+def test_structured_rejections():
+    m = W.grid_trunc_linear(seed=0, **CASES["potts_L16"])
+    dense = W.complete(5, 3, seed=0)
+    with pytest.raises(MplppError) as ei:
+        Solver([dense], mode="structured")
+    assert ei.value.status == -7
+    bad = W.grid_trunc_linear(seed=0, **CASES["potts_L16"])
+    bad.pair_param = bad.pair_param.copy()
+    bad.pair_param[3, 0] = -1.0
+    with pytest.raises(MplppError) as ei:
+        Solver([bad])
+    assert ei.value.status == -1
+    with pytest.raises(MplppError) as ei:
+        Solver([m], record_every=5)
+    assert ei.value.status == -1
+    s = Solver([m])
+    with pytest.raises(MplppError) as ei:
+        s.update_costs([m.unary], [m.pairwise])
+    assert ei.value.status == -7
+
+
+def test_autotune_measures_the_structured_driver():
+    m = W.grid_trunc_linear(seed=2, **CASES["tl_L40"])
+    s = Solver([m])
+    rep = s.autotune(2)
+    assert any(c[2] == "structured" for c in rep["candidates"])
+    assert s.info()["mode"] == rep["best"]["mode"]

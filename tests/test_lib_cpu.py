@@ -83,3 +83,33 @@ def test_struct_sizes_match_header():
     assert ctypes.sizeof(_lib.MplppOptions) == 40
     assert ctypes.sizeof(_lib.MplppInfo) == 48
     assert ctypes.sizeof(_lib.MplppStateHeader) == 40
+
+
+def test_ctypes_layout_equals_the_c_header(tmp_path):
+    """Sizes and field offsets of the ABI structs, from a C compiler reading
+    include/mplpp.h, against the ctypes declarations."""
+    import os
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    checks = {"mplpp_model": (_lib.MplppModel, ["n_edges", "labels", "pairwise", "schedule_kind", "edge_order",
+                                                "pair_kind", "pair_param"]),
+              "mplpp_options": (_lib.MplppOptions, ["record_every", "threads", "rule", "spin_limit"])}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "mplpp.h"', "int main(void) {"]
+    for st, (_, fields) in checks.items():
+        lines.append(f'printf("%zu\\n", sizeof({st}));')
+        lines += [f'printf("%zu\\n", offsetof({st}, {f}));' for f in fields]
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-x", "c", "-I", os.path.join(root, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    want = []
+    for _, (cls, fields) in checks.items():
+        want.append(ctypes.sizeof(cls))
+        want += [getattr(cls, f).offset for f in fields]
+    assert got == want
