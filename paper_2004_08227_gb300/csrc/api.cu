@@ -92,6 +92,15 @@ extern "C" const char *mplpp_last_error(const mplpp_solver *s)
 }
 
 // Mapping for one candidate cluster size C: per-CTA tile and vector sizes.
+// The smallest block (a multiple of 32 threads, 64..512) whose warps hold all
+// of a CTA's rows in the register-resident passes for wide rows, or 0.
+static int rr_fit_threads(int rows, int Q, int tile_floats)
+{
+    for (int T = 64; T <= 512; T += 32)
+        if (hs_rr_fits(rows, Q, T, tile_floats)) return T;
+    return 0;
+}
+
 static void mapping_for(mplpp_solver *s, int C, int threads = 0)
 {
     long long tile = 0, rows = 0;
@@ -104,11 +113,17 @@ static void mapping_for(mplpp_solver *s, int C, int threads = 0)
         lmax = std::max(lmax, std::max(ed.Lu, ed.ld));
     }
     s->lmax = lmax;
+    const int tile_floats = static_cast<int>(round4(std::max(4LL, tile)));
     int T = threads > 0 ? threads : s->opt.threads;
-    if (T <= 0) T = (4 * tile >= 48 * 1024) ? 512 : (4 * tile <= 4096 ? 128 : 256);
+    if (T <= 0) {
+        T = (4 * tile >= 48 * 1024) ? 512 : (4 * tile <= 4096 ? 128 : 256);
+        // register-resident passes for wide rows: just enough warps for the rows
+        const int fit = rr_fit_threads(static_cast<int>(rows), ldmax >> 2, tile_floats);
+        if (fit) T = fit;
+    }
     s->C = C;
     s->T = T;
-    s->tile_floats = static_cast<int>(round4(std::max(4LL, tile)));
+    s->tile_floats = tile_floats;
     s->rmax = static_cast<int>(round4(std::max(4LL, rows)));
     s->ldmax = ldmax;
     s->rr = hs_rr_fits(static_cast<int>(rows), ldmax >> 2, T, s->tile_floats);
@@ -1022,7 +1037,21 @@ extern "C" mplpp_status mplpp_autotune(mplpp_solver *s, int32_t iterations, char
     CK(s, cudaEventCreate(&e1));
     for (int mode : {MPLPP_MODE_PERSISTENT, MPLPP_MODE_LOOPED, MPLPP_MODE_WARP, MPLPP_MODE_STRUCTURED})
         for (int C : {1, 2, 3, 4, 5, 6, 8})
-            for (int T : {128, 256, 512}) {
+            for (int T : {128, 256, 512, 0}) {
+                if (T == 0) {  // the exact fit of the register-resident passes, if another size
+                    if (mode == MPLPP_MODE_WARP || mode == MPLPP_MODE_STRUCTURED) continue;
+                    long long tile = 0, rows = 0;
+                    int ldm = 4;
+                    for (auto &ed : s->h_edges) {
+                        const long long R = (ed.Lu + C - 1) / C;
+                        tile = std::max(tile, R * ed.ld);
+                        rows = std::max(rows, R);
+                        ldm = std::max(ldm, ed.ld);
+                    }
+                    T = rr_fit_threads(static_cast<int>(rows), ldm >> 2,
+                                       static_cast<int>(round4(std::max(4LL, tile))));
+                    if (T == 0 || T == 128 || T == 256 || T == 512) continue;
+                }
                 if (mode == MPLPP_MODE_STRUCTURED && (C != 1 || T != 256 || !s->all_structured)) continue;
                 if (mode == MPLPP_MODE_WARP && C != 1) continue;  // one warp per edge
                 if (mode == MPLPP_MODE_WARP && T == 512) T = 32;  // small blocks: shared memory per warp
