@@ -342,13 +342,14 @@ def pose_dense_study(Solver, stream, args):
 
 
 def structured_study(Solver, stream, args):
-    """Stereo-like grids with truncated-linear and Potts costs: the structured
-    Handshake path (O(L) minimizations, no table reads) against the dense
+    """Stereo-like grids with truncated-linear, Potts and truncated-quadratic
+    costs: the structured Handshake path (no table reads) against the dense
     drivers on the same costs given as tables (autotuned), equal iterations."""
     from paper_2004_08227_gb300 import workloads as W
     T = 50
     rows = []
-    for name, kw in (("truncated_linear_tau4", dict(weight=1.0, tau=4.0)), ("potts", dict(weight=1.0, tau=1.0))):
+    for name, kw in (("truncated_linear_tau4", dict(weight=1.0, tau=4.0)), ("potts", dict(weight=1.0, tau=1.0)),
+                     ("truncated_quadratic_tau16", dict(weight=0.1, tau=16.0, quad=True))):
         m = W.grid_trunc_linear(128, 128, 64, seed=0, **kw)
         row = {"costs": name}
         for key, structured in (("structured", True), ("dense", False)):

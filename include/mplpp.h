@@ -69,20 +69,23 @@ enum {
     MPLPP_MODE_WARP = 3,       /* as PERSISTENT with one warp per edge instead of a cluster of
                                   CTAs per edge (for many small tables: every label count
                                   <= 128); options.cluster is ignored                          */
-    MPLPP_MODE_STRUCTURED = 4  /* every model MPLPP_PAIR_TRUNC_LINEAR, rule H, label counts
+    MPLPP_MODE_STRUCTURED = 4  /* every model MPLPP_PAIR_TRUNC_*, rule H, label counts
                                   <= 256: one launch per matching, one warp per edge, O(L)
                                   minimizations (AUTO picks it when all models qualify)       */
 };
 
 /* How a model's pairwise costs are given.  TRUNC_LINEAR: theta_uv(s,t) =
- * w_uv * min(|s - t|, tau_uv) (labels on a line; Potts is tau = 1), the FP32
- * product rounded once, as if the caller had passed those tables.  The
- * solver materializes the tables on the device (bound, rounding, the dense
- * drivers, backward) and, in MPLPP_MODE_STRUCTURED, runs the Handshake update
- * with O(L) minimizations that never read them. */
+ * w_uv * min(|s - t|, tau_uv) (labels on a line; Potts is tau = 1);
+ * TRUNC_QUAD: w_uv * min((s - t)^2, tau_uv).  In both the FP32 product is
+ * rounded once, as if the caller had passed those tables.  The solver
+ * materializes the tables on the device (bound, rounding, the dense drivers)
+ * and, in MPLPP_MODE_STRUCTURED, runs the Handshake update without reading
+ * them: O(L) minimizations for truncated-linear costs, a window of the labels
+ * within the truncation around each label for truncated-quadratic ones. */
 enum {
     MPLPP_PAIR_DENSE = 0,
-    MPLPP_PAIR_TRUNC_LINEAR = 1
+    MPLPP_PAIR_TRUNC_LINEAR = 1,
+    MPLPP_PAIR_TRUNC_QUAD = 2
 };
 
 /* Which block-coordinate-ascent update mplpp_run applies to each edge (Sec. 4;
@@ -113,7 +116,7 @@ typedef struct {
     const int32_t *edge_order;   /* MPLPP_SCHED_USER only: [n_edges] host, edge ids            */
     int32_t pair_kind;           /* MPLPP_PAIR_*; 0 = dense tables in `pairwise`                */
     int32_t reserved;            /* 0                                                          */
-    const float *pair_param;     /* MPLPP_PAIR_TRUNC_LINEAR only: [n_edges][2] = (w, tau) per
+    const float *pair_param;     /* MPLPP_PAIR_TRUNC_*: [n_edges][2] = (w, tau) per
                                     edge, w >= 0, tau >= 0, finite (host, or device if
                                     inputs_on_device); `pairwise` must then be NULL            */
 } mplpp_model;

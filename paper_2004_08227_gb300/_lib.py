@@ -22,7 +22,7 @@ STATUS = {0: "MPLPP_OK", -1: "MPLPP_E_INVALID", -2: "MPLPP_E_NOMEM", -3: "MPLPP_
           -4: "MPLPP_E_TIMEOUT", -5: "MPLPP_E_NONFINITE", -6: "MPLPP_E_STATE", -7: "MPLPP_E_UNSUPPORTED"}
 SCHED = {"round_robin": 0, "greedy_color": 1, "alg1": 2, "user": 3}
 MODE = {"auto": 0, "looped": 1, "persistent": 2, "warp": 3, "structured": 4}
-PAIR = {"dense": 0, "trunc_linear": 1}  # pairwise given as tables, or as w min(|s - t|, tau) per edge
+PAIR = {"dense": 0, "trunc_linear": 1, "trunc_quad": 2}  # tables, or w min(|s - t|, tau) / w min((s - t)^2, tau)
 MODE_NAME = {v: k for k, v in MODE.items()}
 RULE = {"H": 0, "M": 1, "U": 2}  # Sec. 4: eqs. (H), (M), (U)
 

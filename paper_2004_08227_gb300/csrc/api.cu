@@ -316,7 +316,7 @@ static mplpp_status apply_rule_mapping(mplpp_solver *s, int optin)
     return MPLPP_OK;
 }
 
-// The structured Handshake kernel: every model truncated-linear, one warp per
+// The structured Handshake kernel: every model truncated-linear or -quadratic, one warp per
 // edge, vectors of up to kStructMaxL labels in shared memory.
 static bool struct_fits(mplpp_solver *s)
 {
@@ -328,7 +328,7 @@ static bool struct_fits(mplpp_solver *s)
 static mplpp_status apply_struct_mapping(mplpp_solver *s, int optin)
 {
     if (!s->all_structured)
-        return fail(s, MPLPP_E_UNSUPPORTED, "structured mode needs every model's costs as MPLPP_PAIR_TRUNC_LINEAR");
+        return fail(s, MPLPP_E_UNSUPPORTED, "structured mode needs every model's costs as MPLPP_PAIR_TRUNC_*");
     if (!struct_fits(s))
         return fail(s, MPLPP_E_UNSUPPORTED,
                     "structured mode takes label counts up to " + std::to_string(kStructMaxL));
@@ -421,9 +421,10 @@ extern "C" mplpp_status mplpp_create(const mplpp_model *models, int32_t n_models
         const mplpp_model &md = models[m];
         ModelHost &mh = s->models[m];
         if (md.n_nodes < 1 || md.n_edges < 0) return fail(nullptr, MPLPP_E_INVALID, "model " + std::to_string(m) + ": bad sizes");
-        if (md.pair_kind != MPLPP_PAIR_DENSE && md.pair_kind != MPLPP_PAIR_TRUNC_LINEAR)
+        if (md.pair_kind < MPLPP_PAIR_DENSE || md.pair_kind > MPLPP_PAIR_TRUNC_QUAD)
             return fail(nullptr, MPLPP_E_INVALID, "model " + std::to_string(m) + ": unknown pair_kind");
-        mh.structured = md.pair_kind == MPLPP_PAIR_TRUNC_LINEAR;
+        mh.structured = md.pair_kind != MPLPP_PAIR_DENSE;
+        mh.pair_kind = md.pair_kind;
         const bool pairs_given = mh.structured ? (md.pair_param != nullptr) : (md.pairwise != nullptr);
         if (!md.labels || !md.unary || (md.n_edges > 0 && (!md.edge_u || !md.edge_v || !pairs_given)))
             return fail(nullptr, MPLPP_E_INVALID, "model " + std::to_string(m) + ": NULL array");
@@ -603,7 +604,13 @@ extern "C" mplpp_status mplpp_create(const mplpp_model *models, int32_t n_models
     }
     if (any_structured) {
         CKC(S->alloc(&S->d_pair_param, S->EE));
+        CKC(S->alloc(&S->d_pair_kind, S->EE));
         CKC(cudaMemsetAsync(S->d_pair_param, 0, sizeof(float2) * S->EE, st));
+        std::vector<int> kinds;
+        kinds.reserve(S->EE);
+        for (auto &mh : S->models) kinds.insert(kinds.end(), mh.E, mh.pair_kind);
+        CKC(cudaMemcpyAsync(S->d_pair_kind, kinds.data(), sizeof(int) * kinds.size(), cudaMemcpyHostToDevice, st));
+        CKC(cudaStreamSynchronize(st));  // kinds is a host temporary
         for (int m = 0; m < n_models; ++m) {
             const ModelHost &mh = S->models[m];
             if (!mh.structured || mh.E == 0) continue;
@@ -641,8 +648,8 @@ extern "C" mplpp_status mplpp_create(const mplpp_model *models, int32_t n_models
             pe = launch_pack(S->d_edges + mh.edge_base, mh.structured ? 0 : mh.E, S->d_nodes + mh.node_base, mh.n, su,
                              sp, S->d_tab, S->d_un0, S->d_agg, S->d_err, st);
         if (pe == cudaSuccess && mh.structured)
-            pe = launch_materialize(S->d_edges + mh.edge_base, S->d_pair_param + mh.edge_base, mh.E, S->d_tab,
-                                    S->d_err, st);
+            pe = launch_materialize(S->d_edges + mh.edge_base, S->d_pair_param + mh.edge_base,
+                                    S->d_pair_kind + mh.edge_base, mh.E, S->d_tab, S->d_err, st);
         ub += mh.unary_size;
         pb += mh.pair_size;
     }
@@ -690,7 +697,8 @@ static HsParams make_params(mplpp_solver *s)
 cudaError_t enqueue_looped_iteration(mplpp_solver *s, cudaStream_t st)
 {
     if (s->mode == MPLPP_MODE_STRUCTURED) {
-        StructParams sp = {s->d_edges, nullptr, 0, s->struct_lmax, s->d_pair_param, s->d_agg, s->d_msg};
+        StructParams sp = {s->d_edges, nullptr, 0, s->struct_lmax, s->d_pair_param, s->d_pair_kind, s->d_agg,
+                           s->d_msg};
         for (int ph = 0; ph + 1 < static_cast<int>(s->phase_off.size()); ++ph) {
             sp.items = s->d_phase_edges + s->phase_off[ph];
             sp.n_items = s->phase_off[ph + 1] - s->phase_off[ph];

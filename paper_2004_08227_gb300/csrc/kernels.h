@@ -74,7 +74,8 @@ cudaError_t rule_prepare(size_t smem_bytes);
 cudaError_t launch_rule(const RuleParams &p, int rule, int n_items, size_t smem, cudaStream_t st);
 
 // structured.cu: the Handshake update for truncated-linear costs
-// w min(|s - t|, tau) in O(L) per minimization, one warp per edge, looped.
+// w min(|s - t|, tau) in O(L) per minimization and for truncated-quadratic
+// costs w min((s - t)^2, tau) over a window, one warp per edge, looped.
 constexpr int kStructMaxL = 256;  // largest label count the structured kernel takes
 struct StructParams {
     const EdgeDesc *edges;
@@ -82,6 +83,7 @@ struct StructParams {
     int n_items;
     int lmax;              // >= every label count of the solver, multiple of 4
     const float2 *param;   // [edges] (w, tau) per edge id
+    const int *kind;       // [edges] MPLPP_PAIR_* per edge id
     ulonglong2 *agg;
     ulonglong2 *msg;
 };
@@ -91,9 +93,12 @@ __host__ __device__ inline size_t struct_bytes_per_warp(int lmax)
 }
 cudaError_t struct_prepare(int lmax);
 cudaError_t launch_struct(const StructParams &p, cudaStream_t st);
-// tables of n consecutive edges from their (w, tau): w min(|s - t|, tau),
-// rows padded with +inf; a negative or non-finite parameter sets ERR_NONFINITE
-cudaError_t launch_materialize(const EdgeDesc *edges, const float2 *param, int n, float *tab, int *err, cudaStream_t st);
+// tables of n consecutive edges from their (w, tau) and kind: w min(|s - t|,
+// tau) or w min((s - t)^2, tau), rows padded with +inf; a negative or
+// non-finite parameter sets ERR_NONFINITE
+cudaError_t launch_materialize(const EdgeDesc *edges, const float2 *param, const int *kind, int n, float *tab,
+                               int *err, cudaStream_t st);
+constexpr int kPairLinear = 1, kPairQuad = 2;  // the MPLPP_PAIR_TRUNC_* values
 
 // dual.cu
 cudaError_t launch_pack(const EdgeDesc *edges, int n_edges, const NodeDesc *nodes, int n_nodes,

@@ -15,7 +15,8 @@ struct ModelHost {
     int n = 0, E = 0;
     int node_base = 0, edge_base = 0;
     long long unary_size = 0, pair_size = 0;
-    bool structured = false;  // MPLPP_PAIR_TRUNC_LINEAR
+    bool structured = false;  // MPLPP_PAIR_TRUNC_*
+    int pair_kind = 0;        // MPLPP_PAIR_*
     std::vector<int> L, eu, ev, off, order;
 };
 }  // namespace mplpp
@@ -60,6 +61,7 @@ struct mplpp_solver {
     bool all_structured = false;  // every model MPLPP_PAIR_TRUNC_LINEAR (and at least one edge)
     int struct_lmax = 0;          // structured kernel: vector capacity (multiple of 4)
     float2 *d_pair_param = nullptr;  // [EE] (w, tau) per edge (structured models)
+    int *d_pair_kind = nullptr;      // [EE] MPLPP_PAIR_* per edge
 
     // device
     std::vector<void *> allocations;

@@ -1,7 +1,8 @@
 // structured.cu -- the Handshake update (Sec. 4, eq. (H), three-minimization
 // form) for truncated-linear pairwise costs theta_uv(s,t) = w_uv min(|s - t|,
 // tau_uv) (Potts: tau = 1), with O(L) minimizations instead of O(L^2) table
-// passes (the paper notes the speed-up that lower envelopes give in message
+// passes, and for truncated-quadratic costs w_uv min((s - t)^2, tau_uv) over
+// the labels within the truncation (a window of 2 sqrt(tau) labels) (the paper notes the speed-up that lower envelopes give in message
 // passing for such costs, Sec. 1 and Sec. 4).
 //
 // Each of the three minimizations has the form
@@ -62,15 +63,42 @@ __device__ __forceinline__ VI vi_shfl_xor(VI a, int o)
 
 // the dense table's entry theta(s,t) in FP32: the product rounded on its own
 // (never fused with a following addition, as a table entry is not)
-__device__ __forceinline__ float theta_tl(int s, int t, float w, float tau)
+__device__ __forceinline__ float theta_tl(int s, int t, float w, float tau, bool quad)
 {
-    return __fmul_rn(w, fminf(fabsf(static_cast<float>(s - t)), tau));
+    const float d = fabsf(static_cast<float>(s - t));
+    return __fmul_rn(w, fminf(quad ? __fmul_rn(d, d) : d, tau));
+}
+
+// The largest distance R with theta below w tau: |s - t| < tau (linear),
+// (s - t)^2 < tau (quadratic); -1 if none.  At most 1024 (beyond any label
+// count the kernel takes).
+__device__ __forceinline__ int trunc_radius(float tau, bool quad)
+{
+    if (!(tau > 0.f)) return -1;
+    if (!quad) return static_cast<int>(fminf(ceilf(tau), 1025.f)) - 1;
+    float r = fminf(floorf(sqrtf(tau)), 1024.f);  // distances squared are exact up to 4096
+    if (r * r >= tau) r -= 1.f;
+    if (r < 1024.f && (r + 1.f) * (r + 1.f) < tau) r += 1.f;
+    return static_cast<int>(r);
+}
+
+// out[s] = min over t in [s - R, s + R] and t_g of theta(s,t) + h[t]
+template <bool QUAD>
+__device__ __forceinline__ void dt_window(const float *h, int Lh, int Ls, float w, float tau, int R, VI g, float *out,
+                                          int lane)
+{
+    for (int s = lane; s < Ls; s += 32) {
+        float best = theta_tl(s, g.i, w, tau, QUAD) + g.v;
+        const int lo = s - R > 0 ? s - R : 0, hi = s + R < Lh - 1 ? s + R : Lh - 1;
+        for (int t = lo; t <= hi; ++t) best = fminf(best, theta_tl(s, t, w, tau, QUAD) + h[t]);
+        out[s] = best;
+    }
 }
 
 // out[s] = min_t [theta(s,t) + h[t]] for s < Ls, t < Lh (1 <= Lh, Ls <= 32 k);
 // lane owns t in [lane k, lane k + k).  pre / suf: [Lh] scratch of the warp.
-__device__ void dt_trunc_linear(const float *h, int Lh, int Ls, float w, float tau, float *out, VI *pre, VI *suf,
-                                int lane, int k)
+__device__ void dt_trunc(const float *h, int Lh, int Ls, float w, float tau, bool quad, float *out, VI *pre,
+                         VI *suf, int lane, int k)
 {
     const VI none = {INFINITY, 0x7fffffff};
     const int t0 = lane * k;
@@ -78,20 +106,18 @@ __device__ void dt_trunc_linear(const float *h, int Lh, int Ls, float w, float t
     VI g = none;
     for (int t = lane; t < Lh; t += 32) g = vi_min(g, VI{h[t], t});
     for (int o = 16; o > 0; o >>= 1) g = vi_min(g, vi_shfl_xor(g, o));
-    // Short truncation (Potts included): only t with |s - t| < tau can cost
-    // less than w tau, so the window |s - t| <= R = ceil(tau) - 1 plus the
-    // global minimizer hold the minimum.  Every t outside the window costs w
-    // tau + h(t) >= w tau + h(t_g) >= theta(s, t_g) + h(t_g) after rounding
+    // Short truncation (Potts included) and every quadratic cost: only t
+    // within distance R of s can cost less than w tau, so that window plus the
+    // global minimizer hold the minimum.  Every t outside the window costs
+    // w tau + h(t) >= w tau + h(t_g) >= theta(s, t_g) + h(t_g) after rounding
     // (rounding is monotone), so the result is the dense kernel's minimum of
     // the same rounded values, bit for bit.
-    const int R = static_cast<int>(ceilf(tau)) - 1;
-    if (R <= kWindowMax) {
-        for (int s = lane; s < Ls; s += 32) {
-            float best = theta_tl(s, g.i, w, tau) + g.v;
-            const int lo = s - R > 0 ? s - R : 0, hi = s + R < Lh - 1 ? s + R : Lh - 1;
-            for (int t = lo; t <= hi; ++t) best = fminf(best, theta_tl(s, t, w, tau) + h[t]);
-            out[s] = best;
-        }
+    const int R = trunc_radius(tau, quad);
+    if (quad || R <= kWindowMax) {
+        if (quad)
+            dt_window<true>(h, Lh, Ls, w, tau, R, g, out, lane);
+        else
+            dt_window<false>(h, Lh, Ls, w, tau, R, g, out, lane);
         __syncwarp();
         return;
     }
@@ -141,12 +167,12 @@ __device__ void dt_trunc_linear(const float *h, int Lh, int Ls, float w, float t
     // w t, so they only choose within each part)
     for (int s = lane; s < Ls; s += 32) {
         const int tp = pre[min(s, Lh - 1)].i;
-        VI best = {theta_tl(s, tp, w, tau) + h[tp], tp};
+        VI best = {theta_tl(s, tp, w, tau, false) + h[tp], tp};
         if (s < Lh) {
             const int ts = suf[s].i;
-            best = vi_min(best, VI{theta_tl(s, ts, w, tau) + h[ts], ts});
+            best = vi_min(best, VI{theta_tl(s, ts, w, tau, false) + h[ts], ts});
         }
-        best = vi_min(best, VI{theta_tl(s, g.i, w, tau) + g.v, g.i});
+        best = vi_min(best, VI{theta_tl(s, g.i, w, tau, false) + g.v, g.i});
         out[s] = best.v;
     }
     __syncwarp();
@@ -172,6 +198,7 @@ __global__ void __launch_bounds__(kStructThreads) struct_kernel(StructParams p)
     const EdgeDesc ed = p.edges[e];
     const float2 wt = p.param[e];
     const float w = wt.x, tau = wt.y;
+    const bool quad = p.kind[e] == kPairQuad;
     const int Lu = ed.Lu, Lv = ed.Lv;
     ulonglong2 *agg = p.agg;
     ulonglong2 *msg = p.msg;
@@ -207,14 +234,14 @@ __global__ void __launch_bounds__(kStructThreads) struct_kernel(StructParams p)
     const int ku = (Lu + 31) >> 5, kv = (Lv + 31) >> 5;
 
     // pass 1: a(s) = 1/2 (min_t [theta(s,t) + w1(t)] + vh(0) + uh(s)); alpha = uh - a
-    dt_trunc_linear(h, Lv, Lu, w, tau, m, pre, suf, lane, kv);
+    dt_trunc(h, Lv, Lu, w, tau, quad, m, pre, suf, lane, kv);
     for (int s = lane; s < Lu; s += 32) {
         const float2 a = df_half(df_add(df_add_f(vref, m[s]), uh[s]));
         h[s] = df_to_f(df_sub(uh[s], a));
     }
     __syncwarp();
     // pass 2: b(t) = min_s [theta(s,t) + alpha(s)] + vh(t); beta = vh - b; node v's new vector
-    dt_trunc_linear(h, Lu, Lv, w, tau, m, pre, suf, lane, ku);
+    dt_trunc(h, Lu, Lv, w, tau, quad, m, pre, suf, lane, ku);
     for (int t = lane; t < Lv; t += 32) {
         const float2 b = df_add_f(vh[t], m[t]);
         h[t] = df_to_f(df_sub(vh[t], b));
@@ -223,7 +250,7 @@ __global__ void __launch_bounds__(kStructThreads) struct_kernel(StructParams p)
     }
     __syncwarp();
     // pass 3: c(s) = min_t [theta(s,t) + beta(t)] + uh(s); node u's new vector
-    dt_trunc_linear(h, Lv, Lu, w, tau, m, pre, suf, lane, kv);
+    dt_trunc(h, Lv, Lu, w, tau, quad, m, pre, suf, lane, kv);
     for (int s = lane; s < Lu; s += 32) {
         const float2 c = df_add_f(uh[s], m[s]);
         st_se(agg + ed.au + s, se_make(c, 1u));
@@ -233,11 +260,13 @@ __global__ void __launch_bounds__(kStructThreads) struct_kernel(StructParams p)
 
 // tables of structured edges from their parameters, as the caller would have
 // given them densely (rows padded to ld with +inf)
-__global__ void materialize_kernel(const EdgeDesc *edges, const float2 *param, int n, float *tab, int *err)
+__global__ void materialize_kernel(const EdgeDesc *edges, const float2 *param, const int *kind, int n, float *tab,
+                                   int *err)
 {
     for (int e = blockIdx.x; e < n; e += gridDim.x) {
         const EdgeDesc ed = edges[e];
         const float2 wt = param[e];
+        const bool quad = kind[e] == kPairQuad;
         if (!(isfinite(wt.x) && isfinite(wt.y) && wt.x >= 0.f && wt.y >= 0.f)) {
             if (threadIdx.x == 0) atomicCAS(err, 0, ERR_NONFINITE);
             continue;
@@ -246,7 +275,7 @@ __global__ void materialize_kernel(const EdgeDesc *edges, const float2 *param, i
         for (long long i = threadIdx.x; i < n_ent; i += blockDim.x) {
             const int s = static_cast<int>(i / ed.ld);
             const int t = static_cast<int>(i - static_cast<long long>(s) * ed.ld);
-            tab[ed.toff + i] = t < ed.Lv ? theta_tl(s, t, wt.x, wt.y) : INFINITY;
+            tab[ed.toff + i] = t < ed.Lv ? theta_tl(s, t, wt.x, wt.y, quad) : INFINITY;
         }
     }
 }
@@ -267,10 +296,11 @@ cudaError_t launch_struct(const StructParams &p, cudaStream_t st)
     return cudaGetLastError();
 }
 
-cudaError_t launch_materialize(const EdgeDesc *edges, const float2 *param, int n, float *tab, int *err, cudaStream_t st)
+cudaError_t launch_materialize(const EdgeDesc *edges, const float2 *param, const int *kind, int n, float *tab,
+                               int *err, cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
-    materialize_kernel<<<n < 4096 ? n : 4096, 256, 0, st>>>(edges, param, n, tab, err);
+    materialize_kernel<<<n < 4096 ? n : 4096, 256, 0, st>>>(edges, param, kind, n, tab, err);
     return cudaGetLastError();
 }
 

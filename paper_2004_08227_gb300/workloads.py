@@ -36,8 +36,9 @@ class Model:
     schedule: str = "greedy_color"
     name: str = ""
     meta: dict = field(default_factory=dict)
-    pair_kind: str = "dense"    # "trunc_linear": pairwise(s,t) = w_e min(|s - t|, tau_e) (also given densely)
-    pair_param: np.ndarray = None  # float32 [E, 2]: (w_e, tau_e) for "trunc_linear"
+    pair_kind: str = "dense"    # "trunc_linear": pairwise(s,t) = w_e min(|s - t|, tau_e); "trunc_quad":
+                                # w_e min((s - t)^2, tau_e) (both also given densely in pairwise)
+    pair_param: np.ndarray = None  # float32 [E, 2]: (w_e, tau_e) for the structured kinds
 
     @property
     def n(self) -> int:
@@ -148,23 +149,28 @@ def pose_dense(n: int, L: int = 13, seed: int = 0, sigma: float = 0.05) -> Model
     return m
 
 
-def trunc_linear_tables(labels: np.ndarray, eu: np.ndarray, ev: np.ndarray, param: np.ndarray) -> np.ndarray:
-    """Dense tables of truncated-linear costs w min(|s - t|, tau), in float32
-    arithmetic (the distance exact, the product rounded once)."""
+def trunc_linear_tables(labels: np.ndarray, eu: np.ndarray, ev: np.ndarray, param: np.ndarray,
+                        quad: bool = False) -> np.ndarray:
+    """Dense tables of truncated-linear costs w min(|s - t|, tau) (or, with
+    quad, w min((s - t)^2, tau)), in float32 arithmetic (the distance exact,
+    its square and the product each rounded once)."""
     out = []
     for e in range(eu.shape[0]):
         Lu, Lv = int(labels[eu[e]]), int(labels[ev[e]])
         d = np.abs(np.arange(Lu, dtype=np.float32)[:, None] - np.arange(Lv, dtype=np.float32)[None, :])
+        if quad:
+            d = (d * d).astype(np.float32)
         out.append((np.float32(param[e, 0]) * np.minimum(d, np.float32(param[e, 1]))).astype(np.float32).ravel())
     return np.concatenate(out) if out else np.zeros(0, np.float32)
 
 
 def grid_trunc_linear(rows: int, cols: int, L: int, weight: float, tau: float, seed: int = 0,
-                      Lmin: int = 0) -> Model:
+                      Lmin: int = 0, quad: bool = False) -> Model:
     """Stereo-like model: a 4-connected rows x cols grid, labels on a line
     (L per node, or U{Lmin..L} when Lmin > 0), unary U[0, 4), pairwise
-    w_e min(|s - t|, tau) with w_e = weight * U[0.5, 1.5) (tau = 1: Potts);
-    greedy edge colouring.  Carries both the parameters and the dense tables."""
+    w_e min(|s - t|, tau) (tau = 1: Potts), or w_e min((s - t)^2, tau) with
+    quad, w_e = weight * U[0.5, 1.5); greedy edge colouring.  Carries both the
+    parameters and the dense tables."""
     rng = np.random.default_rng(seed)
     n = rows * cols
     labels = (rng.integers(Lmin, L + 1, size=n) if Lmin > 0 else np.full(n, L)).astype(np.int32)
@@ -176,8 +182,9 @@ def grid_trunc_linear(rows: int, cols: int, L: int, weight: float, tau: float, s
     eu, ev = eu[order].astype(np.int32), ev[order].astype(np.int32)
     param = np.stack([weight * rng.uniform(0.5, 1.5, size=eu.shape[0]), np.full(eu.shape[0], tau)], axis=1)
     param = param.astype(np.float32)
-    return Model(labels, eu, ev, unary, trunc_linear_tables(labels, eu, ev, param), schedule="greedy_color",
-                 name=f"grid{rows}x{cols}_L{L}_tl{tau:g}_s{seed}", pair_kind="trunc_linear", pair_param=param)
+    return Model(labels, eu, ev, unary, trunc_linear_tables(labels, eu, ev, param, quad), schedule="greedy_color",
+                 name=f"grid{rows}x{cols}_L{L}_{'tq' if quad else 'tl'}{tau:g}_s{seed}",
+                 pair_kind="trunc_quad" if quad else "trunc_linear", pair_param=param)
 
 
 def knn(n: int = 2000, k: int = 50, L: int = 64, seed: int = 0) -> Model:

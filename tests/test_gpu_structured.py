@@ -1,8 +1,8 @@
 """GPU parity of the structured Handshake path (truncated-linear costs
-w min(|s - t|, tau), Potts for tau = 1; O(L) minimizations by prefix, suffix
-and global minima) against the FP64 oracle on the same costs given as dense
-tables, and against the dense GPU drivers.  Tolerances as in
-test_gpu_parity.py."""
+w min(|s - t|, tau), Potts for tau = 1: O(L) minimizations by prefix, suffix
+and global minima or a window; truncated-quadratic w min((s - t)^2, tau): a
+window) against the FP64 oracle on the same costs given as dense tables, and
+against the dense GPU drivers.  Tolerances as in test_gpu_parity.py."""
 import numpy as np
 import pytest
 
@@ -41,6 +41,9 @@ CASES = {
     "tl_L256_untruncated": dict(rows=3, cols=4, L=256, weight=0.05, tau=1000.0),
     "ragged_1_33": dict(rows=6, cols=6, L=33, weight=1.0, tau=3.0, Lmin=1),
     "ragged_2_70": dict(rows=5, cols=5, L=70, weight=0.3, tau=8.0, Lmin=2),
+    "quad_L40_tau16": dict(rows=5, cols=6, L=40, weight=0.1, tau=16.0, quad=True),
+    "quad_L64_untruncated": dict(rows=4, cols=4, L=64, weight=0.002, tau=1e6, quad=True),
+    "quad_ragged_tau30": dict(rows=5, cols=5, L=50, weight=0.05, tau=30.0, Lmin=3, quad=True),
 }
 
 
@@ -53,7 +56,9 @@ def test_structured_parity_with_oracle(case):
 
 
 @pytest.mark.parametrize("case,exact", [("potts_L16", True), ("tl_L40", True), ("ragged_2_70", True),
-                                        ("tl_L200", False), ("tl_L256_untruncated", False)])
+                                        ("quad_L40_tau16", True), ("quad_L64_untruncated", True),
+                                        ("quad_ragged_tau30", True), ("tl_L200", False),
+                                        ("tl_L256_untruncated", False)])
 def test_structured_equals_dense_drivers(case, exact):
     """Short truncation (tau <= 8, Potts included): the window of candidates
     plus the global minimizer give the dense kernel's minimum of the same
