@@ -232,9 +232,9 @@ def batched_vs_looped(Solver, stream, args):
     persistent = {}
     for name, mode, sizes in (("cluster", "persistent", (128, 256, 512)), ("warp", "warp", (32, 64, 128))):
         best = None
-        for T in sizes:
+        for nt in sizes:
             try:
-                sp = Solver(models, mode=mode, threads=T, cluster=1)
+                sp = Solver(models, mode=mode, threads=nt, cluster=1)
             except Exception as e:  # a mapping the shapes do not admit
                 best = best or {"unavailable": str(e)}
                 continue
