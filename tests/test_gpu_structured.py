@@ -143,3 +143,25 @@ def test_autotune_measures_the_structured_driver():
     rep = s.autotune(2)
     assert any(c[2] == "structured" for c in rep["candidates"])
     assert s.info()["mode"] == rep["best"]["mode"]
+
+
+def test_mixed_structured_and_dense_models_in_one_solver():
+    """A batch mixing a structured model with dense ones runs the dense
+    drivers on the materialized tables; every model matches the oracle, and
+    the M update runs on them as well."""
+    ms = [W.grid_trunc_linear(seed=11, **CASES["tl_L40"]), W.uneven_complete(6, 3, 30, seed=4),
+          W.grid_trunc_linear(seed=12, **CASES["quad_ragged_tau30"])]
+    T = 10
+    s = Solver(ms)
+    assert s.info()["mode"] != "structured"
+    s.run(T)
+    D = s.bound(exact=True)
+    for i, m in enumerate(ms):
+        Do = oracle.bound(m, *oracle.run(m, _order(m), T))
+        assert abs(D[i] - Do) <= RTOL_D * max(abs(Do), 1.0), (i, D[i], Do)
+    r = Solver(ms, rule="M")
+    r.run(T)
+    D = r.bound(exact=True)
+    for i, m in enumerate(ms):
+        Do = oracle.bound(m, *oracle.run(m, _order(m), T, rule="M"))
+        assert abs(D[i] - Do) <= RTOL_D * max(abs(Do), 1.0), (i, D[i], Do)
