@@ -529,7 +529,9 @@ def run_ours(args):
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": et * 1e3,
                "timer": "host wall clock"}
 
-    launches_per_step = (1 if info["mode"] == "persistent" else T * info["phases"]) + 3 + 2
+    # per step: reset (1), the run (restamp + one persistent launch, or one
+    # launch per matching and iteration), exact bound (3), rounding + energy (2)
+    launches_per_step = 1 + (2 if info["mode"] in ("persistent", "warp") else T * info["phases"]) + 3 + 2
     line = {
         "metric": "edge_updates_per_s", "value": value, "unit": "edge_updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
