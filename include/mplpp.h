@@ -48,7 +48,8 @@ typedef enum {
     MPLPP_E_TIMEOUT = -4,     /* a device-side wait exceeded options.spin_limit polls          */
     MPLPP_E_NONFINITE = -5,   /* a result is NaN or infinite                                   */
     MPLPP_E_STATE = -6,       /* call not valid in the current state (e.g. backward w/o record) */
-    MPLPP_E_UNSUPPORTED = -7  /* the shape exceeds a compiled limit (message says which)       */
+    MPLPP_E_UNSUPPORTED = -7  /* a shape beyond a compiled limit, or a driver / update / cost
+                                 combination not built (the message says which)               */
 } mplpp_status;
 
 /* Edge schedule kinds (Sec. 6, Alg. 1). */
@@ -61,7 +62,8 @@ enum {
 
 /* How mplpp_run drives the matchings. */
 enum {
-    MPLPP_MODE_AUTO = 0,       /* persistent when the device allows it, else looped            */
+    MPLPP_MODE_AUTO = 0,       /* STRUCTURED when every model qualifies, else persistent when
+                                  the device allows it, else looped                            */
     MPLPP_MODE_LOOPED = 1,     /* one kernel launch per matching (launch boundary = barrier)  */
     MPLPP_MODE_PERSISTENT = 2, /* one launch for all iterations; every state entry carries the
                                   update count that wrote it, which orders the matchings on
@@ -70,8 +72,8 @@ enum {
                                   CTAs per edge (for many small tables: every label count
                                   <= 128); options.cluster is ignored                          */
     MPLPP_MODE_STRUCTURED = 4  /* every model MPLPP_PAIR_TRUNC_*, rule H, label counts
-                                  <= 256: one launch per matching, one warp per edge, O(L)
-                                  minimizations (AUTO picks it when all models qualify)       */
+                                  <= 256: one launch per matching, one warp per edge, no
+                                  table reads (see MPLPP_PAIR_*)                               */
 };
 
 /* How a model's pairwise costs are given.  TRUNC_LINEAR: theta_uv(s,t) =
@@ -93,8 +95,9 @@ enum {
  * the solver's purpose; M and U are there for the paper's comparison (Prop. 2:
  * after one update of the same edge D_H >= D_M >= D_U; Thm. 2: the same for
  * one iteration from equal states).  M and U run in the looped driver only
- * (MPLPP_MODE_AUTO or _LOOPED; persistent or warp mode: MPLPP_E_UNSUPPORTED),
- * one CTA per edge, and have no backward (record_every must be 0). */
+ * (MPLPP_MODE_AUTO or _LOOPED; persistent, warp or structured mode:
+ * MPLPP_E_UNSUPPORTED), one CTA per edge, and have no backward (record_every
+ * must be 0). */
 enum {
     MPLPP_RULE_H = 0, /* eq. (H), the Handshake (MPLP++) update: three minimizations     */
     MPLPP_RULE_M = 1, /* eq. (M), the MPLP update: theta_u := 1/2 min_t g(.,t),
@@ -128,7 +131,7 @@ typedef struct {
                                  mplpp_backward writes device gradients                         */
     int32_t record_every;     /* > 0: enables mplpp_backward, which replays the run in FP64 with
                                  a state checkpoint every k iterations (memory ~ T/k states);
-                                 0: backward disabled                                          */
+                                 0: backward disabled.  Rule H and dense costs only.           */
     int32_t cluster;          /* CTAs sharing one edge (1..8); 0 = chosen from the shapes      */
     int32_t threads;          /* threads per CTA: 0 = chosen from the shapes, else a multiple
                                  of 32 in 64..512 (32..512 for MPLPP_MODE_WARP)                */
