@@ -530,8 +530,9 @@ def run_ours(args):
                "timer": "host wall clock"}
 
     # per step: reset (1), the run (restamp + one persistent launch, or one
-    # launch per matching and iteration), exact bound (3), rounding + energy (2)
-    launches_per_step = 1 + (2 if info["mode"] in ("persistent", "warp") else T * info["phases"]) + 3 + 2
+    # launch per matching and iteration), exact bound (3), rounding + energy
+    launches_per_step = (1 + (2 if info["mode"] in ("persistent", "warp") else T * info["phases"]) + 3
+                         + info["labeling_launches"])
     line = {
         "metric": "edge_updates_per_s", "value": value, "unit": "edge_updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,

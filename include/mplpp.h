@@ -248,6 +248,9 @@ typedef struct {
     int32_t threads;            /* threads per CTA                                            */
     int32_t grid;               /* persistent mode: CTAs launched                             */
     int32_t launches_per_iteration; /* kernel launches one iteration takes (looped: phases)   */
+    int32_t labeling_launches;  /* kernel launches of one mplpp_labeling: the rounding (one,
+                                   or one per level of the rounding order) and the energy      */
+    int32_t reserved;           /* 0                                                          */
 } mplpp_info_t;
 mplpp_status mplpp_info(const mplpp_solver *s, mplpp_info_t *info);
 

@@ -50,7 +50,7 @@ class MplppOptions(ctypes.Structure):
 class MplppInfo(ctypes.Structure):
     _fields_ = [("iterations", c_i64), ("bytes_per_iteration", c_i64), ("edges", c_i64), ("phases", c_i32),
                 ("mode", c_i32), ("cluster", c_i32), ("threads", c_i32), ("grid", c_i32),
-                ("launches_per_iteration", c_i32)]
+                ("launches_per_iteration", c_i32), ("labeling_launches", c_i32), ("reserved", c_i32)]
 
 
 class MplppStateHeader(ctypes.Structure):

@@ -528,6 +528,28 @@ extern "C" mplpp_status mplpp_create(const mplpp_model *models, int32_t n_models
             s->in_rec[k] = InRec{ed.toff, ed.mu, ed.mv, ed.ld, ed.gu};
         }
     }
+    // levels of the rounding order: level(u) = 1 + the largest level of u's
+    // earlier neighbours (0 without any).  Worth a launch per level only when
+    // there are far fewer levels than nodes in the largest model.
+    {
+        std::vector<int> level(s->N, 0);
+        int n_levels = 0, max_n = 0;
+        for (int u = 0; u < s->N; ++u) {
+            for (int k = s->in_off[u]; k < s->in_off[u + 1]; ++k)
+                level[u] = std::max(level[u], level[s->in_rec[k].gu] + 1);
+            n_levels = std::max(n_levels, level[u] + 1);
+        }
+        for (auto &mh : s->models) max_n = std::max(max_n, mh.n);
+        s->level_off.clear();
+        if (s->N > 0 && 4 * n_levels <= max_n) {
+            s->level_off.assign(n_levels + 1, 0);
+            for (int u = 0; u < s->N; ++u) s->level_off[level[u] + 1]++;
+            for (int l = 0; l < n_levels; ++l) s->level_off[l + 1] += s->level_off[l];
+            s->level_nodes.assign(s->N, 0);
+            std::vector<int> fill(s->level_off.begin(), s->level_off.end() - 1);
+            for (int u = 0; u < s->N; ++u) s->level_nodes[fill[level[u]]++] = u;
+        }
+    }
     s->mnode_off.assign(1, 0);
     s->medge_off.assign(1, 0);
     for (auto &mh : s->models) {
@@ -593,6 +615,10 @@ extern "C" mplpp_status mplpp_create(const mplpp_model *models, int32_t n_models
     CKC(h2d(S->d_phase_edges, S->phase_edges.data(), S->phase_edges.size() * sizeof(int)));
     CKC(h2d(S->d_in_off, S->in_off.data(), S->in_off.size() * sizeof(int)));
     CKC(h2d(S->d_in_rec, S->in_rec.data(), S->in_rec.size() * sizeof(InRec)));
+    if (!S->level_off.empty()) {
+        CKC(S->alloc(&S->d_level_nodes, S->level_nodes.size()));
+        CKC(h2d(S->d_level_nodes, S->level_nodes.data(), S->level_nodes.size() * sizeof(int)));
+    }
     CKC(h2d(S->d_mnode_off, S->mnode_off.data(), S->mnode_off.size() * sizeof(int)));
     CKC(h2d(S->d_medge_off, S->medge_off.data(), S->medge_off.size() * sizeof(int)));
     // structured costs: (w, tau) per edge
@@ -844,7 +870,8 @@ extern "C" mplpp_status mplpp_labeling(mplpp_solver *s, int32_t *labels, double 
     s->err.clear();
     CK(s, launch_round(s->d_edges, s->d_nodes, s->d_in_off, s->d_in_rec, s->d_mnode_off, s->d_medge_off,
                        static_cast<int>(s->models.size()), s->d_tab, s->d_agg, s->d_msg, s->d_un0, s->d_labels,
-                       s->d_energy, s->d_err, s->stream));
+                       s->d_energy, s->d_err, s->d_level_nodes, s->level_off.data(),
+                       static_cast<int>(s->level_off.empty() ? 0 : s->level_off.size() - 1), s->stream));
     CK(s, cudaMemcpyAsync(labels, s->d_labels, sizeof(int) * s->N, cudaMemcpyDeviceToHost, s->stream));
     if (energy)
         CK(s, cudaMemcpyAsync(energy, s->d_energy, sizeof(double) * s->models.size(), cudaMemcpyDeviceToHost,
@@ -1116,6 +1143,8 @@ extern "C" mplpp_status mplpp_info(const mplpp_solver *s, mplpp_info_t *info)
                  : s->mode == MPLPP_MODE_WARP     ? s->warp_blocks
                                                   : 0;
     info->launches_per_iteration = (s->mode == MPLPP_MODE_LOOPED || s->mode == MPLPP_MODE_STRUCTURED) ? s->P : 0;
+    info->labeling_launches = (s->level_off.empty() ? 1 : static_cast<int>(s->level_off.size()) - 1) + 1;
+    info->reserved = 0;
     return MPLPP_OK;
 }
 

@@ -244,10 +244,14 @@ __global__ void __launch_bounds__(kThreads) bound_sum_kernel(const int *model_no
 // L2 by the threads without labels while node u is decided.
 constexpr int kRoundThreads = 512;
 
+// Block b decides the nodes of model b in order, or (level_nodes given) the
+// single node level_nodes[b]: a node whose earlier neighbours were all decided
+// by earlier launches, so the nodes of one level are decided in parallel.
 __global__ void __launch_bounds__(kRoundThreads) round_kernel(const NodeDesc *nodes, const int *in_off,
                                                               const InRec *in_rec, const int *model_node_off,
-                                                              const float *tab, const ulonglong2 *agg,
-                                                              const ulonglong2 *msg, int *labels, int *err)
+                                                              const int *level_nodes, const float *tab,
+                                                              const ulonglong2 *agg, const ulonglong2 *msg,
+                                                              int *labels, int *err)
 {
     constexpr int T = kRoundThreads;
     __shared__ double rv[T / 32];
@@ -262,7 +266,8 @@ __global__ void __launch_bounds__(kRoundThreads) round_kernel(const NodeDesc *no
     const int tid = threadIdx.x;
     const int w = tid >> 5, l = tid & 31;
     constexpr int kBatch = 16;  // rows of different tables miss in L2: loads in flight
-    const int u0 = model_node_off[m], u1 = model_node_off[m + 1];
+    const int u0 = level_nodes ? level_nodes[m] : model_node_off[m];
+    const int u1 = level_nodes ? u0 + 1 : model_node_off[m + 1];
     auto stage_one = [&](int set, int slot, const InRec &r, int xv) {
         k_row[set][slot] = r.toff + static_cast<long long>(xv) * r.ld;
         k_mv[set][slot] = r.mv;
@@ -562,11 +567,22 @@ cudaError_t launch_bound(const EdgeDesc *edges, int n_edges, const NodeDesc *nod
 cudaError_t launch_round(const EdgeDesc *edges, const NodeDesc *nodes, const int *in_off, const InRec *in_rec,
                          const int *model_node_off, const int *model_edge_off, int n_models, const float *tab,
                          const ulonglong2 *agg, const ulonglong2 *msg, const float *un0, int *labels, double *energy, int *err,
-                         cudaStream_t st)
+                         const int *level_nodes, const int *level_off, int n_levels, cudaStream_t st)
 {
-    round_kernel<<<n_models, kRoundThreads, 0, st>>>(nodes, in_off, in_rec, model_node_off, tab, agg, msg, labels, err);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    if (n_levels > 0) {  // one launch per level, one block per node of the level
+        for (int lv = 0; lv < n_levels; ++lv) {
+            const int nb = level_off[lv + 1] - level_off[lv];
+            round_kernel<<<nb, kRoundThreads, 0, st>>>(nodes, in_off, in_rec, model_node_off,
+                                                       level_nodes + level_off[lv], tab, agg, msg, labels, err);
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+        }
+    } else {
+        round_kernel<<<n_models, kRoundThreads, 0, st>>>(nodes, in_off, in_rec, model_node_off, nullptr, tab, agg, msg,
+                                                         labels, err);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     energy_kernel<<<n_models, kThreads, 0, st>>>(edges, nodes, model_node_off, model_edge_off, tab, un0, labels,
                                                 energy);
     return cudaGetLastError();

@@ -108,10 +108,14 @@ cudaError_t launch_bound(const EdgeDesc *edges, int n_edges, const NodeDesc *nod
                          const float *tab, const ulonglong2 *agg, const ulonglong2 *msg, double *emin, double *nmin,
                          const int *model_node_off, const int *model_edge_off, int n_models, int exact,
                          int lmax, double *out, cudaStream_t st);  // lmax >= every label count and row stride
+// Sequential rounding (one block per model walking its nodes in order), or
+// with n_levels > 0 one launch per level of level_nodes (device) delimited by
+// level_off (host, [n_levels + 1]): the nodes of a level have all earlier
+// neighbours in earlier levels.  Then the energies.
 cudaError_t launch_round(const EdgeDesc *edges, const NodeDesc *nodes, const int *in_off, const InRec *in_rec,
                          const int *model_node_off, const int *model_edge_off, int n_models, const float *tab,
                          const ulonglong2 *agg, const ulonglong2 *msg, const float *un0, int *labels, double *energy,
-                         int *err, cudaStream_t st);
+                         int *err, const int *level_nodes, const int *level_off, int n_levels, cudaStream_t st);
 cudaError_t launch_init_state(const float *un0, ulonglong2 *agg, long long n_agg, ulonglong2 *msg, long long n_msg,
                               cudaStream_t st);
 // Sets the version of every state entry to 0, keeping the values.

@@ -62,6 +62,10 @@ struct mplpp_solver {
     int struct_lmax = 0;          // structured kernel: vector capacity (multiple of 4)
     float2 *d_pair_param = nullptr;  // [EE] (w, tau) per edge (structured models)
     int *d_pair_kind = nullptr;      // [EE] MPLPP_PAIR_* per edge
+    // rounding by levels (nodes whose earlier neighbours lie in earlier levels)
+    std::vector<int> level_off;      // [n_levels + 1] into d_level_nodes; empty: sequential rounding
+    std::vector<int> level_nodes;    // node ids by level
+    int *d_level_nodes = nullptr;
 
     // device
     std::vector<void *> allocations;

@@ -273,7 +273,8 @@ class Solver:
         self._check(self._lib.mplpp_info(self._h, ctypes.byref(inf)))
         return {"iterations": inf.iterations, "bytes_per_iteration": inf.bytes_per_iteration, "edges": inf.edges,
                 "phases": inf.phases, "mode": MODE_NAME.get(inf.mode, inf.mode), "cluster": inf.cluster,
-                "threads": inf.threads, "grid": inf.grid, "launches_per_iteration": inf.launches_per_iteration}
+                "threads": inf.threads, "grid": inf.grid, "launches_per_iteration": inf.launches_per_iteration,
+                "labeling_launches": inf.labeling_launches}
 
 
 if torch is not None:

@@ -187,14 +187,25 @@ def test_checkpoint_resume_bitwise():
     assert a.bound()[0] == c.bound()[0]
 
 
-def test_rounding_decisions_match_oracle_bit_for_bit():
+def _round_case(kind, seed):
+    if kind == "complete":  # one node per level: sequential rounding
+        return W.uneven_complete(12, 2, 33, seed=100 + seed)
+    if kind == "knn":  # few levels: one launch per level
+        return W.knn(300, 6, 12, seed=seed)
+    return W.grid_trunc_linear(12, 13, 9, 1.0, 3.0, seed=seed, Lmin=2)
+
+
+@pytest.mark.parametrize("kind", ["complete", "knn", "grid"])
+def test_rounding_decisions_match_oracle_bit_for_bit(kind):
     """Rounding from a given state: both sides take every argmin decision in
     binary64 with the same summation order (unary, then earlier neighbours by
-    increasing index), so the labels must be identical."""
+    increasing index), so the labels must be identical -- whether the nodes are
+    decided one after another or level by level (a node's earlier neighbours
+    all in earlier levels)."""
     rng = np.random.default_rng(0)
     for seed in range(4):
-        m = W.uneven_complete(12, 2, 33, seed=100 + seed)
-        s = Solver([m])
+        m = _round_case(kind, seed)
+        s = Solver([m], structured=False)
         agg = rng.standard_normal(int(m.labels.sum()))
         g = oracle.Graph.of(m)
         Lu = m.labels[m.edge_u]
