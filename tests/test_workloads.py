@@ -52,3 +52,31 @@ def test_pose_dense_shape():
     assert np.all((m.pairwise >= 0) & (m.pairwise <= 1))  # truncated quadratic costs
     off, _ = osched.build(m.schedule, m.n, m.edge_u, m.edge_v)
     assert len(off) - 1 == 23 and np.all(np.diff(off) == 12)
+
+
+@pytest.mark.parametrize("quad", [False, True])
+def test_grid_structured_costs_match_their_parameters(quad):
+    """The dense tables of the stereo-like grid are w min(d, tau) (or
+    w min(d^2, tau)) entry by entry, the product rounded once in float32 --
+    the value the structured GPU path evaluates -- on a 4-connected grid with
+    a valid greedy schedule."""
+    rows, cols = 5, 7
+    m = W.grid_trunc_linear(rows, cols, 9, 0.8, 5.0, seed=2, Lmin=3, quad=quad)
+    assert m.pair_kind == ("trunc_quad" if quad else "trunc_linear")
+    assert m.E == rows * (cols - 1) + (rows - 1) * cols and np.all(m.edge_u < m.edge_v)
+    assert m.pair_param.shape == (m.E, 2) and m.pair_param.dtype == np.float32
+    assert np.all(m.pair_param[:, 0] >= 0.4) and np.all(m.pair_param[:, 1] == 5.0)
+    L = m.labels
+    off = 0
+    for e in range(m.E):
+        Lu, Lv = int(L[m.edge_u[e]]), int(L[m.edge_v[e]])
+        w, tau = m.pair_param[e]
+        for s in range(Lu):
+            for t in range(Lv):
+                d = np.float32(abs(s - t))
+                d = np.float32(d * d) if quad else d
+                assert m.pairwise[off + s * Lv + t] == np.float32(w * np.float32(min(d, tau)))
+        off += Lu * Lv
+    assert off == m.pairwise.shape[0]
+    off_m, order = osched.build(m.schedule, m.n, m.edge_u, m.edge_v)
+    assert osched.is_valid(m.n, m.E, m.edge_u, m.edge_v, off_m, order)
