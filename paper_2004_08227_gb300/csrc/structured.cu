@@ -1,26 +1,29 @@
 // structured.cu -- the Handshake update (Sec. 4, eq. (H), three-minimization
-// form) for truncated-linear pairwise costs theta_uv(s,t) = w_uv min(|s - t|,
-// tau_uv) (Potts: tau = 1), with O(L) minimizations instead of O(L^2) table
-// passes, and for truncated-quadratic costs w_uv min((s - t)^2, tau_uv) over
-// the labels within the truncation (a window of 2 sqrt(tau) labels) (the paper notes the speed-up that lower envelopes give in message
-// passing for such costs, Sec. 1 and Sec. 4).
+// form) without reading the pairwise tables, for truncated-linear costs
+// theta_uv(s,t) = w_uv min(|s - t|, tau_uv) (Potts: tau = 1) and
+// truncated-quadratic costs w_uv min((s - t)^2, tau_uv).  The paper notes the
+// speed-up that lower envelopes give in message passing for such costs
+// (Sec. 1 and Sec. 4).
 //
 // Each of the three minimizations has the form
-//   m(s) = min_t [w min(|s - t|, tau) + h(t)],   t < Lh, s < Ls,
-// and for w, tau >= 0 splits into three parts:
+//   m(s) = min_t [theta(s,t) + h(t)],   t < Lh, s < Ls.
+// Window: only t within distance R of s can cost less than w tau (R the
+// largest distance with |s - t| < tau, or (s - t)^2 < tau), so the window
+// plus the global minimizer of h hold the minimum; used for every quadratic
+// cost and for linear truncation up to R = 7 (Potts included), it reproduces
+// the dense kernel's minimum of the same rounded values bit for bit.
+// Scans, for longer linear truncation (w, tau >= 0): the minimum splits into
 //   min_{t <= s} (h(t) - w t) + w s,   min_{t >= s} (h(t) + w t) - w s,
 //   min_t h(t) + w tau,
-// i.e. a prefix minimum, a suffix minimum and the global minimum of h, all
-// three warp-parallel scans.  For short truncation (tau <= 8, Potts included)
-// a window of candidates around s and the global minimizer are evaluated
-// directly instead, which reproduces the dense minimum bit for bit.  The scans only choose a minimizer in each part;
-// the three are then evaluated as the dense path evaluates an entry,
-// theta(s,t) + h(t) with theta rounded to FP32 once (the entry of the
-// materialized table), and the smallest is taken, so a minimum differs from
-// the dense kernel's only where rounding decides between candidates of equal
-// exact value (common: reparametrized vectors form linear ramps along which
-// w |s - t| + h(t) is constant), by rounding.  The vectors h, the O(L) double-float arithmetic and the write-back
-// are those of the dense kernel (uh, vh; w1 = vh - vh(0), alpha, beta).
+// a prefix minimum, a suffix minimum and the global minimum of h, found by
+// warp scans.  The scans only choose a minimizer in each part; the three are
+// then evaluated as the dense path evaluates an entry (theta rounded to FP32
+// once, as in the materialized table, then h added) and the smallest is
+// taken, so a minimum differs from the dense kernel's only where rounding
+// decides between candidates of equal exact value (common: reparametrized
+// vectors form linear ramps along which w |s - t| + h(t) is constant).
+// The vectors h, the O(L) double-float arithmetic and the write-back are
+// those of the dense kernel (uh, vh; w1 = vh - vh(0), alpha, beta).
 //
 // One warp per edge of a matching, looped (one launch per matching): the
 // tables are not read at all, so an update moves O(L) bytes.
