@@ -17,6 +17,9 @@ Parity status of each function (see the test files named):
   run, bound               pinned: Lemma B.4 monotone D, D <= brute-force MAP,
                            Prop. 1 single-edge exactness, Thm. 2, trees
                            [test_oracle_solver]
+  run_parallel             pinned: equals run bit for bit (any thread count),
+                           rejects a matching that repeats a node
+                           [test_oracle_solver]
   round, energy            pinned: brute-force argmin definition, energy
                            invariance under reparametrization [test_oracle_solver]
   grad                     pinned: FP64 central finite differences
@@ -45,12 +48,17 @@ _RULES = {"U": RULE_U, "M": RULE_M, "H": RULE_H}
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (no FP contraction, so x86 and Arm agree)."""
+    """Compile the oracle with gcc (no FP contraction, so x86 and Arm agree),
+    with OpenMP where the compiler has it (orc_run_parallel; without it that
+    function runs on one thread)."""
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
-                               "-o", tmp, _SRC, "-lm"])
+        base = ["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+        try:
+            subprocess.check_call(base[:1] + ["-fopenmp"] + base[1:], stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(base)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -72,8 +80,10 @@ def _load():
             lib.orc_energy.restype = D
             lib.orc_round.argtypes = [I, P, P, I, P, P, P, P, P, P, P]
             lib.orc_round.restype = I
-            lib.orc_round_f32.argtypes = [I, P, P, I, P, P, P, P, P, P]
-            lib.orc_round_f32.restype = I
+            lib.orc_run_parallel.argtypes = [I, I, P, P, I, P, P, P, I, P, P, I, P, P, I]
+            lib.orc_run_parallel.restype = I
+            lib.orc_max_threads.argtypes = []
+            lib.orc_max_threads.restype = I
             lib.orc_grad.argtypes = [I, P, P, I, P, P, P, I, P, I, P, P, P, P, P]
             lib.orc_grad.restype = I
             _lib = lib
@@ -160,6 +170,31 @@ def run(model, order, iterations: int, rule: str = "H", state=None, history: boo
     return th_u, th_uv
 
 
+def run_parallel(model, matching_off, order, iterations: int, rule: str = "H", state=None,
+                 threads: int = 0):
+    """The iterations of ``run`` with the edges of each matching updated by
+    host threads (OpenMP; Sec. 6: edges of a matching are independent).  The
+    result equals ``run``'s bit for bit.  threads <= 0: the OpenMP default."""
+    lib = _load()
+    g = Graph.of(model)
+    th_u, th_uv = initial_state(model) if state is None else (_f64(state[0]).copy(), _f64(state[1]).copy())
+    off = np.ascontiguousarray(matching_off, dtype=np.int32)
+    order = np.ascontiguousarray(order, dtype=np.int32)
+    rc = lib.orc_run_parallel(_RULES[rule], g.n, _p(g.L), _p(g.uoff), g.E, _p(g.eu), _p(g.ev), _p(g.poff),
+                              int(off.shape[0]) - 1, _p(off), _p(order), int(iterations), _p(th_u), _p(th_uv),
+                              int(threads))
+    if rc == -2:
+        raise ValueError("a matching repeats a node")
+    if rc:
+        raise MemoryError("oracle run failed")
+    return th_u, th_uv
+
+
+def max_threads() -> int:
+    """Host threads orc_run_parallel uses by default (1 without OpenMP)."""
+    return int(_load().orc_max_threads())
+
+
 def bound(model, th_u, th_uv) -> float:
     """Dual bound D (eq. LP-lower-bound) of reparametrized costs."""
     lib = _load()
@@ -191,21 +226,6 @@ def round_labels(model, th_u, th_uv, margins: bool = False):
                      _p(th_u), _p(th_uv), _p(x), _p(m)):
         raise MemoryError("oracle rounding failed")
     return (x, m) if margins else x
-
-
-def round_labels_f32(model, th_u32, th_uv32):
-    """Primal rounding with binary32 additions in a fixed order (unary, then
-    earlier neighbours by increasing index): the integer decision taken in the
-    precision of a binary32 implementation."""
-    lib = _load()
-    g = Graph.of(model)
-    tu = np.ascontiguousarray(th_u32, dtype=np.float32)
-    tuv = np.ascontiguousarray(th_uv32, dtype=np.float32)
-    x = np.zeros(g.n, np.int32)
-    if lib.orc_round_f32(g.n, _p(g.L), _p(g.uoff), g.E, _p(g.eu), _p(g.ev), _p(g.poff),
-                         _p(tu), _p(tuv), _p(x)):
-        raise MemoryError("oracle rounding failed")
-    return x
 
 
 def grad(model, order, iterations: int):

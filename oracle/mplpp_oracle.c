@@ -32,6 +32,9 @@
  * differences for the gradient.
  */
 #include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdlib.h>
 #include <string.h>
 
@@ -185,6 +188,69 @@ int orc_run(int rule, int n, const int *L, const long *uoff, int E,
 }
 
 /* ---------------------------------------------------------------------- */
+/* The same T iterations with the edges of one matching updated by       */
+/* several host threads (Sec. 6: the edges of a matching share no node,   */
+/* so their updates touch disjoint data and commute).  Matching k is      */
+/* order[moff[k] .. moff[k+1]); matchings run in order.  Every update is  */
+/* the same sequence of FP64 operations on the same data as in orc_run,   */
+/* so the result equals orc_run's bit for bit for any thread count.       */
+/* threads <= 0: the OpenMP default.  Returns -1 on allocation failure,   */
+/* -2 if an edge of a matching shares a node with another one.            */
+/* ---------------------------------------------------------------------- */
+int orc_run_parallel(int rule, int n, const int *L, const long *uoff, int E,
+                     const int *eu, const int *ev, const long *poff,
+                     int n_match, const int *moff, const int *order, int T,
+                     double *th_u, double *th_uv, int threads)
+{
+    int *seen = (int *)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+    if (!seen) return -1;
+    for (int u = 0; u < n; ++u) seen[u] = -1;
+    for (int k = 0; k < n_match; ++k)
+        for (int i = moff[k]; i < moff[k + 1]; ++i) {
+            int e = order[i];
+            if (seen[eu[e]] == k || seen[ev[e]] == k) {
+                free(seen);
+                return -2;
+            }
+            seen[eu[e]] = k;
+            seen[ev[e]] = k;
+        }
+    free(seen);
+    (void)E;
+    int failed = 0;
+#ifdef _OPENMP
+    if (threads > 0) omp_set_num_threads(threads);
+#else
+    (void)threads;
+#endif
+    for (int it = 0; it < T && !failed; ++it)
+        for (int k = 0; k < n_match && !failed; ++k) {
+            int lo = moff[k], hi = moff[k + 1];
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1) reduction(|| : failed)
+#endif
+            for (int i = lo; i < hi; ++i) {
+                int e = order[i];
+                int u = eu[e], v = ev[e];
+                if (orc_update_edge(rule, L[u], L[v], th_u + uoff[u], th_u + uoff[v],
+                                    th_uv + poff[e], NULL, NULL, NULL))
+                    failed = 1;
+            }
+        }
+    return failed ? -1 : 0;
+}
+
+/* Threads the OpenMP runtime uses by default (1 without OpenMP). */
+int orc_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* ---------------------------------------------------------------------- */
 /* Energy E(y|theta) (Sec. 3, eq. energy-min).                            */
 /* ---------------------------------------------------------------------- */
 double orc_energy(int n, const int *L, const long *uoff, int E, const int *eu,
@@ -262,38 +328,6 @@ int orc_round(int n, const int *L, const long *uoff, int E, const int *eu,
                 if (s != best && obj[s] < second) second = obj[s];
             margin[u] = second - obj[best];
         }
-    }
-    free(obj); free(eid); free(cnt);
-    return 0;
-}
-
-/* The same rounding rule with every addition rounded to binary32, in the */
-/* same order (unary first, then earlier neighbours by increasing index).  */
-/* Used only where an integer decision must be compared with a binary32   */
-/* computation: both sides then decide in the same precision.             */
-int orc_round_f32(int n, const int *L, const long *uoff, int E, const int *eu,
-                  const int *ev, const long *poff, const float *th_u,
-                  const float *th_uv, int *x)
-{
-    int Lmax = 1;
-    for (int u = 0; u < n; ++u) if (L[u] > Lmax) Lmax = L[u];
-    float *obj = (float *)malloc(sizeof(float) * (size_t)Lmax);
-    int *eid = NULL, *cnt = NULL;
-    if (!obj || orc_in_edges(n, E, eu, ev, &eid, &cnt)) {
-        free(obj);
-        return -1;
-    }
-    for (int u = 0; u < n; ++u) {
-        for (int s = 0; s < L[u]; ++s) obj[s] = th_u[uoff[u] + s];
-        for (int i = cnt[u]; i < cnt[u + 1]; ++i) {
-            int e = eid[i];
-            int v = eu[e];
-            for (int s = 0; s < L[u]; ++s)
-                obj[s] = obj[s] + th_uv[poff[e] + (long)x[v] * L[u] + s];
-        }
-        int best = 0;
-        for (int s = 1; s < L[u]; ++s) if (obj[s] < obj[best]) best = s;
-        x[u] = best;
     }
     free(obj); free(eid); free(cnt);
     return 0;

@@ -110,17 +110,27 @@ def test_rounding_energy_above_bound(seed):
     assert sol["energy"] >= Emap - 1e-9
 
 
-def test_rounding_f32_agrees_when_margins_large():
-    m = W.tiny(6, 4, seed=3, density=0.9, pairwise="normal")
-    th_u, th_uv = oracle.run(m, _order(m), 10)
-    x, marg = oracle.round_labels(m, th_u, th_uv, margins=True)
-    x32 = oracle.round_labels_f32(m, th_u.astype(np.float32), th_uv.astype(np.float32))
-    if np.all(marg > 1e-4):
-        assert np.array_equal(x, x32)
-
-
 def test_rounding_uses_earlier_neighbours_only():
     """Node 0 is rounded on its unary alone (it has no earlier neighbour)."""
     m = W.tiny(4, 3, seed=8, density=1.0, pairwise="normal")
     x = oracle.round_labels(m, m.unary, m.pairwise)
     assert x[0] == int(np.argmin(m.unary[:3]))
+
+
+@pytest.mark.parametrize("threads", [1, 3, 8])
+def test_run_parallel_equals_run_bitwise(threads):
+    """Sec. 6: the edges of one matching share no node, so updating them on
+    several threads gives the sequential result exactly."""
+    m = W.uneven_complete(11, 2, 9, seed=5)
+    off, order = osched.build(m.schedule, m.n, m.edge_u, m.edge_v)
+    a = oracle.run(m, order, 4)
+    b = oracle.run_parallel(m, off, order, 4, threads=threads)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    assert oracle.max_threads() >= 1
+
+
+def test_run_parallel_rejects_a_matching_that_repeats_a_node():
+    m = W.uneven_complete(5, 2, 3, seed=1)
+    off, order = osched.build(m.schedule, m.n, m.edge_u, m.edge_v)
+    with pytest.raises(ValueError):
+        oracle.run_parallel(m, [0, len(order)], order, 1)
