@@ -7,7 +7,12 @@ differentiation shape also central finite differences (h = 1e-4) of D_T at
 sampled entries.  The oracle is plain IEEE double C built without FP
 contraction, so the values do not depend on the machine that writes them.
 
-usage: python tests/golden/make_golden.py {1,2,3,4,5} [...]
+The states file (full_size_config<c>_states.json) holds the oracle's
+reparametrized unaries theta^phi_u after the full iteration count at a seeded
+sample of nodes (of a seeded sample of models for the batches), computed with
+oracle.run_parallel (bit-identical to oracle.run).
+
+usage: python tests/golden/make_golden.py [--states] {1,2,3,4,5} [...]
 """
 from __future__ import annotations
 
@@ -81,6 +86,43 @@ def fd_entries(m, T, count, seed=0, steps=(1e-4, 1e-5, 1e-6)):
     return {"D": D, "steps": list(steps), "entries": out}
 
 
+# sampled nodes per model and models per workload of the states file
+STATE_SAMPLE = {1: (20, 1), 2: (32, 1), 3: (128, 1), 4: (8, 16), 5: (8, 16)}
+
+
+def states_entry(c, models, T):
+    """theta^phi_u of the oracle at sampled nodes of sampled models."""
+    nodes_per, models_per = STATE_SAMPLE[c]
+    rng = np.random.default_rng(1000 + c)
+    picks = sorted(rng.choice(len(models), size=min(models_per, len(models)), replace=False).tolist())
+    out = []
+    for i in picks:
+        m = models[i]
+        off, order = osched.build(m.schedule, m.n, m.edge_u, m.edge_v)
+        th_u, _ = oracle.run_parallel(m, off, order, T)
+        nodes = sorted(rng.choice(m.n, size=min(nodes_per, m.n), replace=False).tolist())
+        uoff = np.concatenate([[0], np.cumsum(m.labels.astype(np.int64))])
+        vals = np.concatenate([th_u[uoff[u]:uoff[u + 1]] for u in nodes])
+        out.append({"model": int(i), "name": m.name, "inputs_sha256_16": _digest(m), "nodes": nodes,
+                    "theta_u": [float(v) for v in vals]})
+    return out
+
+
+def main_states(cfgs):
+    for c in cfgs:
+        t0 = time.time()
+        models, T = W.config(c)
+        if not isinstance(models, list):
+            models = [models]
+        res = {"workload_config": c, "iterations": T,
+               "writer": "tests/golden/make_golden.py --states (FP64 oracle only)",
+               "samples": states_entry(c, models, T)}
+        res["seconds"] = time.time() - t0
+        with open(os.path.join(HERE, f"full_size_config{c}_states.json"), "w") as f:
+            json.dump(res, f)
+        print(f"config {c} states: {time.time() - t0:.0f} s", flush=True)
+
+
 def main(cfgs):
     for c in cfgs:
         t0 = time.time()
@@ -99,4 +141,8 @@ def main(cfgs):
 
 
 if __name__ == "__main__":
-    main([int(a) for a in sys.argv[1:]] or [1, 2, 3, 4, 5])
+    args = sys.argv[1:]
+    if args and args[0] == "--states":
+        main_states([int(a) for a in args[1:]] or [1, 2, 3, 4, 5])
+    else:
+        main([int(a) for a in args] or [1, 2, 3, 4, 5])

@@ -1,17 +1,26 @@
 """Full-size parity: the workloads at their full sizes and iteration counts, in
-the launch configuration the benchmark uses, against expected values written
-by tests/golden/make_golden.py (FP64 oracle only).
+the launch configuration the benchmark uses, against the FP64 oracle.
+
+Expected values come from tests/golden/make_golden.py (FP64 oracle only): the
+dual bound, the rounded labeling with its decision margins and energy, the
+reparametrized unaries theta^phi_u at sampled nodes (the states files), and
+for the differentiation shape central finite differences.  Where the oracle
+finishes within about a minute on the host's cores (oracle.run_parallel, equal
+to oracle.run bit for bit) the test also runs it and compares every node's
+theta^phi_u, every implied reparametrized table entry and every label
+(conditional check of tests/_parity.py).
 
 Tolerances:
   * dual bound: 1e-5 relative (of max(|D|, 1)) on the tie-free workloads
     (continuous random costs); the pose-shaped workload has truncated costs
     (most entries exactly 1.0), where binary32 rounding decides near-ties that
-    binary64 decides otherwise, so its FP32 trajectory may sit on a
-    different BCA path: 1e-4 relative there (measured 5.1e-5 at 500
-    iterations);
-  * labels: identical, or the first differing node is one whose FP64 rounding
-    decision margin is below 1e-4 of the largest reparametrized unary (a
-    near-tie); energies of the returned labelings equal their definition;
+    binary64 decides otherwise, so its FP32 trajectory may sit on a different
+    BCA path: 1e-4 relative there;
+  * theta^phi_u: 1e-5 of each node's scale on the tie-free workloads;
+  * labels: every label within twice the FP32 error bound of the minimum of
+    the oracle's objective conditioned on the GPU's earlier labels where the
+    oracle state is at hand; otherwise the first differing node's oracle
+    margin within that bound; the number of differing labels is printed;
   * gradient: the oracle's gradient at 200 sampled entries (1e-4 relative,
     floor 1e-3) and FP64 central differences where the one-sided differences
     agree (no kink within h).
@@ -22,16 +31,20 @@ import os
 import numpy as np
 import pytest
 
+import oracle
+from oracle import schedule as osched
 from paper_2004_08227_gb300 import workloads as W
 from paper_2004_08227_gb300.solver import Solver
+
+import _parity as P
 
 pytestmark = pytest.mark.gpu
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 
-def _golden(c):
-    with open(os.path.join(GOLDEN, f"full_size_config{c}.json")) as f:
+def _golden(c, states=False):
+    with open(os.path.join(GOLDEN, f"full_size_config{c}{'_states' if states else ''}.json")) as f:
         return json.load(f)
 
 
@@ -45,41 +58,85 @@ def _energy_def(m, x):
     return E
 
 
-def _check_model(m, g, D, x, en, rtol):
-    assert abs(D - g["bound"]) <= rtol * max(abs(g["bound"]), 1.0), (m.name, D, g["bound"])
-    xo = np.asarray(g["labels"])
-    diff = np.flatnonzero(x != xo)
-    if diff.size:
-        u = int(diff[0])
-        assert g["margins"][u] <= 1e-4 * max(1.0, abs(g["bound"])), (m.name, u, g["margins"][u])
-    assert abs(en - _energy_def(m, x)) <= 1e-9 * max(1.0, abs(en))
-
-
 def _solve(models, T, **kw):
     s = Solver(models, **kw)
     s.run(T)
     D = s.bound(exact=True)
     xs, en = s.labels_per_model()
-    return s, D, xs, en
+    _, agg, msg = s.state_arrays()
+    return s, D, xs, en, P.split_state(models, agg, msg)
 
 
-@pytest.mark.parametrize("c,rtol", [(1, 1e-5), (2, 1e-4), (3, 1e-5)])
-def test_full_size_single_model(c, rtol):
-    models, T = W.config(c)
-    m = models
+def _check_golden(models, c, D, xs, en, states, rtol_D, rtol_state):
+    """Bound, labels (first divergence) and energy of every model against the
+    golden file, and theta^phi_u at the sampled nodes against the states file."""
     g = _golden(c)
-    assert g["iterations"] == T
-    s, D, xs, en = _solve([m], T)
-    _check_model(m, g["models"][0], D[0], xs[0], en[0], rtol)
+    assert g["iterations"] == W.config(c)[1]
+    differ = 0
+    for i, m in enumerate(models):
+        gm = g["models"][i]
+        assert abs(D[i] - gm["bound"]) <= rtol_D * max(abs(gm["bound"]), 1.0), (m.name, D[i], gm["bound"])
+        agg, msg = states[i]
+        eps = P.objective_eps(m, agg, msg, xs[i], rtol=rtol_state)
+        differ += P.first_divergence(xs[i], gm["labels"], gm["margins"], eps, what=m.name)
+        assert abs(en[i] - _energy_def(m, xs[i])) <= 1e-9 * max(1.0, abs(en[i]))
+    worst = 0.0
+    for smp in _golden(c, states=True)["samples"]:
+        i = smp["model"]
+        agg, _ = states[i]
+        worst = max(worst, P.check_state(models[i], agg, np.asarray(smp["theta_u"]), rtol=rtol_state,
+                                         nodes=smp["nodes"], what=models[i].name))
+    print(f"config {c}: sampled theta^phi_u within {worst:.3g} of node scale; {differ} labels differ")
+
+
+def _check_oracle(m, T, state, x, rtol_state):
+    """Every node, table entry and label against an oracle run in the test."""
+    off, order = osched.build(m.schedule, m.n, m.edge_u, m.edge_v)
+    th_u, th_uv = oracle.run_parallel(m, off, order, T)
+    agg, msg = state
+    a = P.check_state(m, agg, th_u, rtol=rtol_state, what=m.name)
+    b = P.check_tables(m, msg, th_uv, rtol=rtol_state, what=m.name)
+    P.check_labels(m, th_u, th_uv, x, oracle.round_labels(m, th_u, th_uv), rtol=rtol_state, what=m.name)
+    print(f"{m.name}: theta^phi_u within {a:.3g}, tables within {b:.3g} of their scales")
+
+
+def _many_threads():
+    return oracle.max_threads() >= 8
+
+
+@pytest.mark.parametrize("c", [1, 3])
+def test_full_size_single_model(c):
+    m, T = W.config(c)
+    s, D, xs, en, states = _solve([m], T)
+    _check_golden([m], c, D, xs, en, states, 1e-5, P.RTOL_STATE)
+    if c == 1 or _many_threads():
+        _check_oracle(m, T, states[0], xs[0], P.RTOL_STATE)
+
+
+def test_full_size_pose_K60_L300():
+    """Not tie-free (truncated costs): FP32 and FP64 may decide near-ties
+    differently and continue on different, equally valid BCA paths, so after
+    500 iterations the bound is compared at 1e-4 and the state at 1e-3 of each
+    node's scale; the first 20 iterations, before the paths part, are
+    compared at 1e-5 entry by entry with an oracle run in the test."""
+    m, T = W.config(2)
+    s, D, xs, en, states = _solve([m], T)
+    _check_golden([m], 2, D, xs, en, states, 1e-4, 1e-3)
+    if _many_threads():
+        T0 = 20
+        s0, D0, xs0, _, st0 = _solve([m], T0)
+        _check_oracle(m, T0, st0[0], xs0[0], P.RTOL_STATE)
 
 
 def test_full_size_batch256():
     models, T = W.config(4)
-    g = _golden(4)
     for mode in ("persistent", "looped"):
-        s, D, xs, en = _solve(models, T, mode=mode)
-        for i, m in enumerate(models):
-            _check_model(m, g["models"][i], D[i], xs[i], en[i], 1e-5)
+        s, D, xs, en, states = _solve(models, T, mode=mode)
+        _check_golden(models, 4, D, xs, en, states, 1e-5, P.RTOL_STATE)
+    # every node, table and label of the sampled models (oracle in the test)
+    for smp in _golden(4, states=True)["samples"][:8 if _many_threads() else 2]:
+        i = smp["model"]
+        _check_oracle(models[i], T, states[i], xs[i], P.RTOL_STATE)
 
 
 def test_full_size_differentiation_batch16():
@@ -88,8 +145,12 @@ def test_full_size_differentiation_batch16():
     s = Solver(models, record_every=10)
     s.run(T)
     D = s.bound(exact=True)
-    for i, m in enumerate(models):
-        assert abs(D[i] - g["models"][i]["bound"]) <= 1e-5 * max(1.0, abs(g["models"][i]["bound"]))
+    xs, en = s.labels_per_model()
+    _, agg, msg = s.state_arrays()
+    states = P.split_state(models, agg, msg)
+    _check_golden(models, 5, D, xs, en, states, 1e-5, P.RTOL_STATE)
+    for i in range(len(models) if _many_threads() else 2):
+        _check_oracle(models[i], T, states[i], xs[i], P.RTOL_STATE)
     gu, gp = s.backward()
     fd = g["finite_differences_model0"]
     Dabs = abs(fd["D"])

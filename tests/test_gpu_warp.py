@@ -14,6 +14,8 @@ from paper_2004_08227_gb300 import workloads as W
 from paper_2004_08227_gb300._lib import MplppError
 from paper_2004_08227_gb300.solver import Solver
 
+import _parity as P
+
 pytestmark = pytest.mark.gpu
 
 RTOL_D = 1e-5
@@ -27,13 +29,13 @@ def _check_D(Dg, Do):
     assert abs(Dg - Do) <= RTOL_D * max(abs(Do), 1.0), (Dg, Do)
 
 
-def _check_labels(m, xg, sol):
-    xo, margins = sol["labels"], sol["margins"]
-    diff = np.flatnonzero(xg != xo)
-    if diff.size:
-        u = int(diff[0])
-        scale = max(1.0, float(np.abs(sol["th_u"]).max()))
-        assert margins[u] <= 1e-4 * scale, (u, margins[u])
+def _check_labels(s, models, i, xg, sol):
+    """State, tables and conditional labels of model i (tests/_parity.py)."""
+    m = models[i]
+    agg, msg = P.model_state(s, models, i)
+    P.check_state(m, agg, sol["th_u"], what=m.name)
+    P.check_tables(m, msg, sol["th_uv"], what=m.name)
+    P.check_labels(m, sol["th_u"], sol["th_uv"], xg, sol["labels"], what=m.name)
 
 
 def _solve(models, T, **kw):
@@ -51,7 +53,7 @@ def test_warp_parity_complete_K20_L8(graph):
     s, D, xs = _solve([m], T, mode="warp", use_graph=graph)
     assert s.info()["mode"] == "warp"
     _check_D(D[0], sol["bound"])
-    _check_labels(m, xs[0], sol)
+    _check_labels(s, [m], 0, xs[0], sol)
 
 
 @pytest.mark.parametrize("threads", [32, 64, 128])
@@ -63,7 +65,7 @@ def test_warp_parity_uneven_labels(threads):
     s, D, xs = _solve([m], T, mode="warp", threads=threads)
     assert s.info()["threads"] == threads
     _check_D(D[0], sol["bound"])
-    _check_labels(m, xs[0], sol)
+    _check_labels(s, [m], 0, xs[0], sol)
 
 
 @pytest.mark.parametrize("threads", [32, 128])
@@ -74,9 +76,9 @@ def test_warp_parity_streamed_tables(threads):
     m = W.uneven_complete(6, 65, 128, seed=5)
     T = 8
     sol = oracle.solve(m, _order(m), T)
-    _, D, xs = _solve([m], T, mode="warp", threads=threads)
+    sw, D, xs = _solve([m], T, mode="warp", threads=threads)
     _check_D(D[0], sol["bound"])
-    _check_labels(m, xs[0], sol)
+    _check_labels(sw, [m], 0, xs[0], sol)
     ref = Solver([m], mode="persistent")
     ref.run(T)
     s = Solver([m], mode="warp", threads=threads)
@@ -89,11 +91,11 @@ def test_warp_parity_knn_and_batch():
     models = [W.knn(240, 8, 20, seed=3)]
     models += [W.uneven_complete(n, 3, 40, seed=50 + n) for n in (3, 5, 8, 11, 2)]
     T = 20
-    _, D, xs = _solve(models, T, mode="warp")
+    s, D, xs = _solve(models, T, mode="warp")
     for i, m in enumerate(models):
         sol = oracle.solve(m, _order(m), T)
         _check_D(D[i], sol["bound"])
-        _check_labels(m, xs[i], sol)
+        _check_labels(s, models, i, xs[i], sol)
 
 
 def test_warp_bitwise_equal_to_cluster_and_looped_drivers():

@@ -10,6 +10,8 @@ from oracle import schedule as osched
 from paper_2004_08227_gb300 import workloads as W
 from paper_2004_08227_gb300.solver import Solver
 
+import _parity as P
+
 pytestmark = pytest.mark.gpu
 
 RTOL_D = 1e-5
@@ -26,10 +28,10 @@ def _check(m, T, kw):
     D = s.bound(exact=True)[0]
     assert abs(D - sol["bound"]) <= RTOL_D * max(abs(sol["bound"]), 1.0), (D, sol["bound"])
     xs, _ = s.labels_per_model()
-    diff = np.flatnonzero(xs[0] != sol["labels"])
-    if diff.size:
-        u = int(diff[0])
-        assert sol["margins"][u] <= 1e-4 * max(1.0, float(np.abs(sol["th_u"]).max())), (u, sol["margins"][u])
+    agg, msg = P.model_state(s, [m], 0)
+    P.check_state(m, agg, sol["th_u"], what=m.name)
+    P.check_tables(m, msg, sol["th_uv"], what=m.name)
+    P.check_labels(m, sol["th_u"], sol["th_uv"], xs[0], sol["labels"], what=m.name)
     return s.state_arrays()
 
 
