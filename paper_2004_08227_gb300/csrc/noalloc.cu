@@ -10,16 +10,19 @@
 // lives in one file-scope device array of fixed size instead.
 //
 // The array is reached from host code only through its device address,
-// obtained once per device with cudaGetSymbolAddress; the name itself, in host
-// code, is not a device address.  Every call shares the array: calls that
-// overlap on the GPU (other streams, other host threads) race on it.  Every
-// word a call reads is written earlier by the same call, so nothing needs
-// clearing between calls.
+// obtained with cudaGetSymbolAddress once per device context (the first call
+// on a device, and again after that device's context was destroyed and
+// recreated, e.g. by cudaDeviceReset: the cache is keyed by the context's
+// unique id); the name itself, in host code, is not a device address.  Every
+// call shares the array: calls that overlap on the GPU (other streams, other
+// host threads) race on it.  Every word a call reads is written earlier by the
+// same call, so nothing needs clearing between calls.
 #include <climits>
 #include <cstdint>
 #include <mutex>
 #include <string>
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "mplpp.h"
@@ -101,7 +104,7 @@ __global__ void __launch_bounds__(kScanThreads) offsets_kernel(unsigned char *sc
     if (threadIdx.x == 0) *s.status = 0;
     __syncthreads();
     for (int u = threadIdx.x; u < n; u += blockDim.x)
-        if (labels[u] < 1) atomicOr(s.status, 1);
+        if (labels[u] < 1 || labels[u] > 65535) atomicOr(s.status, 1);
     for (int e = threadIdx.x; e < E; e += blockDim.x)
         if (eu[e] < 0 || ev[e] >= n || eu[e] >= ev[e]) atomicOr(s.status, 2);
     __syncthreads();
@@ -126,7 +129,9 @@ __global__ void node_min_kernel(const unsigned char *scratch, int n, const int *
     }
 }
 
-// min_{s,t} (theta_uv(s,t) - phi_{v->u}(s)) - phi_{u->v}(t) per edge (one CTA per edge)
+// min_{s,t} (theta_uv(s,t) - phi_{v->u}(s)) - phi_{u->v}(t) per edge (one CTA
+// per edge): rows by warp, columns by lane, 32-bit indices within a table
+// (L_u, L_v <= 65,535 as for the solver, so a row offset a * L_v fits).
 __global__ void __launch_bounds__(kThreads) edge_min_kernel(const unsigned char *scratch, int E, const int *labels,
                                                             const int *eu, const int *ev, const float *pairwise,
                                                             const float *msg)
@@ -134,19 +139,20 @@ __global__ void __launch_bounds__(kThreads) edge_min_kernel(const unsigned char 
     __shared__ float red[kThreads / 32];
     const Scratch s = carve(const_cast<unsigned char *>(scratch));
     if (*s.status) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int e = blockIdx.x; e < E; e += gridDim.x) {
         const int Lu = labels[eu[e]], Lv = labels[ev[e]];
         const float *th = pairwise + s.pair_off[e];
         const float *pu = msg + s.msg_off[e];
         const float *pv = pu + Lu;
         float m = INFINITY;
-        const long long cnt = static_cast<long long>(Lu) * Lv;
-        for (long long i = threadIdx.x; i < cnt; i += blockDim.x) {
-            const int a = static_cast<int>(i / Lv), b = static_cast<int>(i - static_cast<long long>(a) * Lv);
-            m = fminf(m, (th[i] - pu[a]) - pv[b]);
+        for (int a = warp; a < Lu; a += kThreads / 32) {
+            const float *row = th + static_cast<unsigned>(a) * static_cast<unsigned>(Lv);
+            const float pa = pu[a];
+            for (int b = lane; b < Lv; b += 32) m = fminf(m, (row[b] - pa) - pv[b]);
         }
         for (int o = 16; o > 0; o >>= 1) m = fminf(m, __shfl_xor_sync(0xffffffffu, m, o));
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+        if (lane == 0) red[warp] = m;
         __syncthreads();
         if (threadIdx.x == 0) {
             float r = red[0];
@@ -176,13 +182,43 @@ __global__ void __launch_bounds__(kThreads) sum_kernel(const unsigned char *scra
 }
 
 std::mutex g_mu;
-void *g_addr[64] = {};
+struct ScratchAddr {
+    unsigned long long ctx_id;  // unique id of the context the address belongs to
+    void *addr;
+};
+ScratchAddr g_addr[64] = {};
 thread_local std::string g_error;
 
 mplpp_status fail(mplpp_status st, const std::string &m)
 {
     g_error = m;
     return st;
+}
+
+// Unique id of the current context (cuCtxGetCurrent + cuCtxGetId through the
+// runtime's driver entry points, so the library does not link libcuda);
+// false where the driver does not offer them.
+bool current_context_id(unsigned long long *id)
+{
+    using GetCurrent = CUresult (*)(CUcontext *);
+    using GetId = CUresult (*)(CUcontext, unsigned long long *);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<GetCurrent>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<GetId>(f);
+    });
+    CUcontext ctx = nullptr;
+    if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx) return false;
+    return get_id(ctx, id) == CUDA_SUCCESS;
 }
 
 }  // namespace
@@ -208,17 +244,26 @@ extern "C" mplpp_status mplpp_bound_noalloc(int32_t n_nodes, int32_t n_edges, co
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return fail(MPLPP_E_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
     if (dev < 0 || dev >= 64) return fail(MPLPP_E_UNSUPPORTED, "device index above 63");
+    // the current device's primary context must exist before its id is read
+    // (cudaSetDevice initializes it; no allocation)
+    if ((e = cudaSetDevice(dev)) != cudaSuccess)
+        return fail(MPLPP_E_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
     void *base = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_mu);
-        if (!g_addr[dev]) {  // set-up, once per device, with that device current
-            e = cudaGetSymbolAddress(&g_addr[dev], g_bound_scratch);
+        unsigned long long ctx = 0;
+        const bool have_id = current_context_id(&ctx);
+        if (!have_id || !g_addr[dev].addr || g_addr[dev].ctx_id != ctx) {
+            // set-up: once per device context, with that device current
+            void *a = nullptr;
+            e = cudaGetSymbolAddress(&a, g_bound_scratch);
             if (e != cudaSuccess) {
-                g_addr[dev] = nullptr;
+                g_addr[dev] = ScratchAddr{0, nullptr};
                 return fail(MPLPP_E_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
             }
+            g_addr[dev] = ScratchAddr{have_id ? ctx : 0, a};
         }
-        base = g_addr[dev];
+        base = g_addr[dev].addr;
     }
     unsigned char *scratch = static_cast<unsigned char *>(base);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -233,7 +278,7 @@ extern "C" mplpp_status mplpp_bound_noalloc(int32_t n_nodes, int32_t n_edges, co
     e = cudaMemcpyAsync(&status, scratch + kOffStatus, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return fail(MPLPP_E_CUDA, cudaGetErrorString(e));
-    if (status & 1) return fail(MPLPP_E_INVALID, "labels must be >= 1");
+    if (status & 1) return fail(MPLPP_E_INVALID, "labels must be in 1..65535");
     if (status & 2) return fail(MPLPP_E_INVALID, "edges must satisfy 0 <= u < v < n_nodes");
     return MPLPP_OK;
 }

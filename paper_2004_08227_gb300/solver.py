@@ -46,11 +46,47 @@ def schedule(kind: str, n: int, edge_u, edge_v):
 def bound_noalloc(labels, edge_u, edge_v, pairwise, agg, msg, out, stream=None):
     """mplpp_bound_noalloc: dual bound of one model from caller-owned CUDA
     tensors (int32 labels / edges, FP32 pairwise / agg / msg in the state
-    layout, FP64 out[1]); allocates no device memory."""
+    layout, FP64 out[1]); allocates no device memory.
+
+    The C entry point trusts the array lengths, so they are checked here:
+    every argument a contiguous CUDA tensor of the right dtype on the current
+    device, and (for valid labels and edges; invalid ones are left to the
+    library's own check, MPLPP_E_INVALID) agg, msg and pairwise holding
+    sum L_u, sum (L_u + L_v) and sum L_u L_v entries."""
+    dev = torch.cuda.current_device()
+    for name, t, dt in (("labels", labels, torch.int32), ("edge_u", edge_u, torch.int32),
+                        ("edge_v", edge_v, torch.int32), ("pairwise", pairwise, torch.float32),
+                        ("agg", agg, torch.float32), ("msg", msg, torch.float32), ("out", out, torch.float64)):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or t.device.index != dev:
+            raise ValueError(f"{name} must be a CUDA tensor on the current device (cuda:{dev})")
+        if t.dtype != dt:
+            raise ValueError(f"{name} must be {dt}, got {t.dtype}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    n, E = int(labels.numel()), int(edge_u.numel())
+    if int(edge_v.numel()) != E:
+        raise ValueError("edge_u and edge_v must have the same length")
+    if out.numel() < 1:
+        raise ValueError("out must hold one value")
+    L = labels.to(torch.int64)
+    valid = n >= 1 and bool(((L >= 1) & (L <= 65535)).all())
+    if valid and E:
+        eu, ev = edge_u.to(torch.int64), edge_v.to(torch.int64)
+        valid = bool(((eu >= 0) & (eu < ev) & (ev < n)).all())
+    if valid:
+        need = {"agg": int(L.sum()), "msg": 0, "pairwise": 0}
+        if E:
+            Lu, Lv = L[edge_u.long()], L[edge_v.long()]
+            need["msg"] = int((Lu + Lv).sum())
+            need["pairwise"] = int((Lu * Lv).sum())
+        for name, t in (("agg", agg), ("msg", msg), ("pairwise", pairwise)):
+            if (E or name == "agg") and int(t.numel()) != need[name]:
+                raise ValueError(f"{name} must hold {need[name]} entries for these labels and edges, "
+                                 f"got {int(t.numel())}")
     lib = _lib.load()
     st = _current_stream() if stream is None else ctypes.c_void_p(stream)
-    status = lib.mplpp_bound_noalloc(int(labels.numel()), int(edge_u.numel()), _ptr(labels), _ptr(edge_u),
-                                     _ptr(edge_v), _ptr(pairwise), _ptr(agg), _ptr(msg), _ptr(out), st)
+    status = lib.mplpp_bound_noalloc(n, E, _ptr(labels), _ptr(edge_u), _ptr(edge_v), _ptr(pairwise), _ptr(agg),
+                                     _ptr(msg), _ptr(out), st)
     if status != _lib.MPLPP_OK:
         msg_ = lib.mplpp_noalloc_last_error()
         raise _lib.MplppError(status, msg_.decode() if msg_ else "")
@@ -274,7 +310,8 @@ class Solver:
         return {"iterations": inf.iterations, "bytes_per_iteration": inf.bytes_per_iteration, "edges": inf.edges,
                 "phases": inf.phases, "mode": MODE_NAME.get(inf.mode, inf.mode), "cluster": inf.cluster,
                 "threads": inf.threads, "grid": inf.grid, "launches_per_iteration": inf.launches_per_iteration,
-                "labeling_launches": inf.labeling_launches}
+                "labeling_launches": inf.labeling_launches, "poller_warp": inf.poller_warp,
+                "device_bytes": inf.device_bytes}
 
 
 if torch is not None:
