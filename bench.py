@@ -51,6 +51,35 @@ def models_for(cfg: int, seed: int):
     return models, T
 
 
+def algorithmic_bytes(models):
+    """Algorithmic HBM bytes of one iteration: per edge update the FP32 table
+    read once (4 L_u L_v) and the FP32 node vectors and messages of both ends
+    read and written (16 (L_u + L_v))."""
+    total = 0
+    for m in models:
+        L = np.asarray(m.labels, np.int64)
+        Lu, Lv = L[np.asarray(m.edge_u)], L[np.asarray(m.edge_v)]
+        total += int(np.sum(4 * Lu * Lv + 16 * (Lu + Lv)))
+    return total
+
+
+def host_cpu():
+    """CPU model and logical core count of the host."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        import platform
+        model = platform.processor() or platform.machine()
+    return {"model": model, "nproc": os.cpu_count()}
+
+
 def kernel_traffic(iterations):
     """DRAM bytes per launch of the Handshake kernel from the committed ncu
     summary, scaled from its 500-iteration figure; None when the kernel
@@ -142,6 +171,32 @@ def cpu_oracle_rate(models, T_full, budget_s: float):
                             f"{t1 + dt:.1f} s"}
 
 
+def cpu_oracle_rate_parallel(models, T_full, budget_s: float):
+    """The FP64 oracle with the edges of each matching updated on every host
+    core (oracle.run_parallel: OpenMP, equal to the sequential oracle bit for
+    bit) on a bounded sample: the first model for as many iterations as fit
+    the budget."""
+    import oracle
+    from oracle import schedule as osched
+    m = models[0]
+    off, order = osched.build(m.schedule, m.n, m.edge_u, m.edge_v)
+    threads = oracle.max_threads()
+    t0 = time.perf_counter()
+    st = oracle.run_parallel(m, off, order, 1, threads=threads)
+    t1 = time.perf_counter() - t0
+    iters = int(max(1, min(T_full - 1, budget_s / max(t1, 1e-9) - 1)))
+    t0 = time.perf_counter()
+    oracle.run_parallel(m, off, order, iters, state=st, threads=threads)
+    dt = time.perf_counter() - t0
+    total_iters = iters + 1
+    rate = total_iters * m.E / (t1 + dt)
+    cpu = host_cpu()
+    return rate, {"value": rate, "unit": "edge_updates/s", "cores": threads, "kind": "oracle",
+                  "cpu": cpu["model"], "nproc": cpu["nproc"],
+                  "sample": f"{m.name}: {total_iters} of {T_full} iterations, FP64 C oracle, edges of each "
+                            f"matching on {threads} threads (OpenMP), {t1 + dt:.1f} s"}
+
+
 def run_reference(args):
     """--impl reference: the FP64 oracle on the host cores (rank 0 only)."""
     rank = int(os.environ.get("RANK", "0"))
@@ -152,25 +207,29 @@ def run_reference(args):
     import oracle
     from oracle import schedule as osched
     m = models[0]
-    order = osched.build(m.schedule, m.n, m.edge_u, m.edge_v)[1]
+    off, order = osched.build(m.schedule, m.n, m.edge_u, m.edge_v)
+    threads = oracle.max_threads()
     st = None
     per = max(1, args.ref_iters)
     for _ in range(args.warmup):
-        st = oracle.run(m, order, per, state=st)
+        st = oracle.run_parallel(m, off, order, per, state=st, threads=threads)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        st = oracle.run(m, order, per, state=st)
+        st = oracle.run_parallel(m, off, order, per, state=st, threads=threads)
         times.append(time.perf_counter() - t0)
     ms = 1e3 * sum(times) / len(times)
     value = per * m.E / (ms / 1e3)
     name = CONFIGS[cfg][0]
+    cpu = host_cpu()
     line = {"impl": "reference", "metric": "edge_updates_per_s", "value": value, "unit": "edge_updates/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": name, "sample": f"{per} iteration(s) of {m.name} per step"},
-            "cpu_baseline": {"value": value, "unit": "edge_updates/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{per} of {T} iterations of {m.name} per step, single-thread FP64 C oracle"},
+            "cpu_baseline": {"value": value, "unit": "edge_updates/s", "cores": threads, "kind": "oracle",
+                             "cpu": cpu["model"], "nproc": cpu["nproc"],
+                             "sample": f"{per} of {T} iterations of {m.name} per step, FP64 C oracle, edges of "
+                                       f"each matching on {threads} threads (OpenMP)"},
             "e2e": {"value": value, "unit": "edge_updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -247,7 +306,8 @@ def batched_vs_looped(Solver, stream, args):
     # the same batch through each persistent driver: one kernel launch per solve
     # (the fastest of a few block sizes per driver)
     persistent = {}
-    for name, mode, sizes in (("cluster", "persistent", (128, 256, 512)), ("warp", "warp", (32, 64, 128))):
+    for name, mode, sizes in (("cluster", "persistent", (128, 256, 512)), ("warp", "warp", (32, 64, 128)),
+                              ("queue", "queue", (128,))):
         best = None
         for nt in sizes:
             try:
@@ -272,6 +332,85 @@ def batched_vs_looped(Solver, stream, args):
             "bound_equal": lp["bound_equal"], "speedup": lp["ms_per_step"] / bms,
             "mapping": {k: info[k] for k in ("mode", "cluster", "threads", "grid")},
             "autotune": tune.get("best") if tune else None, "persistent_drivers": persistent}
+
+
+def replicas_study(Solver, stream, args, peak):
+    """The K_20, L = 8 workload (200 iterations): one model, whose chain of 3,800
+    dependent matchings of 10 small edges is latency-bound, and many seeded
+    replicas solved together through the batched path (autotuned mapping), so
+    that the Handshake kernel's HBM throughput shows."""
+    from paper_2004_08227_gb300 import workloads as W
+    T = 200
+    rows = []
+    for nrep in (1, args.replicas):
+        models = [W.config(1, seed=k)[0] for k in range(nrep)]
+        s = Solver(models)
+        tune = s.autotune(2) if args.autotune > 0 else None
+
+        def run(sol=s):
+            sol.reset()
+            sol.run(T)
+        run()
+        ms, _ = _timed(stream, run, 2)
+        inf = s.info()
+        gbs = T * algorithmic_bytes(models) / (ms / 1e3) / 1e9
+        rows.append({"models": nrep, "edges": inf["edges"], "ms": ms, "us_per_iteration": 1e3 * ms / T,
+                     "edge_updates_per_s": T * inf["edges"] / (ms / 1e3), "gbs": gbs, "frac_of_peak": gbs / peak,
+                     "mapping": {k: inf[k] for k in ("mode", "cluster", "threads", "grid")},
+                     "autotune": tune.get("best") if tune else None})
+        s.close()
+    return {"workload": CONFIGS[1][0], "iterations": T, "rows": rows}
+
+
+def knn_study(Solver, stream, args, peak):
+    """The semi-dense kNN model (n = 2000, 50 nearest neighbours, L = 64,
+    greedy colouring, 300 iterations): the Handshake run alone, autotuned."""
+    models, T = models_for(3, seed=0)
+    s = Solver(models)
+    tune = s.autotune(2) if args.autotune > 0 else None
+
+    def run():
+        s.reset()
+        s.run(T)
+    run()
+    ms, _ = _timed(stream, run, 2)
+    inf = s.info()
+    gbs = T * algorithmic_bytes(models) / (ms / 1e3) / 1e9
+    s.close()
+    return {"workload": CONFIGS[3][0], "edges": inf["edges"], "matchings": inf["phases"], "iterations": T, "ms": ms,
+            "edge_updates_per_s": T * inf["edges"] / (ms / 1e3), "gbs": gbs, "frac_of_peak": gbs / peak,
+            "mapping": {k: inf[k] for k in ("mode", "cluster", "threads", "grid")},
+            "autotune": tune.get("best") if tune else None}
+
+
+def differentiation_study(Solver, stream, args):
+    """16 x K_50, L = 64, T = 50 with a state checkpoint every 10 iterations:
+    the forward run (with the bound) and the backward (mplpp_backward, host
+    gradients) timed separately; device memory the solver holds afterwards,
+    and the peak including the backward's transient gradient buffers."""
+    models, T = models_for(5, seed=0)
+    s = Solver(models, record_every=10)
+
+    def fwd():
+        s.reset()
+        s.run(T)
+        s.bound(exact=True)
+
+    def bwd():
+        s.backward()
+    fwd()
+    bwd()
+    fms, _ = _timed(stream, fwd, 3)
+    fwd()
+    bms, _ = _timed(stream, bwd, 2)
+    inf = s.info()
+    transient = 4 * sum(int(np.sum(np.asarray(m.labels, np.int64))) for m in models)
+    transient += 4 * sum(int(np.sum(np.asarray(m.labels, np.int64)[m.edge_u] *
+                                    np.asarray(m.labels, np.int64)[m.edge_v])) for m in models)
+    s.close()
+    return {"workload": CONFIGS[5][0], "iterations": T, "record_every": 10, "forward_ms": fms, "backward_ms": bms,
+            "backward_over_forward": bms / fms, "solver_device_bytes": inf["device_bytes"],
+            "peak_device_bytes": inf["device_bytes"] + transient}
 
 
 def rules_comparison(Solver, stream, args):
@@ -406,11 +545,12 @@ def run_ours(args):
     if args.iters:
         T = args.iters
     # cpu baseline first (before any GPU work), rank 0 only
-    cpu = None
+    cpu = cpu1 = None
     models, _ = models_for(cfg, seed=rank)
     if rank == 0 and world == 1 and not args.no_cpu:
         log("timing the oracle on the host ...")
-        _, cpu = cpu_oracle_rate(models, T, args.cpu_budget)
+        _, cpu = cpu_oracle_rate_parallel(models, T, args.cpu_budget)
+        _, cpu1 = cpu_oracle_rate(models, T, args.cpu_budget)
     stream = torch.cuda.current_stream()
     s = Solver(models, mode=args.mode, cluster=args.cluster, threads=args.threads)
     tune = None
@@ -464,9 +604,11 @@ def run_ours(args):
     ck = clocks.stop()
     ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, "cuda")
     value = whole_job_rate(T * E_total, world, ms)
-    bytes_iter = info["bytes_per_iteration"]
+    bytes_iter = algorithmic_bytes(models)
+    bytes_iter32 = info["bytes_per_iteration"]
     kms = statistics.mean(kern_ms)
     achieved = T * bytes_iter / (kms / 1e3) / 1e9
+    achieved32 = T * bytes_iter32 / (kms / 1e3) / 1e9
     peak, peak_kind = load_peak()
     kernel = "hs_persistent_kernel" if info["mode"] == "persistent" else "hs_looped_kernel"
 
@@ -480,6 +622,14 @@ def run_ours(args):
     batched = None
     if args.batched and cfg != 4:
         batched = batched_vs_looped(Solver, stream, args)
+
+    # K_20 replicas, the kNN model and the differentiation batch
+    replicas = knn = diff = None
+    if args.extra and rank == 0:
+        replicas = replicas_study(Solver, stream, args, peak)
+        if cfg != 3:
+            knn = knn_study(Solver, stream, args, peak)
+        diff = differentiation_study(Solver, stream, args)
 
     # the M and U updates beside H (equal iterations)
     rules = None
@@ -531,7 +681,7 @@ def run_ours(args):
 
     # per step: reset (1), the run (restamp + one persistent launch, or one
     # launch per matching and iteration), exact bound (3), rounding + energy
-    launches_per_step = (1 + (2 if info["mode"] in ("persistent", "warp") else T * info["phases"]) + 3
+    launches_per_step = (1 + (2 if info["mode"] in ("persistent", "warp", "queue") else T * info["phases"]) + 3
                          + info["labeling_launches"])
     line = {
         "metric": "edge_updates_per_s", "value": value, "unit": "edge_updates/s", "n_gpus": world,
@@ -546,7 +696,14 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": peak_kind,
                      "traffic": kernel_traffic(T) if (cfg == 2 and info["mode"] == "persistent") else None,
-                     "algorithmic_bytes_per_launch": T * bytes_iter, "launch_ms": kms},
+                     "algorithmic_bytes_per_launch": T * bytes_iter,
+                     "bytes_formula": "per edge update 4 L_u L_v + 16 (L_u + L_v)",
+                     "achieved_state32": achieved32, "frac_state32": achieved32 / peak,
+                     "bytes_formula_state32": "per edge update 4 L_u L_v + 32 (L_u + L_v) (double-float state)",
+                     "launch_ms": kms},
+        "config1_replicas": replicas,
+        "knn": knn,
+        "differentiation": diff,
         "looped": looped,
         "batched": batched,
         "rules": rules,
@@ -555,6 +712,7 @@ def run_ours(args):
         "structured": structured,
         "e2e": e2e,
         "cpu_baseline": cpu,
+        "cpu_baseline_single_thread": cpu1,
         "clocks": ck,
         "gpu_launches": launches_per_step * args.steps,
     }
@@ -583,7 +741,10 @@ def main():
     ap.add_argument("--studies", type=int, default=1, help="also run the sparsified pose, dense L=13 and structured-cost workloads")
     ap.add_argument("--rules", type=int, default=1, help="also run the M and U updates beside H (pose and kNN)")
     ap.add_argument("--autotune", type=int, default=3, help="iterations per candidate of the mapping autotuner (0: off)")
-    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--extra", type=int, default=1,
+                    help="also run K_20 replicas, the kNN model and the differentiation batch")
+    ap.add_argument("--replicas", type=int, default=4096, help="K_20 replicas solved together")
     ap.add_argument("--ref-iters", type=int, default=1)
     args = ap.parse_args()
     if args.impl == "reference":

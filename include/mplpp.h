@@ -71,9 +71,15 @@ enum {
     MPLPP_MODE_WARP = 3,       /* as PERSISTENT with one warp per edge instead of a cluster of
                                   CTAs per edge (for many small tables: every label count
                                   <= 128); options.cluster is ignored                          */
-    MPLPP_MODE_STRUCTURED = 4  /* every model MPLPP_PAIR_TRUNC_*, rule H, label counts
+    MPLPP_MODE_STRUCTURED = 4, /* every model MPLPP_PAIR_TRUNC_*, rule H, label counts
                                   <= 256: one launch per matching, one warp per edge, no
                                   table reads (see MPLPP_PAIR_*)                               */
+    MPLPP_MODE_QUEUE = 5       /* one launch for all iterations; one CTA per edge at a time,
+                                  every CTA taking the next edge from one queue of all models'
+                                  updates (each model in schedule order, the models interleaved
+                                  by their progress); tables read from memory by every pass
+                                  instead of staged, so many CTAs share an SM (for many small
+                                  models); options.cluster is ignored                        */
 };
 
 /* How a model's pairwise costs are given.  TRUNC_LINEAR: theta_uv(s,t) =
@@ -141,6 +147,10 @@ typedef struct {
                                  run must end with MPLPP_E_TIMEOUT instead of hanging            */
     int32_t rule;             /* MPLPP_RULE_* (0 = the Handshake update)                        */
     int64_t spin_limit;       /* polls before a device-side wait gives up with MPLPP_E_TIMEOUT */
+    int32_t test_fp64_replay; /* testing only (0 otherwise): mplpp_backward replays every
+                                 minimization in FP64 instead of screening it in FP32 first
+                                 (the two give the same argmins and gradient bit for bit)    */
+    int32_t reserved;         /* 0                                                             */
 } mplpp_options;
 
 /* Fills *opt with defaults: AUTO mode, graphs on, host inputs, no record,
@@ -240,7 +250,9 @@ mplpp_status mplpp_load_state(mplpp_solver *s, const void *buf, size_t size);
 /* Facts about a solver, for benchmarks and tests. */
 typedef struct {
     int64_t iterations;         /* iterations run since the last reset                        */
-    int64_t bytes_per_iteration;/* algorithmic HBM bytes: sum_e 4 L_u L_v + 32 (L_u + L_v)    */
+    int64_t bytes_per_iteration;/* HBM bytes of one iteration in this layout: sum_e 4 L_u L_v
+                                   + 32 (L_u + L_v) (tables once; double-float agg and msg
+                                   values of both ends read and written)                      */
     int64_t edges;              /* total edges over all models                                */
     int32_t phases;             /* matchings per iteration (max over models)                 */
     int32_t mode;               /* MPLPP_MODE_LOOPED or _PERSISTENT actually used             */
@@ -250,7 +262,11 @@ typedef struct {
     int32_t launches_per_iteration; /* kernel launches one iteration takes (looped: phases)   */
     int32_t labeling_launches;  /* kernel launches of one mplpp_labeling: the rounding (one,
                                    or one per level of the rounding order) and the energy      */
-    int32_t reserved;           /* 0                                                          */
+    int32_t poller_warp;        /* 1: the persistent driver's CTAs have one warp beyond those
+                                   holding table rows, which fetches node u's vector while
+                                   the others start on node v's (threads permitting)          */
+    int64_t device_bytes;       /* device memory the solver holds now (its allocations,
+                                   including the backward's replay buffers once allocated)   */
 } mplpp_info_t;
 mplpp_status mplpp_info(const mplpp_solver *s, mplpp_info_t *info);
 
@@ -274,7 +290,7 @@ mplpp_status mplpp_autotune(mplpp_solver *s, int32_t iterations, char *report, s
  * allocation's latency or implicit synchronization, plugins whose host
  * runtime must see every device byte.  It computes what mplpp_bound(exact = 1)
  * computes, from buffers the caller owns:
- *   labels [n_nodes], edge_u, edge_v [n_edges]   int32, device (u < v)
+ *   labels [n_nodes], edge_u, edge_v [n_edges]   int32, device (L_u in 1..65535, u < v)
  *   pairwise [sum L_u L_v]  FP32, device, the ORIGINAL tables, caller layout
  *   agg [sum L_u]           FP32, device, theta^phi_u per node (state layout)
  *   msg [sum (L_u + L_v)]   FP32, device, phi_{v->u} then phi_{u->v} per edge
@@ -285,12 +301,16 @@ mplpp_status mplpp_autotune(mplpp_solver *s, int32_t iterations, char *report, s
  * loading the library holds until the process exits; hence the size limits
  * below, beyond which the call returns MPLPP_E_UNSUPPORTED.  The first call on
  * a device looks up that array's device address (cudaGetSymbolAddress, with
- * the device current); make that first call before any stream capture.  All
- * calls share the array: calls that overlap on the GPU (other streams, other
- * host threads) race on it.  Work runs on `stream` (a cudaStream_t, NULL =
- * legacy default); the call synchronizes it to report bad labels or edges
- * (MPLPP_E_INVALID).  Calls no cudaMalloc, cudaFree or allocating library
- * routine.  Message of a failure: mplpp_noalloc_last_error(). */
+ * the device current) and keeps it for that device's context (a call after
+ * the context was destroyed and recreated, e.g. by cudaDeviceReset, looks it
+ * up again); make that first call before any stream capture.  All calls share
+ * the array: calls that overlap on the GPU (other streams, other host threads)
+ * race on it.  Work runs on `stream` (a cudaStream_t, NULL = legacy default);
+ * every call then waits for that stream to finish, to read back the check of
+ * the labels and edges (MPLPP_E_INVALID, with out left untouched).  The call
+ * trusts that the array lengths above match labels, edge_u and edge_v.  Calls
+ * no cudaMalloc, cudaFree or allocating library routine.  Message of a
+ * failure: mplpp_noalloc_last_error(). */
 #define MPLPP_NOALLOC_MAX_NODES 65536
 #define MPLPP_NOALLOC_MAX_EDGES 262144
 #define MPLPP_NOALLOC_SCRATCH_BYTES 6030336

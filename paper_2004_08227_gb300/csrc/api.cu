@@ -127,6 +127,8 @@ static void mapping_for(mplpp_solver *s, int C, int threads = 0)
     s->rmax = static_cast<int>(round4(std::max(4LL, rows)));
     s->ldmax = ldmax;
     s->rr = hs_rr_fits(static_cast<int>(rows), ldmax >> 2, T, s->tile_floats);
+    // a spare warp beyond those holding the rows becomes node u's poller
+    s->pw = s->rr && hs_pw_fits(static_cast<int>(rows), ldmax >> 2, T, s->tile_floats);
     s->smem_looped = hs_smem_bytes(1, s->tile_floats, s->rmax, s->ldmax, s->T, C);
     s->smem_persist = hs_smem_bytes(2, s->tile_floats, s->rmax, s->ldmax, s->T, C);
 }
@@ -221,6 +223,48 @@ static void build_work(mplpp_solver *s, int clusters)
     }
     s->max_deg = 0;
     for (int d : deg) s->max_deg = std::max(s->max_deg, d);
+}
+
+// Queue driver: one list of every update of an iteration.  A model's items
+// keep its schedule order; the models are interleaved by their progress
+// through an iteration (item of matching p of a model with P matchings at
+// position (p + 1/2) / P), so consecutive matchings of one model lie far
+// apart in the queue and a CTA rarely waits for an input.  Every item's
+// inputs come from items earlier in the list (or in an earlier iteration).
+static void build_queue(mplpp_solver *s)
+{
+    const int N = s->N;
+    std::vector<int> pos(N, 0), deg(N, 0);
+    for (int e : s->phase_edges) {
+        deg[s->h_edges[e].gu]++;
+        deg[s->h_edges[e].gv]++;
+    }
+    struct Q {
+        double key;
+        int seq;
+        WorkItem w;
+    };
+    std::vector<Q> q;
+    q.reserve(s->phase_edges.size());
+    for (size_t p = 0; p + 1 < s->phase_off.size(); ++p)
+        for (int i = s->phase_off[p]; i < s->phase_off[p + 1]; ++i) {
+            const int e = s->phase_edges[i];
+            const EdgeDesc &ed = s->h_edges[e];
+            const int Pm = static_cast<int>(s->models[ed.model].off.size()) - 1;
+            WorkItem w = {};
+            w.ed = ed;
+            w.edge = e;
+            w.pos_u = pos[ed.gu]++;
+            w.pos_v = pos[ed.gv]++;
+            w.deg_u = deg[ed.gu];
+            w.deg_v = deg[ed.gv];
+            w.rows = ed.Lu;
+            q.push_back({(static_cast<double>(p) + 0.5) / std::max(1, Pm), static_cast<int>(q.size()), w});
+        }
+    std::stable_sort(q.begin(), q.end(), [](const Q &a, const Q &b) { return a.key < b.key; });
+    s->work.clear();
+    for (auto &x : q) s->work.push_back(x.w);
+    s->work_off.assign({0, static_cast<int>(s->work.size())});
 }
 
 static void drop_graphs(mplpp_solver *s)
@@ -345,6 +389,33 @@ static mplpp_status apply_struct_mapping(mplpp_solver *s, int optin)
     return MPLPP_OK;
 }
 
+// The queue driver: CTAs of T threads (default 128), vectors and the column
+// partials in shared memory, tables read from memory; as many CTAs as are
+// co-resident (at most one per edge).
+static mplpp_status apply_queue_mapping(mplpp_solver *s, int T, int optin)
+{
+    if (T == 0) T = 128;
+    if (T % 32 || T < 64 || T > 512) return fail(s, MPLPP_E_INVALID, "threads must be a multiple of 32 in 64..512");
+    if (T != 128) return fail(s, MPLPP_E_UNSUPPORTED, "the queue driver runs 128 threads per CTA");
+    if (s->EE == 0) return fail(s, MPLPP_E_UNSUPPORTED, "the queue driver needs edges");
+    mapping_for(s, 1, T);  // sizes of the other drivers stay consistent
+    s->smem_queue = hs_smem_bytes(1, 4, s->rmax, s->ldmax, T, 1);
+    if (s->smem_queue > static_cast<size_t>(optin)) return fail(s, MPLPP_E_UNSUPPORTED, "queue driver: shared memory");
+    int blocks = hs_queue_max_blocks(T, s->smem_queue);
+    blocks = std::min(blocks, s->EE);
+    if (blocks < 1) return fail(s, MPLPP_E_UNSUPPORTED, "queue driver: no block fits");
+    if (!s->d_queue) CK(s, s->alloc(&s->d_queue, 1));
+    build_queue(s);
+    CK(s, cudaMemcpyAsync(s->d_work, s->work.data(), s->work.size() * sizeof(WorkItem), cudaMemcpyHostToDevice,
+                          s->stream));
+    CK(s, cudaStreamSynchronize(s->stream));
+    s->mode = MPLPP_MODE_QUEUE;
+    s->queue_blocks = blocks;
+    s->T = T;
+    drop_graphs(s);
+    return MPLPP_OK;
+}
+
 static mplpp_status apply_mapping(mplpp_solver *s, int C, int T, int want)
 {
     int optin = 0;
@@ -353,6 +424,7 @@ static mplpp_status apply_mapping(mplpp_solver *s, int C, int T, int want)
     if (want == MPLPP_MODE_STRUCTURED || (want == MPLPP_MODE_AUTO && s->all_structured && struct_fits(s)))
         return apply_struct_mapping(s, optin);
     if (want == MPLPP_MODE_WARP) return apply_warp_mapping(s, T, optin);
+    if (want == MPLPP_MODE_QUEUE) return apply_queue_mapping(s, T, optin);
     mapping_for(s, C, T);
     if (s->smem_looped > static_cast<size_t>(optin))
         return fail(s, MPLPP_E_UNSUPPORTED,
@@ -396,14 +468,15 @@ extern "C" mplpp_status mplpp_create(const mplpp_model *models, int32_t n_models
     s->stream = static_cast<cudaStream_t>(stream);
     {
         const mplpp_options &o = s->opt;
-        if (o.mode < MPLPP_MODE_AUTO || o.mode > MPLPP_MODE_STRUCTURED)
+        if (o.mode < MPLPP_MODE_AUTO || o.mode > MPLPP_MODE_QUEUE)
             return fail(nullptr, MPLPP_E_INVALID, "unknown mode");
         if (o.cluster < 0 || o.cluster > 8) return fail(nullptr, MPLPP_E_INVALID, "cluster must be 0 or 1..8");
         if (o.rule < MPLPP_RULE_H || o.rule > MPLPP_RULE_U) return fail(nullptr, MPLPP_E_INVALID, "unknown rule");
         if (o.rule != MPLPP_RULE_H && o.record_every > 0)
             return fail(nullptr, MPLPP_E_INVALID, "backward is defined for the Handshake update only");
         if (o.rule != MPLPP_RULE_H &&
-            (o.mode == MPLPP_MODE_PERSISTENT || o.mode == MPLPP_MODE_WARP || o.mode == MPLPP_MODE_STRUCTURED))
+            (o.mode == MPLPP_MODE_PERSISTENT || o.mode == MPLPP_MODE_WARP || o.mode == MPLPP_MODE_STRUCTURED ||
+             o.mode == MPLPP_MODE_QUEUE))
             return fail(nullptr, MPLPP_E_UNSUPPORTED, "the M and U updates run in the looped driver only");
         // a CTA of the cluster drivers splits its warps between the two node
         // vectors, so it needs two warps at least
@@ -709,6 +782,9 @@ static HsParams make_params(mplpp_solver *s)
     p.spin_limit = s->opt.spin_limit;
     p.test_wait = s->opt.test_unreachable_wait ? 1 : 0;
     p.rr = s->rr ? 1 : 0;
+    p.pw = s->pw ? 1 : 0;
+    p.queue = s->d_queue;
+    p.queue_items = s->EE;
     p.C = s->C;
     p.tile_floats = s->tile_floats;
     p.workers = s->mode == MPLPP_MODE_WARP ? s->clusters : 0;
@@ -762,6 +838,12 @@ cudaError_t enqueue_persistent(mplpp_solver *s, cudaStream_t st, int iterations)
     if (e != cudaSuccess) return e;
     p.iterations = iterations;
     if (s->mode == MPLPP_MODE_WARP) return hs_launch_warp(p, s->warp_blocks, s->T, s->smem_warp, st);
+    if (s->mode == MPLPP_MODE_QUEUE) {
+        e = cudaMemsetAsync(s->d_queue, 0, sizeof(unsigned long long), st);
+        if (e != cudaSuccess) return e;
+        p.tile_floats = 4;  // no staged tables
+        return hs_launch_queue(p, s->queue_blocks, s->T, s->smem_queue, st);
+    }
     return hs_launch_persistent(p, s->clusters, s->T, s->smem_persist, st);
 }
 
@@ -814,7 +896,7 @@ static mplpp_status run_plain(mplpp_solver *s, int iterations)
         } else {
             CK(s, enqueue_persistent(s, s->stream, iterations));
         }
-        s->launches += 2;  // restamp + persistent kernel
+        s->launches += s->mode == MPLPP_MODE_QUEUE ? 3 : 2;  // restamp (+ queue reset) + persistent kernel
     }
     return MPLPP_OK;
 }
@@ -1027,6 +1109,7 @@ static const char *mode_name(int mode)
     return mode == MPLPP_MODE_PERSISTENT   ? "persistent"
            : mode == MPLPP_MODE_WARP       ? "warp"
            : mode == MPLPP_MODE_STRUCTURED ? "structured"
+           : mode == MPLPP_MODE_QUEUE      ? "queue"
                                            : "looped";
 }
 
@@ -1070,7 +1153,8 @@ extern "C" mplpp_status mplpp_autotune(mplpp_solver *s, int32_t iterations, char
     cudaEvent_t e0, e1;
     CK(s, cudaEventCreate(&e0));
     CK(s, cudaEventCreate(&e1));
-    for (int mode : {MPLPP_MODE_PERSISTENT, MPLPP_MODE_LOOPED, MPLPP_MODE_WARP, MPLPP_MODE_STRUCTURED})
+    for (int mode : {MPLPP_MODE_PERSISTENT, MPLPP_MODE_LOOPED, MPLPP_MODE_WARP, MPLPP_MODE_STRUCTURED,
+                     MPLPP_MODE_QUEUE})
         for (int C : {1, 2, 3, 4, 5, 6, 8})
             for (int T : {128, 256, 512, 0}) {
                 if (T == 0) {  // the exact fit of the register-resident passes, if another size
@@ -1088,6 +1172,7 @@ extern "C" mplpp_status mplpp_autotune(mplpp_solver *s, int32_t iterations, char
                     if (T == 0 || T == 128 || T == 256 || T == 512) continue;
                 }
                 if (mode == MPLPP_MODE_STRUCTURED && (C != 1 || T != 256 || !s->all_structured)) continue;
+                if (mode == MPLPP_MODE_QUEUE && (C != 1 || T != 128)) continue;
                 if (mode == MPLPP_MODE_WARP && C != 1) continue;  // one warp per edge
                 if (mode == MPLPP_MODE_WARP && T == 512) T = 32;  // small blocks: shared memory per warp
                 if (apply_mapping(s, C, T, mode) != MPLPP_OK) {
@@ -1141,10 +1226,12 @@ extern "C" mplpp_status mplpp_info(const mplpp_solver *s, mplpp_info_t *info)
     info->threads = s->T;
     info->grid = s->mode == MPLPP_MODE_PERSISTENT ? s->clusters * s->C
                  : s->mode == MPLPP_MODE_WARP     ? s->warp_blocks
+                 : s->mode == MPLPP_MODE_QUEUE    ? s->queue_blocks
                                                   : 0;
     info->launches_per_iteration = (s->mode == MPLPP_MODE_LOOPED || s->mode == MPLPP_MODE_STRUCTURED) ? s->P : 0;
     info->labeling_launches = (s->level_off.empty() ? 1 : static_cast<int>(s->level_off.size()) - 1) + 1;
-    info->reserved = 0;
+    info->poller_warp = (s->mode == MPLPP_MODE_PERSISTENT && s->pw) ? 1 : 0;
+    info->device_bytes = s->device_bytes;
     return MPLPP_OK;
 }
 

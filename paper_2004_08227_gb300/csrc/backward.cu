@@ -306,13 +306,17 @@ cudaError_t ensure(mplpp_solver *s, T **p, size_t count)
     return s->alloc(p, count);
 }
 
-// One FP64 iteration: every matching in schedule order.
-cudaError_t rec64_iteration(mplpp_solver *s, unsigned char *rec, int lmax)
+// One FP64 iteration: every matching in schedule order (screened kernel when
+// the largest table fits shared memory, tab_floats > 0; else all-FP64 scans).
+cudaError_t rec64_iteration(mplpp_solver *s, unsigned char *rec, int lmax, long long tab_floats, cudaStream_t st)
 {
     for (int ph = 0; ph < s->P; ++ph) {
-        cudaError_t e = launch_rec64_phase(s->d_edges, s->d_phase_edges + s->phase_off[ph],
-                                           s->phase_off[ph + 1] - s->phase_off[ph], s->d_tab, s->d_agg64, s->d_msg64,
-                                           rec, s->d_rec_off, lmax, s->stream);
+        const int *items = s->d_phase_edges + s->phase_off[ph];
+        const int n = s->phase_off[ph + 1] - s->phase_off[ph];
+        cudaError_t e = tab_floats > 0 ? launch_rec_screen_phase(s->d_edges, items, n, s->d_tab, s->d_agg64,
+                                                                 s->d_msg64, rec, s->d_rec_off, lmax, tab_floats, st)
+                                       : launch_rec64_phase(s->d_edges, items, n, s->d_tab, s->d_agg64, s->d_msg64, rec,
+                                                            s->d_rec_off, lmax, st);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -338,6 +342,10 @@ extern "C" mplpp_status mplpp_backward(mplpp_solver *s, const float *dD, float *
     if (rec64_smem_bytes(lmax) > static_cast<size_t>(optin) ||
         static_cast<size_t>(lmax) * (7 * sizeof(double) + 3 * sizeof(int)) > static_cast<size_t>(optin))
         return bfail(s, MPLPP_E_UNSUPPORTED, "backward supports at most ~2700 labels per node");
+    long long tab_floats = 0;  // the screened replay stages the largest table in shared memory
+    for (auto &ed : s->h_edges) tab_floats = std::max(tab_floats, 1LL * ed.Lu * (ed.ld | 1));
+    if (s->opt.test_fp64_replay || rec_screen_smem_bytes(lmax, tab_floats) > static_cast<size_t>(optin))
+        tab_floats = 0;
 
     // buffers
     if (!s->d_rec_off) {
@@ -391,7 +399,7 @@ extern "C" mplpp_status mplpp_backward(mplpp_solver *s, const float *dD, float *
             BCK(cudaMemcpyAsync(c, s->d_agg64, sizeof(double) * s->aggN, cudaMemcpyDeviceToDevice, st));
             BCK(cudaMemcpyAsync(c + s->aggN, s->d_msg64, sizeof(double) * s->msgN, cudaMemcpyDeviceToDevice, st));
         }
-        BCK(rec64_iteration(s, nullptr, lmax));
+        BCK(rec64_iteration(s, nullptr, lmax, tab_floats, st));
     }
     BCK(cudaMemcpyAsync(s->d_dD, dD, sizeof(float) * nm, cudaMemcpyHostToDevice, st));
     BCK(cudaMemsetAsync(s->d_adj_agg, 0, sizeof(double) * s->aggN, st));
@@ -413,7 +421,7 @@ extern "C" mplpp_status mplpp_backward(mplpp_solver *s, const float *dD, float *
         BCK(cudaMemcpyAsync(s->d_msg64, s->ckpt64[j] + s->aggN, sizeof(double) * s->msgN, cudaMemcpyDeviceToDevice,
                             st));
         for (int i = 0; i < len; ++i)
-            BCK(rec64_iteration(s, s->d_rec + static_cast<long long>(i) * s->rec_stride, lmax));
+            BCK(rec64_iteration(s, s->d_rec + static_cast<long long>(i) * s->rec_stride, lmax, tab_floats, st));
         for (int i = len - 1; i >= 0; --i) {
             bp.rec = s->d_rec + static_cast<long long>(i) * s->rec_stride;
             for (int ph = s->P - 1; ph >= 0; --ph)

@@ -15,6 +15,12 @@ size_t rec64_smem_bytes(int lmax);
 cudaError_t launch_rec64_phase(const EdgeDesc *edges, const int *items, int n_items, const float *tab, double *agg,
                                double *msg, unsigned char *rec, const long long *rec_off, int lmax, cudaStream_t st);
 cudaError_t launch_widen(const float *src, double *dst, long long n, cudaStream_t st);
+// the same update with an FP32 screen and FP64 only for the candidates (bit for
+// bit the same minima and argmins); tab_floats >= L_u * (ld | 1) of every edge
+size_t rec_screen_smem_bytes(int lmax, long long tab_floats);
+cudaError_t launch_rec_screen_phase(const EdgeDesc *edges, const int *items, int n_items, const float *tab,
+                                    double *agg, double *msg, unsigned char *rec, const long long *rec_off, int lmax,
+                                    long long tab_floats, cudaStream_t st);
 
 // backward.cu
 struct BwParams {

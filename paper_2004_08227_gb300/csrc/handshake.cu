@@ -64,7 +64,7 @@ struct Smem {
     float *w1;          // vh(t) - vh(0) in FP32 (pass 1)
     float *alpha, *beta, *pm;
     float4 *part;
-    uint64_t *bar;      // [4]: table buffers 0 and 1, exchange slots 0 and 1
+    uint64_t *bar;      // [6]: table buffers 0 and 1, exchange slots 0 and 1, node u ready 0 and 1
 };
 
 __device__ __forceinline__ Smem carve(char *base, const HsParams &p, int nbuf)
@@ -181,6 +181,7 @@ __device__ __forceinline__ float row_min(const float4 *row, const float4 *w, int
 {
     float m0 = INFINITY, m1 = INFINITY;
     int q = lg;
+#pragma unroll 4
     for (; q + G < Q; q += 2 * G) {
         m0 = min_add4(m0, row[q], w[q]);
         m1 = min_add4(m1, row[q + G], w[q + G]);
@@ -215,6 +216,14 @@ __device__ __host__ __forceinline__ int part_stride(int Q)
 __device__ __forceinline__ bool rr_fits(int nr, int Q, int T, int tile_floats)
 {
     return Q > 32 && Q <= 32 * kCR && nr <= kRR * (T >> 5) && (T >> 5) * part_stride(Q) * 4 <= tile_floats;
+}
+
+// The same with the last warp as node u's poller (it holds no rows); at most
+// 3 rows per poller lane.
+__device__ __host__ __forceinline__ bool pw_fits(int nr, int Q, int T, int tile_floats)
+{
+    const int W = (T >> 5) - 1;
+    return W >= 1 && Q >= 1 && Q <= 32 * kCR && nr <= kRR * W && nr <= 96 && W * part_stride(Q) * 4 <= tile_floats;
 }
 
 // Minimum over the warp of each of the kRR = 5 row values (five independent
@@ -334,10 +343,19 @@ __device__ __forceinline__ void slot_min8(float (&a)[kSR], int c, int G, F emit)
 // SIGNAL: wait for the expected versions of the inputs (persistent driver).
 // RM: 0 passes over the shared-memory slice, 1 register-resident passes
 // (rr_fits must hold), 2 register-resident passes for narrow rows (rs_fits).
-template <bool CLUSTER, bool SIGNAL, int RM>
+// PW (persistent driver, RM == 1 only): the last warp holds no rows; it polls
+// node u's rows and stages the next item while the other warps, once node v
+// has arrived, run pass 1's minima; node u's unaries are needed only by pass
+// 1's emit, which waits for the poller's arrival on `ubar` (phase `upar`).
+// STREAM (queue driver): `tile` is the table itself in global memory (read by
+// every pass, from L2 after the first), not a staged copy; no mbarrier.
+template <bool CLUSTER, bool SIGNAL, int RM, bool PW = false, bool STREAM = false>
 __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile, const Smem &sm, int rank,
-                        int r0, int nr, uint64_t *bar, uint32_t parity, int xpar, Versions ver, Next nx)
+                        int r0, int nr, uint64_t *bar, uint32_t parity, int xpar, Versions ver, Next nx,
+                        uint64_t *ubar = nullptr, uint32_t upar = 0)
 {
+    static_assert(!PW || (SIGNAL && RM == 1), "the poller warp serves the persistent register-resident passes");
+    static_assert(!STREAM || (SIGNAL && RM == 0 && !CLUSTER && !PW), "streamed tables: shared-memory-free passes");
     const int T = blockDim.x, tid = threadIdx.x;
     const int C = CLUSTER ? p.C : 1;
     const int ld = ed.ld, Q = ld >> 2, Lv = ed.Lv;
@@ -349,7 +367,8 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
     // passes, load this thread's fragment.  Independent of the node vectors:
     // both drivers do it while the requests for the vectors are in flight.
     const float4 *t4 = reinterpret_cast<const float4 *>(tile);
-    const int lane = tid & 31, warp = tid >> 5, W = T >> 5;
+    const int lane = tid & 31, warp = tid >> 5, W = (T >> 5) - (PW ? 1 : 0);  // W: warps holding rows
+    const bool poller = PW && warp == W;
     const float4 inf4 = make_float4(INFINITY, INFINITY, INFINITY, INFINITY);
     float4 tr[RM == 1 ? kRR : 1][RM == 1 ? kCR : 1];
     float4 ts[RM == 2 ? kSR : 1];
@@ -361,8 +380,8 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
     if (CLUSTER && tid == 0)
         mbar_arrive_expect_tx(sm.bar + 2 + xpar, static_cast<uint32_t>(C) * static_cast<uint32_t>(Q) * 16u);
     auto load_tile = [&]() {
-        if (!mbar_wait(bar, parity, p.spin_limit)) set_err(p.err, ERR_TIMEOUT);
-        if (RM == 1) {
+        if (!STREAM && !mbar_wait(bar, parity, p.spin_limit)) set_err(p.err, ERR_TIMEOUT);
+        if (RM == 1 && !poller) {
 #pragma unroll
             for (int k = 0; k < kRR; ++k)
 #pragma unroll
@@ -385,7 +404,66 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
     // in proportion to the entries), so the two waits overlap and every entry
     // is requested at once; the first requests are in flight while the table
     // fragment is loaded.
-    if (SIGNAL) {
+    if (PW) {
+        if (poller) {
+            // node u's rows: every request first (at most 3 per lane), then the checks
+            const ulonglong2 *A = agg + ed.au + r0;
+            const ulonglong2 *M = msg + ed.mu + r0;
+            const unsigned va = ver.u + ver.bump;
+            ulonglong2 xa[3], ya[3];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const int j = lane + 32 * i;
+                xa[i] = ya[i] = make_ulonglong2(0ull, 0ull);
+                if (j < nr) {
+                    xa[i] = ld_se(A + j);
+                    ya[i] = ld_se(M + j);
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const int j = lane + 32 * i;
+                if (j < nr)
+                    poll_diff<true>(p, A, M, j, va, ver.e, xa[i], ya[i], [&](int jj, float2 d) { uh[jj] = d; });
+            }
+            for (int j = lane + 96; j < nr; j += 32)
+                poll_diff<true>(p, A, M, j, va, ver.e, ld_se(A + j), ld_se(M + j),
+                                [&](int jj, float2 d) { uh[jj] = d; });
+            __syncwarp();
+            if (lane == 0) mbar_arrive(ubar);
+            // the next item: its work record, then (once the record is in
+            // shared memory) its table slice
+            if (nx.rec_dst) *nx.rec_dst = nx.rec;
+            __syncwarp();
+            if (lane == 31 && nx.on) {
+                fence_proxy_async();
+                issue_tile(nx.wi->ed, rank, nx.wi->rows, p.tab, nx.dst, nx.bar);
+            }
+        } else {
+            // node v's entries over every thread of the row warps
+            const int nv = 32 * W;
+            const ulonglong2 *A = agg + ed.av;
+            const ulonglong2 *M = msg + ed.mv;
+            ulonglong2 x = make_ulonglong2(0ull, 0ull), y = x;
+            if (tid < Lv) {
+                x = ld_se(A + tid);
+                y = ld_se(M + tid);
+            }
+            load_tile();
+            for (int j = tid; j < Lv; j += nv) {
+                if (j != tid) {
+                    x = ld_se(A + j);
+                    y = ld_se(M + j);
+                }
+                poll_diff<true>(p, A, M, j, ver.v, ver.e, x, y, [&](int jj, float2 d) { sm.vh[jj] = d; });
+            }
+            for (int t = Lv + tid; t < ld; t += nv) sm.vh[t] = make_float2(0.f, 0.f);
+            named_barrier_1(nv);
+            const float2 vref = sm.vh[0];
+            for (int t = tid; t < ld; t += nv) sm.w1[t] = t < Lv ? df_to_f(df_sub(sm.vh[t], vref)) : 0.f;
+            asm volatile("bar.sync 2, %0;" ::"r"(nv) : "memory");
+        }
+    } else if (SIGNAL) {
         // (any split in 1 .. W - 1 is correct: a float estimate, no division)
         const int uw = min(W - 1, max(1, __float2int_rn(static_cast<float>(W * nr) *
                                                          __frcp_rn(static_cast<float>(nr + Lv)))));
@@ -433,14 +511,16 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
         for (int t = tid; t < ld; t += T) sm.w1[t] = t < Lv ? df_to_f(df_sub(sm.vh[t], vref)) : 0.f;
     }
 
-    if (SIGNAL && nx.rec_dst) *nx.rec_dst = nx.rec;
-    if (!SIGNAL) load_tile();
-    __syncthreads();
-    // the last thread (its warp has the fewest rows in the passes): the buffer's
-    // previous item has finished
-    if (SIGNAL && tid == T - 1 && nx.on) {
-        fence_proxy_async();
-        issue_tile(nx.wi->ed, rank, nx.wi->rows, p.tab, nx.dst, nx.bar);
+    if (!PW) {
+        if (SIGNAL && nx.rec_dst) *nx.rec_dst = nx.rec;
+        if (!SIGNAL) load_tile();
+        __syncthreads();
+        // the last thread (its warp has the fewest rows in the passes): the buffer's
+        // previous item has finished
+        if (SIGNAL && tid == T - 1 && nx.on) {
+            fence_proxy_async();
+            issue_tile(nx.wi->ed, rank, nx.wi->rows, p.tab, nx.dst, nx.bar);
+        }
     }
 
     const int G = row_lanes(nr, Q, T);
@@ -458,6 +538,7 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
             sm.alpha[s] = df_to_f(df_sub(u, a));
         };
         if (RM == 1) {
+          if (!poller) {
             float acc[kRR];
             float4 wv[kCR];
 #pragma unroll
@@ -470,7 +551,11 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
             }
             const float mk = warp_min_rows5(acc, lane);
             const int s = warp + W * rs_row(lane);  // the five owners emit at once
-            if (rs_owner(lane) && s < nr) emit(s, mk);
+            if (rs_owner(lane) && s < nr) {
+                if (PW && !mbar_wait(ubar, upar, p.spin_limit)) set_err(p.err, ERR_TIMEOUT);
+                emit(s, mk);
+            }
+          }
         } else if (RM == 2) {
             const float4 wv = sc < Q ? w[sc] : make_float4(0.f, 0.f, 0.f, 0.f);
             float acc[kSR];
@@ -515,15 +600,17 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
             float4 al[kRR];
 #pragma unroll
             for (int k = 0; k < kRR; ++k) {
-                const float a = warp + W * k < nr ? sm.alpha[warp + W * k] : 0.f;
+                const float a = (!poller && warp + W * k < nr) ? sm.alpha[warp + W * k] : 0.f;
                 al[k] = make_float4(a, a, a, a);
             }
             const int Qp = part_stride(Q);
+            if (!poller) {
 #pragma unroll
-            for (int i = 0; i < kCR; ++i) {
-                const float4 m = min5_4(add4(tr[0][i], al[0]), add4(tr[1][i], al[1]), add4(tr[2][i], al[2]),
-                                        add4(tr[3][i], al[3]), add4(tr[4][i], al[4]));
-                if (lane + 32 * i < Q) part2[warp * Qp + lane + 32 * i] = m;
+                for (int i = 0; i < kCR; ++i) {
+                    const float4 m = min5_4(add4(tr[0][i], al[0]), add4(tr[1][i], al[1]), add4(tr[2][i], al[2]),
+                                            add4(tr[3][i], al[3]), add4(tr[4][i], al[4]));
+                    if (lane + 32 * i < Q) part2[warp * Qp + lane + 32 * i] = m;
+                }
             }
             __syncthreads();
             // 4 consecutive lanes per chunk, each over every 4th warp, then 2 shuffles
@@ -566,6 +653,7 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
                 const int q = tid % Q, sub = tid / Q;
                 float4 m = make_float4(INFINITY, INFINITY, INFINITY, INFINITY);
                 int s = sub;
+#pragma unroll 4
                 for (; s + nsub < nr; s += 2 * nsub) {  // two rows per step: packed adds, 3-input mins
                     const float a1 = sm.alpha[s], a2 = sm.alpha[s + nsub];
                     const float4 v1 = add4(t4[static_cast<size_t>(s) * Q + q], make_float4(a1, a1, a1, a1));
@@ -637,6 +725,7 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
             st_se(msg + ed.mu + r0 + s, se_make(df_sub(c, u), ver.e + 1u));
         };
         if (RM == 1) {
+          if (!poller) {
             float acc[kRR];
             float4 bw[kCR];
 #pragma unroll
@@ -650,6 +739,7 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
             const float mk = warp_min_rows5(acc, lane);
             const int s = warp + W * rs_row(lane);  // the five owners emit at once
             if (rs_owner(lane) && s < nr) emit(s, mk);
+          }
         } else if (RM == 2) {
             const float4 bv = sc < Q ? w[sc] : make_float4(0.f, 0.f, 0.f, 0.f);
             float acc[kSR];
@@ -710,7 +800,7 @@ __global__ void __launch_bounds__(512, CLUSTER || RRK ? 1 : 2) hs_looped_kernel(
     }
 }
 
-template <bool CLUSTER, bool RRK>
+template <bool CLUSTER, bool RRK, bool PW>
 __global__ void __launch_bounds__(512) hs_persistent_kernel(HsParams p)
 {
     extern __shared__ __align__(16) char smem_raw[];
@@ -722,7 +812,7 @@ __global__ void __launch_bounds__(512) hs_persistent_kernel(HsParams p)
     const int n = p.work_off[cid + 1] - begin;
     const long long total = static_cast<long long>(n) * p.iterations;
     if (threadIdx.x == 0) {
-        for (int j = 0; j < 4; ++j) mbar_init(&sm.bar[j], 1);
+        for (int j = 0; j < 6; ++j) mbar_init(&sm.bar[j], 1);
         fence_mbar_init();
     }
     __syncthreads();
@@ -740,6 +830,7 @@ __global__ void __launch_bounds__(512) hs_persistent_kernel(HsParams p)
     __syncthreads();
     if (tid == 0) issue_tile(sm.wi[0].ed, rank, sm.wi[0].rows, p.tab, sm.tile, &sm.bar[0]);
     int i = 0, it = 0;
+    unsigned npw = 0;  // items that took the poller-warp passes (their mbarrier phases)
     for (long long k = 0; k < total; ++k) {
         const WorkItem &w = sm.wi[k & 1];
         const EdgeDesc ed = w.ed;
@@ -764,12 +855,22 @@ __global__ void __launch_bounds__(512) hs_persistent_kernel(HsParams p)
         int r0, nr;
         rows_of_R(ed, rank, w.rows, r0, nr);
         const uint32_t par = static_cast<uint32_t>((k >> 1) & 1);
-        if (RRK && rr_fits(nr, ed.ld >> 2, blockDim.x, p.tile_floats))
-            hs_item<CLUSTER, true, 1>(p, ed, sm.tile + b * p.tile_floats, sm, rank, r0, nr, sm.bar + b, par, b, ver, nx);
-        else if (!RRK && rs_fits(nr, ed.ld >> 2, blockDim.x, p.tile_floats))
-            hs_item<CLUSTER, true, 2>(p, ed, sm.tile + b * p.tile_floats, sm, rank, r0, nr, sm.bar + b, par, b, ver, nx);
-        else
-            hs_item<CLUSTER, true, 0>(p, ed, sm.tile + b * p.tile_floats, sm, rank, r0, nr, sm.bar + b, par, b, ver, nx);
+        if constexpr (PW) {
+            // the host launches this variant only when every item fits (hs_pw_fits)
+            hs_item<CLUSTER, true, 1, true>(p, ed, sm.tile + b * p.tile_floats, sm, rank, r0, nr, sm.bar + b, par, b,
+                                            ver, nx, sm.bar + 4 + (npw & 1), (npw >> 1) & 1);
+            ++npw;
+        } else {
+            if (RRK && rr_fits(nr, ed.ld >> 2, blockDim.x, p.tile_floats))
+                hs_item<CLUSTER, true, 1>(p, ed, sm.tile + b * p.tile_floats, sm, rank, r0, nr, sm.bar + b, par, b, ver,
+                                          nx);
+            else if (!RRK && rs_fits(nr, ed.ld >> 2, blockDim.x, p.tile_floats))
+                hs_item<CLUSTER, true, 2>(p, ed, sm.tile + b * p.tile_floats, sm, rank, r0, nr, sm.bar + b, par, b, ver,
+                                          nx);
+            else
+                hs_item<CLUSTER, true, 0>(p, ed, sm.tile + b * p.tile_floats, sm, rank, r0, nr, sm.bar + b, par, b, ver,
+                                          nx);
+        }
         if (++i == n) {
             i = 0;
             ++it;
@@ -778,6 +879,70 @@ __global__ void __launch_bounds__(512) hs_persistent_kernel(HsParams p)
     if (CLUSTER) {  // no CTA leaves while another may still access its shared memory
         cluster_arrive_release();
         cluster_wait_acquire();
+    }
+}
+
+// Queue driver: one CTA per edge at a time, every CTA taking the next item of
+// one global queue (an atomic counter over a list that repeats every
+// iteration).  The list orders each model's items by its matchings and
+// interleaves the models by their progress through an iteration, so an
+// item's inputs were produced by items far earlier in the queue; every wait is
+// on an earlier item, taken by a co-resident CTA, so the waits end.  Tables
+// are read from global memory by every pass (the first pass from HBM, the
+// others from L2: nothing staged in shared memory, so many CTAs fit an SM),
+// and the next item's table is prefetched into L2 while the current one runs.
+__device__ __forceinline__ void prefetch_l2(const void *src, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
+__global__ void __launch_bounds__(128) hs_queue_kernel(HsParams p)
+{
+    extern __shared__ __align__(16) char smem_raw[];
+    Smem sm = carve(smem_raw, p, 1);
+    long long *s_g = reinterpret_cast<long long *>(sm.bar + 6);  // [2] item index of this and the next item
+    constexpr int kRec = static_cast<int>(sizeof(WorkItem) / sizeof(int4));
+    const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31;
+    const bool last_warp = tid >= T - 32, rec_lane = tid >= T - kRec;
+    const long long EE = p.queue_items;
+    const long long total = EE * static_cast<long long>(p.iterations);
+    if (tid == T - 1) s_g[0] = static_cast<long long>(atomicAdd(p.queue, 1ull));
+    __syncthreads();
+    long long g = s_g[0];
+    if (g < total && rec_lane)
+        reinterpret_cast<int4 *>(&sm.wi[0])[tid - (T - kRec)] =
+            reinterpret_cast<const int4 *>(p.work + g % EE)[tid - (T - kRec)];
+    __syncthreads();
+    for (long long k = 0; g < total; ++k) {
+        const WorkItem &w = sm.wi[k & 1];
+        const EdgeDesc ed = w.ed;
+        const long long it = g / EE;
+        Next nx = {};
+        if (last_warp) {  // the next item: index, work record, table into L2
+            unsigned long long v = 0;
+            if (lane == 31) v = atomicAdd(p.queue, 1ull);
+            v = __shfl_sync(0xffffffffu, v, 31);
+            const long long g2 = static_cast<long long>(v);
+            if (lane == 31) s_g[(k + 1) & 1] = g2;
+            if (g2 < total) {
+                const WorkItem *src = p.work + g2 % EE;
+                if (rec_lane) {
+                    nx.rec = __ldg(reinterpret_cast<const int4 *>(src) + (tid - (T - kRec)));
+                    nx.rec_dst = reinterpret_cast<int4 *>(&sm.wi[(k + 1) & 1]) + (tid - (T - kRec));
+                }
+                if (lane == 31) {
+                    const long long toff = __ldg(&src->ed.toff);
+                    const int Lu = __ldg(&src->ed.Lu), ld = __ldg(&src->ed.ld);
+                    prefetch_l2(p.tab + toff, static_cast<uint32_t>(Lu) * static_cast<uint32_t>(ld) * 4u);
+                }
+            }
+        }
+        const Versions ver = {static_cast<unsigned>(it) * static_cast<unsigned>(w.deg_u) + static_cast<unsigned>(w.pos_u),
+                              static_cast<unsigned>(it) * static_cast<unsigned>(w.deg_v) + static_cast<unsigned>(w.pos_v),
+                              static_cast<unsigned>(it), (p.test_wait && k == 0 && blockIdx.x == 0) ? 1u : 0u};
+        hs_item<false, true, 0, false, true>(p, ed, p.tab + ed.toff, sm, 0, 0, ed.Lu, nullptr, 0u,
+                                             static_cast<int>(k & 1), ver, nx);
+        g = s_g[(k + 1) & 1];
     }
 }
 
@@ -821,7 +986,7 @@ size_t hs_smem_bytes(int nbuf, int tile_floats, int rmax, int ldmax, int threads
     const size_t d = static_cast<size_t>(nbuf) * rmax + static_cast<size_t>(ldmax);
     const size_t f = static_cast<size_t>(nbuf) * tile_floats + static_cast<size_t>(rmax) +
                      (2 + static_cast<size_t>(nbuf) * C) * static_cast<size_t>(ldmax) + 4 * static_cast<size_t>(threads);
-    return 2 * sizeof(WorkItem) + d * 8 + f * 4 + 32;
+    return 2 * sizeof(WorkItem) + d * 8 + f * 4 + 64;
 }
 
 cudaError_t hs_prepare(size_t smem)
@@ -831,10 +996,12 @@ cudaError_t hs_prepare(size_t smem)
     if ((e = set_attrs(hs_looped_kernel<true, false>, smem)) != cudaSuccess) return e;
     if ((e = set_attrs(hs_looped_kernel<false, true>, smem)) != cudaSuccess) return e;
     if ((e = set_attrs(hs_looped_kernel<true, true>, smem)) != cudaSuccess) return e;
-    if ((e = set_attrs(hs_persistent_kernel<false, false>, smem)) != cudaSuccess) return e;
-    if ((e = set_attrs(hs_persistent_kernel<true, false>, smem)) != cudaSuccess) return e;
-    if ((e = set_attrs(hs_persistent_kernel<false, true>, smem)) != cudaSuccess) return e;
-    return set_attrs(hs_persistent_kernel<true, true>, smem);
+    if ((e = set_attrs(hs_persistent_kernel<false, false, false>, smem)) != cudaSuccess) return e;
+    if ((e = set_attrs(hs_persistent_kernel<true, false, false>, smem)) != cudaSuccess) return e;
+    if ((e = set_attrs(hs_persistent_kernel<false, true, false>, smem)) != cudaSuccess) return e;
+    if ((e = set_attrs(hs_persistent_kernel<true, true, false>, smem)) != cudaSuccess) return e;
+    if ((e = set_attrs(hs_persistent_kernel<false, true, true>, smem)) != cudaSuccess) return e;
+    return set_attrs(hs_persistent_kernel<true, true, true>, smem);
 }
 
 cudaError_t hs_launch_looped(const HsParams &p, int n_items, int threads, size_t smem, cudaStream_t st)
@@ -851,11 +1018,41 @@ cudaError_t hs_launch_looped(const HsParams &p, int n_items, int threads, size_t
 cudaError_t hs_launch_persistent(const HsParams &p, int clusters, int threads, size_t smem, cudaStream_t st)
 {
     const int grid = clusters * p.C;
+    if (p.rr && p.pw)
+        return p.C > 1 ? launch(hs_persistent_kernel<true, true, true>, p, grid, threads, smem, p.C, st)
+                       : launch(hs_persistent_kernel<false, true, true>, p, grid, threads, smem, 1, st);
     if (p.rr)
-        return p.C > 1 ? launch(hs_persistent_kernel<true, true>, p, grid, threads, smem, p.C, st)
-                       : launch(hs_persistent_kernel<false, true>, p, grid, threads, smem, 1, st);
-    return p.C > 1 ? launch(hs_persistent_kernel<true, false>, p, grid, threads, smem, p.C, st)
-                   : launch(hs_persistent_kernel<false, false>, p, grid, threads, smem, 1, st);
+        return p.C > 1 ? launch(hs_persistent_kernel<true, true, false>, p, grid, threads, smem, p.C, st)
+                       : launch(hs_persistent_kernel<false, true, false>, p, grid, threads, smem, 1, st);
+    return p.C > 1 ? launch(hs_persistent_kernel<true, false, false>, p, grid, threads, smem, p.C, st)
+                   : launch(hs_persistent_kernel<false, false, false>, p, grid, threads, smem, 1, st);
+}
+
+cudaError_t hs_launch_queue(const HsParams &p, int blocks, int threads, size_t smem, cudaStream_t st)
+{
+    cudaError_t e = cudaFuncSetAttribute(hs_queue_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    return launch(hs_queue_kernel, p, blocks, threads, smem, 1, st);
+}
+
+int hs_queue_max_blocks(int threads, size_t smem)
+{
+    if (cudaFuncSetAttribute(hs_queue_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) !=
+        cudaSuccess)
+        return 0;
+    int per_sm = 0, dev = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hs_queue_kernel, threads, smem) != cudaSuccess) return 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return per_sm * sms;
+}
+
+bool hs_pw_fits(int nr_max, int Q_max, int threads, int tile_floats)
+{
+    // every row count up to nr_max and chunk count up to Q_max must fit
+    return Q_max > 32 && pw_fits(nr_max, Q_max, threads, tile_floats) &&
+           (((threads >> 5) - 1) * (Q_max + 7) * 4 <= tile_floats);
 }
 
 bool hs_rr_fits(int nr_max, int Q_max, int threads, int tile_floats)
@@ -870,9 +1067,9 @@ int hs_max_active_clusters(int C, int threads, size_t smem, bool rr)
     if (hs_prepare(smem) != cudaSuccess) return 0;
     if (C <= 1) {
         int per_sm = 0;
-        const cudaError_t e = rr ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hs_persistent_kernel<false, true>,
+        const cudaError_t e = rr ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hs_persistent_kernel<false, true, true>,
                                                                                   threads, smem)
-                                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hs_persistent_kernel<false, false>,
+                                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hs_persistent_kernel<false, false, false>,
                                                                                   threads, smem);
         if (e != cudaSuccess) return 0;
         int dev = 0, sms = 0;
@@ -892,8 +1089,8 @@ int hs_max_active_clusters(int C, int threads, size_t smem, bool rr)
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int n = 0;
-    const cudaError_t e = rr ? cudaOccupancyMaxActiveClusters(&n, hs_persistent_kernel<true, true>, &cfg)
-                             : cudaOccupancyMaxActiveClusters(&n, hs_persistent_kernel<true, false>, &cfg);
+    const cudaError_t e = rr ? cudaOccupancyMaxActiveClusters(&n, hs_persistent_kernel<true, true, true>, &cfg)
+                             : cudaOccupancyMaxActiveClusters(&n, hs_persistent_kernel<true, false, false>, &cfg);
     return e == cudaSuccess ? n : 0;
 }
 

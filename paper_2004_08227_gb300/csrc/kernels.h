@@ -22,6 +22,7 @@ struct HsParams {
     int iterations;          // persistent: iterations to run
     int test_wait;           // testing: first item of worker 0 waits for an update that never comes
     int rr;                  // launch the variant with register-resident passes
+    int pw;                  // persistent, with rr: the last warp of a CTA polls node u (no rows)
     int C;                   // CTAs per edge (cluster size)
     int tile_floats;         // capacity of one table buffer (floats)
     int workers;             // warp driver: number of warp workers (lists in work_off / work)
@@ -29,6 +30,8 @@ struct HsParams {
     int cap;                 // warp driver: floats per table buffer (>= 32 rows of any table)
     int rmax;                // capacity of row vectors (floats, multiple of 4)
     int ldmax;               // capacity of column vectors (floats, multiple of 4)
+    unsigned long long *queue;  // queue driver: next item index (0 before the launch)
+    long long queue_items;      // queue driver: items per iteration (the list in work)
 };
 
 // Update counts an item expects of its inputs (persistent drivers): node u's
@@ -58,6 +61,10 @@ cudaError_t hs_launch_looped(const HsParams &p, int n_items, int threads, size_t
 cudaError_t hs_launch_persistent(const HsParams &p, int clusters, int threads, size_t smem, cudaStream_t st);
 int hs_max_active_clusters(int C, int threads, size_t smem, bool rr);
 bool hs_rr_fits(int nr_max, int Q_max, int threads, int tile_floats);
+bool hs_pw_fits(int nr_max, int Q_max, int threads, int tile_floats);  // rr_fits with a poller warp
+// queue driver (one launch, a global item queue, tables streamed from memory)
+cudaError_t hs_launch_queue(const HsParams &p, int blocks, int threads, size_t smem, cudaStream_t st);
+int hs_queue_max_blocks(int threads, size_t smem);  // co-resident blocks on the device
 
 // rules.cu: the MPLP (eq. (M)) and uniform (eq. (U)) updates of Sec. 4, one
 // CTA per edge, one launch per matching.

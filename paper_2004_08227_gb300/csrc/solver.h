@@ -54,8 +54,12 @@ struct mplpp_solver {
     int lmax = 1;          // >= every label count and row stride (exact bound's buffers)
     int work_off_cap = 0;  // capacity of d_work_off
     bool rr = false;       // register-resident pass variant
+    bool pw = false;       // with rr, persistent: a poller warp for node u (threads beyond the rows' warps)
     size_t smem_looped = 0, smem_persist = 0;
     int warp_blocks = 0, lw = 0, cap = 0;  // warp driver: blocks, per-warp vector and buffer capacity
+    int queue_blocks = 0;                  // queue driver: co-resident CTAs launched
+    size_t smem_queue = 0;
+    unsigned long long *d_queue = nullptr; // queue driver: next item index
     size_t smem_warp = 0;
     size_t smem_rule = 0;  // M and U updates (rules.cu)
     bool all_structured = false;  // every model MPLPP_PAIR_TRUNC_LINEAR (and at least one edge)
@@ -69,6 +73,7 @@ struct mplpp_solver {
 
     // device
     std::vector<void *> allocations;
+    long long device_bytes = 0;  // sum of the sizes in `allocations`
     mplpp::EdgeDesc *d_edges = nullptr;
     mplpp::NodeDesc *d_nodes = nullptr;
     float *d_tab = nullptr, *d_un0 = nullptr;
@@ -108,7 +113,10 @@ cudaError_t mplpp_solver::alloc(Ty **p, size_t count)
 {
     *p = nullptr;
     cudaError_t e = cudaMalloc(reinterpret_cast<void **>(p), (count ? count : 1) * sizeof(Ty));
-    if (e == cudaSuccess) allocations.push_back(*p);
+    if (e == cudaSuccess) {
+        allocations.push_back(*p);
+        device_bytes += static_cast<long long>((count ? count : 1) * sizeof(Ty));
+    }
     return e;
 }
 

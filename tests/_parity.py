@@ -6,7 +6,8 @@ reparametrized costs themselves (table form).  ``check_state`` compares
 theta^phi_u entry by entry, each node against its own scale (the largest
 magnitude of its oracle vector, at least 1); ``check_tables`` compares the
 implied reparametrized tables theta_uv - phi_{v->u} - phi_{u->v} with the
-oracle's tables entry by entry, each edge against its own scale.
+oracle's tables entry by entry, each edge against its own scale (its table,
+messages and end nodes: see check_tables).
 
 Labels (Sec. 4, Primal Rounding): the rounding decides node u on
 obj_u(s) = theta^phi_u(s) + sum over earlier neighbours v of theta^phi_vu(x_v, s).
@@ -91,17 +92,26 @@ def gpu_table(m, msg, e, poff=None, moff=None):
     return (tab - pu[:, None]) - pv[None, :]
 
 
-def check_tables(m, msg, th_uv, rtol=RTOL_STATE, what=""):
+def check_tables(m, msg, th_uv, agg, rtol=RTOL_STATE, what=""):
     """Every implied reparametrized table entry against the oracle's table,
-    each edge against its own scale (largest magnitude of its oracle table or
-    of the original table, at least 1).  Returns the largest relative error."""
-    _, poff, moff = offsets(m)
+    each edge against its own scale, at least 1: the largest magnitude among
+    the original table, the oracle's table, the edge's messages and the
+    reparametrized unaries of its two end nodes.  An entry is
+    theta_uv - phi_{v->u} - phi_{u->v}, and a message is the difference of two
+    quantities of its end node's scale (Sec. 4: phi_{v->u} = c - uh), so the
+    rounding error of an entry scales with its end nodes.  Returns the largest
+    relative error."""
+    uoff, poff, moff = offsets(m)
     worst = 0.0
     for e in range(m.E):
         g = gpu_table(m, msg, e, poff, moff)
         o = th_uv[poff[e]:poff[e + 1]].reshape(g.shape)
+        a, b = int(m.edge_u[e]), int(m.edge_v[e])
         scale = max(1.0, float(np.max(np.abs(o))),
-                    float(np.max(np.abs(np.asarray(m.pairwise[poff[e]:poff[e + 1]], np.float64)))))
+                    float(np.max(np.abs(np.asarray(m.pairwise[poff[e]:poff[e + 1]], np.float64)))),
+                    float(np.max(np.abs(msg[moff[e]:moff[e + 1]]))),
+                    float(np.max(np.abs(agg[uoff[a]:uoff[a + 1]]))),
+                    float(np.max(np.abs(agg[uoff[b]:uoff[b + 1]]))))
         err = float(np.max(np.abs(g - o))) / scale
         worst = max(worst, err)
         assert err <= rtol, f"{what} edge {e}: reparametrized table differs by {err:.3g} of its scale {scale:.3g}"

@@ -145,3 +145,32 @@ def test_grad_K50_L64_matches_oracle_and_central_differences():
             checked += 1
             break
     assert checked >= 3 * len(picks) // 4
+
+
+@pytest.mark.parametrize("case", ["uneven", "integer_ties", "pose_truncated", "wide_rows"])
+def test_screened_replay_equals_all_fp64_replay_bitwise(case):
+    """The backward's replay screens every minimization in FP32 and evaluates
+    only the candidates its error bound admits in FP64; its argmins, and so
+    the gradient, must equal those of the replay that evaluates every entry in
+    FP64, bit for bit -- also with exact ties (integer costs), the truncated
+    pose costs (most entries exactly 1.0) and rows wider than a warp."""
+    if case == "uneven":
+        m, T = W.uneven_complete(9, 1, 70, seed=12), 12
+    elif case == "integer_ties":
+        m, T = W.uneven_complete(8, 3, 17, seed=4), 10
+        m.unary[:] = np.round(4 * m.unary)
+        m.pairwise[:] = np.round(3 * m.pairwise)
+    elif case == "pose_truncated":
+        m, T = W.pose_like(6, 120, seed=2), 8
+    else:
+        m, T = W.uneven_complete(4, 150, 260, seed=3), 4
+    grads = []
+    for fp64 in (False, True):
+        s = Solver([m], record_every=3, test_fp64_replay=fp64)
+        s.run(T)
+        grads.append(s.backward())
+        s.close()
+    assert np.array_equal(grads[0][0], grads[1][0]) and np.array_equal(grads[0][1], grads[1][1])
+    _, gu_o, gp_o = oracle.grad(m, _order(m), T)
+    if case in ("uneven", "wide_rows"):  # tie-free costs: the oracle's argmins too
+        assert np.all(_close(grads[0][0], gu_o)) and np.all(_close(grads[0][1], gp_o))

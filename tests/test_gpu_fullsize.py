@@ -95,7 +95,7 @@ def _check_oracle(m, T, state, x, rtol_state):
     th_u, th_uv = oracle.run_parallel(m, off, order, T)
     agg, msg = state
     a = P.check_state(m, agg, th_u, rtol=rtol_state, what=m.name)
-    b = P.check_tables(m, msg, th_uv, rtol=rtol_state, what=m.name)
+    b = P.check_tables(m, msg, th_uv, agg, rtol=rtol_state, what=m.name)
     P.check_labels(m, th_u, th_uv, x, oracle.round_labels(m, th_u, th_uv), rtol=rtol_state, what=m.name)
     print(f"{m.name}: theta^phi_u within {a:.3g}, tables within {b:.3g} of their scales")
 

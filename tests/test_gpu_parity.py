@@ -53,7 +53,7 @@ def _check(s, models, i, xg, sol, eg, rtol=P.RTOL_STATE):
     m = models[i]
     agg, msg = P.model_state(s, models, i)
     P.check_state(m, agg, sol["th_u"], rtol=rtol, what=m.name)
-    P.check_tables(m, msg, sol["th_uv"], rtol=rtol, what=m.name)
+    P.check_tables(m, msg, sol["th_uv"], agg, rtol=rtol, what=m.name)
     P.check_labels(m, sol["th_u"], sol["th_uv"], xg, sol["labels"], rtol=rtol, what=m.name)
     assert abs(eg - _energy_def(m, xg)) <= 1e-9 * max(1.0, abs(eg))
 
@@ -143,8 +143,9 @@ def test_parity_batch_uneven_models():
     models = [W.uneven_complete(n, 3, 40, seed=50 + n) for n in (3, 5, 8, 11, 2)]
     models.append(W.tiny(7, 9, seed=4, density=0.5, uneven=True, pairwise="normal"))
     T = 20
-    for mode in ("looped", "persistent"):
+    for mode in ("looped", "persistent", "queue"):
         s, D, xs, en = _solve_gpu(models, T, mode=mode)
+        assert s.info()["mode"] == mode
         for i, m in enumerate(models):
             sol = oracle.solve(m, _order(m), T)
             _check_D(D[i], sol["bound"])
@@ -166,7 +167,7 @@ def test_dual_monotone_on_gpu():
 def test_looped_and_persistent_bitwise_equal_and_deterministic():
     m = W.uneven_complete(10, 4, 90, seed=9)
     states = []
-    for mode in ("looped", "persistent", "persistent"):
+    for mode in ("looped", "persistent", "persistent", "queue", "queue"):
         s = Solver([m], mode=mode)
         s.run(17)
         states.append(s.state_arrays())
@@ -584,3 +585,35 @@ def test_narrow_row_passes_ragged(cluster, threads, mode):
     ref.run(T)
     a, b = s.state_arrays(), ref.state_arrays()
     assert np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
+
+
+def test_queue_driver_batch_bitwise_equal_to_looped():
+    """The queue driver (one launch, one global queue of every model's updates)
+    on a batch of uneven models: bit for bit the looped driver's state."""
+    models = [W.uneven_complete(n, 2, 50, seed=70 + n) for n in (2, 3, 6, 9, 13, 4)]
+    models.append(W.knn(60, 5, 12, seed=1))
+    a = Solver(models, mode="looped")
+    b = Solver(models, mode="queue")
+    assert b.info()["mode"] == "queue" and b.info()["grid"] > 0
+    a.run(9)
+    b.run(9)
+    sa, sb = a.state_arrays(), b.state_arrays()
+    assert np.array_equal(sa[1], sb[1]) and np.array_equal(sa[2], sb[2])
+    b.run(4)  # continues from the state (versions reset per launch)
+    a.run(4)
+    sa, sb = a.state_arrays(), b.state_arrays()
+    assert np.array_equal(sa[1], sb[1]) and np.array_equal(sa[2], sb[2])
+
+
+def test_queue_driver_bounded_wait_times_out():
+    m = W.complete(10, 8, seed=0)
+    s = Solver([m], mode="queue", test_unreachable_wait=True, spin_limit=2000)
+    s.run(3)
+    with pytest.raises(MplppError) as ei:
+        s.sync()
+    assert ei.value.status == -4
+    s.close()
+    m2, _ = W.config(1)
+    sol = oracle.solve(m2, _order(m2), 20)
+    s2, D, _, _ = _solve_gpu([m2], 20, mode="queue")
+    _check_D(D[0], sol["bound"])

@@ -35,7 +35,7 @@ def _check_D(Dg, Do):
 def _check_state_labels(s, m, xg, th_u, th_uv):
     agg, msg = P.model_state(s, [m], 0)
     P.check_state(m, agg, th_u, what=m.name)
-    P.check_tables(m, msg, th_uv, what=m.name)
+    P.check_tables(m, msg, th_uv, agg, what=m.name)
     P.check_labels(m, th_u, th_uv, xg, oracle.round_labels(m, th_u, th_uv), what=m.name)
 
 

@@ -31,7 +31,7 @@ def _check(m, T, s):
     xs, _ = s.labels_per_model()
     agg, msg = P.model_state(s, [m], 0)
     P.check_state(m, agg, sol["th_u"], what=m.name)
-    P.check_tables(m, msg, sol["th_uv"], what=m.name)
+    P.check_tables(m, msg, sol["th_uv"], agg, what=m.name)
     P.check_labels(m, sol["th_u"], sol["th_uv"], xs[0], sol["labels"], what=m.name)
     return D
 

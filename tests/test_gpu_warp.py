@@ -34,7 +34,7 @@ def _check_labels(s, models, i, xg, sol):
     m = models[i]
     agg, msg = P.model_state(s, models, i)
     P.check_state(m, agg, sol["th_u"], what=m.name)
-    P.check_tables(m, msg, sol["th_uv"], what=m.name)
+    P.check_tables(m, msg, sol["th_uv"], agg, what=m.name)
     P.check_labels(m, sol["th_u"], sol["th_uv"], xg, sol["labels"], what=m.name)
 
 

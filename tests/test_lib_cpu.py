@@ -80,8 +80,8 @@ def test_round_robin_rejects_incomplete_graph():
 
 def test_struct_sizes_match_header():
     # layout of the option / info structs as the C compiler sees them
-    assert ctypes.sizeof(_lib.MplppOptions) == 40
-    assert ctypes.sizeof(_lib.MplppInfo) == 56
+    assert ctypes.sizeof(_lib.MplppOptions) == 48
+    assert ctypes.sizeof(_lib.MplppInfo) == 64
     assert ctypes.sizeof(_lib.MplppStateHeader) == 40
 
 
@@ -98,7 +98,8 @@ def test_ctypes_layout_equals_the_c_header(tmp_path):
     checks = {"mplpp_model": (_lib.MplppModel, ["n_edges", "labels", "pairwise", "schedule_kind", "edge_order",
                                                 "pair_kind", "pair_param"]),
               "mplpp_options": (_lib.MplppOptions, ["record_every", "threads", "rule", "spin_limit"]),
-              "mplpp_info_t": (_lib.MplppInfo, ["edges", "phases", "launches_per_iteration", "labeling_launches"])}
+              "mplpp_info_t": (_lib.MplppInfo, ["edges", "phases", "launches_per_iteration", "labeling_launches",
+                                                 "poller_warp", "device_bytes"])}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "mplpp.h"', "int main(void) {"]
     for st, (_, fields) in checks.items():
         lines.append(f'printf("%zu\\n", sizeof({st}));')
