@@ -74,12 +74,21 @@ enum {
     MPLPP_MODE_STRUCTURED = 4, /* every model MPLPP_PAIR_TRUNC_*, rule H, label counts
                                   <= 256: one launch per matching, one warp per edge, no
                                   table reads (see MPLPP_PAIR_*)                               */
-    MPLPP_MODE_QUEUE = 5       /* one launch for all iterations; one CTA per edge at a time,
+    MPLPP_MODE_QUEUE = 5,      /* one launch for all iterations; one CTA per edge at a time,
                                   every CTA taking the next edge from one queue of all models'
                                   updates (each model in schedule order, the models interleaved
                                   by their progress); tables read from memory by every pass
                                   instead of staged, so many CTAs share an SM (for many small
                                   models); options.cluster is ignored                        */
+    MPLPP_MODE_RESIDENT = 6,   /* one launch for all iterations; one CTA per model keeps the
+                                  model's reparametrization in shared memory and separates
+                                  its matchings by a block barrier (many small models: every
+                                  label count <= 32, the state of the largest model within
+                                  shared memory); options.cluster is ignored                  */
+    MPLPP_MODE_STRUCTURED_QUEUE = 7 /* the updates of MPLPP_MODE_STRUCTURED in one launch for
+                                  all iterations: every warp takes the next edge from the
+                                  queue of MPLPP_MODE_QUEUE and waits for its node entries by
+                                  their update counts (as MPLPP_MODE_PERSISTENT)             */
 };
 
 /* How a model's pairwise costs are given.  TRUNC_LINEAR: theta_uv(s,t) =
@@ -135,9 +144,11 @@ typedef struct {
     int32_t use_graph;        /* nonzero: replay the launches of an iteration from a CUDA graph */
     int32_t inputs_on_device; /* nonzero: model.unary / model.pairwise are device pointers and
                                  mplpp_backward writes device gradients                         */
-    int32_t record_every;     /* > 0: enables mplpp_backward, which replays the run in FP64 with
-                                 a state checkpoint every k iterations (memory ~ T/k states);
-                                 0: backward disabled.  Rule H and dense costs only.           */
+    int32_t record_every;     /* > 0: enables mplpp_backward, which replays the run in FP64:
+                                 recording the argmins of every iteration in one replay when
+                                 those records fit 1 GiB, else with a state checkpoint every k
+                                 iterations (memory ~ T/k states) and a second replay of each
+                                 segment; 0: backward disabled.  Rule H and dense costs only. */
     int32_t cluster;          /* CTAs sharing one edge (1..8); 0 = chosen from the shapes      */
     int32_t threads;          /* threads per CTA: 0 = chosen from the shapes, else a multiple
                                  of 32 in 64..512 (32..512 for MPLPP_MODE_WARP)                */
@@ -147,9 +158,11 @@ typedef struct {
                                  run must end with MPLPP_E_TIMEOUT instead of hanging            */
     int32_t rule;             /* MPLPP_RULE_* (0 = the Handshake update)                        */
     int64_t spin_limit;       /* polls before a device-side wait gives up with MPLPP_E_TIMEOUT */
-    int32_t test_fp64_replay; /* testing only (0 otherwise): mplpp_backward replays every
-                                 minimization in FP64 instead of screening it in FP32 first
-                                 (the two give the same argmins and gradient bit for bit)    */
+    int32_t test_backward;    /* testing only (0 otherwise), bit flags for mplpp_backward:
+                                 1 = replay every minimization in FP64 instead of screening
+                                 it in FP32 first; 2 = checkpoints and a second replay per
+                                 segment even where every record fits (both paths give the
+                                 same argmins and gradient bit for bit)                       */
     int32_t reserved;         /* 0                                                             */
 } mplpp_options;
 

@@ -21,7 +21,8 @@ MPLPP_OK = 0
 STATUS = {0: "MPLPP_OK", -1: "MPLPP_E_INVALID", -2: "MPLPP_E_NOMEM", -3: "MPLPP_E_CUDA",
           -4: "MPLPP_E_TIMEOUT", -5: "MPLPP_E_NONFINITE", -6: "MPLPP_E_STATE", -7: "MPLPP_E_UNSUPPORTED"}
 SCHED = {"round_robin": 0, "greedy_color": 1, "alg1": 2, "user": 3}
-MODE = {"auto": 0, "looped": 1, "persistent": 2, "warp": 3, "structured": 4, "queue": 5}
+MODE = {"auto": 0, "looped": 1, "persistent": 2, "warp": 3, "structured": 4, "queue": 5, "resident": 6,
+        "structured_queue": 7}
 PAIR = {"dense": 0, "trunc_linear": 1, "trunc_quad": 2}  # tables, or w min(|s - t|, tau) / w min((s - t)^2, tau)
 MODE_NAME = {v: k for k, v in MODE.items()}
 RULE = {"H": 0, "M": 1, "U": 2}  # Sec. 4: eqs. (H), (M), (U)
@@ -44,7 +45,7 @@ class MplppModel(ctypes.Structure):
 class MplppOptions(ctypes.Structure):
     _fields_ = [("mode", c_i32), ("use_graph", c_i32), ("inputs_on_device", c_i32), ("record_every", c_i32),
                 ("cluster", c_i32), ("threads", c_i32), ("test_unreachable_wait", c_i32), ("rule", c_i32),
-                ("spin_limit", c_i64), ("test_fp64_replay", c_i32), ("reserved", c_i32)]
+                ("spin_limit", c_i64), ("test_backward", c_i32), ("reserved", c_i32)]
 
 
 class MplppInfo(ctypes.Structure):

@@ -369,7 +369,7 @@ static bool struct_fits(mplpp_solver *s)
     return lmax <= kStructMaxL;
 }
 
-static mplpp_status apply_struct_mapping(mplpp_solver *s, int optin)
+static mplpp_status apply_struct_mapping(mplpp_solver *s, int optin, bool queue = false)
 {
     if (!s->all_structured)
         return fail(s, MPLPP_E_UNSUPPORTED, "structured mode needs every model's costs as MPLPP_PAIR_TRUNC_*");
@@ -385,6 +385,17 @@ static mplpp_status apply_struct_mapping(mplpp_solver *s, int optin)
     cudaError_t ce = struct_prepare(s->struct_lmax);
     if (ce != cudaSuccess) return cuda_fail(s, ce, "kernel attributes");
     s->mode = MPLPP_MODE_STRUCTURED;
+    if (queue) {  // persistent: the queue list, co-resident blocks of 8 warps
+        int blocks = std::min(struct_queue_max_blocks(s->struct_lmax), (s->EE + 7) / 8);
+        if (blocks < 1) return fail(s, MPLPP_E_UNSUPPORTED, "structured queue driver: no block fits");
+        if (!s->d_queue) CK(s, s->alloc(&s->d_queue, 1));
+        build_queue(s);
+        CK(s, cudaMemcpyAsync(s->d_work, s->work.data(), s->work.size() * sizeof(WorkItem), cudaMemcpyHostToDevice,
+                              s->stream));
+        CK(s, cudaStreamSynchronize(s->stream));
+        s->queue_blocks = blocks;
+        s->mode = MPLPP_MODE_STRUCTURED_QUEUE;
+    }
     drop_graphs(s);
     return MPLPP_OK;
 }
@@ -399,7 +410,7 @@ static mplpp_status apply_queue_mapping(mplpp_solver *s, int T, int optin)
     if (T != 128) return fail(s, MPLPP_E_UNSUPPORTED, "the queue driver runs 128 threads per CTA");
     if (s->EE == 0) return fail(s, MPLPP_E_UNSUPPORTED, "the queue driver needs edges");
     mapping_for(s, 1, T);  // sizes of the other drivers stay consistent
-    s->smem_queue = hs_smem_bytes(1, 4, s->rmax, s->ldmax, T, 1);
+    s->smem_queue = hs_smem_bytes(2, 4, s->rmax, s->ldmax, T, 1);
     if (s->smem_queue > static_cast<size_t>(optin)) return fail(s, MPLPP_E_UNSUPPORTED, "queue driver: shared memory");
     int blocks = hs_queue_max_blocks(T, s->smem_queue);
     blocks = std::min(blocks, s->EE);
@@ -416,6 +427,68 @@ static mplpp_status apply_queue_mapping(mplpp_solver *s, int T, int optin)
     return MPLPP_OK;
 }
 
+// The resident driver: one CTA per model with the model's state in shared
+// memory; one warp per edge of a matching (threads: the largest matching, at
+// most 16 warps, unless given).
+static mplpp_status apply_resident_mapping(mplpp_solver *s, int T, int optin)
+{
+    if (T % 32 || T < 0 || T > 512) return fail(s, MPLPP_E_INVALID, "threads must be a multiple of 32 in 32..512");
+    if (s->EE == 0) return fail(s, MPLPP_E_UNSUPPORTED, "the resident driver needs edges");
+    int lmax = 1, wmax = 1;
+    for (auto &nd : s->h_nodes) lmax = std::max(lmax, nd.L);
+    if (lmax > kResMaxL)
+        return fail(s, MPLPP_E_UNSUPPORTED,
+                    "the resident driver takes label counts up to " + std::to_string(kResMaxL) + " (largest here " +
+                        std::to_string(lmax) + ")");
+    const int nm = static_cast<int>(s->models.size());
+    std::vector<ResModel> rm(nm);
+    std::vector<int> off, edges;
+    long long state_max = 0;
+    for (int m = 0; m < nm; ++m) {
+        const ModelHost &mh = s->models[m];
+        const int n0 = mh.node_base, n1 = mh.node_base + mh.n;
+        rm[m].agg_base = s->h_nodes[n0].aoff;
+        rm[m].agg_n = (n1 < s->N ? s->h_nodes[n1].aoff : s->aggN) - rm[m].agg_base;
+        if (mh.E > 0) {
+            rm[m].msg_base = s->h_edges[mh.edge_base].mu;
+            const int e1 = mh.edge_base + mh.E;
+            rm[m].msg_n = (e1 < s->EE ? s->h_edges[e1].mu : s->msgN) - rm[m].msg_base;
+        } else {
+            rm[m].msg_base = 0;
+            rm[m].msg_n = 0;
+        }
+        rm[m].sched = static_cast<int>(off.size());
+        rm[m].P = static_cast<int>(mh.off.size()) - 1;
+        for (size_t k = 0; k < mh.off.size(); ++k) off.push_back(static_cast<int>(edges.size()) + mh.off[k]);
+        for (int i = 0; i < mh.E; ++i) edges.push_back(mh.edge_base + mh.order[i]);
+        for (size_t k = 0; k + 1 < mh.off.size(); ++k) wmax = std::max(wmax, mh.off[k + 1] - mh.off[k]);
+        state_max = std::max(state_max, rm[m].agg_n + rm[m].msg_n);
+    }
+    if (T == 0) T = 32 * std::min(16, wmax);
+    const size_t smem = static_cast<size_t>(state_max) * sizeof(float2) + static_cast<size_t>(T / 32) * kResWarpBytes;
+    if (smem > static_cast<size_t>(optin))
+        return fail(s, MPLPP_E_UNSUPPORTED,
+                    "the resident driver needs " + std::to_string(smem) + " B of shared memory for the largest model");
+    mapping_for(s, 1, 256);  // sizes of the other drivers stay consistent
+    cudaError_t ce = res_prepare(smem);
+    if (ce != cudaSuccess) return cuda_fail(s, ce, "kernel attributes");
+    if (!s->d_res_models) {
+        CK(s, s->alloc(&s->d_res_models, nm));
+        CK(s, s->alloc(&s->d_res_off, off.size()));
+        CK(s, s->alloc(&s->d_res_edges, std::max<size_t>(1, edges.size())));
+        CK(s, cudaMemcpyAsync(s->d_res_models, rm.data(), sizeof(ResModel) * nm, cudaMemcpyHostToDevice, s->stream));
+        CK(s, cudaMemcpyAsync(s->d_res_off, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice, s->stream));
+        CK(s, cudaMemcpyAsync(s->d_res_edges, edges.data(), sizeof(int) * edges.size(), cudaMemcpyHostToDevice,
+                              s->stream));
+        CK(s, cudaStreamSynchronize(s->stream));
+    }
+    s->mode = MPLPP_MODE_RESIDENT;
+    s->T = T;
+    s->smem_res = smem;
+    drop_graphs(s);
+    return MPLPP_OK;
+}
+
 static mplpp_status apply_mapping(mplpp_solver *s, int C, int T, int want)
 {
     int optin = 0;
@@ -423,8 +496,10 @@ static mplpp_status apply_mapping(mplpp_solver *s, int C, int T, int want)
     if (s->opt.rule != kRuleH) return apply_rule_mapping(s, optin);
     if (want == MPLPP_MODE_STRUCTURED || (want == MPLPP_MODE_AUTO && s->all_structured && struct_fits(s)))
         return apply_struct_mapping(s, optin);
+    if (want == MPLPP_MODE_STRUCTURED_QUEUE) return apply_struct_mapping(s, optin, true);
     if (want == MPLPP_MODE_WARP) return apply_warp_mapping(s, T, optin);
     if (want == MPLPP_MODE_QUEUE) return apply_queue_mapping(s, T, optin);
+    if (want == MPLPP_MODE_RESIDENT) return apply_resident_mapping(s, T, optin);
     mapping_for(s, C, T);
     if (s->smem_looped > static_cast<size_t>(optin))
         return fail(s, MPLPP_E_UNSUPPORTED,
@@ -468,7 +543,7 @@ extern "C" mplpp_status mplpp_create(const mplpp_model *models, int32_t n_models
     s->stream = static_cast<cudaStream_t>(stream);
     {
         const mplpp_options &o = s->opt;
-        if (o.mode < MPLPP_MODE_AUTO || o.mode > MPLPP_MODE_QUEUE)
+        if (o.mode < MPLPP_MODE_AUTO || o.mode > MPLPP_MODE_STRUCTURED_QUEUE)
             return fail(nullptr, MPLPP_E_INVALID, "unknown mode");
         if (o.cluster < 0 || o.cluster > 8) return fail(nullptr, MPLPP_E_INVALID, "cluster must be 0 or 1..8");
         if (o.rule < MPLPP_RULE_H || o.rule > MPLPP_RULE_U) return fail(nullptr, MPLPP_E_INVALID, "unknown rule");
@@ -476,7 +551,7 @@ extern "C" mplpp_status mplpp_create(const mplpp_model *models, int32_t n_models
             return fail(nullptr, MPLPP_E_INVALID, "backward is defined for the Handshake update only");
         if (o.rule != MPLPP_RULE_H &&
             (o.mode == MPLPP_MODE_PERSISTENT || o.mode == MPLPP_MODE_WARP || o.mode == MPLPP_MODE_STRUCTURED ||
-             o.mode == MPLPP_MODE_QUEUE))
+             o.mode == MPLPP_MODE_QUEUE || o.mode == MPLPP_MODE_RESIDENT || o.mode == MPLPP_MODE_STRUCTURED_QUEUE))
             return fail(nullptr, MPLPP_E_UNSUPPORTED, "the M and U updates run in the looped driver only");
         // a CTA of the cluster drivers splits its warps between the two node
         // vectors, so it needs two warps at least
@@ -833,6 +908,28 @@ cudaError_t enqueue_looped_iteration(mplpp_solver *s, cudaStream_t st)
 // first (whatever ran before: looped launches, an aborted run, load_state).
 cudaError_t enqueue_persistent(mplpp_solver *s, cudaStream_t st, int iterations)
 {
+    if (s->mode == MPLPP_MODE_STRUCTURED_QUEUE) {
+        cudaError_t e = launch_restamp(s->d_agg, s->aggN, s->d_msg, s->msgN, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(s->d_queue, 0, sizeof(unsigned long long), st);
+        if (e != cudaSuccess) return e;
+        StructParams sp = {s->d_edges, nullptr, 0, s->struct_lmax, s->d_pair_param, s->d_pair_kind, s->d_agg,
+                           s->d_msg};
+        sp.work = s->d_work;
+        sp.queue = s->d_queue;
+        sp.queue_items = s->EE;
+        sp.iterations = iterations;
+        sp.test_wait = s->opt.test_unreachable_wait ? 1 : 0;
+        sp.err = s->d_err;
+        sp.spin_limit = s->opt.spin_limit;
+        return launch_struct_queue(sp, s->queue_blocks, st);
+    }
+    if (s->mode == MPLPP_MODE_RESIDENT) {  // reads values only, writes version 0: no restamp
+        ResParams rp = {s->d_edges, s->d_tab, s->d_agg, s->d_msg, s->d_res_models, s->d_res_off, s->d_res_edges,
+                        iterations};
+        int lmax = 1;
+        for (auto &nd : s->h_nodes) lmax = std::max(lmax, nd.L);
+        return launch_resident(rp, static_cast<int>(s->models.size()), s->T, s->smem_res, lmax, st);
+    }
     HsParams p = make_params(s);
     cudaError_t e = launch_restamp(s->d_agg, s->aggN, s->d_msg, s->msgN, st);
     if (e != cudaSuccess) return e;
@@ -896,7 +993,7 @@ static mplpp_status run_plain(mplpp_solver *s, int iterations)
         } else {
             CK(s, enqueue_persistent(s, s->stream, iterations));
         }
-        s->launches += s->mode == MPLPP_MODE_QUEUE ? 3 : 2;  // restamp (+ queue reset) + persistent kernel
+        s->launches += s->mode == MPLPP_MODE_RESIDENT ? 1 : 2;  // (restamp +) the kernel
     }
     return MPLPP_OK;
 }
@@ -1110,6 +1207,8 @@ static const char *mode_name(int mode)
            : mode == MPLPP_MODE_WARP       ? "warp"
            : mode == MPLPP_MODE_STRUCTURED ? "structured"
            : mode == MPLPP_MODE_QUEUE      ? "queue"
+           : mode == MPLPP_MODE_RESIDENT   ? "resident"
+           : mode == MPLPP_MODE_STRUCTURED_QUEUE ? "structured_queue"
                                            : "looped";
 }
 
@@ -1154,11 +1253,12 @@ extern "C" mplpp_status mplpp_autotune(mplpp_solver *s, int32_t iterations, char
     CK(s, cudaEventCreate(&e0));
     CK(s, cudaEventCreate(&e1));
     for (int mode : {MPLPP_MODE_PERSISTENT, MPLPP_MODE_LOOPED, MPLPP_MODE_WARP, MPLPP_MODE_STRUCTURED,
-                     MPLPP_MODE_QUEUE})
+                     MPLPP_MODE_QUEUE, MPLPP_MODE_RESIDENT, MPLPP_MODE_STRUCTURED_QUEUE})
         for (int C : {1, 2, 3, 4, 5, 6, 8})
             for (int T : {128, 256, 512, 0}) {
                 if (T == 0) {  // the exact fit of the register-resident passes, if another size
-                    if (mode == MPLPP_MODE_WARP || mode == MPLPP_MODE_STRUCTURED) continue;
+                    if (mode == MPLPP_MODE_WARP || mode == MPLPP_MODE_STRUCTURED || mode == MPLPP_MODE_STRUCTURED_QUEUE)
+                        continue;
                     long long tile = 0, rows = 0;
                     int ldm = 4;
                     for (auto &ed : s->h_edges) {
@@ -1171,14 +1271,19 @@ extern "C" mplpp_status mplpp_autotune(mplpp_solver *s, int32_t iterations, char
                                        static_cast<int>(round4(std::max(4LL, tile))));
                     if (T == 0 || T == 128 || T == 256 || T == 512) continue;
                 }
-                if (mode == MPLPP_MODE_STRUCTURED && (C != 1 || T != 256 || !s->all_structured)) continue;
+                if ((mode == MPLPP_MODE_STRUCTURED || mode == MPLPP_MODE_STRUCTURED_QUEUE) &&
+                    (C != 1 || T != 256 || !s->all_structured))
+                    continue;
                 if (mode == MPLPP_MODE_QUEUE && (C != 1 || T != 128)) continue;
+                if (mode == MPLPP_MODE_RESIDENT && (C != 1 || T != 128)) continue;
+                const int Tm = mode == MPLPP_MODE_RESIDENT ? 0 : T;  // the resident driver sizes its blocks
                 if (mode == MPLPP_MODE_WARP && C != 1) continue;  // one warp per edge
                 if (mode == MPLPP_MODE_WARP && T == 512) T = 32;  // small blocks: shared memory per warp
-                if (apply_mapping(s, C, T, mode) != MPLPP_OK) {
+                if (apply_mapping(s, C, Tm, mode) != MPLPP_OK) {
                     s->err.clear();
                     continue;
                 }
+                if (mode == MPLPP_MODE_RESIDENT) T = s->T;
                 bool ok = restore() == cudaSuccess && run_plain(s, 1) == MPLPP_OK && restore() == cudaSuccess;
                 ok = ok && cudaEventRecord(e0, st) == cudaSuccess && run_plain(s, iterations) == MPLPP_OK &&
                      cudaEventRecord(e1, st) == cudaSuccess && cudaStreamSynchronize(st) == cudaSuccess;
@@ -1226,7 +1331,8 @@ extern "C" mplpp_status mplpp_info(const mplpp_solver *s, mplpp_info_t *info)
     info->threads = s->T;
     info->grid = s->mode == MPLPP_MODE_PERSISTENT ? s->clusters * s->C
                  : s->mode == MPLPP_MODE_WARP     ? s->warp_blocks
-                 : s->mode == MPLPP_MODE_QUEUE    ? s->queue_blocks
+                 : (s->mode == MPLPP_MODE_QUEUE || s->mode == MPLPP_MODE_STRUCTURED_QUEUE) ? s->queue_blocks
+                 : s->mode == MPLPP_MODE_RESIDENT ? static_cast<int>(s->models.size())
                                                   : 0;
     info->launches_per_iteration = (s->mode == MPLPP_MODE_LOOPED || s->mode == MPLPP_MODE_STRUCTURED) ? s->P : 0;
     info->labeling_launches = (s->level_off.empty() ? 1 : static_cast<int>(s->level_off.size()) - 1) + 1;

@@ -125,6 +125,29 @@ __global__ void __launch_bounds__(kThreads) bw_init_edges_kernel(const EdgeDesc 
     }
 }
 
+// Sums of values over the preimages of an index map, deterministic: every
+// element k < n holds key[k] (< m) and value val[k]; per warp, the lanes with
+// equal keys (__match_any_sync) are summed in lane order by the lowest of them
+// into that warp's partial part[warp][key]; afterwards (after a barrier) the
+// caller adds the warps' partials in warp order.  part[w][*] must be zero for
+// keys a warp does not hold; zero_part restores that after use.
+__device__ __forceinline__ void warp_preimage_sums(int n, const int *key, const double *val, double *part, int m)
+{
+    const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int base = 0; base < n; base += T) {  // the same trip count in every thread
+        const int k = base + tid;
+        const bool on = k < n;
+        const int kk = on ? key[k] : -1 - lane;  // idle lanes never match an active one
+        const unsigned grp = __match_any_sync(0xffffffffu, kk);
+        if (on && (grp & ((1u << lane) - 1u)) == 0) {  // the group's lowest lane
+            double acc = 0.0;
+            const int b0 = k - lane;
+            for (unsigned g = grp; g; g &= g - 1) acc += val[b0 + (__ffs(g) - 1)];
+            part[((base / T) * (T >> 5) + warp) * m + kk] = acc;
+        }
+    }
+}
+
 // Reverse of one Handshake update per CTA (one matching per launch).
 __global__ void __launch_bounds__(kThreads) bw_phase_kernel(BwParams p, const int *items)
 {
@@ -133,6 +156,7 @@ __global__ void __launch_bounds__(kThreads) bw_phase_kernel(BwParams p, const in
     const EdgeDesc ed = p.edges[e];
     const int Lu = ed.Lu, Lv = ed.Lv, T = blockDim.x, tid = threadIdx.x;
     const int lm = p.lmax;
+    const int nw = ((lm + T - 1) / T) * (T >> 5);  // warp partial rows (a warp per 32 keys of a pass)
     double *cb = sh;         // cbar = m3bar            [Lu]
     double *uhb = cb + lm;   // uhbar                   [Lu]
     double *alb = uhb + lm;  // alphabar                [Lu]
@@ -140,12 +164,13 @@ __global__ void __launch_bounds__(kThreads) bw_phase_kernel(BwParams p, const in
     double *bb = m1b + lm;   // bbar = m2bar            [Lv]
     double *vhb = bb + lm;   // vhbar                   [Lv]
     double *beb = vhb + lm;  // betabar                 [Lv]
-    int *t1 = reinterpret_cast<int *>(beb + lm);
+    double *part = beb + lm;  // [nw][lm] warp partial sums
+    int *t1 = reinterpret_cast<int *>(part + static_cast<size_t>(nw) * lm);
     int *s2 = t1 + lm;
     int *t3 = s2 + lm;
     const unsigned short *rec = reinterpret_cast<const unsigned short *>(p.rec + p.rec_off[e]);
     double *g = p.gtab + ed.toff;
-
+    for (int i = tid; i < nw * lm; i += T) part[i] = 0.0;
     for (int s = tid; s < Lu; s += T) {
         const double Au = p.adj_agg[ed.au + s];
         const double Pu = p.adj_msg[ed.mu + s];
@@ -165,47 +190,48 @@ __global__ void __launch_bounds__(kThreads) bw_phase_kernel(BwParams p, const in
     }
     __syncthreads();
     // pass 3 reversed: c(s) = theta(s, t3(s)) + beta(t3(s)) + uh(s)
-    for (int t = tid; t < Lv; t += T) {
-        double acc = 0.0;
-        for (int s = 0; s < Lu; ++s)
-            if (t3[s] == t) acc += cb[s];
-        beb[t] = acc;
-    }
+    warp_preimage_sums(Lu, t3, cb, part, lm);
     for (int s = tid; s < Lu; s += T) g[static_cast<long long>(s) * ed.ld + t3[s]] += cb[s];
     __syncthreads();
     // beta = vh - b;  b = m2 + vh
     for (int t = tid; t < Lv; t += T) {
-        const double v = vhb[t] + beb[t];
-        const double b = bb[t] - beb[t];
+        double acc = 0.0;
+        for (int w = 0; w < nw; ++w) {
+            acc += part[w * lm + t];
+            part[w * lm + t] = 0.0;
+        }
+        const double v = vhb[t] + acc;
+        const double b = bb[t] - acc;
         bb[t] = b;
         vhb[t] = v + b;
     }
     __syncthreads();
     // pass 2 reversed: m2(t) = theta(s2(t), t) + alpha(s2(t))
     for (int t = tid; t < Lv; t += T) g[static_cast<long long>(s2[t]) * ed.ld + t] += bb[t];
-    for (int s = tid; s < Lu; s += T) {
-        double acc = 0.0;
-        for (int t = 0; t < Lv; ++t)
-            if (s2[t] == s) acc += bb[t];
-        alb[s] = acc;
-    }
+    warp_preimage_sums(Lv, s2, bb, part, lm);
     __syncthreads();
     // alpha = uh - a;  a = (m1 + uh) / 2
     for (int s = tid; s < Lu; s += T) {
-        const double ab = -alb[s];
-        uhb[s] = (uhb[s] + alb[s]) + 0.5 * ab;
+        double acc = 0.0;
+        for (int w = 0; w < nw; ++w) {
+            acc += part[w * lm + s];
+            part[w * lm + s] = 0.0;
+        }
+        alb[s] = acc;
+        const double ab = -acc;
+        uhb[s] = (uhb[s] + acc) + 0.5 * ab;
         m1b[s] = 0.5 * ab;
     }
     __syncthreads();
     // pass 1 reversed: m1(s) = theta(s, t1(s)) + vh(t1(s))
     for (int s = tid; s < Lu; s += T) g[static_cast<long long>(s) * ed.ld + t1[s]] += m1b[s];
+    warp_preimage_sums(Lu, t1, m1b, part, lm);
+    __syncthreads();
     for (int t = tid; t < Lv; t += T) {
         double acc = 0.0;
-        for (int s = 0; s < Lu; ++s)
-            if (t1[s] == t) acc += m1b[s];
+        for (int w = 0; w < nw; ++w) acc += part[w * lm + t];
         vhb[t] += acc;
     }
-    __syncthreads();
     // uh = agg_u - phi_{v->u}, vh = agg_v - phi_{u->v} (values before the update)
     for (int s = tid; s < Lu; s += T) {
         p.adj_agg[ed.au + s] = uhb[s];
@@ -258,10 +284,16 @@ cudaError_t launch_bw_init(const EdgeDesc *edges, int n_edges, const NodeDesc *n
     return cudaSuccess;
 }
 
+size_t bw_phase_smem_bytes(int lmax)
+{
+    const size_t nw = static_cast<size_t>((lmax + kThreads - 1) / kThreads) * (kThreads / 32);
+    return static_cast<size_t>(lmax) * ((7 + nw) * sizeof(double) + 3 * sizeof(int));
+}
+
 cudaError_t launch_bw_phase(const BwParams &p, const int *items, int n_items, cudaStream_t st)
 {
     if (n_items <= 0) return cudaSuccess;
-    const size_t smem = static_cast<size_t>(p.lmax) * (7 * sizeof(double) + 3 * sizeof(int));
+    const size_t smem = bw_phase_smem_bytes(p.lmax);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(bw_phase_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              static_cast<int>(smem));
@@ -298,6 +330,8 @@ mplpp_status bfail(mplpp_solver *s, mplpp_status st, const std::string &m)
         cudaError_t e_ = (call);                                                                           \
         if (e_ != cudaSuccess) return bfail(s, MPLPP_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
     } while (0)
+
+constexpr long long kRecordAllBytes = 1LL << 30;  // argmin records kept for a one-replay backward
 
 template <typename T>
 cudaError_t ensure(mplpp_solver *s, T **p, size_t count)
@@ -339,12 +373,11 @@ extern "C" mplpp_status mplpp_backward(mplpp_solver *s, const float *dD, float *
     for (auto &nd : s->h_nodes) lmax = std::max(lmax, nd.L);
     int optin = 0;
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->device);
-    if (rec64_smem_bytes(lmax) > static_cast<size_t>(optin) ||
-        static_cast<size_t>(lmax) * (7 * sizeof(double) + 3 * sizeof(int)) > static_cast<size_t>(optin))
-        return bfail(s, MPLPP_E_UNSUPPORTED, "backward supports at most ~2700 labels per node");
+    if (rec64_smem_bytes(lmax) > static_cast<size_t>(optin) || bw_phase_smem_bytes(lmax) > static_cast<size_t>(optin))
+        return bfail(s, MPLPP_E_UNSUPPORTED, "backward supports at most ~1400 labels per node");
     long long tab_floats = 0;  // the screened replay stages the largest table in shared memory
     for (auto &ed : s->h_edges) tab_floats = std::max(tab_floats, 1LL * ed.Lu * (ed.ld | 1));
-    if (s->opt.test_fp64_replay || rec_screen_smem_bytes(lmax, tab_floats) > static_cast<size_t>(optin))
+    if ((s->opt.test_backward & 1) || rec_screen_smem_bytes(lmax, tab_floats) > static_cast<size_t>(optin))
         tab_floats = 0;
 
     // buffers
@@ -381,25 +414,36 @@ extern "C" mplpp_status mplpp_backward(mplpp_solver *s, const float *dD, float *
     BCK(ensure(s, &s->d_adj_agg, s->aggN));
     BCK(ensure(s, &s->d_adj_msg, s->msgN));
     BCK(ensure(s, &s->d_gtab, s->tabN));
-    BCK(ensure(s, &s->d_rec, static_cast<size_t>(s->rec_stride) * k));
+    // When the argmin records of every iteration fit kRecordAllBytes, the one
+    // replay records them all (no checkpoints, no second replay); otherwise a
+    // state checkpoint every k iterations and each segment replayed again,
+    // recording, before its reverse sweep.
+    const bool record_all = Ttot > 0 && s->rec_stride * Ttot <= kRecordAllBytes && !(s->opt.test_backward & 2);
+    const long long rec_slots = record_all ? Ttot : k;
+    if (s->rec_slots < rec_slots) {
+        BCK(s->release(s->d_rec));
+        s->d_rec = nullptr;
+        BCK(s->alloc(&s->d_rec, static_cast<size_t>(s->rec_stride) * rec_slots));
+        s->rec_slots = rec_slots;
+    }
     BCK(ensure(s, &s->d_dD, nm));
-    const long long nseg = (Ttot + k - 1) / k;
+    const long long nseg = record_all ? 0 : (Ttot + k - 1) / k;
     while (static_cast<long long>(s->ckpt64.size()) < nseg) {
         double *c = nullptr;
         BCK(s->alloc(&c, static_cast<size_t>(s->aggN + s->msgN)));
         s->ckpt64.push_back(c);
     }
 
-    // FP64 replay from phi = 0, checkpoint every k iterations
+    // FP64 replay from phi = 0: recording every iteration, or a checkpoint every k
     BCK(launch_widen(s->d_un0, s->d_agg64, s->aggN, st));
     BCK(cudaMemsetAsync(s->d_msg64, 0, sizeof(double) * s->msgN, st));
     for (long long it = 0; it < Ttot; ++it) {
-        if (it % k == 0) {
+        if (!record_all && it % k == 0) {
             double *c = s->ckpt64[it / k];
             BCK(cudaMemcpyAsync(c, s->d_agg64, sizeof(double) * s->aggN, cudaMemcpyDeviceToDevice, st));
             BCK(cudaMemcpyAsync(c + s->aggN, s->d_msg64, sizeof(double) * s->msgN, cudaMemcpyDeviceToDevice, st));
         }
-        BCK(rec64_iteration(s, nullptr, lmax, tab_floats, st));
+        BCK(rec64_iteration(s, record_all ? s->d_rec + it * s->rec_stride : nullptr, lmax, tab_floats, st));
     }
     BCK(cudaMemcpyAsync(s->d_dD, dD, sizeof(float) * nm, cudaMemcpyHostToDevice, st));
     BCK(cudaMemsetAsync(s->d_adj_agg, 0, sizeof(double) * s->aggN, st));
@@ -415,6 +459,11 @@ extern "C" mplpp_status mplpp_backward(mplpp_solver *s, const float *dD, float *
     bp.adj_msg = s->d_adj_msg;
     bp.gtab = s->d_gtab;
     bp.lmax = lmax;
+    for (long long it = record_all ? Ttot - 1 : -1; it >= 0; --it) {
+        bp.rec = s->d_rec + it * s->rec_stride;
+        for (int ph = s->P - 1; ph >= 0; --ph)
+            BCK(launch_bw_phase(bp, s->d_phase_edges + s->phase_off[ph], s->phase_off[ph + 1] - s->phase_off[ph], st));
+    }
     for (long long j = nseg - 1; j >= 0; --j) {
         const int len = static_cast<int>(std::min<long long>(k, Ttot - j * k));
         BCK(cudaMemcpyAsync(s->d_agg64, s->ckpt64[j], sizeof(double) * s->aggN, cudaMemcpyDeviceToDevice, st));

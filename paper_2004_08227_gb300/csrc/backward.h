@@ -36,6 +36,7 @@ struct BwParams {
 cudaError_t launch_bw_init(const EdgeDesc *edges, int n_edges, const NodeDesc *nodes, int n_nodes, const float *tab,
                            const double *agg, const double *msg, const float *dD, double *adj_agg, double *adj_msg,
                            double *gtab, cudaStream_t st);
+size_t bw_phase_smem_bytes(int lmax);
 cudaError_t launch_bw_phase(const BwParams &p, const int *items, int n_items, cudaStream_t st);
 cudaError_t launch_unpack_grad(const EdgeDesc *edges, int n_edges, const NodeDesc *nodes, int n_nodes,
                                const long long *pair_base, const long long *unary_base, const double *gtab,

@@ -899,7 +899,7 @@ __device__ __forceinline__ void prefetch_l2(const void *src, uint32_t bytes)
 __global__ void __launch_bounds__(128) hs_queue_kernel(HsParams p)
 {
     extern __shared__ __align__(16) char smem_raw[];
-    Smem sm = carve(smem_raw, p, 1);
+    Smem sm = carve(smem_raw, p, 2);  // node u's unaries and the column partials alternate by item parity
     long long *s_g = reinterpret_cast<long long *>(sm.bar + 6);  // [2] item index of this and the next item
     constexpr int kRec = static_cast<int>(sizeof(WorkItem) / sizeof(int4));
     const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31;
@@ -982,7 +982,7 @@ cudaError_t launch(K kernel, const HsParams &p, int grid, int threads, size_t sm
 size_t hs_smem_bytes(int nbuf, int tile_floats, int rmax, int ldmax, int threads, int C)
 {
     // 2 work records; double-float uh (nbuf), vh; FP32 tiles, w1, alpha, beta, pm (nbuf x C slots), part (float4 x T);
-    // 4 mbarriers
+    // 64 bytes: 6 mbarriers and the queue driver's two item indices
     const size_t d = static_cast<size_t>(nbuf) * rmax + static_cast<size_t>(ldmax);
     const size_t f = static_cast<size_t>(nbuf) * tile_floats + static_cast<size_t>(rmax) +
                      (2 + static_cast<size_t>(nbuf) * C) * static_cast<size_t>(ldmax) + 4 * static_cast<size_t>(threads);
@@ -1030,9 +1030,7 @@ cudaError_t hs_launch_persistent(const HsParams &p, int clusters, int threads, s
 
 cudaError_t hs_launch_queue(const HsParams &p, int blocks, int threads, size_t smem, cudaStream_t st)
 {
-    cudaError_t e = cudaFuncSetAttribute(hs_queue_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
-    if (e != cudaSuccess) return e;
+    // (shared memory attribute set by hs_queue_max_blocks when the mapping was made)
     return launch(hs_queue_kernel, p, blocks, threads, smem, 1, st);
 }
 

@@ -66,6 +66,29 @@ bool hs_pw_fits(int nr_max, int Q_max, int threads, int tile_floats);  // rr_fit
 cudaError_t hs_launch_queue(const HsParams &p, int blocks, int threads, size_t smem, cudaStream_t st);
 int hs_queue_max_blocks(int threads, size_t smem);  // co-resident blocks on the device
 
+// resident.cu: one CTA per model, the model's state in shared memory for all
+// iterations, a block barrier between matchings (label counts <= kResMaxL).
+constexpr int kResMaxL = 32;
+constexpr int kResWarpBytes = 2 * kResMaxL * 8 + 3 * kResMaxL * 4;  // per-warp vectors
+struct ResModel {
+    long long agg_base, agg_n;  // the model's entries in agg
+    long long msg_base, msg_n;  // ... and in msg
+    int sched;                  // offset of its matching offsets in sched_off
+    int P;                      // its matchings
+};
+struct ResParams {
+    const EdgeDesc *edges;
+    const float *tab;
+    ulonglong2 *agg;
+    ulonglong2 *msg;
+    const ResModel *models;
+    const int *sched_off;    // per model P + 1 offsets into sched_edges
+    const int *sched_edges;  // edge ids, every model's matchings in schedule order
+    int iterations;
+};
+cudaError_t res_prepare(size_t smem);
+cudaError_t launch_resident(const ResParams &p, int n_models, int threads, size_t smem, int lmax, cudaStream_t st);
+
 // rules.cu: the MPLP (eq. (M)) and uniform (eq. (U)) updates of Sec. 4, one
 // CTA per edge, one launch per matching.
 constexpr int kRuleH = 0, kRuleM = 1, kRuleU = 2;  // the MPLPP_RULE_* values
@@ -93,6 +116,15 @@ struct StructParams {
     const int *kind;       // [edges] MPLPP_PAIR_* per edge id
     ulonglong2 *agg;
     ulonglong2 *msg;
+    // persistent form (struct_queue_kernel): every warp takes the next item of
+    // the queue driver's list (work, queue_items per iteration); versioned waits
+    const WorkItem *work;
+    unsigned long long *queue;
+    long long queue_items;
+    int iterations;
+    int test_wait;
+    int *err;
+    long long spin_limit;
 };
 __host__ __device__ inline size_t struct_bytes_per_warp(int lmax)
 {
@@ -100,6 +132,8 @@ __host__ __device__ inline size_t struct_bytes_per_warp(int lmax)
 }
 cudaError_t struct_prepare(int lmax);
 cudaError_t launch_struct(const StructParams &p, cudaStream_t st);
+cudaError_t launch_struct_queue(const StructParams &p, int blocks, cudaStream_t st);
+int struct_queue_max_blocks(int lmax);  // co-resident blocks of 8 warps
 // tables of n consecutive edges from their (w, tau) and kind: w min(|s - t|,
 // tau) or w min((s - t)^2, tau), rows padded with +inf; a negative or
 // non-finite parameter sets ERR_NONFINITE

@@ -147,17 +147,21 @@ __global__ void __launch_bounds__(kThreads) rec64_phase_kernel(const EdgeDesc *e
 //         <= v(jc) - x(0) + e1 + e2 <= c(jc) + 2 e1 + 2 e2,
 // so every j with c(j) <= c(jc) + 2 e1 + 2 e2 (threshold rounded upwards) is a
 // candidate, and the FP64 argmin (the lowest index among equal FP64 minima)
-// is among the candidates.  The candidates of a pass go to a per-CTA list;
-// each is evaluated in FP64 by one thread and merged into its row's / column's
-// minimum with 64-bit shared-memory atomics on an order-preserving key (value
-// first, then the lowest index among equal values), so the order of the list
-// does not matter.  A pass whose candidates overflow the list takes the
-// all-FP64 scan instead.  The table is staged in shared memory with an odd row
-// stride (conflict-free row and column access).
+// is among the candidates.  One group of G threads (a power of two, G lines
+// per block of threads; the groups of a warp hold consecutive lines) handles
+// a line: both FP32 scans and the bound from the line's own h and
+// max |w(j)|.  The warp's candidates are appended to a per-warp list and
+// evaluated in FP64 32 at a time (one candidate per lane: GB300 issues an FP64
+// instruction at the cost of a full warp however few lanes are active), and
+// merged into their line's minimum with 64-bit shared-memory atomics on an
+// order-preserving key (value first, then the lowest index among equal
+// values), so neither the order of the list nor of the lanes matters.  A warp
+// whose list overflows scans its lines in FP64 entirely.  One block barrier
+// per pass.  The table is staged in shared memory with an odd row stride.
 namespace {
 
 constexpr int kScrThreads = 256;
-constexpr int kCandMax = 2048;  // candidates per pass
+constexpr int kWarpCands = 128;  // candidates per warp and pass
 
 __device__ __forceinline__ unsigned long long order_key(double v)
 {
@@ -172,101 +176,76 @@ __device__ __forceinline__ double key_value(unsigned long long k)
     return __longlong_as_double(static_cast<long long>(b));
 }
 
-struct ScreenSmem {
-    float *tab;                 // [Lu][ldp] staged table, ldp odd
-    double *uh, *vh, *al, *be;  // FP64 vectors (uh, alpha: Lu; vh, beta: Lv)
-    double *bv;                 // b(t) [Lv]
-    float *w;                   // FP32 shifted vector of the current pass [lmax]
-    float *pmin, *pmax;         // partial FP32 minima and |theta| maxima [G][n]
-    float *thr;                 // per row / column threshold [lmax]
-    unsigned long long *key;    // per row / column FP64 minimum key [lmax]
-    int *arg;                   // per row / column argmin [lmax]
-    int2 *cand;                 // [kCandMax] (row or column, index along it)
-    int *count;                 // [2] candidate count, scratch
-    float *red;                 // [kScrThreads / 32]
-};
-
-__device__ __forceinline__ float block_max_f(float v, float *red)
+// m(i) = min_j [theta(i, j) + x(j)], j < len, for every line i < n (rows of the
+// staged table when ROWS, else columns), with its lowest argmin; w(j) =
+// fl32(x(j) - x(0)).  key / arg: [n] per-line scratch; cand: this warp's list
+// [kWarpCands].  emit(i, m, argmin) runs on the line group's first thread.
+template <bool ROWS, typename F>
+__device__ __forceinline__ void screened_lines(const float *tab, int ldp, int n, int len, const double *xv,
+                                               const float *w, unsigned long long *key, int *arg, int2 *cand, F emit)
 {
-    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-    __syncthreads();
-    float r = 0.f;
-    for (int i = 0; i < static_cast<int>(blockDim.x >> 5); ++i) r = fmaxf(r, red[i]);
-    __syncthreads();
-    return r;
-}
-
-// One minimization family: for every line i < n (rows of the table when
-// ROWS, else columns), m(i) = min_j [theta(i, j) + x(j)] over j < len with
-// its lowest argmin, where x is the FP64 vector xv (x(0) = xv[0]) and w its
-// FP32 shifted copy (in sm.w, max |w| = D).  Results in sm.key / sm.arg.
-template <bool ROWS>
-__device__ void screened_min(const ScreenSmem &sm, int ldp, int n, int len, const double *xv, float D)
-{
-    const int T = blockDim.x, tid = threadIdx.x;
-    const int G = max(1, T / max(n, 1));  // threads per line
-    const int span = (len + G - 1) / G;   // elements per thread
-    auto th = [&](int i, int j) { return ROWS ? sm.tab[i * ldp + j] : sm.tab[j * ldp + i]; };
-    const double x0 = xv[0];
-    // scan 1: partial FP32 minima and |theta| maxima
-    for (int q = tid; q < G * n; q += T) {
-        const int i = q % n, g = q / n;
-        const int j0 = g * span, j1 = min(len, j0 + span);
-        float mn = INFINITY, mx = 0.f;
-        for (int j = j0; j < j1; ++j) {
-            const float t = th(i, j);
-            mn = fminf(mn, t + sm.w[j]);
-            mx = fmaxf(mx, fabsf(t));
-        }
-        sm.pmin[g * n + i] = mn;
-        sm.pmax[g * n + i] = mx;
-    }
-    if (tid == 0) sm.count[0] = 0;
-    __syncthreads();
-    const float ax0 = __double2float_ru(fabs(x0));
-    for (int i = tid; i < n; i += T) {
-        float mn = INFINITY, h = 0.f;
-        for (int g = 0; g < G; ++g) {
-            mn = fminf(mn, sm.pmin[g * n + i]);
-            h = fmaxf(h, sm.pmax[g * n + i]);
-        }
-        const float e1 = __fmul_ru(0x1p-22f, __fadd_ru(h, D));
-        const float e2 = __fmul_ru(0x1p-50f, __fadd_ru(__fadd_ru(h, D), ax0));
-        sm.thr[i] = __fadd_ru(__fadd_ru(mn, __fmul_ru(2.f, e1)), __fadd_ru(__fmul_ru(2.f, e2), 0x1p-126f));
-        sm.key[i] = ~0ull;
-        sm.arg[i] = INT_MAX;
-    }
-    __syncthreads();
-    // scan 2: candidates
-    for (int q = tid; q < G * n; q += T) {
-        const int i = q % n, g = q / n;
-        const int j0 = g * span, j1 = min(len, j0 + span);
-        const float tr = sm.thr[i];
-        for (int j = j0; j < j1; ++j)
-            if (th(i, j) + sm.w[j] <= tr) {
-                const int k = atomicAdd(&sm.count[0], 1);
-                if (k < kCandMax) sm.cand[k] = make_int2(i, j);
+    const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31;
+    int G = 32;
+    while (G > 1 && G * n > T) G >>= 1;
+    const int k = tid & (G - 1), g0 = tid / G, ng = T / G;
+    const float ax0 = __double2float_ru(fabs(xv[0]));
+    auto th = [&](int i, int j) { return ROWS ? tab[i * ldp + j] : tab[j * ldp + i]; };
+    for (int base = 0; base < n; base += ng) {  // the same trip count in every thread
+        const int i = base + g0;
+        const bool on = i < n;
+        float mn = INFINITY, h = 0.f, d = 0.f;
+        if (on)
+            for (int j = k; j < len; j += G) {
+                const float t = th(i, j);
+                const float wj = w[j];
+                mn = fminf(mn, t + wj);
+                h = fmaxf(h, fabsf(t));
+                d = fmaxf(d, fabsf(wj));
             }
-    }
-    __syncthreads();
-    const int nc = sm.count[0];
-    if (nc <= kCandMax) {
-        // FP64 values of the candidates, merged per line: value, then index
-        for (int k = tid; k < nc; k += T) {
-            const int2 c = sm.cand[k];
-            const double v = static_cast<double>(th(c.x, c.y)) + xv[c.y];
-            atomicMin(&sm.key[c.x], order_key(v));
+        for (int o = G >> 1; o > 0; o >>= 1) {
+            mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+            h = fmaxf(h, __shfl_xor_sync(0xffffffffu, h, o));
+            d = fmaxf(d, __shfl_xor_sync(0xffffffffu, d, o));
         }
-        __syncthreads();
-        for (int k = tid; k < nc; k += T) {
-            const int2 c = sm.cand[k];
-            const double v = static_cast<double>(th(c.x, c.y)) + xv[c.y];
-            if (order_key(v) == sm.key[c.x]) atomicMin(&sm.arg[c.x], c.y);
+        // c(jc) + 2 e1 + 2 e2, every operation rounded upwards (d bounds |w| on the line)
+        const float e1 = __fmul_ru(0x1p-22f, __fadd_ru(h, d));
+        const float e2 = __fmul_ru(0x1p-50f, __fadd_ru(__fadd_ru(h, d), ax0));
+        const float thr = __fadd_ru(__fadd_ru(mn, __fmul_ru(2.f, e1)), __fadd_ru(__fmul_ru(2.f, e2), 0x1p-126f));
+        if (on && k == 0) {
+            key[i] = ~0ull;
+            arg[i] = INT_MAX;
         }
-    } else {
-        // too many near-ties: every element in FP64 (the all-FP64 scan)
-        for (int i = tid; i < n; i += T) {
+        // the warp's candidates into its list (warp-uniform trip count)
+        int nc = 0;
+        bool over = false;
+        const int span = (len + G - 1) / G;
+        for (int r = 0; r < span; ++r) {
+            const int j = k + r * G;
+            const bool c = on && j < len && th(i, j) + w[j] <= thr;
+            const unsigned mask = __ballot_sync(0xffffffffu, c);
+            const int slot = nc + __popc(mask & ((1u << lane) - 1u));
+            if (c && slot < kWarpCands) cand[slot] = make_int2(i, j);
+            nc += __popc(mask);
+        }
+        if (nc > kWarpCands) {
+            over = true;
+            nc = 0;
+        }
+        __syncwarp();
+        if (!over) {
+            // FP64 values, 32 candidates per instruction, merged per line
+            for (int c = lane; c < nc; c += 32) {
+                const int2 q = cand[c];
+                atomicMin(&key[q.x], order_key(static_cast<double>(th(q.x, q.y)) + xv[q.y]));
+            }
+            __syncwarp();
+            for (int c = lane; c < nc; c += 32) {
+                const int2 q = cand[c];
+                if (order_key(static_cast<double>(th(q.x, q.y)) + xv[q.y]) == key[q.x]) atomicMin(&arg[q.x], q.y);
+            }
+            __syncwarp();
+        } else if (on && k == 0) {
+            // too many near-ties in this warp's lines: every element in FP64
             double m = INFINITY;
             int mi = 0;
             for (int j = 0; j < len; ++j) {
@@ -276,24 +255,12 @@ __device__ void screened_min(const ScreenSmem &sm, int ldp, int n, int len, cons
                     mi = j;
                 }
             }
-            sm.key[i] = order_key(m);
-            sm.arg[i] = mi;
+            key[i] = order_key(m);
+            arg[i] = mi;
         }
+        __syncwarp();
+        if (on && k == 0) emit(i, key_value(key[i]), arg[i]);
     }
-    __syncthreads();
-}
-
-// w = fl32(x - x(0)) for j < len (0 beyond, up to pad), returns max |w|
-__device__ __forceinline__ float shifted(const double *x, int len, int pad, float *w, float *red)
-{
-    const double x0 = x[0];
-    float m = 0.f;
-    for (int j = threadIdx.x; j < pad; j += blockDim.x) {
-        const float v = j < len ? static_cast<float>(x[j] - x0) : 0.f;
-        w[j] = v;
-        m = fmaxf(m, fabsf(v));
-    }
-    return block_max_f(m, red);
 }
 
 template <bool REC>
@@ -306,70 +273,69 @@ __global__ void __launch_bounds__(kScrThreads) rec_screen_kernel(const EdgeDesc 
     const int e = items[blockIdx.x];
     const EdgeDesc ed = edges[e];
     const int Lu = ed.Lu, Lv = ed.Lv, ld = ed.ld, ldp = ld | 1;
-    const int T = blockDim.x, tid = threadIdx.x;
-    const int PM = max(T, lmax);  // partials: G groups x n lines <= max(T, n)
-    ScreenSmem sm;
-    sm.uh = shd;
-    sm.vh = sm.uh + lmax;
-    sm.al = sm.vh + lmax;
-    sm.be = sm.al + lmax;
-    sm.bv = sm.be + lmax;
-    sm.key = reinterpret_cast<unsigned long long *>(sm.bv + lmax);
-    sm.cand = reinterpret_cast<int2 *>(sm.key + lmax);
-    sm.w = reinterpret_cast<float *>(sm.cand + kCandMax);
-    sm.thr = sm.w + lmax;
-    sm.arg = reinterpret_cast<int *>(sm.thr + lmax);
-    sm.count = sm.arg + lmax;
-    sm.red = reinterpret_cast<float *>(sm.count + 4);
-    sm.pmin = sm.red + kScrThreads / 32;
-    sm.pmax = sm.pmin + PM;
-    sm.tab = sm.pmax + PM;
+    const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    double *uh = shd, *vh = uh + lmax, *al = vh + lmax, *be = al + lmax, *bv = be + lmax;
+    unsigned long long *key = reinterpret_cast<unsigned long long *>(bv + lmax);  // [lmax] per-line minima
+    int2 *cand = reinterpret_cast<int2 *>(key + lmax) + warp * kWarpCands;      // this warp's list
+    int *arg = reinterpret_cast<int *>(reinterpret_cast<int2 *>(key + lmax) + (kScrThreads / 32) * kWarpCands);
+    float *w = reinterpret_cast<float *>(arg + lmax);  // [lmax] the current pass's shifted vector
+    float *st = w + lmax;                              // [Lu][ldp] staged table
     unsigned short *t1 = nullptr, *s2 = nullptr, *t3 = nullptr;
     if (REC) {
         t1 = reinterpret_cast<unsigned short *>(rec + rec_off[e]);
         s2 = t1 + Lu;
         t3 = s2 + Lv;
     }
-    const float *th = tab + ed.toff;
-    for (int i = tid; i < Lu * ld; i += T) {
-        const int s = i / ld, t = i - s * ld;
-        sm.tab[s * ldp + t] = th[i];
+    // the table (rows by warp, 16-byte chunks by lane), node vectors, shifted vh
+    const float4 *th4 = reinterpret_cast<const float4 *>(tab + ed.toff);
+    const int Q = ld >> 2;
+    for (int s = warp; s < Lu; s += T >> 5)
+        for (int c = lane; c < Q; c += 32) {
+            const float4 v = th4[s * Q + c];
+            float *d = st + s * ldp + 4 * c;
+            d[0] = v.x;
+            d[1] = v.y;
+            d[2] = v.z;
+            d[3] = v.w;
+        }
+    const double vh0 = agg[ed.av] - msg[ed.mv];
+    for (int s = tid; s < Lu; s += T) uh[s] = agg[ed.au + s] - msg[ed.mu + s];
+    for (int t = tid; t < Lv; t += T) {
+        const double v = agg[ed.av + t] - msg[ed.mv + t];
+        vh[t] = v;
+        w[t] = static_cast<float>(v - vh0);
     }
-    for (int s = tid; s < Lu; s += T) sm.uh[s] = agg[ed.au + s] - msg[ed.mu + s];
-    for (int t = tid; t < Lv; t += T) sm.vh[t] = agg[ed.av + t] - msg[ed.mv + t];
     __syncthreads();
     // pass 1: a(s) = 1/2 (min_t [theta(s,t) + vh(t)] + uh(s)),  alpha = uh - a
-    float D = shifted(sm.vh, Lv, Lv, sm.w, sm.red);
-    screened_min<true>(sm, ldp, Lu, Lv, sm.vh, D);
-    for (int s = tid; s < Lu; s += T) {
-        const double a = 0.5 * (key_value(sm.key[s]) + sm.uh[s]);
-        sm.al[s] = sm.uh[s] - a;
-        if (REC) t1[s] = static_cast<unsigned short>(sm.arg[s]);
-    }
+    screened_lines<true>(st, ldp, Lu, Lv, vh, w, key, arg, cand, [&](int s, double m, int mi) {
+        const double a = 0.5 * (m + uh[s]);
+        al[s] = uh[s] - a;
+        if (REC) t1[s] = static_cast<unsigned short>(mi);
+    });
+    __syncthreads();
+    for (int s = tid; s < Lu; s += T) w[s] = static_cast<float>(al[s] - al[0]);
     __syncthreads();
     // pass 2: b(t) = min_s [theta(s,t) + alpha(s)] + vh(t),  beta = vh - b
-    D = shifted(sm.al, Lu, Lu, sm.w, sm.red);
-    screened_min<false>(sm, ldp, Lv, Lu, sm.al, D);
+    screened_lines<false>(st, ldp, Lv, Lu, al, w, key, arg, cand, [&](int t, double m, int mi) {
+        const double b = m + vh[t];
+        bv[t] = b;
+        be[t] = vh[t] - b;
+        if (REC) s2[t] = static_cast<unsigned short>(mi);
+    });
+    __syncthreads();
     for (int t = tid; t < Lv; t += T) {
-        const double b = key_value(sm.key[t]) + sm.vh[t];
-        sm.bv[t] = b;
-        sm.be[t] = sm.vh[t] - b;
-        if (REC) s2[t] = static_cast<unsigned short>(sm.arg[t]);
+        w[t] = static_cast<float>(be[t] - be[0]);
+        agg[ed.av + t] = bv[t];
+        msg[ed.mv + t] = bv[t] - vh[t];
     }
     __syncthreads();
     // pass 3: c(s) = min_t [theta(s,t) + beta(t)] + uh(s)
-    D = shifted(sm.be, Lv, Lv, sm.w, sm.red);
-    screened_min<true>(sm, ldp, Lu, Lv, sm.be, D);
-    for (int s = tid; s < Lu; s += T) {
-        const double c = key_value(sm.key[s]) + sm.uh[s];
+    screened_lines<true>(st, ldp, Lu, Lv, be, w, key, arg, cand, [&](int s, double m, int mi) {
+        const double c = m + uh[s];
         agg[ed.au + s] = c;
-        msg[ed.mu + s] = c - sm.uh[s];
-        if (REC) t3[s] = static_cast<unsigned short>(sm.arg[s]);
-    }
-    for (int t = tid; t < Lv; t += T) {
-        agg[ed.av + t] = sm.bv[t];
-        msg[ed.mv + t] = sm.bv[t] - sm.vh[t];
-    }
+        msg[ed.mu + s] = c - uh[s];
+        if (REC) t3[s] = static_cast<unsigned short>(mi);
+    });
 }
 
 }  // namespace
@@ -390,11 +356,9 @@ size_t rec64_smem_bytes(int lmax)
 
 size_t rec_screen_smem_bytes(int lmax, long long tab_floats)
 {
-    // uh, vh, alpha, beta, b (FP64), keys; candidates; w, thr (FP32), arg; count; red;
-    // pmin, pmax; the staged table
-    const size_t PM = static_cast<size_t>(std::max(kScrThreads, lmax));
-    return static_cast<size_t>(lmax) * (6 * 8 + 2 * 4 + 4) + kCandMax * sizeof(int2) + 4 * 4 + 4 * (kScrThreads / 32) +
-           2 * 4 * PM + 4 * static_cast<size_t>(tab_floats);
+    // uh, vh, alpha, beta, b (FP64), keys; the warps' candidate lists; args; w (FP32); the staged table
+    return static_cast<size_t>(lmax) * (6 * 8 + 4 + 4) + sizeof(int2) * (kScrThreads / 32) * kWarpCands +
+           4 * static_cast<size_t>(tab_floats);
 }
 
 cudaError_t launch_rec_screen_phase(const EdgeDesc *edges, const int *items, int n_items, const float *tab,

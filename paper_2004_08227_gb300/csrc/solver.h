@@ -9,6 +9,7 @@
 
 #include "mplpp.h"
 #include "common.cuh"
+#include "kernels.h"
 
 namespace mplpp {
 struct ModelHost {
@@ -25,6 +26,7 @@ struct mplpp_solver {
     ~mplpp_solver();
     template <typename Ty>
     cudaError_t alloc(Ty **p, size_t count);
+    cudaError_t release(void *p);  // frees one of the solver's allocations (nullptr: nothing)
 
     int device = 0;
     int sms = 0;
@@ -57,7 +59,10 @@ struct mplpp_solver {
     bool pw = false;       // with rr, persistent: a poller warp for node u (threads beyond the rows' warps)
     size_t smem_looped = 0, smem_persist = 0;
     int warp_blocks = 0, lw = 0, cap = 0;  // warp driver: blocks, per-warp vector and buffer capacity
-    int queue_blocks = 0;                  // queue driver: co-resident CTAs launched
+    int queue_blocks = 0;                  // queue drivers: co-resident CTAs launched
+    size_t smem_res = 0;                   // resident driver: shared memory per CTA
+    mplpp::ResModel *d_res_models = nullptr;
+    int *d_res_off = nullptr, *d_res_edges = nullptr;
     size_t smem_queue = 0;
     unsigned long long *d_queue = nullptr; // queue driver: next item index
     size_t smem_warp = 0;
@@ -74,6 +79,7 @@ struct mplpp_solver {
     // device
     std::vector<void *> allocations;
     long long device_bytes = 0;  // sum of the sizes in `allocations`
+    std::vector<size_t> allocation_bytes;
     mplpp::EdgeDesc *d_edges = nullptr;
     mplpp::NodeDesc *d_nodes = nullptr;
     float *d_tab = nullptr, *d_un0 = nullptr;
@@ -94,7 +100,8 @@ struct mplpp_solver {
     bool history_valid = true;       // the state is T iterations from phi = 0 (false after load_state)
     double *d_agg64 = nullptr, *d_msg64 = nullptr;
     double *d_adj_agg = nullptr, *d_adj_msg = nullptr, *d_gtab = nullptr;
-    unsigned char *d_rec = nullptr;  // argmin records of one segment
+    unsigned char *d_rec = nullptr;  // argmin records of one segment, or of every iteration
+    long long rec_slots = 0;         // iterations d_rec holds
     float *d_dD = nullptr;
     long long *d_pbase = nullptr, *d_ubase = nullptr;  // per-model offsets of the caller's layouts
     ulonglong2 *d_save_agg = nullptr, *d_save_msg = nullptr;
@@ -115,9 +122,23 @@ cudaError_t mplpp_solver::alloc(Ty **p, size_t count)
     cudaError_t e = cudaMalloc(reinterpret_cast<void **>(p), (count ? count : 1) * sizeof(Ty));
     if (e == cudaSuccess) {
         allocations.push_back(*p);
-        device_bytes += static_cast<long long>((count ? count : 1) * sizeof(Ty));
+        allocation_bytes.push_back((count ? count : 1) * sizeof(Ty));
+        device_bytes += static_cast<long long>(allocation_bytes.back());
     }
     return e;
+}
+
+inline cudaError_t mplpp_solver::release(void *p)
+{
+    if (!p) return cudaSuccess;
+    for (size_t i = 0; i < allocations.size(); ++i)
+        if (allocations[i] == p) {
+            device_bytes -= static_cast<long long>(allocation_bytes[i]);
+            allocations.erase(allocations.begin() + static_cast<long>(i));
+            allocation_bytes.erase(allocation_bytes.begin() + static_cast<long>(i));
+            return cudaFree(p);
+        }
+    return cudaSuccess;
 }
 
 // api.cu

@@ -25,8 +25,9 @@
 // The vectors h, the O(L) double-float arithmetic and the write-back are
 // those of the dense kernel (uh, vh; w1 = vh - vh(0), alpha, beta).
 //
-// One warp per edge of a matching, looped (one launch per matching): the
-// tables are not read at all, so an update moves O(L) bytes.
+// One warp per edge: looped (one launch per matching) or persistent (every
+// warp taking edges from one global queue, versioned waits); the tables are
+// not read at all, so an update moves O(L) bytes.
 #include "kernels.h"
 
 namespace mplpp {
@@ -181,15 +182,15 @@ __device__ void dt_trunc(const float *h, int Lh, int Ls, float w, float tau, boo
     __syncwarp();
 }
 
-__global__ void __launch_bounds__(kStructThreads) struct_kernel(StructParams p)
+// One structured Handshake update of edge e by one warp.  SIGNAL (persistent
+// form): the node entries are polled until they carry the versions in ver, and
+// the new entries carry ver + 1; otherwise versions are not checked and the
+// new entries carry 1 (the looped driver orders the matchings by launches).
+template <bool SIGNAL>
+__device__ void struct_item(const StructParams &p, int e, const EdgeDesc &ed, Versions ver, char *base, int lane)
 {
-    extern __shared__ __align__(16) char smem_raw[];
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int item = blockIdx.x * kStructWarps + wib;
-    if (item >= p.n_items) return;
     const int lmax = p.lmax;
     // per warp: uh, vh (double-float), h and m (FP32), pre and suf (value, index)
-    char *base = smem_raw + static_cast<size_t>(wib) * struct_bytes_per_warp(lmax);
     float2 *uh = reinterpret_cast<float2 *>(base);
     float2 *vh = uh + lmax;
     float *h = reinterpret_cast<float *>(vh + lmax);
@@ -197,23 +198,22 @@ __global__ void __launch_bounds__(kStructThreads) struct_kernel(StructParams p)
     VI *pre = reinterpret_cast<VI *>(m + lmax);
     VI *suf = pre + lmax;
 
-    const int e = p.items[item];
-    const EdgeDesc ed = p.edges[e];
     const float2 wt = p.param[e];
     const float w = wt.x, tau = wt.y;
     const bool quad = p.kind[e] == kPairQuad;
     const int Lu = ed.Lu, Lv = ed.Lv;
     ulonglong2 *agg = p.agg;
     ulonglong2 *msg = p.msg;
+    const unsigned va = ver.u + ver.bump;
 
     // unaries without this edge's messages: up to 4 entries of each node per
     // lane requested before any is used (one round trip per 128 labels)
     const int Lm = Lu > Lv ? Lu : Lv;
-    for (int base = 0; base < Lm; base += 128) {
+    for (int base0 = 0; base0 < Lm; base0 += 128) {
         ulonglong2 xu[4], mu[4], xv[4], mv[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            const int i = base + lane + 32 * j;
+            const int i = base0 + lane + 32 * j;
             if (i < Lu) {
                 xu[j] = ld_se(agg + ed.au + i);
                 mu[j] = ld_se(msg + ed.mu + i);
@@ -223,9 +223,39 @@ __global__ void __launch_bounds__(kStructThreads) struct_kernel(StructParams p)
                 mv[j] = ld_se(msg + ed.mv + i);
             }
         }
+        if (SIGNAL) {  // bounded wait for the expected versions; only stale words are requested again
+            for (long long spins = 1;; ++spins) {
+                bool ok = true;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int i = base0 + lane + 32 * j;
+                    if (i < Lu) ok = ok && se_ok(xu[j], va) && se_ok(mu[j], ver.e);
+                    if (i < Lv) ok = ok && se_ok(xv[j], ver.v) && se_ok(mv[j], ver.e);
+                }
+                if (ok) break;
+                if ((spins & 63) == 0 && *reinterpret_cast<volatile int *>(p.err) != 0) break;  // draining
+                if (spins > p.spin_limit) {
+                    atomicCAS(p.err, 0, ERR_TIMEOUT);
+                    break;
+                }
+                if (spins > 64) __nanosleep(64);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int i = base0 + lane + 32 * j;
+                    if (i < Lu) {
+                        if (!se_ok(xu[j], va)) xu[j] = ld_se(agg + ed.au + i);
+                        if (!se_ok(mu[j], ver.e)) mu[j] = ld_se(msg + ed.mu + i);
+                    }
+                    if (i < Lv) {
+                        if (!se_ok(xv[j], ver.v)) xv[j] = ld_se(agg + ed.av + i);
+                        if (!se_ok(mv[j], ver.e)) mv[j] = ld_se(msg + ed.mv + i);
+                    }
+                }
+            }
+        }
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            const int i = base + lane + 32 * j;
+            const int i = base0 + lane + 32 * j;
             if (i < Lu) uh[i] = df_sub(se_df(xu[j]), se_df(mu[j]));
             if (i < Lv) vh[i] = df_sub(se_df(xv[j]), se_df(mv[j]));
         }
@@ -235,6 +265,7 @@ __global__ void __launch_bounds__(kStructThreads) struct_kernel(StructParams p)
     for (int t = lane; t < Lv; t += 32) h[t] = df_to_f(df_sub(vh[t], vref));
     __syncwarp();
     const int ku = (Lu + 31) >> 5, kv = (Lv + 31) >> 5;
+    const unsigned nu = SIGNAL ? ver.u + 1u : 1u, nv = SIGNAL ? ver.v + 1u : 1u, ne = SIGNAL ? ver.e + 1u : 1u;
 
     // pass 1: a(s) = 1/2 (min_t [theta(s,t) + w1(t)] + vh(0) + uh(s)); alpha = uh - a
     dt_trunc(h, Lv, Lu, w, tau, quad, m, pre, suf, lane, kv);
@@ -248,16 +279,57 @@ __global__ void __launch_bounds__(kStructThreads) struct_kernel(StructParams p)
     for (int t = lane; t < Lv; t += 32) {
         const float2 b = df_add_f(vh[t], m[t]);
         h[t] = df_to_f(df_sub(vh[t], b));
-        st_se(agg + ed.av + t, se_make(b, 1u));
-        st_se(msg + ed.mv + t, se_make(df_sub(b, vh[t]), 1u));
+        st_se(agg + ed.av + t, se_make(b, nv));
+        st_se(msg + ed.mv + t, se_make(df_sub(b, vh[t]), ne));
     }
     __syncwarp();
     // pass 3: c(s) = min_t [theta(s,t) + beta(t)] + uh(s); node u's new vector
     dt_trunc(h, Lv, Lu, w, tau, quad, m, pre, suf, lane, kv);
     for (int s = lane; s < Lu; s += 32) {
         const float2 c = df_add_f(uh[s], m[s]);
-        st_se(agg + ed.au + s, se_make(c, 1u));
-        st_se(msg + ed.mu + s, se_make(df_sub(c, uh[s]), 1u));
+        st_se(agg + ed.au + s, se_make(c, nu));
+        st_se(msg + ed.mu + s, se_make(df_sub(c, uh[s]), ne));
+    }
+    __syncwarp();  // the warp's vectors are rewritten by its next item
+}
+
+__global__ void __launch_bounds__(kStructThreads) struct_kernel(StructParams p)
+{
+    extern __shared__ __align__(16) char smem_raw[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int item = blockIdx.x * kStructWarps + wib;
+    if (item >= p.n_items) return;
+    const int e = p.items[item];
+    struct_item<false>(p, e, p.edges[e], Versions{0u, 0u, 0u, 0u},
+                       smem_raw + static_cast<size_t>(wib) * struct_bytes_per_warp(p.lmax), lane);
+}
+
+// Persistent form: every warp takes the next item of one global queue (the
+// list of the queue driver, handshake.cu: each model's updates in schedule
+// order, the models interleaved by progress) until the iterations are done.
+// Every wait is on an earlier item, held by a co-resident warp, so the waits
+// end; no block barrier.
+__global__ void __launch_bounds__(kStructThreads) struct_queue_kernel(StructParams p)
+{
+    extern __shared__ __align__(16) char smem_raw[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    char *base = smem_raw + static_cast<size_t>(wib) * struct_bytes_per_warp(p.lmax);
+    const long long EE = p.queue_items, total = EE * static_cast<long long>(p.iterations);
+    for (long long k = 0;; ++k) {
+        unsigned long long g = 0;
+        if (lane == 0) g = atomicAdd(p.queue, 1ull);
+        g = __shfl_sync(kAll, g, 0);
+        if (static_cast<long long>(g) >= total) break;
+        const WorkItem *w = p.work + static_cast<long long>(g) % EE;
+        const long long it = static_cast<long long>(g) / EE;
+        const int e = __ldg(&w->edge);
+        const Versions ver = {static_cast<unsigned>(it) * static_cast<unsigned>(__ldg(&w->deg_u)) +
+                                  static_cast<unsigned>(__ldg(&w->pos_u)),
+                              static_cast<unsigned>(it) * static_cast<unsigned>(__ldg(&w->deg_v)) +
+                                  static_cast<unsigned>(__ldg(&w->pos_v)),
+                              static_cast<unsigned>(it),
+                              (p.test_wait && k == 0 && blockIdx.x == 0 && wib == 0) ? 1u : 0u};
+        struct_item<true>(p, e, p.edges[e], ver, base, lane);
     }
 }
 
@@ -297,6 +369,28 @@ cudaError_t launch_struct(const StructParams &p, cudaStream_t st)
     const int blocks = (p.n_items + kStructWarps - 1) / kStructWarps;
     struct_kernel<<<blocks, kStructThreads, kStructWarps * struct_bytes_per_warp(p.lmax), st>>>(p);
     return cudaGetLastError();
+}
+
+cudaError_t launch_struct_queue(const StructParams &p, int blocks, cudaStream_t st)
+{
+    if (blocks <= 0) return cudaSuccess;  // (shared memory attribute set by struct_queue_max_blocks)
+    struct_queue_kernel<<<blocks, kStructThreads, kStructWarps * struct_bytes_per_warp(p.lmax), st>>>(p);
+    return cudaGetLastError();
+}
+
+int struct_queue_max_blocks(int lmax)
+{
+    const size_t smem = kStructWarps * struct_bytes_per_warp(lmax);
+    if (cudaFuncSetAttribute(struct_queue_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(smem)) != cudaSuccess)
+        return 0;
+    int per_sm = 0, dev = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, struct_queue_kernel, kStructThreads, smem) !=
+        cudaSuccess)
+        return 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return per_sm * sms;
 }
 
 cudaError_t launch_materialize(const EdgeDesc *edges, const float2 *param, const int *kind, int n, float *tab,

@@ -117,7 +117,7 @@ class Solver:
     def __init__(self, models, *, mode: str = "auto", use_graph: bool = True, record_every: int = 0,
                  cluster: int = 0, threads: int = 0, spin_limit: int = 1 << 22, device_inputs: bool = False,
                  user_schedules=None, stream=None, test_unreachable_wait: bool = False, rule: str = "H",
-                 structured: bool = True, test_fp64_replay: bool = False):
+                 structured: bool = True, test_fp64_replay: bool = False, test_checkpoints: bool = False):
         self._lib = _lib.load()
         self._h = ctypes.c_void_p(0)
         models = list(models)
@@ -168,7 +168,7 @@ class Solver:
         opt.threads = int(threads)
         opt.spin_limit = int(spin_limit)
         opt.test_unreachable_wait = int(bool(test_unreachable_wait))
-        opt.test_fp64_replay = int(bool(test_fp64_replay))
+        opt.test_backward = (1 if test_fp64_replay else 0) | (2 if test_checkpoints else 0)
         opt.rule = _lib.RULE[rule]
         self.rule = rule
         self.device_inputs = bool(device_inputs)

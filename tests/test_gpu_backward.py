@@ -174,3 +174,17 @@ def test_screened_replay_equals_all_fp64_replay_bitwise(case):
     _, gu_o, gp_o = oracle.grad(m, _order(m), T)
     if case in ("uneven", "wide_rows"):  # tie-free costs: the oracle's argmins too
         assert np.all(_close(grads[0][0], gu_o)) and np.all(_close(grads[0][1], gp_o))
+
+
+@pytest.mark.parametrize("T,k", [(7, 3), (10, 10), (5, 1)])
+def test_checkpointed_replay_equals_one_pass_replay_bitwise(T, k):
+    """Records of every iteration in one replay, or state checkpoints every k
+    iterations and a second replay per segment: the same gradient bit for bit."""
+    m = W.uneven_complete(8, 2, 40, seed=T + 10 * k)
+    grads = []
+    for ck in (False, True):
+        s = Solver([m], record_every=k, test_checkpoints=ck)
+        s.run(T)
+        grads.append(s.backward())
+        s.close()
+    assert np.array_equal(grads[0][0], grads[1][0]) and np.array_equal(grads[0][1], grads[1][1])

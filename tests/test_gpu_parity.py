@@ -617,3 +617,42 @@ def test_queue_driver_bounded_wait_times_out():
     sol = oracle.solve(m2, _order(m2), 20)
     s2, D, _, _ = _solve_gpu([m2], 20, mode="queue")
     _check_D(D[0], sol["bound"])
+
+
+@pytest.mark.parametrize("lmax", [8, 16, 32])
+def test_resident_driver_bitwise_equal_to_looped(lmax):
+    """The resident driver (one CTA per model, its state in shared memory, a
+    block barrier between matchings): bit for bit the looped driver's state,
+    on uneven small models (label counts 1..lmax, odd and even n, a sparse
+    graph with greedy colouring)."""
+    models = [W.uneven_complete(n, 1, lmax, seed=90 + n + lmax) for n in (2, 3, 7, 12, 21)]
+    models.append(W.knn(40, 4, lmax, seed=5))
+    a = Solver(models, mode="looped")
+    b = Solver(models, mode="resident")
+    inf = b.info()
+    assert inf["mode"] == "resident" and inf["grid"] == len(models)
+    for T in (5, 3):  # continues from the state
+        a.run(T)
+        b.run(T)
+        sa, sb = a.state_arrays(), b.state_arrays()
+        assert np.array_equal(sa[1], sb[1]) and np.array_equal(sa[2], sb[2])
+    np.testing.assert_array_equal(a.bound(), b.bound())
+
+
+def test_resident_driver_parity_K20_L8_replicas():
+    """K_20, L = 8 (the small dense workload) and seeded replicas of it solved
+    together by the resident driver, against the oracle."""
+    models = [W.config(1, seed=k)[0] for k in range(3)]
+    T = 40
+    s, D, xs, en = _solve_gpu(models, T, mode="resident")
+    for i, m in enumerate(models):
+        sol = oracle.solve(m, _order(m), T)
+        _check_D(D[i], sol["bound"])
+        _check(s, models, i, xs[i], sol, en[i])
+
+
+def test_resident_driver_rejects_large_labels():
+    m = W.uneven_complete(5, 30, 40, seed=1)
+    with pytest.raises(MplppError) as ei:
+        Solver([m], mode="resident")
+    assert ei.value.status == -7

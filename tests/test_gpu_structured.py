@@ -167,3 +167,27 @@ def test_mixed_structured_and_dense_models_in_one_solver():
     for i, m in enumerate(ms):
         Do = oracle.bound(m, *oracle.run(m, _order(m), T, rule="M"))
         assert abs(D[i] - Do) <= RTOL_D * max(abs(Do), 1.0), (i, D[i], Do)
+
+
+@pytest.mark.parametrize("case", ["potts_L16", "tl_L200", "ragged_2_70", "quad_L40_tau16"])
+def test_structured_queue_driver_bitwise_equal_to_looped(case):
+    """The structured update in one launch (every warp taking edges from one
+    queue, versioned waits): bit for bit the looped structured driver."""
+    m = W.grid_trunc_linear(seed=3, **CASES[case])
+    a = Solver([m], mode="structured")
+    b = Solver([m], mode="structured_queue")
+    assert b.info()["mode"] == "structured_queue"
+    for T in (6, 2):
+        a.run(T)
+        b.run(T)
+        sa, sb = a.state_arrays(), b.state_arrays()
+        assert np.array_equal(sa[1], sb[1]) and np.array_equal(sa[2], sb[2])
+
+
+def test_structured_queue_bounded_wait_times_out():
+    m = W.grid_trunc_linear(seed=1, **CASES["potts_L16"])
+    s = Solver([m], mode="structured_queue", test_unreachable_wait=True, spin_limit=2000)
+    s.run(2)
+    with pytest.raises(MplppError) as ei:
+        s.sync()
+    assert ei.value.status == -4
