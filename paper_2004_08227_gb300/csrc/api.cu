@@ -443,7 +443,7 @@ static mplpp_status apply_resident_mapping(mplpp_solver *s, int T, int optin)
     const int nm = static_cast<int>(s->models.size());
     std::vector<ResModel> rm(nm);
     std::vector<int> off, edges;
-    long long state_max = 0;
+    long long state_max = 0, tab_max = 0;
     for (int m = 0; m < nm; ++m) {
         const ModelHost &mh = s->models[m];
         const int n0 = mh.node_base, n1 = mh.node_base + mh.n;
@@ -457,6 +457,15 @@ static mplpp_status apply_resident_mapping(mplpp_solver *s, int T, int optin)
             rm[m].msg_base = 0;
             rm[m].msg_n = 0;
         }
+        if (mh.E > 0) {
+            rm[m].tab_base = s->h_edges[mh.edge_base].toff;
+            const int e1 = mh.edge_base + mh.E;
+            rm[m].tab_n = (e1 < s->EE ? s->h_edges[e1].toff : s->tabN) - rm[m].tab_base;
+        } else {
+            rm[m].tab_base = 0;
+            rm[m].tab_n = 0;
+        }
+        tab_max = std::max(tab_max, rm[m].tab_n);
         rm[m].sched = static_cast<int>(off.size());
         rm[m].P = static_cast<int>(mh.off.size()) - 1;
         for (size_t k = 0; k < mh.off.size(); ++k) off.push_back(static_cast<int>(edges.size()) + mh.off[k]);
@@ -465,7 +474,11 @@ static mplpp_status apply_resident_mapping(mplpp_solver *s, int T, int optin)
         state_max = std::max(state_max, rm[m].agg_n + rm[m].msg_n);
     }
     if (T == 0) T = 32 * std::min(16, wmax);
-    const size_t smem = static_cast<size_t>(state_max) * sizeof(float2) + static_cast<size_t>(T / 32) * kResWarpBytes;
+    size_t smem = static_cast<size_t>(state_max) * sizeof(float2) + static_cast<size_t>(T / 32) * kResWarpBytes;
+    // (the tables are read from L2: staging them in shared memory as well
+    // measured slower on the K_20 replicas -- fewer models per SM)
+    s->res_stage = false;
+    (void)tab_max;
     if (smem > static_cast<size_t>(optin))
         return fail(s, MPLPP_E_UNSUPPORTED,
                     "the resident driver needs " + std::to_string(smem) + " B of shared memory for the largest model");
@@ -925,7 +938,7 @@ cudaError_t enqueue_persistent(mplpp_solver *s, cudaStream_t st, int iterations)
     }
     if (s->mode == MPLPP_MODE_RESIDENT) {  // reads values only, writes version 0: no restamp
         ResParams rp = {s->d_edges, s->d_tab, s->d_agg, s->d_msg, s->d_res_models, s->d_res_off, s->d_res_edges,
-                        iterations};
+                        iterations, s->res_stage ? 1 : 0};
         int lmax = 1;
         for (auto &nd : s->h_nodes) lmax = std::max(lmax, nd.L);
         return launch_resident(rp, static_cast<int>(s->models.size()), s->T, s->smem_res, lmax, st);

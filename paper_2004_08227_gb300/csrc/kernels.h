@@ -73,6 +73,7 @@ constexpr int kResWarpBytes = 2 * kResMaxL * 8 + 3 * kResMaxL * 4;  // per-warp 
 struct ResModel {
     long long agg_base, agg_n;  // the model's entries in agg
     long long msg_base, msg_n;  // ... and in msg
+    long long tab_base, tab_n;  // ... and its tables in tab (floats)
     int sched;                  // offset of its matching offsets in sched_off
     int P;                      // its matchings
 };
@@ -85,6 +86,7 @@ struct ResParams {
     const int *sched_off;    // per model P + 1 offsets into sched_edges
     const int *sched_edges;  // edge ids, every model's matchings in schedule order
     int iterations;
+    int stage_tables;        // nonzero: every model's tables fit shared memory beside its state
 };
 cudaError_t res_prepare(size_t smem);
 cudaError_t launch_resident(const ResParams &p, int n_models, int threads, size_t smem, int lmax, cudaStream_t st);

@@ -10,8 +10,9 @@
 // memory, and separates the matchings by a block barrier -- the barrier
 // between matchings of the paper's GPU implementation (Sec. 6) at the scope
 // of a CTA.  Nothing waits on another CTA and no state crosses L2 between
-// updates; only the tables are read (from L2 once the first iteration has
-// touched them).  One warp updates one edge of a matching: lane s holds row s
+// updates; the tables are read from L2 once the first iteration has touched
+// them (the kernel can stage a model's tables in shared memory too, which
+// the host does not select: fewer models then share an SM).  One warp updates one edge of a matching: lane s holds row s
 // of the table and lane t column t (loaded together, in registers), so every
 // minimization is a sequential loop in one lane, with no shuffles.
 #include <cfloat>
@@ -45,15 +46,15 @@ __device__ __forceinline__ ResWarp res_warp(char *base, int warp)
 // model's shared-memory state: agg and msg hold the model's entries (offsets
 // relative to the model's first node and first edge).
 template <int LM>
-__device__ __forceinline__ void res_update(const EdgeDesc &ed, const float *tab, float2 *agg, float2 *msg,
-                                           long long abase, long long mbase, const ResWarp &w, int lane)
+__device__ __forceinline__ void res_update(const EdgeDesc &ed, const float *tab, long long tbase, float2 *agg,
+                                           float2 *msg, long long abase, long long mbase, const ResWarp &w, int lane)
 {
     const int Lu = ed.Lu, Lv = ed.Lv, ld = ed.ld;
     float2 *au = agg + (ed.au - abase), *av = agg + (ed.av - abase);
     float2 *mu = msg + (ed.mu - mbase), *mv = msg + (ed.mv - mbase);
     // row `lane` and column `lane` of the table (FP32, +inf beyond the labels)
     float row[LM], col[LM];
-    const float *th = tab + ed.toff;
+    const float *th = tab + (ed.toff - tbase);
 #pragma unroll
     for (int t = 0; t < LM; ++t) row[t] = (lane < Lu && t < Lv) ? th[lane * ld + t] : INFINITY;
 #pragma unroll
@@ -113,16 +114,25 @@ __global__ void __launch_bounds__(512) hs_resident_kernel(ResParams p)
     float2 *msg = agg + md.agg_n;
     char *wbase = reinterpret_cast<char *>(msg + md.msg_n);
     const ResWarp w = res_warp(wbase, warp);
-    // the model's state from the solver's versioned entries
+    // the model's state from the solver's versioned entries, and its tables
     for (long long i = tid; i < md.agg_n; i += blockDim.x) agg[i] = se_df(p.agg[md.agg_base + i]);
     for (long long i = tid; i < md.msg_n; i += blockDim.x) msg[i] = se_df(p.msg[md.msg_base + i]);
+    const float *tab = p.tab;
+    long long tbase = 0;
+    if (p.stage_tables) {  // 16-byte aligned: the warp vectors are a multiple of 16 bytes
+        float4 *st = reinterpret_cast<float4 *>(wbase + static_cast<size_t>(W) * kResWarpBytes);
+        const float4 *src = reinterpret_cast<const float4 *>(p.tab + md.tab_base);
+        for (long long i = tid; i < md.tab_n / 4; i += blockDim.x) st[i] = src[i];
+        tab = reinterpret_cast<const float *>(st);
+        tbase = md.tab_base;
+    }
     __syncthreads();
     const int *off = p.sched_off + md.sched;  // [P + 1] matchings of this model
     for (int it = 0; it < p.iterations; ++it)
         for (int k = 0; k < md.P; ++k) {
             for (int j = off[k] + warp; j < off[k + 1]; j += W) {
                 const EdgeDesc ed = p.edges[p.sched_edges[j]];
-                res_update<LM>(ed, p.tab, agg, msg, md.agg_base, md.msg_base, w, lane);
+                res_update<LM>(ed, tab, tbase, agg, msg, md.agg_base, md.msg_base, w, lane);
             }
             __syncthreads();  // the barrier between matchings
         }

@@ -9,9 +9,11 @@
 //   m(s) = min_t [theta(s,t) + h(t)],   t < Lh, s < Ls.
 // Window: only t within distance R of s can cost less than w tau (R the
 // largest distance with |s - t| < tau, or (s - t)^2 < tau), so the window
-// plus the global minimizer of h hold the minimum; used for every quadratic
-// cost and for linear truncation up to R = 7 (Potts included), it reproduces
-// the dense kernel's minimum of the same rounded values bit for bit.
+// plus the global minimizer of h hold the minimum; used for quadratic costs
+// up to R = 16 and for linear truncation up to R = 7 (Potts included), it
+// reproduces the dense kernel's minimum of the same rounded values bit for
+// bit.  Envelope, for quadratic costs with R > 16: the lower envelope of the
+// untruncated parabolas and the global minimizer (dt_envelope).
 // Scans, for longer linear truncation (w, tau >= 0): the minimum splits into
 //   min_{t <= s} (h(t) - w t) + w s,   min_{t >= s} (h(t) + w t) - w s,
 //   min_t h(t) + w tau,
@@ -37,7 +39,8 @@ namespace {
 constexpr int kStructThreads = 256;
 constexpr int kStructWarps = kStructThreads / 32;
 constexpr unsigned kAll = 0xffffffffu;
-constexpr int kWindowMax = 7;  // truncation radius up to which the direct window beats the scans
+constexpr int kWindowMax = 7;       // linear truncation radius up to which the direct window beats the scans
+constexpr int kQuadWindowMax = 16;  // quadratic truncation radius up to which the window beats the envelope
 
 struct VI {
     float v;
@@ -99,6 +102,61 @@ __device__ __forceinline__ void dt_window(const float *h, int Lh, int Ls, float 
     }
 }
 
+// Truncated quadratic costs with a wide truncation radius: min_t [w min((s-t)^2,
+// tau) + h(t)] = min(min_t [w (s-t)^2 + h(t)], w tau + min_t h(t)), and the
+// first part is the lower envelope of the parabolas w (s - t)^2 + h(t) (the
+// distance transform of sampled functions, Felzenszwalb and Huttenlocher):
+// lane 0 builds it in one pass over t (parabola t replaces those it covers;
+// env[k] = {left end of parabola k's interval, t}), then every lane finds the
+// parabola over each of its s by binary search.  The envelope only chooses
+// candidates: that parabola, its two neighbours on the envelope (against the
+// rounding of the breakpoints) and the global minimizer of h are evaluated as
+// the dense path evaluates an entry, and the smallest is taken, so a minimum
+// differs from the dense kernel's only where rounding decides between
+// candidates of nearly equal value.  O(L) per minimization plus O(log L) per
+// label, instead of a window of O(L) labels per label.
+__device__ void dt_envelope(const float *h, int Lh, int Ls, float w, float tau, VI g, float *out, VI *env, int lane)
+{
+    if (lane == 0) {
+        int K = 1;
+        env[0] = VI{-INFINITY, 0};
+        for (int q = 1; q < Lh; ++q) {
+            const float fq = h[q] + w * static_cast<float>(q) * static_cast<float>(q);
+            float z;
+            for (;;) {
+                const int p0 = env[K - 1].i;
+                const float fp = h[p0] + w * static_cast<float>(p0) * static_cast<float>(p0);
+                z = (fq - fp) / (2.f * w * static_cast<float>(q - p0));
+                if (K > 1 && z <= env[K - 1].v) {
+                    --K;  // parabola p0 lies above the envelope everywhere
+                } else {
+                    break;
+                }
+            }
+            env[K++] = VI{z, q};
+        }
+        env[Lh] = VI{static_cast<float>(K), -1};  // the envelope's length, after its last entry
+    }
+    __syncwarp();
+    const int K = static_cast<int>(env[Lh].v);
+    for (int s = lane; s < Ls; s += 32) {
+        const float x = static_cast<float>(s);
+        int lo = 0, hi = K - 1;  // the last k with env[k].v <= x
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (env[mid].v <= x) lo = mid;
+            else hi = mid - 1;
+        }
+        float best = theta_tl(s, g.i, w, tau, true) + g.v;
+        for (int k = lo > 0 ? lo - 1 : 0; k <= lo + 1 && k < K; ++k) {
+            const int t = env[k].i;
+            best = fminf(best, theta_tl(s, t, w, tau, true) + h[t]);
+        }
+        out[s] = best;
+    }
+    __syncwarp();
+}
+
 // out[s] = min_t [theta(s,t) + h[t]] for s < Ls, t < Lh (1 <= Lh, Ls <= 32 k);
 // lane owns t in [lane k, lane k + k).  pre / suf: [Lh] scratch of the warp.
 __device__ void dt_trunc(const float *h, int Lh, int Ls, float w, float tau, bool quad, float *out, VI *pre,
@@ -117,6 +175,10 @@ __device__ void dt_trunc(const float *h, int Lh, int Ls, float w, float tau, boo
     // (rounding is monotone), so the result is the dense kernel's minimum of
     // the same rounded values, bit for bit.
     const int R = trunc_radius(tau, quad);
+    if (quad && R > kQuadWindowMax && w > 0.f) {
+        dt_envelope(h, Lh, Ls, w, tau, g, out, pre, lane);
+        return;
+    }
     if (quad || R <= kWindowMax) {
         if (quad)
             dt_window<true>(h, Lh, Ls, w, tau, R, g, out, lane);

@@ -46,6 +46,8 @@ CASES = {
     "quad_L40_tau16": dict(rows=5, cols=6, L=40, weight=0.1, tau=16.0, quad=True),
     "quad_L64_untruncated": dict(rows=4, cols=4, L=64, weight=0.002, tau=1e6, quad=True),
     "quad_ragged_tau30": dict(rows=5, cols=5, L=50, weight=0.05, tau=30.0, Lmin=3, quad=True),
+    "quad_L80_tau400": dict(rows=4, cols=5, L=80, weight=0.01, tau=400.0, quad=True),
+    "quad_ragged_env": dict(rows=4, cols=4, L=120, weight=0.004, tau=2000.0, Lmin=17, quad=True),
 }
 
 
@@ -58,17 +60,19 @@ def test_structured_parity_with_oracle(case):
 
 
 @pytest.mark.parametrize("case,exact", [("potts_L16", True), ("tl_L40", True), ("ragged_2_70", True),
-                                        ("quad_L40_tau16", True), ("quad_L64_untruncated", True),
-                                        ("quad_ragged_tau30", True), ("tl_L200", False),
+                                        ("quad_L40_tau16", True), ("quad_ragged_tau30", True),
+                                        ("quad_L64_untruncated", False), ("quad_L80_tau400", False),
+                                        ("quad_ragged_env", False), ("tl_L200", False),
                                         ("tl_L256_untruncated", False)])
 def test_structured_equals_dense_drivers(case, exact):
-    """Short truncation (tau <= 8, Potts included): the window of candidates
-    plus the global minimizer give the dense kernel's minimum of the same
-    rounded values, so the states agree bit for bit.  Longer truncation: the
-    scans pick the minimizers, which rounding may decide differently where
-    several have the same exact value (reparametrized vectors form linear
-    ramps along which w|s - t| + h(t) is constant): bounds within 1e-6
-    relative, state entries within 1e-5."""
+    """Short truncation (linear radius <= 7, Potts included; quadratic radius
+    <= 16): the window of candidates plus the global minimizer give the dense
+    kernel's minimum of the same rounded values, so the states agree bit for
+    bit.  Longer truncation: the linear scans or the quadratic lower envelope
+    pick the minimizers, which rounding may decide differently where several
+    have nearly the same value (reparametrized vectors form linear ramps
+    along which w|s - t| + h(t) is constant): bounds within 1e-6 relative,
+    state entries within 1e-5."""
     m = W.grid_trunc_linear(seed=5, **CASES[case])
     T = 20
     a = Solver([m])
