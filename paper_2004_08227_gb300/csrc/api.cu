@@ -6,6 +6,7 @@
 #include <cstring>
 #include <functional>
 #include <memory>
+#include <mutex>
 #include <queue>
 #include <string>
 #include <vector>
@@ -430,6 +431,19 @@ static mplpp_status apply_queue_mapping(mplpp_solver *s, int T, int optin)
 // The resident driver: one CTA per model with the model's state in shared
 // memory; one warp per edge of a matching (threads: the largest matching, at
 // most 16 warps, unless given).
+namespace mplpp {
+cudaError_t raise_smem_limit_ptr(const void *kernel, size_t smem)
+{
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lock(mu);
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, kernel);
+    if (e != cudaSuccess) return e;
+    if (static_cast<size_t>(a.maxDynamicSharedSizeBytes) >= smem) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+}
+}  // namespace mplpp
+
 static mplpp_status apply_resident_mapping(mplpp_solver *s, int T, int optin)
 {
     if (T % 32 || T < 0 || T > 512) return fail(s, MPLPP_E_INVALID, "threads must be a multiple of 32 in 32..512");
@@ -443,7 +457,7 @@ static mplpp_status apply_resident_mapping(mplpp_solver *s, int T, int optin)
     const int nm = static_cast<int>(s->models.size());
     std::vector<ResModel> rm(nm);
     std::vector<int> off, edges;
-    long long state_max = 0, tab_max = 0;
+    long long state_max = 0, sched_max = 0;
     for (int m = 0; m < nm; ++m) {
         const ModelHost &mh = s->models[m];
         const int n0 = mh.node_base, n1 = mh.node_base + mh.n;
@@ -465,7 +479,7 @@ static mplpp_status apply_resident_mapping(mplpp_solver *s, int T, int optin)
             rm[m].tab_base = 0;
             rm[m].tab_n = 0;
         }
-        tab_max = std::max(tab_max, rm[m].tab_n);
+        sched_max = std::max(sched_max, static_cast<long long>(mh.off.size()) + mh.E);
         rm[m].sched = static_cast<int>(off.size());
         rm[m].P = static_cast<int>(mh.off.size()) - 1;
         for (size_t k = 0; k < mh.off.size(); ++k) off.push_back(static_cast<int>(edges.size()) + mh.off[k]);
@@ -473,12 +487,17 @@ static mplpp_status apply_resident_mapping(mplpp_solver *s, int T, int optin)
         for (size_t k = 0; k + 1 < mh.off.size(); ++k) wmax = std::max(wmax, mh.off[k + 1] - mh.off[k]);
         state_max = std::max(state_max, rm[m].agg_n + rm[m].msg_n);
     }
-    if (T == 0) T = 32 * std::min(16, wmax);
-    size_t smem = static_cast<size_t>(state_max) * sizeof(float2) + static_cast<size_t>(T / 32) * kResWarpBytes;
-    // (the tables are read from L2: staging them in shared memory as well
-    // measured slower on the K_20 replicas -- fewer models per SM)
-    s->res_stage = false;
-    (void)tab_max;
+    // a warp updates 32 / res_lanes(lmax) edges at once: enough warps for the
+    // largest matching, at most 16
+    const int epw = 32 / res_lanes(lmax);
+    if (T == 0) T = 32 * std::min(16, (wmax + epw - 1) / epw);
+    // the state, the groups' vectors and the model's schedule (matching
+    // offsets and edge ids); the tables are read from memory (staging them in
+    // shared memory as well measured slower on the K_20 replicas: fewer
+    // models per SM)
+    size_t smem = static_cast<size_t>(state_max) * sizeof(float2) + static_cast<size_t>(T / 32) * kResWarpBytes +
+                  static_cast<size_t>(sched_max) * sizeof(int);
+    smem = (smem + 15) / 16 * 16;
     if (smem > static_cast<size_t>(optin))
         return fail(s, MPLPP_E_UNSUPPORTED,
                     "the resident driver needs " + std::to_string(smem) + " B of shared memory for the largest model");
@@ -938,7 +957,7 @@ cudaError_t enqueue_persistent(mplpp_solver *s, cudaStream_t st, int iterations)
     }
     if (s->mode == MPLPP_MODE_RESIDENT) {  // reads values only, writes version 0: no restamp
         ResParams rp = {s->d_edges, s->d_tab, s->d_agg, s->d_msg, s->d_res_models, s->d_res_off, s->d_res_edges,
-                        iterations, s->res_stage ? 1 : 0};
+                        iterations};
         int lmax = 1;
         for (auto &nd : s->h_nodes) lmax = std::max(lmax, nd.L);
         return launch_resident(rp, static_cast<int>(s->models.size()), s->T, s->smem_res, lmax, st);

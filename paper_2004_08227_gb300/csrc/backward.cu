@@ -295,8 +295,7 @@ cudaError_t launch_bw_phase(const BwParams &p, const int *items, int n_items, cu
     if (n_items <= 0) return cudaSuccess;
     const size_t smem = bw_phase_smem_bytes(p.lmax);
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(bw_phase_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             static_cast<int>(smem));
+        cudaError_t e = raise_smem_limit(bw_phase_kernel, smem);
         if (e != cudaSuccess) return e;
     }
     bw_phase_kernel<<<n_items, kThreads, smem, st>>>(p, items);

@@ -25,6 +25,19 @@
 #include <cuda_runtime.h>
 
 namespace mplpp {
+// Raises kernel's limit on dynamic shared memory to at least smem bytes on the
+// current device, never lowers it: the limit belongs to the kernel, not to a
+// solver, and solvers of one process share it (a lower value set for one
+// solver would make another's launches fail).  Serialized by a lock.
+cudaError_t raise_smem_limit_ptr(const void *kernel, size_t smem);
+template <typename K>
+inline cudaError_t raise_smem_limit(K *kernel, size_t smem)
+{
+    return raise_smem_limit_ptr(reinterpret_cast<const void *>(kernel), smem);
+}
+}  // namespace mplpp
+
+namespace mplpp {
 
 struct EdgeDesc {
     long long toff;   // float offset of the table in tab (Lu rows, stride ld)

@@ -547,8 +547,7 @@ cudaError_t launch_bound(const EdgeDesc *edges, int n_edges, const NodeDesc *nod
         const int lm = lmax > 0 ? lmax : 1;
         const size_t smem = (2 * sizeof(double) + 2 * sizeof(float)) * static_cast<size_t>(lm);
         if (smem > 48 * 1024) {
-            cudaError_t e = cudaFuncSetAttribute(bound_edges_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 static_cast<int>(smem));
+            cudaError_t e = raise_smem_limit(bound_edges_kernel, smem);
             if (e != cudaSuccess) return e;
         }
         bound_edges_kernel<<<grid_for(n_edges, 1), kThreads, smem, st>>>(edges, n_edges, tab, msg, lm, emin);

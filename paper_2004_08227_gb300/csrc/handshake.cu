@@ -617,8 +617,12 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
             for (int base = warp * 32; base < 4 * Q; base += T) {
                 const int idx = base + lane, q = idx >> 2, part = idx & 3;
                 float4 m = inf4;
-                if (idx < 4 * Q)
-                    for (int w = part; w < W; w += 4) m = min4(m, part2[w * Qp + q]);
+                if (idx < 4 * Q) {  // W <= 16 warps: at most four partials per lane, loaded together
+                    float4 v[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) v[j] = (part + 4 * j < W) ? part2[(part + 4 * j) * Qp + q] : inf4;
+                    m = min4(min4(v[0], v[1]), min4(v[2], v[3]));
+                }
 #pragma unroll
                 for (int o = 1; o <= 2; o <<= 1)
                     m = min4(m, make_float4(__shfl_xor_sync(0xffffffffu, m.x, o), __shfl_xor_sync(0xffffffffu, m.y, o),
@@ -696,10 +700,11 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
         } else {
             m = xbuf[t];
         }
-        if (CLUSTER) {
-            int r = 1;
-            for (; r + 1 < C; r += 2) m = min3f(m, xbuf[r * ld + t], xbuf[(r + 1) * ld + t]);
-            if (r < C) m = fminf(m, xbuf[r * ld + t]);
+        if (CLUSTER) {  // C <= 8 slots, loaded together
+            float v[7];
+#pragma unroll
+            for (int r = 1; r < 8; ++r) v[r - 1] = r < C ? xbuf[r * ld + t] : INFINITY;
+            m = min3f(m, min3f(v[0], v[1], v[2]), min3f(v[3], v[4], fminf(v[5], v[6])));
         }
         const float2 vh = sm.vh[t];
         const float2 b = df_add_f(vh, m);
@@ -949,8 +954,7 @@ __global__ void __launch_bounds__(128) hs_queue_kernel(HsParams p)
 template <typename K>
 cudaError_t set_attrs(K kernel, size_t smem)
 {
-    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
+    cudaError_t e = raise_smem_limit(kernel, smem);
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
 }
@@ -1036,9 +1040,7 @@ cudaError_t hs_launch_queue(const HsParams &p, int blocks, int threads, size_t s
 
 int hs_queue_max_blocks(int threads, size_t smem)
 {
-    if (cudaFuncSetAttribute(hs_queue_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) !=
-        cudaSuccess)
-        return 0;
+    if (raise_smem_limit(hs_queue_kernel, smem) != cudaSuccess) return 0;
     int per_sm = 0, dev = 0, sms = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hs_queue_kernel, threads, smem) != cudaSuccess) return 0;
     cudaGetDevice(&dev);

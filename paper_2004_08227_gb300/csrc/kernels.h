@@ -67,9 +67,14 @@ cudaError_t hs_launch_queue(const HsParams &p, int blocks, int threads, size_t s
 int hs_queue_max_blocks(int threads, size_t smem);  // co-resident blocks on the device
 
 // resident.cu: one CTA per model, the model's state in shared memory for all
-// iterations, a block barrier between matchings (label counts <= kResMaxL).
+// iterations, a block barrier between matchings (label counts <= kResMaxL);
+// groups of res_lanes(lmax) lanes update one edge each.
 constexpr int kResMaxL = 32;
-constexpr int kResWarpBytes = 2 * kResMaxL * 8 + 3 * kResMaxL * 4;  // per-warp vectors
+constexpr int kResWarpBytes = 2 * 32 * 8 + 3 * 32 * 4;  // per-warp vectors (7 words per lane)
+__host__ __device__ constexpr int res_lanes(int lmax)
+{
+    return lmax <= 8 ? 8 : (lmax <= 16 ? 16 : 32);
+}
 struct ResModel {
     long long agg_base, agg_n;  // the model's entries in agg
     long long msg_base, msg_n;  // ... and in msg
@@ -86,7 +91,6 @@ struct ResParams {
     const int *sched_off;    // per model P + 1 offsets into sched_edges
     const int *sched_edges;  // edge ids, every model's matchings in schedule order
     int iterations;
-    int stage_tables;        // nonzero: every model's tables fit shared memory beside its state
 };
 cudaError_t res_prepare(size_t smem);
 cudaError_t launch_resident(const ResParams &p, int n_models, int threads, size_t smem, int lmax, cudaStream_t st);

@@ -368,13 +368,11 @@ cudaError_t launch_rec_screen_phase(const EdgeDesc *edges, const int *items, int
     if (n_items <= 0) return cudaSuccess;
     const size_t smem = rec_screen_smem_bytes(lmax, tab_floats);
     if (rec) {
-        cudaError_t e = cudaFuncSetAttribute(rec_screen_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             static_cast<int>(smem));
+        cudaError_t e = raise_smem_limit(rec_screen_kernel<true>, smem);
         if (e != cudaSuccess) return e;
         rec_screen_kernel<true><<<n_items, kScrThreads, smem, st>>>(edges, items, tab, agg, msg, rec, rec_off, lmax);
     } else {
-        cudaError_t e = cudaFuncSetAttribute(rec_screen_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             static_cast<int>(smem));
+        cudaError_t e = raise_smem_limit(rec_screen_kernel<false>, smem);
         if (e != cudaSuccess) return e;
         rec_screen_kernel<false><<<n_items, kScrThreads, smem, st>>>(edges, items, tab, agg, msg, nullptr, nullptr,
                                                                      lmax);
@@ -389,15 +387,13 @@ cudaError_t launch_rec64_phase(const EdgeDesc *edges, const int *items, int n_it
     const size_t smem = rec64_smem_bytes(lmax);
     if (rec) {
         if (smem > 48 * 1024) {
-            cudaError_t e = cudaFuncSetAttribute(rec64_phase_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 static_cast<int>(smem));
+            cudaError_t e = raise_smem_limit(rec64_phase_kernel<true>, smem);
             if (e != cudaSuccess) return e;
         }
         rec64_phase_kernel<true><<<n_items, kThreads, smem, st>>>(edges, items, tab, agg, msg, rec, rec_off, lmax);
     } else {
         if (smem > 48 * 1024) {
-            cudaError_t e = cudaFuncSetAttribute(rec64_phase_kernel<false>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+            cudaError_t e = raise_smem_limit(rec64_phase_kernel<false>, smem);
             if (e != cudaSuccess) return e;
         }
         rec64_phase_kernel<false><<<n_items, kThreads, smem, st>>>(edges, items, tab, agg, msg, nullptr, nullptr, lmax);

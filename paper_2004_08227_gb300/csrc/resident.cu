@@ -10,11 +10,15 @@
 // memory, and separates the matchings by a block barrier -- the barrier
 // between matchings of the paper's GPU implementation (Sec. 6) at the scope
 // of a CTA.  Nothing waits on another CTA and no state crosses L2 between
-// updates; the tables are read from L2 once the first iteration has touched
-// them (the kernel can stage a model's tables in shared memory too, which
-// the host does not select: fewer models then share an SM).  One warp updates one edge of a matching: lane s holds row s
-// of the table and lane t column t (loaded together, in registers), so every
-// minimization is a sequential loop in one lane, with no shuffles.
+// updates.
+//
+// One group of LM lanes (LM = 8, 16 or 32: the label bound rounded up) updates
+// one edge: lane s of the group holds row s of the table and lane t column t
+// (in registers), so every minimization is a sequential loop in one lane,
+// with no shuffles, and a warp updates 32 / LM edges at once.  The tables are
+// read from memory (they are read-only); for LM <= 16 a group loads the table
+// of the next edge it will update while it updates the current one, so the
+// load latency is hidden behind an update.
 #include <cfloat>
 #include <cstdint>
 
@@ -24,118 +28,186 @@ namespace mplpp {
 
 namespace {
 
-// Per-warp vectors of the edge being updated.
-struct ResWarp {
-    float2 *uh, *vh;           // [32] double-float unaries without this edge's messages
-    float *w1, *alpha, *beta;  // [32] FP32 shifted operands of passes 1, 2 and 3
+// Per-group vectors of the edge being updated (7 LM words per group, so a
+// warp's groups fill kResWarpBytes).
+struct ResVec {
+    float2 *uh, *vh;           // [LM] double-float unaries without this edge's messages
+    float *w1, *alpha, *beta;  // [LM] FP32 shifted operands of passes 1, 2 and 3
 };
 
-__device__ __forceinline__ ResWarp res_warp(char *base, int warp)
+template <int LM>
+__device__ __forceinline__ ResVec res_vec(char *base, int slot)
 {
-    char *b = base + static_cast<size_t>(warp) * kResWarpBytes;
-    ResWarp r;
+    char *b = base + static_cast<size_t>(slot) * (28 * LM);
+    ResVec r;
     r.uh = reinterpret_cast<float2 *>(b);
-    r.vh = r.uh + kResMaxL;
-    r.w1 = reinterpret_cast<float *>(r.vh + kResMaxL);
-    r.alpha = r.w1 + kResMaxL;
-    r.beta = r.alpha + kResMaxL;
+    r.vh = r.uh + LM;
+    r.w1 = reinterpret_cast<float *>(r.vh + LM);
+    r.alpha = r.w1 + LM;
+    r.beta = r.alpha + LM;
     return r;
 }
 
-// One Handshake update of edge ed (L_u, L_v <= LM <= 32) by one warp, on the
-// model's shared-memory state: agg and msg hold the model's entries (offsets
-// relative to the model's first node and first edge).
+// Row l and column l of edge ed's table (FP32, +inf beyond the labels).
 template <int LM>
-__device__ __forceinline__ void res_update(const EdgeDesc &ed, const float *tab, long long tbase, float2 *agg,
-                                           float2 *msg, long long abase, long long mbase, const ResWarp &w, int lane)
+__device__ __forceinline__ void res_load(const EdgeDesc &ed, const float *tab, int l, float (&row)[LM],
+                                         float (&col)[LM])
 {
     const int Lu = ed.Lu, Lv = ed.Lv, ld = ed.ld;
-    float2 *au = agg + (ed.au - abase), *av = agg + (ed.av - abase);
-    float2 *mu = msg + (ed.mu - mbase), *mv = msg + (ed.mv - mbase);
-    // row `lane` and column `lane` of the table (FP32, +inf beyond the labels)
-    float row[LM], col[LM];
-    const float *th = tab + (ed.toff - tbase);
+    const float *th = tab + ed.toff;
 #pragma unroll
-    for (int t = 0; t < LM; ++t) row[t] = (lane < Lu && t < Lv) ? th[lane * ld + t] : INFINITY;
+    for (int t = 0; t < LM; ++t) row[t] = (l < Lu && t < Lv) ? __ldg(th + l * ld + t) : INFINITY;
 #pragma unroll
-    for (int s = 0; s < LM; ++s) col[s] = (lane < Lv && s < Lu) ? th[s * ld + lane] : INFINITY;
-    if (lane < Lu) w.uh[lane] = df_sub(au[lane], mu[lane]);
-    if (lane < Lv) w.vh[lane] = df_sub(av[lane], mv[lane]);
+    for (int s = 0; s < LM; ++s) col[s] = (l < Lv && s < Lu) ? __ldg(th + s * ld + l) : INFINITY;
+}
+
+// One Handshake update of edge ed (L_u, L_v <= LM) by a group of LM lanes (l:
+// the lane's index in the group) on the model's shared-memory state: agg and
+// msg hold the model's entries (offsets relative to the model's first node
+// and first edge).  Every lane of the warp calls it (act false: a group
+// without an edge this round), for the warp-wide synchronizations.
+template <int LM>
+__device__ __forceinline__ void res_update(bool act, const EdgeDesc &ed, const float (&row)[LM],
+                                           const float (&col)[LM], float2 *agg, float2 *msg, long long abase,
+                                           long long mbase, const ResVec &w, int l)
+{
+    const int Lu = act ? ed.Lu : 0, Lv = act ? ed.Lv : 0;
+    float2 *au = agg + (act ? ed.au - abase : 0), *av = agg + (act ? ed.av - abase : 0);
+    float2 *mu = msg + (act ? ed.mu - mbase : 0), *mv = msg + (act ? ed.mv - mbase : 0);
+    if (l < Lu) w.uh[l] = df_sub(au[l], mu[l]);
+    if (l < Lv) w.vh[l] = df_sub(av[l], mv[l]);
     __syncwarp();
     const float2 vref = w.vh[0];
-    if (lane < Lv) w.w1[lane] = df_to_f(df_sub(w.vh[lane], vref));
+    if (l < Lv) w.w1[l] = df_to_f(df_sub(w.vh[l], vref));
     __syncwarp();
     // pass 1: a(s) = 1/2 (min_t [theta(s,t) + w1(t)] + vh(0) + uh(s));  alpha = uh - a
-    if (lane < Lu) {
+    if (l < Lu) {
         float m = INFINITY;
 #pragma unroll
         for (int t = 0; t < LM; ++t)
             if (t < Lv) m = fminf(m, row[t] + w.w1[t]);
-        const float2 u = w.uh[lane];
+        const float2 u = w.uh[l];
         const float2 a = df_half(df_add(df_add_f(vref, m), u));
-        w.alpha[lane] = df_to_f(df_sub(u, a));
+        w.alpha[l] = df_to_f(df_sub(u, a));
     }
     __syncwarp();
     // pass 2: b(t) = min_s [theta(s,t) + alpha(s)] + vh(t),  beta = vh - b
-    if (lane < Lv) {
+    if (l < Lv) {
         float m = INFINITY;
 #pragma unroll
         for (int s = 0; s < LM; ++s)
             if (s < Lu) m = fminf(m, col[s] + w.alpha[s]);
-        const float2 vh = w.vh[lane];
+        const float2 vh = w.vh[l];
         const float2 b = df_add_f(vh, m);
-        w.beta[lane] = df_to_f(df_sub(vh, b));
-        av[lane] = b;
-        mv[lane] = df_sub(b, vh);
+        w.beta[l] = df_to_f(df_sub(vh, b));
+        av[l] = b;
+        mv[l] = df_sub(b, vh);
     }
     __syncwarp();
     // pass 3: c(s) = min_t [theta(s,t) + beta(t)] + uh(s)
-    if (lane < Lu) {
+    if (l < Lu) {
         float m = INFINITY;
 #pragma unroll
         for (int t = 0; t < LM; ++t)
             if (t < Lv) m = fminf(m, row[t] + w.beta[t]);
-        const float2 u = w.uh[lane];
+        const float2 u = w.uh[l];
         const float2 c = df_add_f(u, m);
-        au[lane] = c;
-        mu[lane] = df_sub(c, u);
+        au[l] = c;
+        mu[l] = df_sub(c, u);
     }
-    __syncwarp();  // the warp's vectors are rewritten by its next update
+    __syncwarp();  // the group's vectors are rewritten by its next update
+}
+
+// The walk of one group through a model's schedule: matching k, round r (the
+// group's edge of round r is sch[off[k] + r * slots + slot], if below
+// off[k + 1]), iteration it.  Every group of the CTA takes the same steps.
+struct ResPos {
+    int it, k, r;
+};
+
+__device__ __forceinline__ bool res_next(ResPos &q, const int *off, int P, int slots, int iterations)
+{
+    if ((q.r + 1) * slots < off[q.k + 1] - off[q.k]) {
+        ++q.r;
+        return true;
+    }
+    q.r = 0;
+    if (++q.k < P) return true;
+    q.k = 0;
+    return ++q.it < iterations;
 }
 
 template <int LM>
 __global__ void __launch_bounds__(512) hs_resident_kernel(ResParams p)
 {
+    constexpr int G = LM, EPW = 32 / LM;  // lanes per edge, edges per warp
+    constexpr bool kPrefetch = LM <= 16;  // registers for a second row and column
     extern __shared__ __align__(16) char smem_raw[];
     const int m = blockIdx.x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, W = blockDim.x >> 5;
+    const int l = lane % G, slot = warp * EPW + lane / G, slots = W * EPW;
     const ResModel md = p.models[m];
+    // shared memory: the state, the groups' vectors, the schedule
     float2 *agg = reinterpret_cast<float2 *>(smem_raw);
     float2 *msg = agg + md.agg_n;
-    char *wbase = reinterpret_cast<char *>(msg + md.msg_n);
-    const ResWarp w = res_warp(wbase, warp);
-    // the model's state from the solver's versioned entries, and its tables
+    char *vec = reinterpret_cast<char *>(msg + md.msg_n);
+    const ResVec w = res_vec<LM>(vec, slot);
+    int *off = reinterpret_cast<int *>(vec + static_cast<size_t>(W) * kResWarpBytes);  // [P + 1] from 0
+    int *sch = off + md.P + 1;                                                           // the model's edge ids
+    const int *goff = p.sched_off + md.sched;
+    const int e0 = goff[0], ne = goff[md.P] - e0;
+    for (int i = tid; i <= md.P; i += blockDim.x) off[i] = goff[i] - e0;
+    for (int i = tid; i < ne; i += blockDim.x) sch[i] = p.sched_edges[e0 + i];
     for (long long i = tid; i < md.agg_n; i += blockDim.x) agg[i] = se_df(p.agg[md.agg_base + i]);
     for (long long i = tid; i < md.msg_n; i += blockDim.x) msg[i] = se_df(p.msg[md.msg_base + i]);
-    const float *tab = p.tab;
-    long long tbase = 0;
-    if (p.stage_tables) {  // 16-byte aligned: the warp vectors are a multiple of 16 bytes
-        float4 *st = reinterpret_cast<float4 *>(wbase + static_cast<size_t>(W) * kResWarpBytes);
-        const float4 *src = reinterpret_cast<const float4 *>(p.tab + md.tab_base);
-        for (long long i = tid; i < md.tab_n / 4; i += blockDim.x) st[i] = src[i];
-        tab = reinterpret_cast<const float *>(st);
-        tbase = md.tab_base;
+    __syncthreads();
+    auto edge_at = [&](const ResPos &q, bool more, EdgeDesc &ed) {
+        const int j = off[q.k] + q.r * slots + slot;
+        const bool a = more && j < off[q.k + 1];
+        if (a) ed = p.edges[sch[j]];
+        return a;
+    };
+    if (p.iterations > 0 && md.P > 0) {
+        // three steps in flight: the edge being updated (its table in row,
+        // col), the next one (its table loading), the one after (its
+        // descriptor loading)
+        ResPos q = {0, 0, 0};
+        EdgeDesc ed{}, ed1{};
+        bool act = edge_at(q, true, ed);
+        float row[LM], col[LM];
+        if (act) res_load<LM>(ed, p.tab, l, row, col);
+        ResPos q1 = q;
+        bool more1 = res_next(q1, off, md.P, slots, p.iterations);
+        bool act1 = edge_at(q1, more1, ed1);
+        for (;;) {
+            float rown[LM], coln[LM];
+            if (kPrefetch && act1) res_load<LM>(ed1, p.tab, l, rown, coln);
+            ResPos q2 = q1;
+            const bool more2 = more1 && res_next(q2, off, md.P, slots, p.iterations);
+            EdgeDesc ed2{};
+            const bool act2 = edge_at(q2, more2, ed2);
+            res_update<LM>(act, ed, row, col, agg, msg, md.agg_base, md.msg_base, w, l);
+            if (!more1) break;
+            if (q1.k != q.k || q1.it != q.it) __syncthreads();  // the barrier between matchings
+            q = q1;
+            act = act1;
+            ed = ed1;
+            if (kPrefetch) {
+#pragma unroll
+                for (int t = 0; t < LM; ++t) {
+                    row[t] = rown[t];
+                    col[t] = coln[t];
+                }
+            } else if (act) {
+                res_load<LM>(ed, p.tab, l, row, col);
+            }
+            q1 = q2;
+            more1 = more2;
+            act1 = act2;
+            ed1 = ed2;
+        }
     }
     __syncthreads();
-    const int *off = p.sched_off + md.sched;  // [P + 1] matchings of this model
-    for (int it = 0; it < p.iterations; ++it)
-        for (int k = 0; k < md.P; ++k) {
-            for (int j = off[k] + warp; j < off[k + 1]; j += W) {
-                const EdgeDesc ed = p.edges[p.sched_edges[j]];
-                res_update<LM>(ed, tab, tbase, agg, msg, md.agg_base, md.msg_base, w, lane);
-            }
-            __syncthreads();  // the barrier between matchings
-        }
     for (long long i = tid; i < md.agg_n; i += blockDim.x) p.agg[md.agg_base + i] = se_make(agg[i], 0u);
     for (long long i = tid; i < md.msg_n; i += blockDim.x) p.msg[md.msg_base + i] = se_make(msg[i], 0u);
 }
@@ -145,27 +217,23 @@ __global__ void __launch_bounds__(512) hs_resident_kernel(ResParams p)
 cudaError_t res_prepare(size_t smem)
 {
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(hs_resident_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  static_cast<int>(smem))) != cudaSuccess)
+    if ((e = raise_smem_limit(hs_resident_kernel<8>, smem)) != cudaSuccess)
         return e;
-    if ((e = cudaFuncSetAttribute(hs_resident_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  static_cast<int>(smem))) != cudaSuccess)
+    if ((e = raise_smem_limit(hs_resident_kernel<16>, smem)) != cudaSuccess)
         return e;
-    return cudaFuncSetAttribute(hs_resident_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                static_cast<int>(smem));
+    return raise_smem_limit(hs_resident_kernel<32>, smem);
 }
 
-// lmax: the largest label count of the solver (<= kResMaxL): the register
-// arrays of a lane's row and column are sized 8, 16 or 32.
+// lmax: the largest label count of the solver (<= kResMaxL): lanes per edge
+// res_lanes(lmax) = 8, 16 or 32.
 cudaError_t launch_resident(const ResParams &p, int n_models, int threads, size_t smem, int lmax, cudaStream_t st)
 {
     if (n_models <= 0) return cudaSuccess;
-    if (lmax <= 8)
-        hs_resident_kernel<8><<<n_models, threads, smem, st>>>(p);
-    else if (lmax <= 16)
-        hs_resident_kernel<16><<<n_models, threads, smem, st>>>(p);
-    else
-        hs_resident_kernel<32><<<n_models, threads, smem, st>>>(p);
+    switch (res_lanes(lmax)) {
+    case 8: hs_resident_kernel<8><<<n_models, threads, smem, st>>>(p); break;
+    case 16: hs_resident_kernel<16><<<n_models, threads, smem, st>>>(p); break;
+    default: hs_resident_kernel<32><<<n_models, threads, smem, st>>>(p); break;
+    }
     return cudaGetLastError();
 }
 

@@ -142,11 +142,9 @@ size_t rule_smem_bytes(int lumax, int ldmax)
 
 cudaError_t rule_prepare(size_t smem)
 {
-    cudaError_t e = cudaFuncSetAttribute(rule_kernel<kRuleM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
+    cudaError_t e = raise_smem_limit(rule_kernel<kRuleM>, smem);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(rule_kernel<kRuleU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                static_cast<int>(smem));
+    return raise_smem_limit(rule_kernel<kRuleU>, smem);
 }
 
 cudaError_t launch_rule(const RuleParams &p, int rule, int n_items, size_t smem, cudaStream_t st)

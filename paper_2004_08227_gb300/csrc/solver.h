@@ -61,7 +61,6 @@ struct mplpp_solver {
     int warp_blocks = 0, lw = 0, cap = 0;  // warp driver: blocks, per-warp vector and buffer capacity
     int queue_blocks = 0;                  // queue drivers: co-resident CTAs launched
     size_t smem_res = 0;                   // resident driver: shared memory per CTA
-    bool res_stage = false;                // resident driver: tables staged in shared memory too
     mplpp::ResModel *d_res_models = nullptr;
     int *d_res_off = nullptr, *d_res_edges = nullptr;
     size_t smem_queue = 0;

@@ -421,8 +421,7 @@ __global__ void materialize_kernel(const EdgeDesc *edges, const float2 *param, c
 
 cudaError_t struct_prepare(int lmax)
 {
-    return cudaFuncSetAttribute(struct_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                static_cast<int>(kStructWarps * struct_bytes_per_warp(lmax)));
+    return raise_smem_limit(struct_kernel, kStructWarps * struct_bytes_per_warp(lmax));
 }
 
 cudaError_t launch_struct(const StructParams &p, cudaStream_t st)
@@ -443,9 +442,7 @@ cudaError_t launch_struct_queue(const StructParams &p, int blocks, cudaStream_t 
 int struct_queue_max_blocks(int lmax)
 {
     const size_t smem = kStructWarps * struct_bytes_per_warp(lmax);
-    if (cudaFuncSetAttribute(struct_queue_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(smem)) != cudaSuccess)
-        return 0;
+    if (raise_smem_limit(struct_queue_kernel, smem) != cudaSuccess) return 0;
     int per_sm = 0, dev = 0, sms = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, struct_queue_kernel, kStructThreads, smem) !=
         cudaSuccess)

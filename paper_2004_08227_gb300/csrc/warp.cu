@@ -389,7 +389,7 @@ __global__ void __launch_bounds__(512) hs_warp_kernel(HsParams p)
 
 cudaError_t hs_warp_prepare(size_t smem)
 {
-    return cudaFuncSetAttribute(hs_warp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    return raise_smem_limit(hs_warp_kernel, smem);
 }
 
 int hs_warp_max_blocks(int threads, size_t smem)

@@ -619,18 +619,23 @@ def test_queue_driver_bounded_wait_times_out():
     _check_D(D[0], sol["bound"])
 
 
+@pytest.mark.parametrize("threads", [0, 64, 96])
 @pytest.mark.parametrize("lmax", [8, 16, 32])
-def test_resident_driver_bitwise_equal_to_looped(lmax):
+def test_resident_driver_bitwise_equal_to_looped(lmax, threads):
     """The resident driver (one CTA per model, its state in shared memory, a
-    block barrier between matchings): bit for bit the looped driver's state,
-    on uneven small models (label counts 1..lmax, odd and even n, a sparse
-    graph with greedy colouring)."""
+    block barrier between matchings, groups of 8, 16 or 32 lanes per edge):
+    bit for bit the looped driver's state, on uneven small models (label
+    counts 1..lmax, odd and even n, a sparse graph with greedy colouring).
+    With two or three warps a matching takes several rounds of edges per group,
+    and some groups sit out the last round."""
     models = [W.uneven_complete(n, 1, lmax, seed=90 + n + lmax) for n in (2, 3, 7, 12, 21)]
     models.append(W.knn(40, 4, lmax, seed=5))
     a = Solver(models, mode="looped")
-    b = Solver(models, mode="resident")
+    b = Solver(models, mode="resident", threads=threads)
     inf = b.info()
     assert inf["mode"] == "resident" and inf["grid"] == len(models)
+    if threads:
+        assert inf["threads"] == threads
     for T in (5, 3):  # continues from the state
         a.run(T)
         b.run(T)
@@ -656,3 +661,23 @@ def test_resident_driver_rejects_large_labels():
     with pytest.raises(MplppError) as ei:
         Solver([m], mode="resident")
     assert ei.value.status == -7
+
+
+def test_solvers_of_one_process_keep_their_shared_memory_limits():
+    """A solver created later with smaller tables must not lower the shared
+    memory limit of the kernels an earlier solver launches (the limit belongs
+    to the kernel): the earlier solver still runs, in every driver."""
+    big = W.uneven_complete(6, 200, 300, seed=3)
+    small = W.uneven_complete(5, 2, 4, seed=4)
+    for mode in ("looped", "persistent"):
+        a = Solver([big], mode=mode)
+        b = Solver([small], mode="looped", threads=64)
+        c = Solver([small], mode="resident", threads=64)
+        b.run(2)
+        c.run(2)
+        a.run(3)  # raised an invalid-argument launch error when the limit was lowered
+        ref = Solver([big], mode=mode)
+        ref.run(3)
+        np.testing.assert_array_equal(a.bound(), ref.bound())
+        for s in (a, b, c, ref):
+            s.close()
