@@ -401,9 +401,23 @@ static mplpp_status apply_struct_mapping(mplpp_solver *s, int optin, bool queue 
     return MPLPP_OK;
 }
 
+namespace mplpp {
+cudaError_t raise_smem_limit_ptr(const void *kernel, size_t smem)
+{
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lock(mu);
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, kernel);
+    if (e != cudaSuccess) return e;
+    if (static_cast<size_t>(a.maxDynamicSharedSizeBytes) >= smem) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+}
+}  // namespace mplpp
+
 // The queue driver: CTAs of T threads (default 128), vectors and the column
-// partials in shared memory, tables read from memory; as many CTAs as are
-// co-resident (at most one per edge).
+// partials in shared memory, tables read from memory (passes 2 and 3 find
+// them in L1: the little shared memory leaves most of it to the cache); as
+// many CTAs as are co-resident (at most one per edge).
 static mplpp_status apply_queue_mapping(mplpp_solver *s, int T, int optin)
 {
     if (T == 0) T = 128;
@@ -429,21 +443,8 @@ static mplpp_status apply_queue_mapping(mplpp_solver *s, int T, int optin)
 }
 
 // The resident driver: one CTA per model with the model's state in shared
-// memory; one warp per edge of a matching (threads: the largest matching, at
-// most 16 warps, unless given).
-namespace mplpp {
-cudaError_t raise_smem_limit_ptr(const void *kernel, size_t smem)
-{
-    static std::mutex mu;
-    std::lock_guard<std::mutex> lock(mu);
-    cudaFuncAttributes a;
-    cudaError_t e = cudaFuncGetAttributes(&a, kernel);
-    if (e != cudaSuccess) return e;
-    if (static_cast<size_t>(a.maxDynamicSharedSizeBytes) >= smem) return cudaSuccess;
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-}
-}  // namespace mplpp
-
+// memory; a group of 8, 16 or 32 lanes per edge of a matching (threads: enough
+// warps for the largest matching, at most 16, unless given).
 static mplpp_status apply_resident_mapping(mplpp_solver *s, int T, int optin)
 {
     if (T % 32 || T < 0 || T > 512) return fail(s, MPLPP_E_INVALID, "threads must be a multiple of 32 in 32..512");
