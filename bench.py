@@ -43,8 +43,16 @@ def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
 
-def models_for(cfg: int, seed: int):
+def models_for(cfg: int, seed: int, count: int = 0):
+    """The models of a configuration; count > 0 with configuration 4: that
+    many models of the batch recipe instead of 256 (a smaller case of the
+    same kernel, for profiling); with configuration 1: that many seeded
+    replicas of the K_20 model solved together."""
     from paper_2004_08227_gb300 import workloads as W
+    if cfg == 4 and count > 0:
+        return W.batch(count, seed=seed), CONFIGS[4][1]
+    if cfg == 1 and count > 0:
+        return [W.config(1, seed=seed * count + k)[0] for k in range(count)], CONFIGS[1][1]
     models, T = W.config(cfg, seed=seed)
     if not isinstance(models, list):
         models = [models]
@@ -544,9 +552,13 @@ def run_ours(args):
     name, T = CONFIGS[cfg]
     if args.iters:
         T = args.iters
+    if cfg == 4 and args.models > 0:
+        name = f"batch{args.models}_K10-80_L16-128_T{T}"
+    if cfg == 1 and args.models > 0:
+        name = f"K20_L8_uniform_x{args.models}_T{T}"
     # cpu baseline first (before any GPU work), rank 0 only
     cpu = cpu1 = None
-    models, _ = models_for(cfg, seed=rank)
+    models, _ = models_for(cfg, seed=rank, count=args.models)
     if rank == 0 and world == 1 and not args.no_cpu:
         log("timing the oracle on the host ...")
         _, cpu = cpu_oracle_rate_parallel(models, T, args.cpu_budget)
@@ -610,7 +622,9 @@ def run_ours(args):
     achieved = T * bytes_iter / (kms / 1e3) / 1e9
     achieved32 = T * bytes_iter32 / (kms / 1e3) / 1e9
     peak, peak_kind = load_peak()
-    kernel = "hs_persistent_kernel" if info["mode"] == "persistent" else "hs_looped_kernel"
+    kernel = {"persistent": "hs_persistent_kernel", "queue": "hs_queue_kernel", "resident": "hs_resident_kernel",
+              "warp": "hs_warp_kernel", "structured": "struct_kernel",
+              "structured_queue": "struct_queue_kernel"}.get(info["mode"], "hs_looped_kernel")
 
     # the looped driver (one launch per matching) on the same workload, equal bound
     looped = None
@@ -731,7 +745,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", type=int, default=2, choices=sorted(CONFIGS))
     ap.add_argument("--iters", type=int, default=0, help="override the iteration count")
-    ap.add_argument("--mode", default="auto", choices=["auto", "looped", "persistent"])
+    ap.add_argument("--mode", default="auto", choices=["auto", "looped", "persistent", "queue", "resident", "warp"])
+    ap.add_argument("--models", type=int, default=0,
+                    help="with --config 4: models of the batch recipe (0: the 256 of the workload); "
+                         "with --config 1: replicas of the K_20 model")
     ap.add_argument("--cluster", type=int, default=0, help="CTAs per edge (0: chosen; set: no autotuning)")
     ap.add_argument("--threads", type=int, default=0, help="threads per CTA (0: chosen; set: no autotuning)")
     ap.add_argument("--no-looped", action="store_true")
@@ -745,7 +762,8 @@ def main():
     ap.add_argument("--extra", type=int, default=1,
                     help="also run K_20 replicas, the kNN model and the differentiation batch")
     ap.add_argument("--replicas", type=int, default=4096, help="K_20 replicas solved together")
-    ap.add_argument("--ref-iters", type=int, default=1)
+    ap.add_argument("--ref-iters", type=int, default=10,
+                    help="--impl reference: oracle iterations per step (amortizes the copy of the FP64 state)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

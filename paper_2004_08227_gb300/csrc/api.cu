@@ -496,8 +496,8 @@ static mplpp_status apply_resident_mapping(mplpp_solver *s, int T, int optin)
     // offsets and edge ids); the tables are read from memory (staging them in
     // shared memory as well measured slower on the K_20 replicas: fewer
     // models per SM)
-    size_t smem = static_cast<size_t>(state_max) * sizeof(float2) + static_cast<size_t>(T / 32) * kResWarpBytes +
-                  static_cast<size_t>(sched_max) * sizeof(int);
+    size_t smem = static_cast<size_t>(state_max) * sizeof(float2) + 8 /* alignment of the vectors */ +
+                  static_cast<size_t>(T / 32) * kResWarpBytes + static_cast<size_t>(sched_max) * sizeof(int);
     smem = (smem + 15) / 16 * 16;
     if (smem > static_cast<size_t>(optin))
         return fail(s, MPLPP_E_UNSUPPORTED,

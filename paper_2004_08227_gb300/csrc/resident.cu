@@ -61,6 +61,33 @@ __device__ __forceinline__ void res_load(const EdgeDesc &ed, const float *tab, i
     for (int s = 0; s < LM; ++s) col[s] = (l < Lv && s < Lu) ? __ldg(th + s * ld + l) : INFINITY;
 }
 
+// min_t [x(t) + y(t)] over t < n in order, y read from shared memory (16-byte
+// aligned).  LM <= 16: four at a time over all LM entries -- entries of x
+// beyond the labels are +inf, so they never win (fminf ignores the NaN that
+// inf + -inf would give); LM = 32: one at a time up to n (its registers are
+// taken by the row and the column).
+template <int LM>
+__device__ __forceinline__ float res_min_add(const float (&x)[LM], const float *y, int n)
+{
+    float m = INFINITY;
+    if constexpr (LM <= 16) {
+        const float4 *y4 = reinterpret_cast<const float4 *>(y);
+#pragma unroll
+        for (int j = 0; j < LM / 4; ++j) {
+            const float4 v = y4[j];
+            m = fminf(m, x[4 * j] + v.x);
+            m = fminf(m, x[4 * j + 1] + v.y);
+            m = fminf(m, x[4 * j + 2] + v.z);
+            m = fminf(m, x[4 * j + 3] + v.w);
+        }
+    } else {
+#pragma unroll
+        for (int t = 0; t < LM; ++t)
+            if (t < n) m = fminf(m, x[t] + y[t]);
+    }
+    return m;
+}
+
 // One Handshake update of edge ed (L_u, L_v <= LM) by a group of LM lanes (l:
 // the lane's index in the group) on the model's shared-memory state: agg and
 // msg hold the model's entries (offsets relative to the model's first node
@@ -82,10 +109,7 @@ __device__ __forceinline__ void res_update(bool act, const EdgeDesc &ed, const f
     __syncwarp();
     // pass 1: a(s) = 1/2 (min_t [theta(s,t) + w1(t)] + vh(0) + uh(s));  alpha = uh - a
     if (l < Lu) {
-        float m = INFINITY;
-#pragma unroll
-        for (int t = 0; t < LM; ++t)
-            if (t < Lv) m = fminf(m, row[t] + w.w1[t]);
+        const float m = res_min_add<LM>(row, w.w1, Lv);
         const float2 u = w.uh[l];
         const float2 a = df_half(df_add(df_add_f(vref, m), u));
         w.alpha[l] = df_to_f(df_sub(u, a));
@@ -93,10 +117,7 @@ __device__ __forceinline__ void res_update(bool act, const EdgeDesc &ed, const f
     __syncwarp();
     // pass 2: b(t) = min_s [theta(s,t) + alpha(s)] + vh(t),  beta = vh - b
     if (l < Lv) {
-        float m = INFINITY;
-#pragma unroll
-        for (int s = 0; s < LM; ++s)
-            if (s < Lu) m = fminf(m, col[s] + w.alpha[s]);
+        const float m = res_min_add<LM>(col, w.alpha, Lu);
         const float2 vh = w.vh[l];
         const float2 b = df_add_f(vh, m);
         w.beta[l] = df_to_f(df_sub(vh, b));
@@ -106,10 +127,7 @@ __device__ __forceinline__ void res_update(bool act, const EdgeDesc &ed, const f
     __syncwarp();
     // pass 3: c(s) = min_t [theta(s,t) + beta(t)] + uh(s)
     if (l < Lu) {
-        float m = INFINITY;
-#pragma unroll
-        for (int t = 0; t < LM; ++t)
-            if (t < Lv) m = fminf(m, row[t] + w.beta[t]);
+        const float m = res_min_add<LM>(row, w.beta, Lv);
         const float2 u = w.uh[l];
         const float2 c = df_add_f(u, m);
         au[l] = c;
@@ -150,7 +168,9 @@ __global__ void __launch_bounds__(512) hs_resident_kernel(ResParams p)
     // shared memory: the state, the groups' vectors, the schedule
     float2 *agg = reinterpret_cast<float2 *>(smem_raw);
     float2 *msg = agg + md.agg_n;
-    char *vec = reinterpret_cast<char *>(msg + md.msg_n);
+    // the groups' vectors start on a 16-byte boundary (they are read four
+    // floats at a time; every vector is a multiple of 16 bytes long)
+    char *vec = smem_raw + ((static_cast<size_t>(md.agg_n + md.msg_n) * sizeof(float2) + 15) & ~size_t{15});
     const ResVec w = res_vec<LM>(vec, slot);
     int *off = reinterpret_cast<int *>(vec + static_cast<size_t>(W) * kResWarpBytes);  // [P + 1] from 0
     int *sch = off + md.P + 1;                                                           // the model's edge ids
