@@ -316,7 +316,7 @@ mplpp_status mplpp_autotune(mplpp_solver *s, int32_t iterations, char *report, s
  * a device looks up that array's device address (cudaGetSymbolAddress, with
  * the device current) and keeps it for that device's context (a call after
  * the context was destroyed and recreated, e.g. by cudaDeviceReset, looks it
- * up again); make that first call before any stream capture.  All calls share
+ * up again).  All calls share
  * the array: calls that overlap on the GPU (other streams, other host threads)
  * race on it.  Work runs on `stream` (a cudaStream_t, NULL = legacy default);
  * every call then waits for that stream to finish, to read back the check of

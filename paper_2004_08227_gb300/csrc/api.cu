@@ -2,6 +2,7 @@
 // mapping choice, the iteration drivers, bound, rounding and state I/O.
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <functional>
@@ -457,7 +458,8 @@ static mplpp_status apply_resident_mapping(mplpp_solver *s, int T, int optin)
                         std::to_string(lmax) + ")");
     const int nm = static_cast<int>(s->models.size());
     std::vector<ResModel> rm(nm);
-    std::vector<int> off, edges;
+    std::vector<int> off;
+    std::vector<int4> desc;  // the scheduled edges, relative to their models
     long long state_max = 0, sched_max = 0;
     for (int m = 0; m < nm; ++m) {
         const ModelHost &mh = s->models[m];
@@ -480,11 +482,20 @@ static mplpp_status apply_resident_mapping(mplpp_solver *s, int T, int optin)
             rm[m].tab_base = 0;
             rm[m].tab_n = 0;
         }
-        sched_max = std::max(sched_max, static_cast<long long>(mh.off.size()) + mh.E);
+        sched_max = std::max(sched_max, static_cast<long long>(mh.off.size()));
         rm[m].sched = static_cast<int>(off.size());
         rm[m].P = static_cast<int>(mh.off.size()) - 1;
-        for (size_t k = 0; k < mh.off.size(); ++k) off.push_back(static_cast<int>(edges.size()) + mh.off[k]);
-        for (int i = 0; i < mh.E; ++i) edges.push_back(mh.edge_base + mh.order[i]);
+        for (size_t k = 0; k < mh.off.size(); ++k) off.push_back(static_cast<int>(desc.size()) + mh.off[k]);
+        for (int i = 0; i < mh.E; ++i) {
+            const EdgeDesc &ed = s->h_edges[mh.edge_base + mh.order[i]];
+            const long long t = ed.toff - rm[m].tab_base;
+            const long long au = ed.au - rm[m].agg_base, av = ed.av - rm[m].agg_base;
+            const long long mu = ed.mu - rm[m].msg_base, mv = ed.mv - rm[m].msg_base;
+            if (t > INT32_MAX || au > 0xffff || av > 0xffff || mu > 0xffff || mv > 0xffff)
+                return fail(s, MPLPP_E_UNSUPPORTED, "the resident driver takes models of at most 65,536 state entries");
+            desc.push_back(make_int4(static_cast<int>(t), static_cast<int>(au | (av << 16)),
+                                     static_cast<int>(mu | (mv << 16)), ed.Lu | (ed.Lv << 8) | (ed.ld << 16)));
+        }
         for (size_t k = 0; k + 1 < mh.off.size(); ++k) wmax = std::max(wmax, mh.off[k + 1] - mh.off[k]);
         state_max = std::max(state_max, rm[m].agg_n + rm[m].msg_n);
     }
@@ -492,8 +503,8 @@ static mplpp_status apply_resident_mapping(mplpp_solver *s, int T, int optin)
     // largest matching, at most 16
     const int epw = 32 / res_lanes(lmax);
     if (T == 0) T = 32 * std::min(16, (wmax + epw - 1) / epw);
-    // the state, the groups' vectors and the model's schedule (matching
-    // offsets and edge ids); the tables are read from memory (staging them in
+    // the state, the groups' vectors and the model's matching offsets; the
+    // tables and edge descriptors are read from memory (staging the tables in
     // shared memory as well measured slower on the K_20 replicas: fewer
     // models per SM)
     size_t smem = static_cast<size_t>(state_max) * sizeof(float2) + 8 /* alignment of the vectors */ +
@@ -508,10 +519,10 @@ static mplpp_status apply_resident_mapping(mplpp_solver *s, int T, int optin)
     if (!s->d_res_models) {
         CK(s, s->alloc(&s->d_res_models, nm));
         CK(s, s->alloc(&s->d_res_off, off.size()));
-        CK(s, s->alloc(&s->d_res_edges, std::max<size_t>(1, edges.size())));
+        CK(s, s->alloc(&s->d_res_desc, std::max<size_t>(1, desc.size())));
         CK(s, cudaMemcpyAsync(s->d_res_models, rm.data(), sizeof(ResModel) * nm, cudaMemcpyHostToDevice, s->stream));
         CK(s, cudaMemcpyAsync(s->d_res_off, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice, s->stream));
-        CK(s, cudaMemcpyAsync(s->d_res_edges, edges.data(), sizeof(int) * edges.size(), cudaMemcpyHostToDevice,
+        CK(s, cudaMemcpyAsync(s->d_res_desc, desc.data(), sizeof(int4) * desc.size(), cudaMemcpyHostToDevice,
                               s->stream));
         CK(s, cudaStreamSynchronize(s->stream));
     }
@@ -957,8 +968,7 @@ cudaError_t enqueue_persistent(mplpp_solver *s, cudaStream_t st, int iterations)
         return launch_struct_queue(sp, s->queue_blocks, st);
     }
     if (s->mode == MPLPP_MODE_RESIDENT) {  // reads values only, writes version 0: no restamp
-        ResParams rp = {s->d_edges, s->d_tab, s->d_agg, s->d_msg, s->d_res_models, s->d_res_off, s->d_res_edges,
-                        iterations};
+        ResParams rp = {s->d_tab, s->d_agg, s->d_msg, s->d_res_models, s->d_res_off, s->d_res_desc, iterations};
         int lmax = 1;
         for (auto &nd : s->h_nodes) lmax = std::max(lmax, nd.L);
         return launch_resident(rp, static_cast<int>(s->models.size()), s->T, s->smem_res, lmax, st);

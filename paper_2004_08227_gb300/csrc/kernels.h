@@ -82,14 +82,18 @@ struct ResModel {
     int sched;                  // offset of its matching offsets in sched_off
     int P;                      // its matchings
 };
+// A scheduled edge of the resident driver, relative to its model (16 bytes,
+// one load): x = first table entry (floats after the model's first table),
+// y = node u's | node v's first agg entry << 16, z = phi_{v->u}'s | phi_{u->v}'s
+// first msg entry << 16 (entries after the model's first), w = L_u | L_v << 8 |
+// ld << 16.
 struct ResParams {
-    const EdgeDesc *edges;
     const float *tab;
     ulonglong2 *agg;
     ulonglong2 *msg;
     const ResModel *models;
-    const int *sched_off;    // per model P + 1 offsets into sched_edges
-    const int *sched_edges;  // edge ids, every model's matchings in schedule order
+    const int *sched_off;     // per model P + 1 offsets into sched_desc
+    const int4 *sched_desc;   // every model's edges in schedule order, as above
     int iterations;
 };
 cudaError_t res_prepare(size_t smem);

@@ -48,17 +48,37 @@ __device__ __forceinline__ ResVec res_vec(char *base, int slot)
     return r;
 }
 
-// Row l and column l of edge ed's table (FP32, +inf beyond the labels).
+// Fields of a scheduled edge (ResParams::sched_desc).
+struct ResEdge {
+    int toff, au, av, mu, mv, Lu, Lv, ld;
+};
+
+__device__ __forceinline__ ResEdge res_edge(int4 d)
+{
+    return ResEdge{d.x,      d.y & 0xffff, (d.y >> 16) & 0xffff, d.z & 0xffff, (d.z >> 16) & 0xffff,
+                   d.w & 0xff, (d.w >> 8) & 0xff, (d.w >> 16) & 0xff};
+}
+
+// Row l and column l of edge ed's table (FP32, +inf beyond the labels; tab:
+// the model's first table).  The row is read in 16-byte chunks up to the
+// padded stride ld, whose padding columns hold +inf.
 template <int LM>
-__device__ __forceinline__ void res_load(const EdgeDesc &ed, const float *tab, int l, float (&row)[LM],
+__device__ __forceinline__ void res_load(const ResEdge &ed, const float *tab, int l, float (&row)[LM],
                                          float (&col)[LM])
 {
-    const int Lu = ed.Lu, Lv = ed.Lv, ld = ed.ld;
     const float *th = tab + ed.toff;
+    const float4 *r4 = reinterpret_cast<const float4 *>(th + l * ed.ld);
+    const float4 inf4 = make_float4(INFINITY, INFINITY, INFINITY, INFINITY);
 #pragma unroll
-    for (int t = 0; t < LM; ++t) row[t] = (l < Lu && t < Lv) ? __ldg(th + l * ld + t) : INFINITY;
+    for (int j = 0; j < LM / 4; ++j) {
+        const float4 v = (l < ed.Lu && 4 * j < ed.ld) ? __ldg(r4 + j) : inf4;
+        row[4 * j] = v.x;
+        row[4 * j + 1] = v.y;
+        row[4 * j + 2] = v.z;
+        row[4 * j + 3] = v.w;
+    }
 #pragma unroll
-    for (int s = 0; s < LM; ++s) col[s] = (l < Lv && s < Lu) ? __ldg(th + s * ld + l) : INFINITY;
+    for (int s = 0; s < LM; ++s) col[s] = (l < ed.Lv && s < ed.Lu) ? __ldg(th + s * ed.ld + l) : INFINITY;
 }
 
 // min_t [x(t) + y(t)] over t < n in order, y read from shared memory (16-byte
@@ -94,13 +114,12 @@ __device__ __forceinline__ float res_min_add(const float (&x)[LM], const float *
 // and first edge).  Every lane of the warp calls it (act false: a group
 // without an edge this round), for the warp-wide synchronizations.
 template <int LM>
-__device__ __forceinline__ void res_update(bool act, const EdgeDesc &ed, const float (&row)[LM],
-                                           const float (&col)[LM], float2 *agg, float2 *msg, long long abase,
-                                           long long mbase, const ResVec &w, int l)
+__device__ __forceinline__ void res_update(bool act, const ResEdge &ed, const float (&row)[LM],
+                                           const float (&col)[LM], float2 *agg, float2 *msg, const ResVec &w, int l)
 {
     const int Lu = act ? ed.Lu : 0, Lv = act ? ed.Lv : 0;
-    float2 *au = agg + (act ? ed.au - abase : 0), *av = agg + (act ? ed.av - abase : 0);
-    float2 *mu = msg + (act ? ed.mu - mbase : 0), *mv = msg + (act ? ed.mv - mbase : 0);
+    float2 *au = agg + (act ? ed.au : 0), *av = agg + (act ? ed.av : 0);
+    float2 *mu = msg + (act ? ed.mu : 0), *mv = msg + (act ? ed.mv : 0);
     if (l < Lu) w.uh[l] = df_sub(au[l], mu[l]);
     if (l < Lv) w.vh[l] = df_sub(av[l], mv[l]);
     __syncwarp();
@@ -137,8 +156,9 @@ __device__ __forceinline__ void res_update(bool act, const EdgeDesc &ed, const f
 }
 
 // The walk of one group through a model's schedule: matching k, round r (the
-// group's edge of round r is sch[off[k] + r * slots + slot], if below
-// off[k + 1]), iteration it.  Every group of the CTA takes the same steps.
+// group's edge of round r is the model's scheduled edge off[k] + r * slots +
+// slot, if below off[k + 1]), iteration it.  Every group of the CTA takes the
+// same steps.
 struct ResPos {
     int it, k, r;
 };
@@ -165,7 +185,7 @@ __global__ void __launch_bounds__(512) hs_resident_kernel(ResParams p)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, W = blockDim.x >> 5;
     const int l = lane % G, slot = warp * EPW + lane / G, slots = W * EPW;
     const ResModel md = p.models[m];
-    // shared memory: the state, the groups' vectors, the schedule
+    // shared memory: the state, the groups' vectors, the matching offsets
     float2 *agg = reinterpret_cast<float2 *>(smem_raw);
     float2 *msg = agg + md.agg_n;
     // the groups' vectors start on a 16-byte boundary (they are read four
@@ -173,18 +193,18 @@ __global__ void __launch_bounds__(512) hs_resident_kernel(ResParams p)
     char *vec = smem_raw + ((static_cast<size_t>(md.agg_n + md.msg_n) * sizeof(float2) + 15) & ~size_t{15});
     const ResVec w = res_vec<LM>(vec, slot);
     int *off = reinterpret_cast<int *>(vec + static_cast<size_t>(W) * kResWarpBytes);  // [P + 1] from 0
-    int *sch = off + md.P + 1;                                                           // the model's edge ids
     const int *goff = p.sched_off + md.sched;
-    const int e0 = goff[0], ne = goff[md.P] - e0;
+    const int e0 = goff[0];
+    const int4 *desc = p.sched_desc + e0;  // the model's scheduled edges
+    const float *mtab = p.tab + md.tab_base;
     for (int i = tid; i <= md.P; i += blockDim.x) off[i] = goff[i] - e0;
-    for (int i = tid; i < ne; i += blockDim.x) sch[i] = p.sched_edges[e0 + i];
     for (long long i = tid; i < md.agg_n; i += blockDim.x) agg[i] = se_df(p.agg[md.agg_base + i]);
     for (long long i = tid; i < md.msg_n; i += blockDim.x) msg[i] = se_df(p.msg[md.msg_base + i]);
     __syncthreads();
-    auto edge_at = [&](const ResPos &q, bool more, EdgeDesc &ed) {
+    auto edge_at = [&](const ResPos &q, bool more, ResEdge &ed) {
         const int j = off[q.k] + q.r * slots + slot;
         const bool a = more && j < off[q.k + 1];
-        if (a) ed = p.edges[sch[j]];
+        if (a) ed = res_edge(__ldg(desc + j));
         return a;
     };
     if (p.iterations > 0 && md.P > 0) {
@@ -192,21 +212,21 @@ __global__ void __launch_bounds__(512) hs_resident_kernel(ResParams p)
         // col), the next one (its table loading), the one after (its
         // descriptor loading)
         ResPos q = {0, 0, 0};
-        EdgeDesc ed{}, ed1{};
+        ResEdge ed{}, ed1{};
         bool act = edge_at(q, true, ed);
         float row[LM], col[LM];
-        if (act) res_load<LM>(ed, p.tab, l, row, col);
+        if (act) res_load<LM>(ed, mtab, l, row, col);
         ResPos q1 = q;
         bool more1 = res_next(q1, off, md.P, slots, p.iterations);
         bool act1 = edge_at(q1, more1, ed1);
         for (;;) {
             float rown[LM], coln[LM];
-            if (kPrefetch && act1) res_load<LM>(ed1, p.tab, l, rown, coln);
+            if (kPrefetch && act1) res_load<LM>(ed1, mtab, l, rown, coln);
             ResPos q2 = q1;
             const bool more2 = more1 && res_next(q2, off, md.P, slots, p.iterations);
-            EdgeDesc ed2{};
+            ResEdge ed2{};
             const bool act2 = edge_at(q2, more2, ed2);
-            res_update<LM>(act, ed, row, col, agg, msg, md.agg_base, md.msg_base, w, l);
+            res_update<LM>(act, ed, row, col, agg, msg, w, l);
             if (!more1) break;
             if (q1.k != q.k || q1.it != q.it) __syncthreads();  // the barrier between matchings
             q = q1;
@@ -219,7 +239,7 @@ __global__ void __launch_bounds__(512) hs_resident_kernel(ResParams p)
                     col[t] = coln[t];
                 }
             } else if (act) {
-                res_load<LM>(ed, p.tab, l, row, col);
+                res_load<LM>(ed, mtab, l, row, col);
             }
             q1 = q2;
             more1 = more2;

@@ -62,7 +62,8 @@ struct mplpp_solver {
     int queue_blocks = 0;                  // queue drivers: co-resident CTAs launched
     size_t smem_res = 0;                   // resident driver: shared memory per CTA
     mplpp::ResModel *d_res_models = nullptr;
-    int *d_res_off = nullptr, *d_res_edges = nullptr;
+    int *d_res_off = nullptr;
+    int4 *d_res_desc = nullptr;
     size_t smem_queue = 0;
     unsigned long long *d_queue = nullptr; // queue driver: next item index
     size_t smem_warp = 0;
