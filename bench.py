@@ -393,16 +393,19 @@ def knn_study(Solver, stream, args, peak):
 
 def differentiation_study(Solver, stream, args):
     """16 x K_50, L = 64, T = 50 with a state checkpoint every 10 iterations:
-    the forward run (with the bound) and the backward (mplpp_backward, host
-    gradients) timed separately; device memory the solver holds afterwards,
-    and the peak including the backward's transient gradient buffers."""
+    the forward run (with the bound) and the backward (mplpp_backward) timed
+    separately, with host gradients and with device gradients; device memory
+    the solver holds afterwards, and the peak including the backward's
+    transient gradient buffers (host-gradient path)."""
+    import types
+    import torch
     models, T = models_for(5, seed=0)
     s = Solver(models, record_every=10)
 
-    def fwd():
-        s.reset()
-        s.run(T)
-        s.bound(exact=True)
+    def fwd(sol=s):
+        sol.reset()
+        sol.run(T)
+        sol.bound(exact=True)
 
     def bwd():
         s.backward()
@@ -416,8 +419,28 @@ def differentiation_study(Solver, stream, args):
     transient += 4 * sum(int(np.sum(np.asarray(m.labels, np.int64)[m.edge_u] *
                                     np.asarray(m.labels, np.int64)[m.edge_v])) for m in models)
     s.close()
+    # the same with the costs and the gradients in device memory (the
+    # autograd path): no gradient buffers allocated and copied back per call
+    dev = []
+    for m in models:
+        d = types.SimpleNamespace(labels=m.labels, edge_u=m.edge_u, edge_v=m.edge_v, schedule=m.schedule)
+        d.unary = torch.as_tensor(np.ascontiguousarray(m.unary, np.float32)).cuda()
+        d.pairwise = torch.as_tensor(np.ascontiguousarray(m.pairwise, np.float32)).cuda()
+        dev.append(d)
+    sd = Solver(dev, record_every=10, device_inputs=True)
+    gu = torch.empty(sum(sd.unary_sizes), dtype=torch.float32, device="cuda")
+    gp = torch.empty(max(1, sum(sd.pair_sizes)), dtype=torch.float32, device="cuda")
+
+    def bwd_dev():
+        sd.backward(None, gu, gp)
+    fwd(sd)
+    bwd_dev()
+    fwd(sd)
+    dms, _ = _timed(stream, bwd_dev, 2)
+    sd.close()
     return {"workload": CONFIGS[5][0], "iterations": T, "record_every": 10, "forward_ms": fms, "backward_ms": bms,
-            "backward_over_forward": bms / fms, "solver_device_bytes": inf["device_bytes"],
+            "backward_over_forward": bms / fms, "backward_device_gradients_ms": dms,
+            "backward_device_gradients_over_forward": dms / fms, "solver_device_bytes": inf["device_bytes"],
             "peak_device_bytes": inf["device_bytes"] + transient}
 
 

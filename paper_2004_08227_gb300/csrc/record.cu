@@ -162,6 +162,7 @@ namespace {
 
 constexpr int kScrThreads = 256;
 constexpr int kWarpCands = 128;  // candidates per warp and pass
+constexpr int kSpanReg = 16;     // a thread's sums of a line kept in registers (up to this many)
 
 __device__ __forceinline__ unsigned long long order_key(double v)
 {
@@ -190,12 +191,28 @@ __device__ __forceinline__ void screened_lines(const float *tab, int ldp, int n,
     const int k = tid & (G - 1), g0 = tid / G, ng = T / G;
     const float ax0 = __double2float_ru(fabs(xv[0]));
     auto th = [&](int i, int j) { return ROWS ? tab[i * ldp + j] : tab[j * ldp + i]; };
+    const int span = (len + G - 1) / G;  // elements of a line per thread
+    const bool reg = span <= kSpanReg;
     for (int base = 0; base < n; base += ng) {  // the same trip count in every thread
         const int i = base + g0;
         const bool on = i < n;
         float mn = INFINITY, h = 0.f, d = 0.f;
+        float sv[kSpanReg];  // the FP32 sums, for the candidate test
+#pragma unroll
+        for (int r = 0; r < kSpanReg; ++r) {
+            const int j = k + r * G;
+            sv[r] = INFINITY;
+            if (on && j < len) {
+                const float t = th(i, j);
+                const float wj = w[j];
+                sv[r] = t + wj;
+                mn = fminf(mn, sv[r]);
+                h = fmaxf(h, fabsf(t));
+                d = fmaxf(d, fabsf(wj));
+            }
+        }
         if (on)
-            for (int j = k; j < len; j += G) {
+            for (int j = k + kSpanReg * G; j < len; j += G) {
                 const float t = th(i, j);
                 const float wj = w[j];
                 mn = fminf(mn, t + wj);
@@ -215,17 +232,35 @@ __device__ __forceinline__ void screened_lines(const float *tab, int ldp, int n,
             key[i] = ~0ull;
             arg[i] = INT_MAX;
         }
-        // the warp's candidates into its list (warp-uniform trip count)
+        // the warp's candidates into its list (warp-uniform trip count; the
+        // list's order does not matter)
         int nc = 0;
         bool over = false;
-        const int span = (len + G - 1) / G;
-        for (int r = 0; r < span; ++r) {
-            const int j = k + r * G;
-            const bool c = on && j < len && th(i, j) + w[j] <= thr;
-            const unsigned mask = __ballot_sync(0xffffffffu, c);
-            const int slot = nc + __popc(mask & ((1u << lane) - 1u));
-            if (c && slot < kWarpCands) cand[slot] = make_int2(i, j);
-            nc += __popc(mask);
+        if (reg) {
+            // a mask of the thread's candidates, a prefix sum of the counts over the warp
+            unsigned m = 0u;
+#pragma unroll
+            for (int r = 0; r < kSpanReg; ++r)
+                if (sv[r] <= thr) m |= 1u << r;  // +inf beyond the line (thr is finite)
+            const int cnt = __popc(m);
+            int incl = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            nc = __shfl_sync(0xffffffffu, incl, 31);
+            for (int slot = incl - cnt; m; m &= m - 1u, ++slot)
+                if (slot < kWarpCands) cand[slot] = make_int2(i, k + (__ffs(m) - 1) * G);
+        } else {
+            for (int r = 0; r < span; ++r) {
+                const int j = k + r * G;
+                const bool c = on && j < len && th(i, j) + w[j] <= thr;
+                const unsigned mask = __ballot_sync(0xffffffffu, c);
+                const int slot = nc + __popc(mask & ((1u << lane) - 1u));
+                if (c && slot < kWarpCands) cand[slot] = make_int2(i, j);
+                nc += __popc(mask);
+            }
         }
         if (nc > kWarpCands) {
             over = true;
@@ -264,7 +299,7 @@ __device__ __forceinline__ void screened_lines(const float *tab, int ldp, int n,
 }
 
 template <bool REC>
-__global__ void __launch_bounds__(kScrThreads) rec_screen_kernel(const EdgeDesc *edges, const int *items,
+__global__ void __launch_bounds__(kScrThreads, 4) rec_screen_kernel(const EdgeDesc *edges, const int *items,
                                                                  const float *tab, double *agg, double *msg,
                                                                  unsigned char *rec, const long long *rec_off,
                                                                  int lmax)
@@ -273,7 +308,7 @@ __global__ void __launch_bounds__(kScrThreads) rec_screen_kernel(const EdgeDesc 
     const int e = items[blockIdx.x];
     const EdgeDesc ed = edges[e];
     const int Lu = ed.Lu, Lv = ed.Lv, ld = ed.ld, ldp = ld | 1;
-    const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int T = blockDim.x, tid = threadIdx.x, warp = tid >> 5;
     double *uh = shd, *vh = uh + lmax, *al = vh + lmax, *be = al + lmax, *bv = be + lmax;
     unsigned long long *key = reinterpret_cast<unsigned long long *>(bv + lmax);  // [lmax] per-line minima
     int2 *cand = reinterpret_cast<int2 *>(key + lmax) + warp * kWarpCands;      // this warp's list
@@ -286,18 +321,28 @@ __global__ void __launch_bounds__(kScrThreads) rec_screen_kernel(const EdgeDesc 
         s2 = t1 + Lu;
         t3 = s2 + Lv;
     }
-    // the table (rows by warp, 16-byte chunks by lane), node vectors, shifted vh
+    // the table (16-byte chunks, a thread's next eight requested before any is
+    // stored, so the loads overlap), node vectors, shifted vh
     const float4 *th4 = reinterpret_cast<const float4 *>(tab + ed.toff);
-    const int Q = ld >> 2;
-    for (int s = warp; s < Lu; s += T >> 5)
-        for (int c = lane; c < Q; c += 32) {
-            const float4 v = th4[s * Q + c];
-            float *d = st + s * ldp + 4 * c;
-            d[0] = v.x;
-            d[1] = v.y;
-            d[2] = v.z;
-            d[3] = v.w;
+    const int Q = ld >> 2, nq = Lu * Q;
+    for (int base = tid; base < nq; base += 8 * T) {
+        float4 v[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+            if (base + r * T < nq) v[r] = th4[base + r * T];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int c = base + r * T;
+            if (c < nq) {
+                const int s = c / Q;
+                float *d = st + s * ldp + 4 * (c - s * Q);
+                d[0] = v[r].x;
+                d[1] = v[r].y;
+                d[2] = v[r].z;
+                d[3] = v[r].w;
+            }
         }
+    }
     const double vh0 = agg[ed.av] - msg[ed.mv];
     for (int s = tid; s < Lu; s += T) uh[s] = agg[ed.au + s] - msg[ed.mu + s];
     for (int t = tid; t < Lv; t += T) {
