@@ -335,7 +335,9 @@ def batched_vs_looped(Solver, stream, args):
     upd = T * info["edges"]
     return {"workload": CONFIGS[4][0], "models": len(models), "edges": info["edges"], "iterations": T,
             "batched_ms": bms, "batched_edge_updates_per_s": upd / (bms / 1e3),
-            "batched_gbs": T * info["bytes_per_iteration"] / (bms / 1e3) / 1e9,
+            "batched_gbs": T * algorithmic_bytes(models) / (bms / 1e3) / 1e9,
+            "batched_frac_of_peak": T * algorithmic_bytes(models) / (bms / 1e3) / 1e9 / load_peak()[0],
+            "batched_gbs_state32": T * info["bytes_per_iteration"] / (bms / 1e3) / 1e9,
             "per_model_looped_ms": lp["ms_per_step"], "per_model_launches": lp["launches_per_step"],
             "bound_equal": lp["bound_equal"], "speedup": lp["ms_per_step"] / bms,
             "mapping": {k: info[k] for k in ("mode", "cluster", "threads", "grid")},
