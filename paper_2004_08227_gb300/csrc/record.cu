@@ -268,15 +268,26 @@ __device__ __forceinline__ void screened_lines(const float *tab, int ldp, int n,
         }
         __syncwarp();
         if (!over) {
-            // FP64 values, 32 candidates per instruction, merged per line
-            for (int c = lane; c < nc; c += 32) {
-                const int2 q = cand[c];
-                atomicMin(&key[q.x], order_key(static_cast<double>(th(q.x, q.y)) + xv[q.y]));
+            // FP64 values, 32 candidates per instruction, merged per line; the
+            // keys stay in registers for the argmin step (FP64 is computed once)
+            unsigned long long kv[kWarpCands / 32];
+#pragma unroll
+            for (int r = 0; r < kWarpCands / 32; ++r) {
+                const int c = lane + 32 * r;
+                if (c < nc) {
+                    const int2 q = cand[c];
+                    kv[r] = order_key(static_cast<double>(th(q.x, q.y)) + xv[q.y]);
+                    atomicMin(&key[q.x], kv[r]);
+                }
             }
             __syncwarp();
-            for (int c = lane; c < nc; c += 32) {
-                const int2 q = cand[c];
-                if (order_key(static_cast<double>(th(q.x, q.y)) + xv[q.y]) == key[q.x]) atomicMin(&arg[q.x], q.y);
+#pragma unroll
+            for (int r = 0; r < kWarpCands / 32; ++r) {
+                const int c = lane + 32 * r;
+                if (c < nc) {
+                    const int2 q = cand[c];
+                    if (kv[r] == key[q.x]) atomicMin(&arg[q.x], q.y);
+                }
             }
             __syncwarp();
         } else if (on && k == 0) {
@@ -321,8 +332,12 @@ __global__ void __launch_bounds__(kScrThreads, 4) rec_screen_kernel(const EdgeDe
         s2 = t1 + Lu;
         t3 = s2 + Lv;
     }
-    // the table (16-byte chunks, a thread's next eight requested before any is
-    // stored, so the loads overlap), node vectors, shifted vh
+    // the node vectors (requested first), the table (16-byte chunks, a
+    // thread's next eight requested before any is stored, so the loads
+    // overlap), shifted vh
+    const double vh0 = agg[ed.av] - msg[ed.mv];
+    for (int s = tid; s < Lu; s += T) uh[s] = agg[ed.au + s] - msg[ed.mu + s];
+    for (int t = tid; t < Lv; t += T) vh[t] = agg[ed.av + t] - msg[ed.mv + t];
     const float4 *th4 = reinterpret_cast<const float4 *>(tab + ed.toff);
     const int Q = ld >> 2, nq = Lu * Q;
     for (int base = tid; base < nq; base += 8 * T) {
@@ -343,13 +358,7 @@ __global__ void __launch_bounds__(kScrThreads, 4) rec_screen_kernel(const EdgeDe
             }
         }
     }
-    const double vh0 = agg[ed.av] - msg[ed.mv];
-    for (int s = tid; s < Lu; s += T) uh[s] = agg[ed.au + s] - msg[ed.mu + s];
-    for (int t = tid; t < Lv; t += T) {
-        const double v = agg[ed.av + t] - msg[ed.mv + t];
-        vh[t] = v;
-        w[t] = static_cast<float>(v - vh0);
-    }
+    for (int t = tid; t < Lv; t += T) w[t] = static_cast<float>(vh[t] - vh0);
     __syncthreads();
     // pass 1: a(s) = 1/2 (min_t [theta(s,t) + vh(t)] + uh(s)),  alpha = uh - a
     screened_lines<true>(st, ldp, Lu, Lv, vh, w, key, arg, cand, [&](int s, double m, int mi) {
