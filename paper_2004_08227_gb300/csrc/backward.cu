@@ -149,11 +149,11 @@ __device__ __forceinline__ void warp_preimage_sums(int n, const int *key, const 
 }
 
 // Reverse of one Handshake update per CTA (one matching per launch).
-__global__ void __launch_bounds__(kThreads) bw_phase_kernel(BwParams p, const int *items)
+__global__ void __launch_bounds__(kThreads) bw_phase_kernel(BwParams p, int first)
 {
     extern __shared__ __align__(16) double sh[];
-    const int e = items[blockIdx.x];
-    const EdgeDesc ed = p.edges[e];
+    const int j = first + static_cast<int>(blockIdx.x);  // schedule position: descriptor and record offset at once
+    const EdgeDesc ed = p.descs[j];
     const int Lu = ed.Lu, Lv = ed.Lv, T = blockDim.x, tid = threadIdx.x;
     const int lm = p.lmax;
     const int nw = ((lm + T - 1) / T) * (T >> 5);  // warp partial rows (a warp per 32 keys of a pass)
@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(kThreads) bw_phase_kernel(BwParams p, const in
     int *t1 = reinterpret_cast<int *>(part + static_cast<size_t>(nw) * lm);
     int *s2 = t1 + lm;
     int *t3 = s2 + lm;
-    const unsigned short *rec = reinterpret_cast<const unsigned short *>(p.rec + p.rec_off[e]);
+    const unsigned short *rec = reinterpret_cast<const unsigned short *>(p.rec + p.rec_off[j]);
     double *g = p.gtab + ed.toff;
     for (int i = tid; i < nw * lm; i += T) part[i] = 0.0;
     for (int s = tid; s < Lu; s += T) {
@@ -290,7 +290,7 @@ size_t bw_phase_smem_bytes(int lmax)
     return static_cast<size_t>(lmax) * ((7 + nw) * sizeof(double) + 3 * sizeof(int));
 }
 
-cudaError_t launch_bw_phase(const BwParams &p, const int *items, int n_items, cudaStream_t st)
+cudaError_t launch_bw_phase(const BwParams &p, int first, int n_items, cudaStream_t st)
 {
     if (n_items <= 0) return cudaSuccess;
     const size_t smem = bw_phase_smem_bytes(p.lmax);
@@ -298,7 +298,7 @@ cudaError_t launch_bw_phase(const BwParams &p, const int *items, int n_items, cu
         cudaError_t e = raise_smem_limit(bw_phase_kernel, smem);
         if (e != cudaSuccess) return e;
     }
-    bw_phase_kernel<<<n_items, kThreads, smem, st>>>(p, items);
+    bw_phase_kernel<<<n_items, kThreads, smem, st>>>(p, first);
     return cudaGetLastError();
 }
 
@@ -346,8 +346,10 @@ cudaError_t rec64_iteration(mplpp_solver *s, unsigned char *rec, int lmax, long 
     for (int ph = 0; ph < s->P; ++ph) {
         const int *items = s->d_phase_edges + s->phase_off[ph];
         const int n = s->phase_off[ph + 1] - s->phase_off[ph];
-        cudaError_t e = tab_floats > 0 ? launch_rec_screen_phase(s->d_edges, items, n, s->d_tab, s->d_agg64,
-                                                                 s->d_msg64, rec, s->d_rec_off, lmax, tab_floats, st)
+        const int f = s->phase_off[ph];
+        cudaError_t e = tab_floats > 0 ? launch_rec_screen_phase(s->d_sched_desc + f, n, s->d_tab, s->d_agg64,
+                                                                 s->d_msg64, rec, s->d_sched_rec_off + f, lmax,
+                                                                 tab_floats, st)
                                        : launch_rec64_phase(s->d_edges, items, n, s->d_tab, s->d_agg64, s->d_msg64, rec,
                                                             s->d_rec_off, lmax, st);
         if (e != cudaSuccess) return e;
@@ -389,8 +391,20 @@ extern "C" mplpp_status mplpp_backward(mplpp_solver *s, const float *dD, float *
             acc = (acc + 3) & ~3LL;
         }
         s->rec_stride = std::max(4LL, acc);
+        // the same in schedule order, with the edges' descriptors: a block of
+        // the replay or the reverse sweep reads both at once
+        std::vector<EdgeDesc> sd(s->EE);
+        std::vector<long long> so(s->EE);
+        for (int j = 0; j < s->EE; ++j) {
+            sd[j] = s->h_edges[s->phase_edges[j]];
+            so[j] = off[s->phase_edges[j]];
+        }
         BCK(s->alloc(&s->d_rec_off, std::max(1, s->EE)));
+        BCK(s->alloc(&s->d_sched_desc, std::max(1, s->EE)));
+        BCK(s->alloc(&s->d_sched_rec_off, std::max(1, s->EE)));
         BCK(cudaMemcpyAsync(s->d_rec_off, off.data(), sizeof(long long) * s->EE, cudaMemcpyHostToDevice, st));
+        BCK(cudaMemcpyAsync(s->d_sched_desc, sd.data(), sizeof(EdgeDesc) * s->EE, cudaMemcpyHostToDevice, st));
+        BCK(cudaMemcpyAsync(s->d_sched_rec_off, so.data(), sizeof(long long) * s->EE, cudaMemcpyHostToDevice, st));
         BCK(cudaStreamSynchronize(st));
     }
     if (!s->d_pbase) {
@@ -452,8 +466,8 @@ extern "C" mplpp_status mplpp_backward(mplpp_solver *s, const float *dD, float *
                        s->d_adj_msg, s->d_gtab, st));
 
     BwParams bp = {};
-    bp.edges = s->d_edges;
-    bp.rec_off = s->d_rec_off;
+    bp.descs = s->d_sched_desc;
+    bp.rec_off = s->d_sched_rec_off;
     bp.adj_agg = s->d_adj_agg;
     bp.adj_msg = s->d_adj_msg;
     bp.gtab = s->d_gtab;
@@ -461,7 +475,7 @@ extern "C" mplpp_status mplpp_backward(mplpp_solver *s, const float *dD, float *
     for (long long it = record_all ? Ttot - 1 : -1; it >= 0; --it) {
         bp.rec = s->d_rec + it * s->rec_stride;
         for (int ph = s->P - 1; ph >= 0; --ph)
-            BCK(launch_bw_phase(bp, s->d_phase_edges + s->phase_off[ph], s->phase_off[ph + 1] - s->phase_off[ph], st));
+            BCK(launch_bw_phase(bp, s->phase_off[ph], s->phase_off[ph + 1] - s->phase_off[ph], st));
     }
     for (long long j = nseg - 1; j >= 0; --j) {
         const int len = static_cast<int>(std::min<long long>(k, Ttot - j * k));
@@ -473,8 +487,7 @@ extern "C" mplpp_status mplpp_backward(mplpp_solver *s, const float *dD, float *
         for (int i = len - 1; i >= 0; --i) {
             bp.rec = s->d_rec + static_cast<long long>(i) * s->rec_stride;
             for (int ph = s->P - 1; ph >= 0; --ph)
-                BCK(launch_bw_phase(bp, s->d_phase_edges + s->phase_off[ph], s->phase_off[ph + 1] - s->phase_off[ph],
-                                    st));
+                BCK(launch_bw_phase(bp, s->phase_off[ph], s->phase_off[ph + 1] - s->phase_off[ph], st));
         }
     }
     float *d_gu = nullptr, *d_gp = nullptr;

@@ -310,14 +310,14 @@ __device__ __forceinline__ void screened_lines(const float *tab, int ldp, int n,
 }
 
 template <bool REC>
-__global__ void __launch_bounds__(kScrThreads, 4) rec_screen_kernel(const EdgeDesc *edges, const int *items,
-                                                                 const float *tab, double *agg, double *msg,
-                                                                 unsigned char *rec, const long long *rec_off,
-                                                                 int lmax)
+// descs, rec_off: the matching's edges and their record offsets, in schedule
+// order (one independent load each per block)
+__global__ void __launch_bounds__(kScrThreads, 4) rec_screen_kernel(const EdgeDesc *descs, const float *tab,
+                                                                 double *agg, double *msg, unsigned char *rec,
+                                                                 const long long *rec_off, int lmax)
 {
     extern __shared__ __align__(16) double shd[];
-    const int e = items[blockIdx.x];
-    const EdgeDesc ed = edges[e];
+    const EdgeDesc ed = descs[blockIdx.x];
     const int Lu = ed.Lu, Lv = ed.Lv, ld = ed.ld, ldp = ld | 1;
     const int T = blockDim.x, tid = threadIdx.x, warp = tid >> 5;
     double *uh = shd, *vh = uh + lmax, *al = vh + lmax, *be = al + lmax, *bv = be + lmax;
@@ -328,7 +328,7 @@ __global__ void __launch_bounds__(kScrThreads, 4) rec_screen_kernel(const EdgeDe
     float *st = w + lmax;                              // [Lu][ldp] staged table
     unsigned short *t1 = nullptr, *s2 = nullptr, *t3 = nullptr;
     if (REC) {
-        t1 = reinterpret_cast<unsigned short *>(rec + rec_off[e]);
+        t1 = reinterpret_cast<unsigned short *>(rec + rec_off[blockIdx.x]);
         s2 = t1 + Lu;
         t3 = s2 + Lv;
     }
@@ -415,7 +415,7 @@ size_t rec_screen_smem_bytes(int lmax, long long tab_floats)
            4 * static_cast<size_t>(tab_floats);
 }
 
-cudaError_t launch_rec_screen_phase(const EdgeDesc *edges, const int *items, int n_items, const float *tab,
+cudaError_t launch_rec_screen_phase(const EdgeDesc *descs, int n_items, const float *tab,
                                     double *agg, double *msg, unsigned char *rec, const long long *rec_off, int lmax,
                                     long long tab_floats, cudaStream_t st)
 {
@@ -424,12 +424,11 @@ cudaError_t launch_rec_screen_phase(const EdgeDesc *edges, const int *items, int
     if (rec) {
         cudaError_t e = raise_smem_limit(rec_screen_kernel<true>, smem);
         if (e != cudaSuccess) return e;
-        rec_screen_kernel<true><<<n_items, kScrThreads, smem, st>>>(edges, items, tab, agg, msg, rec, rec_off, lmax);
+        rec_screen_kernel<true><<<n_items, kScrThreads, smem, st>>>(descs, tab, agg, msg, rec, rec_off, lmax);
     } else {
         cudaError_t e = raise_smem_limit(rec_screen_kernel<false>, smem);
         if (e != cudaSuccess) return e;
-        rec_screen_kernel<false><<<n_items, kScrThreads, smem, st>>>(edges, items, tab, agg, msg, nullptr, nullptr,
-                                                                     lmax);
+        rec_screen_kernel<false><<<n_items, kScrThreads, smem, st>>>(descs, tab, agg, msg, nullptr, nullptr, lmax);
     }
     return cudaGetLastError();
 }

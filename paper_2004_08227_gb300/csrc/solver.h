@@ -95,7 +95,9 @@ struct mplpp_solver {
     int *d_labels = nullptr;
 
     // backward: FP64 replay buffers (allocated on first use)
-    long long *d_rec_off = nullptr;
+    long long *d_rec_off = nullptr;        // per edge byte offset of its argmin records
+    mplpp::EdgeDesc *d_sched_desc = nullptr;  // backward: every edge in schedule order
+    long long *d_sched_rec_off = nullptr;     // ... and its record offset
     long long rec_stride = 0;
     std::vector<double *> ckpt64;    // FP64 (agg, msg) every record_every iterations of the replay
     bool history_valid = true;       // the state is T iterations from phi = 0 (false after load_state)
