@@ -234,8 +234,11 @@ mplpp_status mplpp_reset(mplpp_solver *s);
  * device layout, mapping, work lists and captured graphs are kept, so a loop
  * over many cost sets (learning, serving) pays only the copy and the packing.
  *   unary[m], pairwise[m]: model m's costs in the layout of mplpp_model, host
- *   pointers (copied through a device staging buffer allocated on the first
- *   call and kept) or device pointers if options.inputs_on_device.
+ *   pointers or device pointers if options.inputs_on_device.  Host arrays in
+ *   pinned, mapped memory (cudaHostAlloc) are read in place by the packing
+ *   kernel; other host arrays are copied through a device staging buffer
+ *   allocated on the first call and kept.  The arrays must stay unchanged
+ *   until the call returns.
  * Non-finite costs: MPLPP_E_INVALID (the state is then reset but the costs
  * are undefined until a successful call).  Models with MPLPP_PAIR_TRUNC_LINEAR
  * costs: MPLPP_E_UNSUPPORTED (create a new solver).  Synchronizes. */

@@ -1111,6 +1111,21 @@ extern "C" mplpp_status mplpp_reset(mplpp_solver *s)
     return MPLPP_OK;
 }
 
+// A host array the device reads in place: pinned and mapped host memory
+// (cudaHostAlloc memory under unified addressing, which a Grace-attached GPU
+// reads over its chip-to-chip link): its device address; else nullptr (the
+// caller copies it to device memory first).
+static const float *device_view(const float *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();  // not a CUDA allocation: clear the error
+        return nullptr;
+    }
+    if (a.type == cudaMemoryTypeHost && a.devicePointer) return static_cast<const float *>(a.devicePointer);
+    return nullptr;
+}
+
 extern "C" mplpp_status mplpp_update_costs(mplpp_solver *s, const float *const *unary, const float *const *pairwise)
 {
     if (!s || !unary || !pairwise) return MPLPP_E_INVALID;
@@ -1134,12 +1149,25 @@ extern "C" mplpp_status mplpp_update_costs(mplpp_solver *s, const float *const *
         const float *su = unary[m];
         const float *sp = pairwise[m];
         if (!s->opt.inputs_on_device) {
-            CK(s, cudaMemcpyAsync(s->d_stage_u + ub, unary[m], mh.unary_size * sizeof(float), cudaMemcpyHostToDevice, st));
-            if (mh.pair_size)
-                CK(s, cudaMemcpyAsync(s->d_stage_p + pb, pairwise[m], mh.pair_size * sizeof(float),
+            // pinned, mapped host arrays are read by the packing kernel in
+            // place; others are copied to the staging buffers first
+            const float *du = device_view(unary[m]);
+            if (du) {
+                su = du;
+            } else {
+                CK(s, cudaMemcpyAsync(s->d_stage_u + ub, unary[m], mh.unary_size * sizeof(float),
                                       cudaMemcpyHostToDevice, st));
-            su = s->d_stage_u + ub;
-            sp = s->d_stage_p + pb;
+                su = s->d_stage_u + ub;
+            }
+            const float *dp = mh.pair_size ? device_view(pairwise[m]) : nullptr;
+            if (dp) {
+                sp = dp;
+            } else {
+                if (mh.pair_size)
+                    CK(s, cudaMemcpyAsync(s->d_stage_p + pb, pairwise[m], mh.pair_size * sizeof(float),
+                                          cudaMemcpyHostToDevice, st));
+                sp = s->d_stage_p + pb;
+            }
         }
         CK(s, launch_pack(s->d_edges + mh.edge_base, mh.E, s->d_nodes + mh.node_base, mh.n, su, sp, s->d_tab, s->d_un0,
                           s->d_agg, s->d_err, st));

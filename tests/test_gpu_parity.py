@@ -681,3 +681,29 @@ def test_solvers_of_one_process_keep_their_shared_memory_limits():
         np.testing.assert_array_equal(a.bound(), ref.bound())
         for s in (a, b, c, ref):
             s.close()
+
+
+def test_update_costs_from_pinned_host_memory_equals_pageable():
+    """mplpp_update_costs reads pinned, mapped host arrays in place and copies
+    pageable ones through a staging buffer: both give the same state, bit for
+    bit, as a new solver with those costs."""
+    import copy
+    import torch
+    m0 = W.uneven_complete(9, 20, 60, seed=31)
+    rng = np.random.default_rng(32)
+    m1 = copy.copy(m0)  # same shapes, other costs
+    m1.unary = rng.standard_normal(np.asarray(m0.unary).shape).astype(np.float32)
+    m1.pairwise = rng.standard_normal(np.asarray(m0.pairwise).shape).astype(np.float32)
+    a = Solver([m0])
+    b = Solver([m0])
+    ref = Solver([m1])
+    a.update_costs([np.ascontiguousarray(m1.unary)], [np.ascontiguousarray(m1.pairwise)])
+    b.update_costs([torch.from_numpy(np.ascontiguousarray(m1.unary, np.float32)).pin_memory()],
+                   [torch.from_numpy(np.ascontiguousarray(m1.pairwise, np.float32)).pin_memory()])
+    for s in (a, b, ref):
+        s.run(7)
+    sa, sb, sr = a.state_arrays(), b.state_arrays(), ref.state_arrays()
+    assert np.array_equal(sa[1], sr[1]) and np.array_equal(sb[1], sr[1])
+    assert np.array_equal(sa[2], sr[2]) and np.array_equal(sb[2], sr[2])
+    for s in (a, b, ref):
+        s.close()
