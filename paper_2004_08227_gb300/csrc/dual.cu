@@ -260,7 +260,6 @@ __global__ void __launch_bounds__(kRoundThreads) round_kernel(const NodeDesc *no
     // staged earlier neighbours (up to T per chunk), two sets: node u's and,
     // prepared meanwhile, node u + 1's
     __shared__ long long k_row[2][T], k_mv[2][T];
-    __shared__ double k_phi[2][T];
     __shared__ float2 k_phf[2][T];
     const int m = blockIdx.x;
     const int tid = threadIdx.x;
@@ -273,7 +272,6 @@ __global__ void __launch_bounds__(kRoundThreads) round_kernel(const NodeDesc *no
         k_mv[set][slot] = r.mv;
         const double ph = se_d(msg[r.mu + xv]);
         const float hi = static_cast<float>(ph);
-        k_phi[set][slot] = ph;
         k_phf[set][slot] = make_float2(hi, static_cast<float>(ph - static_cast<double>(hi)));
     };
     bool pre = false;  // node u's set was staged (except a neighbour u - 1) during node u - 1
