@@ -268,13 +268,16 @@ __device__ void struct_item(const StructParams &p, int e, const EdgeDesc &ed, Ve
     ulonglong2 *msg = p.msg;
     const unsigned va = ver.u + ver.bump;
 
-    // unaries without this edge's messages: up to 4 entries of each node per
-    // lane requested before any is used (one round trip per 128 labels)
+    // unaries without this edge's messages: up to kB entries of each node per
+    // lane requested before any is used (one round trip per 32 kB labels; the
+    // polling form holds them across its waits, so it takes 2 per lane to keep
+    // its registers -- and co-resident warps -- at the looped form's count)
+    constexpr int kB = SIGNAL ? 2 : 4;
     const int Lm = Lu > Lv ? Lu : Lv;
-    for (int base0 = 0; base0 < Lm; base0 += 128) {
-        ulonglong2 xu[4], mu[4], xv[4], mv[4];
+    for (int base0 = 0; base0 < Lm; base0 += 32 * kB) {
+        ulonglong2 xu[kB], mu[kB], xv[kB], mv[kB];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < kB; ++j) {
             const int i = base0 + lane + 32 * j;
             if (i < Lu) {
                 xu[j] = ld_se(agg + ed.au + i);
@@ -289,7 +292,7 @@ __device__ void struct_item(const StructParams &p, int e, const EdgeDesc &ed, Ve
             for (long long spins = 1;; ++spins) {
                 bool ok = true;
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
+                for (int j = 0; j < kB; ++j) {
                     const int i = base0 + lane + 32 * j;
                     if (i < Lu) ok = ok && se_ok(xu[j], va) && se_ok(mu[j], ver.e);
                     if (i < Lv) ok = ok && se_ok(xv[j], ver.v) && se_ok(mv[j], ver.e);
@@ -302,7 +305,7 @@ __device__ void struct_item(const StructParams &p, int e, const EdgeDesc &ed, Ve
                 }
                 if (spins > 64) __nanosleep(64);
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
+                for (int j = 0; j < kB; ++j) {
                     const int i = base0 + lane + 32 * j;
                     if (i < Lu) {
                         if (!se_ok(xu[j], va)) xu[j] = ld_se(agg + ed.au + i);
@@ -316,7 +319,7 @@ __device__ void struct_item(const StructParams &p, int e, const EdgeDesc &ed, Ve
             }
         }
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < kB; ++j) {
             const int i = base0 + lane + 32 * j;
             if (i < Lu) uh[i] = df_sub(se_df(xu[j]), se_df(mu[j]));
             if (i < Lv) vh[i] = df_sub(se_df(xv[j]), se_df(mv[j]));
@@ -371,7 +374,7 @@ __global__ void __launch_bounds__(kStructThreads) struct_kernel(StructParams p)
 // order, the models interleaved by progress) until the iterations are done.
 // Every wait is on an earlier item, held by a co-resident warp, so the waits
 // end; no block barrier.
-__global__ void __launch_bounds__(kStructThreads) struct_queue_kernel(StructParams p)
+__global__ void __launch_bounds__(kStructThreads, 4) struct_queue_kernel(StructParams p)
 {
     extern __shared__ __align__(16) char smem_raw[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
