@@ -291,12 +291,15 @@ mplpp_status mplpp_sync(mplpp_solver *s);
 
 /* Self-measured choice of the mapping (not in the paper): runs `iterations`
  * iterations of the solver's own models under every feasible combination of
- * CTAs per edge (1..8), threads per CTA (128, 256, 512) and driver (persistent,
- * looped), timed with CUDA events on the solver's stream, and keeps the
- * fastest.  All mappings compute bit-identical results; the state before the
- * call is restored afterwards.  report (may be NULL): host buffer receiving a
- * JSON summary (best mapping and every candidate's time in ms).
- * Synchronizes. */
+ * CTAs per edge (1..8), threads per CTA (128, 256, 512 and the exact fit of
+ * the register-resident passes) and driver (persistent, looped, warp, queue,
+ * resident, structured, structured-queue), timed with CUDA events on the
+ * solver's stream, and keeps the fastest.  A candidate whose run takes under
+ * 2 ms is timed again over up to 16 times as many iterations and reported per
+ * `iterations`, so that fixed start-up costs weigh as in a longer run.  All
+ * mappings compute bit-identical results; the state before the call is
+ * restored afterwards.  report (may be NULL): host buffer receiving a JSON
+ * summary (best mapping and every candidate's time in ms).  Synchronizes. */
 mplpp_status mplpp_autotune(mplpp_solver *s, int32_t iterations, char *report, size_t report_size);
 
 /* Dual bound of one model's reparametrized costs without allocating any
