@@ -716,7 +716,7 @@ def run_ours(args):
         et = max_over_ranks(statistics.mean(times) * 1e3, world, "cuda") / 1e3
         e2e = {"value": whole_job_rate(T * E_total, world, et * 1e3), "unit": "edge_updates/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": et * 1e3,
-               "timer": "host wall clock"}
+               "step_ms": [round(t * 1e3, 2) for t in times], "timer": "host wall clock"}
 
     # per step: reset (1), the run (restamp + one persistent launch, or one
     # launch per matching and iteration), exact bound (3), rounding + energy
