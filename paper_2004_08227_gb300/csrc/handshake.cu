@@ -8,7 +8,7 @@
 //                                                               = 1/2 min_t g(s,t)
 //   alpha(s) = uh(s) - a(s)
 //   b(t)  = min_s [theta_uv(s,t) + alpha(s)] + vh(t)            = min_s [g(s,t) - a(s)]
-//   beta(t) = vh(t) - b(t)
+//   beta(t) = vh(t) - b(t) = -min_s [theta_uv(s,t) + alpha(s)]     (formed as the latter)
 //   c(s)  = min_t [theta_uv(s,t) + beta(t)] + uh(s)             = min_t [g(s,t) - b(t)]
 //   agg_u := c, phi_{v->u} := c - uh;  agg_v := b, phi_{u->v} := b - vh.
 // Precision: the O(L) state and vector arithmetic are double-float (hi + lo
@@ -684,7 +684,10 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
     }
 
     // combine the column minima of all CTAs of the edge:
-    //   b(t) = min_s [...] + vh(t),  beta(t) = vh(t) - b(t)
+    //   b(t) = min_s [...] + vh(t),  beta(t) = vh(t) - b(t) = -min_s [...]
+    // (beta formed as the latter, its value in exact arithmetic); node v's new
+    // vector is stored by the CTAs of the cluster, a range of columns each
+    const int vper = (Lv + C - 1) / C, vt0 = rank * vper;
     if (CLUSTER) {
         if (!mbar_wait_cluster(xbar, parity, p.spin_limit)) set_err(p.err, ERR_TIMEOUT);
     } else if (RM != 2) {
@@ -706,12 +709,12 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
             for (int r = 1; r < 8; ++r) v[r - 1] = r < C ? xbuf[r * ld + t] : INFINITY;
             m = min3f(m, min3f(v[0], v[1], v[2]), min3f(v[3], v[4], fminf(v[5], v[6])));
         }
-        const float2 vh = sm.vh[t];
-        const float2 b = df_add_f(vh, m);
-        sm.beta[t] = t < Lv ? df_to_f(df_sub(vh, b)) : 0.f;
-        // node v's new vector (one CTA of the cluster), visible to node v's
-        // next update as soon as it is stored
-        if (rank == 0 && t < Lv) {
+        sm.beta[t] = t < Lv ? -m : 0.f;
+        // node v's new vector, visible to node v's next update as soon as it
+        // is stored
+        if (t >= vt0 && t < vt0 + vper && t < Lv) {
+            const float2 vh = sm.vh[t];
+            const float2 b = df_add_f(vh, m);
             st_se(agg + ed.av + t, se_make(b, ver.v + 1u));
             st_se(msg + ed.mv + t, se_make(df_sub(b, vh), ver.e + 1u));
         }

@@ -139,7 +139,7 @@ __device__ __forceinline__ void res_update(bool act, const ResEdge &ed, const fl
         const float m = res_min_add<LM>(col, w.alpha, Lu);
         const float2 vh = w.vh[l];
         const float2 b = df_add_f(vh, m);
-        w.beta[l] = df_to_f(df_sub(vh, b));
+        w.beta[l] = -m;  // vh - b in exact arithmetic
         av[l] = b;
         mv[l] = df_sub(b, vh);
     }

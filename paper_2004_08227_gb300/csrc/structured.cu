@@ -343,7 +343,7 @@ __device__ void struct_item(const StructParams &p, int e, const EdgeDesc &ed, Ve
     dt_trunc(h, Lu, Lv, w, tau, quad, m, pre, suf, lane, ku);
     for (int t = lane; t < Lv; t += 32) {
         const float2 b = df_add_f(vh[t], m[t]);
-        h[t] = df_to_f(df_sub(vh[t], b));
+        h[t] = -m[t];  // beta = vh - b, in exact arithmetic
         st_se(agg + ed.av + t, se_make(b, nv));
         st_se(msg + ed.mv + t, se_make(df_sub(b, vh[t]), ne));
     }

@@ -296,7 +296,7 @@ __device__ void warp_item(const HsParams &p, const EdgeDesc &ed, const WarpSmem 
                 if (t < Lv) {
                     const float2 vh = sm.vh[t];
                     const float2 b = df_add_f(vh, mc[c]);
-                    sm.beta[t] = df_to_f(df_sub(vh, b));
+                    sm.beta[t] = -mc[c];  // vh - b in exact arithmetic
                     st_se(agg + ed.av + t, se_make(b, ver.v + 1u));
                     st_se(msg + ed.mv + t, se_make(df_sub(b, vh), ver.e + 1u));
                 } else {
