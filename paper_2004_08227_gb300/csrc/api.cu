@@ -415,10 +415,10 @@ cudaError_t raise_smem_limit_ptr(const void *kernel, size_t smem)
 }
 }  // namespace mplpp
 
-// The queue driver: CTAs of T threads (default 128), vectors and the column
-// partials in shared memory, tables read from memory (passes 2 and 3 find
-// them in L1: the little shared memory leaves most of it to the cache); as
-// many CTAs as are co-resident (at most one per edge).
+// The queue driver: CTAs of 128 threads, vectors and the column partials in
+// shared memory, tables read from memory by every pass (from L2 after the
+// first); as many CTAs as are co-resident (at most one per edge): the items
+// in flight per SM set its throughput.
 static mplpp_status apply_queue_mapping(mplpp_solver *s, int T, int optin)
 {
     if (T == 0) T = 128;
