@@ -6,7 +6,7 @@
 //           (the unaries without this edge's messages; g = theta_uv + uh + vh)
 //   a(s)  = 1/2 (min_t [theta_uv(s,t) + (vh(t) - vh(0))] + vh(0) + uh(s))
 //                                                               = 1/2 min_t g(s,t)
-//   alpha(s) = uh(s) - a(s)
+//   alpha(s) = uh(s) - a(s) = 1/2 (uh(s) - vh(0) - min_t [...])    (formed as the latter)
 //   b(t)  = min_s [theta_uv(s,t) + alpha(s)] + vh(t)            = min_s [g(s,t) - a(s)]
 //   beta(t) = vh(t) - b(t) = -min_s [theta_uv(s,t) + alpha(s)]     (formed as the latter)
 //   c(s)  = min_t [theta_uv(s,t) + beta(t)] + uh(s)             = min_t [g(s,t) - b(t)]
@@ -532,15 +532,18 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
     {
         const float4 *w = reinterpret_cast<const float4 *>(sm.w1);
         const float2 vref = sm.vh[0];
-        auto emit = [&](int s, float m) {
-            const float2 u = uh[s];
-            const float2 a = df_half(df_add(df_add_f(vref, m), u));
-            sm.alpha[s] = df_to_f(df_sub(u, a));
-        };
+        // alpha = uh - a = 1/2 (uh - vh(0) - m), its value in exact arithmetic;
+        // d = uh - vh(0) does not depend on the minimum
+        auto alpha_of = [&](float2 d, float m) { return df_to_f(df_half(df_add_f(d, -m))); };
+        auto emit = [&](int s, float m) { sm.alpha[s] = alpha_of(df_sub(uh[s], vref), m); };
         if (RM == 1) {
           if (!poller) {
             float acc[kRR];
             float4 wv[kCR];
+            const int s = warp + W * rs_row(lane);  // the five owners emit at once
+            const bool own = rs_owner(lane) && s < nr;
+            float2 d = make_float2(0.f, 0.f);
+            if (!PW && own) d = df_sub(uh[s], vref);  // node u's rows are in: before the minima
 #pragma unroll
             for (int i = 0; i < kCR; ++i) wv[i] = lane + 32 * i < Q ? w[lane + 32 * i] : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
@@ -550,10 +553,12 @@ __device__ void hs_item(const HsParams &p, const EdgeDesc &ed, const float *tile
                 for (int i = 0; i < kCR; ++i) acc[k] = min_add4(acc[k], tr[k][i], wv[i]);
             }
             const float mk = warp_min_rows5(acc, lane);
-            const int s = warp + W * rs_row(lane);  // the five owners emit at once
-            if (rs_owner(lane) && s < nr) {
-                if (PW && !mbar_wait(ubar, upar, p.spin_limit)) set_err(p.err, ERR_TIMEOUT);
-                emit(s, mk);
+            if (own) {
+                if (PW) {
+                    if (!mbar_wait(ubar, upar, p.spin_limit)) set_err(p.err, ERR_TIMEOUT);
+                    d = df_sub(uh[s], vref);
+                }
+                sm.alpha[s] = alpha_of(d, mk);
             }
           }
         } else if (RM == 2) {

@@ -129,9 +129,8 @@ __device__ __forceinline__ void res_update(bool act, const ResEdge &ed, const fl
     // pass 1: a(s) = 1/2 (min_t [theta(s,t) + w1(t)] + vh(0) + uh(s));  alpha = uh - a
     if (l < Lu) {
         const float m = res_min_add<LM>(row, w.w1, Lv);
-        const float2 u = w.uh[l];
-        const float2 a = df_half(df_add(df_add_f(vref, m), u));
-        w.alpha[l] = df_to_f(df_sub(u, a));
+        // alpha = uh - a = 1/2 (uh - vh(0) - m), its value in exact arithmetic
+        w.alpha[l] = df_to_f(df_half(df_add_f(df_sub(w.uh[l], vref), -m)));
     }
     __syncwarp();
     // pass 2: b(t) = min_s [theta(s,t) + alpha(s)] + vh(t),  beta = vh - b

@@ -335,8 +335,8 @@ __device__ void struct_item(const StructParams &p, int e, const EdgeDesc &ed, Ve
     // pass 1: a(s) = 1/2 (min_t [theta(s,t) + w1(t)] + vh(0) + uh(s)); alpha = uh - a
     dt_trunc(h, Lv, Lu, w, tau, quad, m, pre, suf, lane, kv);
     for (int s = lane; s < Lu; s += 32) {
-        const float2 a = df_half(df_add(df_add_f(vref, m[s]), uh[s]));
-        h[s] = df_to_f(df_sub(uh[s], a));
+        // alpha = uh - a = 1/2 (uh - vh(0) - m), its value in exact arithmetic
+        h[s] = df_to_f(df_half(df_add_f(df_sub(uh[s], vref), -m[s])));
     }
     __syncwarp();
     // pass 2: b(t) = min_s [theta(s,t) + alpha(s)] + vh(t); beta = vh - b; node v's new vector

@@ -261,9 +261,8 @@ __device__ void warp_item(const HsParams &p, const EdgeDesc &ed, const WarpSmem 
             buf = acquire(p, sm, st);
             follow(1, j);
             row_chunk(buf, j * R, min(R, Lu - j * R), wv, [&](int s, float m) {
-                const float2 u = sm.uh[s];
-                const float2 a = df_half(df_add(df_add_f(vref, m), u));
-                sm.alpha[s] = df_to_f(df_sub(u, a));
+                // alpha = uh - a = 1/2 (uh - vh(0) - m), its value in exact arithmetic
+                sm.alpha[s] = df_to_f(df_half(df_add_f(df_sub(sm.uh[s], vref), -m)));
             });
         }
     }
