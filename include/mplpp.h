@@ -240,8 +240,9 @@ mplpp_status mplpp_reset(mplpp_solver *s);
  *   allocated on the first call and kept.  The arrays must stay unchanged
  *   until the call returns.
  * Non-finite costs: MPLPP_E_INVALID (the state is then reset but the costs
- * are undefined until a successful call).  Models with MPLPP_PAIR_TRUNC_LINEAR
- * costs: MPLPP_E_UNSUPPORTED (create a new solver).  Synchronizes. */
+ * are undefined until a successful call).  Models with structured costs
+ * (MPLPP_PAIR_TRUNC_LINEAR or MPLPP_PAIR_TRUNC_QUAD): MPLPP_E_UNSUPPORTED
+ * (create a new solver).  Synchronizes. */
 mplpp_status mplpp_update_costs(mplpp_solver *s, const float *const *unary, const float *const *pairwise);
 
 /* Solver state (the reparametrization) in a portable host format:
