@@ -762,7 +762,7 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def main():
+def make_parser():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
@@ -789,7 +789,11 @@ def main():
     ap.add_argument("--replicas", type=int, default=4096, help="K_20 replicas solved together")
     ap.add_argument("--ref-iters", type=int, default=10,
                     help="--impl reference: oracle iterations per step (amortizes the copy of the FP64 state)")
-    args = ap.parse_args()
+    return ap
+
+
+def main():
+    args = make_parser().parse_args()
     if args.impl == "reference":
         run_reference(args)
     else:
